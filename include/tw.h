@@ -1,0 +1,152 @@
+/*
+ * tw.h -- C ABI of the GB300 online Bayesian inversion library (libtw.so).
+ *
+ * The library implements the online phase (Phase 4) of the offline-online
+ * inversion of arXiv 2504.16344, "Real-time Bayesian inference at extreme
+ * scale: a digital twin for tsunami early warning":
+ *
+ *   posterior mean   m = Gamma_pr F* (Gamma_n + F Gamma_pr F*)^{-1} d
+ *   forecast         q = F_q m
+ *
+ * where F (p2o map) and F_q (p2q map) are block lower-triangular Toeplitz in
+ * time (Sec. "FFT-based Hessian matvecs", Eq. ShiftInvariance) and are
+ * applied by zero-padding time to 2 Nt, a batched real FFT along time, one
+ * complex matrix-vector product per frequency and an inverse FFT.
+ *
+ * Conventions (all entry points):
+ *  - Vectors are time-major and row-major: a parameter vector m is
+ *    [Nt][Nm] (m_j = m[j*Nm .. j*Nm+Nm-1]), a data vector d is [Nt][Nd], a
+ *    QoI vector q is [Nt][Nq]; Nm = Nx*Ny with flat grid index a*Ny + b.
+ *    Several right-hand sides are stacked: [nrhs][Nt][...].
+ *  - Every vector argument is a DEVICE pointer owned by the caller unless the
+ *    comment says host.  Work is enqueued on `stream` (a cudaStream_t passed
+ *    as void*, NULL = legacy default stream) and is stream-ordered: outputs
+ *    are valid once the stream reaches that point.  The context owns every
+ *    other buffer (the frequency-domain operators, K's factor, workspaces);
+ *    online calls allocate nothing.
+ *  - User-facing values are IEEE binary64.
+ *  - Every call returns a tw_status; no C++ exception crosses the ABI.  On
+ *    error tw_last_error() gives a message.  Errors raised by kernels (a
+ *    non-positive pivot, a wait that ran out) are recorded on the device and
+ *    reported by tw_check() after the stream has been synchronised.
+ *  - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef TW_H
+#define TW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tw_ctx tw_ctx;
+
+typedef enum {
+  TW_OK = 0,
+  TW_ERR_ARG = 1,            /* invalid argument (size, pointer, enum)          */
+  TW_ERR_OOM = 2,            /* device allocation failed or budget exceeded     */
+  TW_ERR_CUDA = 3,           /* a CUDA runtime call failed                      */
+  TW_ERR_STATE = 4,          /* call out of order (e.g. infer before factor)    */
+  TW_ERR_NOT_SPD = 5,        /* Cholesky met a non-positive pivot               */
+  TW_ERR_NOT_CONVERGED = 6,  /* iterative refinement did not reach its tolerance*/
+  TW_ERR_TIMEOUT = 7         /* a bounded device wait ran out                   */
+} tw_status;
+
+/* Which Toeplitz map: the p2o map F (Nd rows) or the p2q map F_q (Nq rows). */
+typedef enum { TW_MAP_F = 0, TW_MAP_FQ = 1 } tw_map;
+
+/* Storage / arithmetic of the frequency-domain operator in an apply.
+ *  TW_PREC_FP64   : F^ held as float pairs (hi + lo, 48-bit significand,
+ *                   16 bytes per complex entry, the size of complex128);
+ *                   arithmetic in double-float (error-free FP32 transforms).
+ *                   This is the library's FP64-class path.
+ *  TW_PREC_C64    : F^ held as complex64, FP32 products, blocked FP32 sums.
+ *  TW_PREC_BF16X2 : F^ held as bf16 hi + bf16 lo per real (8 bytes per
+ *                   complex entry), FP32 products and sums.                   */
+typedef enum { TW_PREC_FP64 = 0, TW_PREC_C64 = 1, TW_PREC_BF16X2 = 2 } tw_prec;
+
+/* Storage kept by the context (bit mask for tw_create's `keep`). */
+#define TW_KEEP_FP64   1u
+#define TW_KEEP_C64    2u
+#define TW_KEEP_BF16X2 4u
+
+/*
+ * tw_create -- allocate a context for Nd sensors, Nq forecast points, an
+ * Nx x Ny periodic parameter grid over [0,Lx) x [0,Ly) and Nt time steps.
+ * `keep` selects which operator storages are filled (TW_KEEP_*).  `device`
+ * is the CUDA device ordinal.  Allocates the frequency-domain operators
+ * (Nt+1 frequencies x rows x Nm per kept format) and online workspaces.
+ * Errors: TW_ERR_ARG for non-positive sizes, TW_ERR_OOM, TW_ERR_CUDA.
+ */
+tw_status tw_create(tw_ctx **out, int Nd, int Nq, int Nx, int Ny, int Nt,
+                    double Lx, double Ly, unsigned keep, int device);
+
+/* Free everything the context owns.  Safe on NULL. */
+void tw_destroy(tw_ctx *ctx);
+
+/* Last error message of this context (static storage of the context). */
+const char *tw_last_error(const tw_ctx *ctx);
+
+/*
+ * tw_set_block_column -- load rows [row0, row0+nrows) of the first block
+ * column of F (which = TW_MAP_F, rows are sensors) or F_q (TW_MAP_FQ, rows
+ * are forecast points): col is a device array [Nt][nrows][Nm] in FP64 with
+ * col[l][r][k] = (F_l)[row0+r, k], l the 0-based time lag (Sec. "FFT-based
+ * Hessian matvecs": only the first block column is stored, O(Nm Nd Nt)).
+ * The call computes the rows' frequency-domain blocks F^(w), w = 0..Nt, by a
+ * real FFT of length 2Nt along the lag and stores them in every kept format.
+ * `col` is only read during the call (stream-ordered).  Rows may be loaded
+ * in any order and chunking; all rows must be loaded before an apply.
+ */
+tw_status tw_set_block_column(tw_ctx *ctx, tw_map which, int row0, int nrows,
+                              const double *col, void *stream);
+
+/*
+ * tw_set_prior -- Matern prior Gamma_pr = I_Nt (x) C (Sec. "State of the
+ * art": block diagonal in time, each block a Matern covariance).  C is the
+ * stationary covariance on the periodic grid with Fourier eigenvalues
+ * lambda_k = var * N * s(k) / sum s, s(k) = (kappa^2 + |k|^2)^-(nu+1),
+ * kappa = sqrt(2 nu)/ell, k = 2 pi (p/Lx, q/Ly): the pointwise variance is
+ * exactly var.  Errors: TW_ERR_ARG for non-positive nu, ell or var.
+ */
+tw_status tw_set_prior(tw_ctx *ctx, double nu, double ell, double var);
+
+/*
+ * tw_p2o_apply -- out = F x (which = TW_MAP_F, out [nrhs][Nt][Nd]) or
+ * out = F_q x (TW_MAP_FQ, out [nrhs][Nt][Nq]) for x [nrhs][Nt][Nm]:
+ * out_i = sum_{j<=i} F_{i-j} x_j (Eq. ShiftInvariance), computed as
+ * irfft_2Nt( F^(w) rfft_2Nt(x)(w) ) truncated to Nt steps.
+ * prec selects the operator storage (must have been kept).
+ */
+tw_status tw_p2o_apply(tw_ctx *ctx, tw_map which, tw_prec prec, int nrhs,
+                       const double *x, double *out, void *stream);
+
+/*
+ * tw_p2o_adjoint -- x = F^T y (Euclidean adjoint; y [nrhs][Nt][Nd], x
+ * [nrhs][Nt][Nm]) or F_q^T y: x_j = sum_{i>=j} F_{i-j}^T y_i, computed as
+ * irfft( F^(w)^H rfft(y)(w) ) truncated to Nt steps.
+ */
+tw_status tw_p2o_adjoint(tw_ctx *ctx, tw_map which, tw_prec prec, int nrhs,
+                         const double *y, double *x, void *stream);
+
+/*
+ * tw_prior_apply -- y = Gamma_pr^power x for x, y [nrhs][Nt][Nm], power 1
+ * or 0.5 (the square root used to draw prior samples).  2D real FFT per time
+ * step, scaling by lambda^power, inverse FFT.  x and y may alias.
+ */
+tw_status tw_prior_apply(tw_ctx *ctx, double power, int nrhs, const double *x,
+                         double *y, void *stream);
+
+/* Synchronise `stream` and report errors recorded by kernels (TW_OK,
+ * TW_ERR_NOT_SPD, TW_ERR_TIMEOUT, TW_ERR_CUDA).  Clears the record. */
+tw_status tw_check(tw_ctx *ctx, void *stream);
+
+/* Device bytes held by the context. */
+size_t tw_device_bytes(const tw_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TW_H */

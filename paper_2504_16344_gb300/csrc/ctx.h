@@ -1,0 +1,54 @@
+// ctx.h -- the tw_ctx structure and host helpers shared by the API files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tw.h"
+#include "kernels.h"
+
+struct tw_ctx {
+  int dev = 0;
+  int Nd = 0, Nq = 0, Nx = 0, Ny = 0, Nt = 0, Nm = 0, Nf = 0, Rmax = 0;
+  double Lx = 1.0, Ly = 1.0;
+  unsigned keep = 0;
+  // frequency-domain operators op[which][fmt], [Nf][rows][Nm]
+  void *op[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  std::vector<char> loaded[2];     // per row: loaded?
+  // FFT plans and twiddle tables (df64 and float)
+  tw::FftPlan plT{}, plX{}, plY{};
+  tw::cdd *twT = nullptr, *twL = nullptr, *twX = nullptr, *twY = nullptr;
+  tw::cf *twTf = nullptr, *twLf = nullptr, *twXf = nullptr, *twYf = nullptr;
+  // prior: lambda^power / N, power 1 and 1/2
+  bool prior_set = false;
+  double nu = 1, ell = 0.1, var = 1;
+  tw::dd *lam1 = nullptr, *lamh = nullptr;
+  float *lam1f = nullptr, *lamhf = nullptr;
+  // online workspaces
+  tw::cdd *wf = nullptr;    // [Nf][Nm]
+  tw::cdd *wr = nullptr;    // [Nf][Rmax]
+  tw::cdd *part = nullptr;  // [Nf][nchunk][Rmax]
+  tw::dd *wt = nullptr;     // [Nt][Nm]
+  tw::cdd *ws = nullptr;    // [ceil(Nt/2)][Nm]
+  int *d_err = nullptr;     // device error record: [0] code, [1] info
+  size_t bytes = 0;
+  std::string err;
+  std::vector<void *> allocs;
+};
+
+namespace twh {
+
+tw_status fail(tw_ctx *c, tw_status st, const std::string &msg);
+tw_status cuda_fail(tw_ctx *c, cudaError_t e, const char *where);
+void *dalloc(tw_ctx *c, size_t bytes);   // tracked cudaMalloc; nullptr on failure
+void dfree(tw_ctx *c, void *p);
+tw::FftPlan make_plan(int M);
+
+}  // namespace twh
+
+#define TW_CUDA(c, call)                                             \
+  do {                                                               \
+    cudaError_t _e = (call);                                         \
+    if (_e != cudaSuccess) return twh::cuda_fail((c), _e, #call);    \
+  } while (0)

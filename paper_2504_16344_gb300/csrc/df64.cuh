@@ -1,0 +1,213 @@
+// df64.cuh -- double-float ("df64") arithmetic and complex helpers.
+//
+// GB300 issues FP32 instructions at a far higher rate than FP64 ones, so the
+// library's FP64-class path keeps every quantity as an unevaluated sum of
+// two floats, x = hi + lo with |lo| <= ulp(hi)/2 (48-bit significand), and
+// computes with error-free transformations:
+//   * TwoSum (Knuth, TAOCP vol. 2): s + e == a + b exactly;
+//   * FastTwoSum (Dekker 1971): same when |a| >= |b|;
+//   * TwoProd via FMA: p + e == a * b exactly;
+//   * Dot2-style lazy accumulation (Ogita, Rump & Oishi 2005): a running
+//     float sum plus a float that collects the exact rounding errors.
+// The `_rn` intrinsics keep the compiler from fusing or reordering these.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace tw {
+
+struct __align__(8) dd { float hi, lo; };
+struct __align__(16) cdd { dd re, im; };   // complex double-float, 16 bytes (float4 layout)
+struct __align__(8) cf { float re, im; };  // complex float, 8 bytes
+
+// ---------------------------------------------------------------- basics
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ dd dd_make(float hi, float lo) {
+  dd r; fast_two_sum(hi, lo, r.hi, r.lo); return r;
+}
+__device__ __forceinline__ dd dd_zero() { dd r; r.hi = 0.f; r.lo = 0.f; return r; }
+__device__ __forceinline__ dd dd_neg(dd a) { a.hi = -a.hi; a.lo = -a.lo; return a; }
+
+// sum with relative error O(2^-48) of |a| + |b|
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  dd r; fast_two_sum(s, e, r.hi, r.lo); return r;
+}
+__device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+
+// product with relative error O(2^-47)
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  dd r; fast_two_sum(p, e, r.hi, r.lo); return r;
+}
+__device__ __forceinline__ dd dd_mul_f(dd a, float b) {
+  float p = __fmul_rn(a.hi, b);
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  dd r; fast_two_sum(p, e, r.hi, r.lo); return r;
+}
+// exact scaling by a power of two
+__device__ __forceinline__ dd dd_scale2(dd a, float p2) { a.hi *= p2; a.lo *= p2; return a; }
+
+// quotient a / b: float estimate refined once (Dekker's long division)
+__device__ __forceinline__ dd dd_div(dd a, dd b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  dd r = dd_sub(a, dd_mul_f(b, q1));
+  float q2 = __fdiv_rn(r.hi, b.hi);
+  return dd_make(q1, q2);
+}
+// square root: float estimate x, one correction (a - x^2) / (2x)
+__device__ __forceinline__ dd dd_sqrt(dd a) {
+  if (a.hi <= 0.f) return dd_zero();
+  float x = __fsqrt_rn(a.hi);
+  float p = __fmul_rn(x, x);
+  float pe = fmaf(x, x, -p);
+  dd r = dd_sub(a, dd_make(p, pe));
+  float c = __fdiv_rn(r.hi, __fmul_rn(2.f, x));
+  return dd_make(x, c);
+}
+
+// ------------------------------------------------------- conversions
+// IEEE double <-> df64.  These run at the edges of the library only.
+__device__ __forceinline__ dd dd_from_double(double x) {
+  dd r;
+  r.hi = __double2float_rn(x);
+  r.lo = __double2float_rn(x - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ double dd_to_double(dd a) { return (double)a.hi + (double)a.lo; }
+
+// ------------------------------------------------- lazy accumulation
+// value = s + t; t collects the exact rounding errors of the running sum.
+struct dacc { float s, t; };
+__device__ __forceinline__ dacc dacc_zero() { dacc a; a.s = 0.f; a.t = 0.f; return a; }
+// A += sgn * a * b   (sgn = +1 or -1, folded into the operand signs)
+__device__ __forceinline__ void dacc_mac(dacc &A, dd a, dd b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  float s, r;
+  two_sum(A.s, p, s, r);
+  A.s = s;
+  A.t = __fadd_rn(A.t, __fadd_rn(r, e));
+}
+__device__ __forceinline__ void dacc_add(dacc &A, dd a) {
+  float s, r;
+  two_sum(A.s, a.hi, s, r);
+  A.s = s;
+  A.t = __fadd_rn(A.t, __fadd_rn(r, a.lo));
+}
+__device__ __forceinline__ dd dacc_get(dacc A) { return dd_make(A.s, A.t); }
+
+// ------------------------------------------------------ complex df64
+__device__ __forceinline__ cdd cdd_zero() { cdd z; z.re = dd_zero(); z.im = dd_zero(); return z; }
+__device__ __forceinline__ cdd cdd_add(cdd a, cdd b) { cdd r; r.re = dd_add(a.re, b.re); r.im = dd_add(a.im, b.im); return r; }
+__device__ __forceinline__ cdd cdd_sub(cdd a, cdd b) { cdd r; r.re = dd_sub(a.re, b.re); r.im = dd_sub(a.im, b.im); return r; }
+__device__ __forceinline__ cdd cdd_conj(cdd a) { a.im = dd_neg(a.im); return a; }
+// multiply by -i: (x + iy)(-i) = y - ix
+__device__ __forceinline__ cdd cdd_mul_mi(cdd a) { cdd r; r.re = a.im; r.im = dd_neg(a.re); return r; }
+__device__ __forceinline__ cdd cdd_mul_i(cdd a) { cdd r; r.re = dd_neg(a.im); r.im = a.re; return r; }
+__device__ __forceinline__ cdd cdd_mul(cdd a, cdd b) {
+  dacc re = dacc_zero(), im = dacc_zero();
+  dacc_mac(re, a.re, b.re); dacc_mac(re, dd_neg(a.im), b.im);
+  dacc_mac(im, a.re, b.im); dacc_mac(im, a.im, b.re);
+  cdd r; r.re = dacc_get(re); r.im = dacc_get(im); return r;
+}
+__device__ __forceinline__ cdd cdd_scale(cdd a, dd s) { cdd r; r.re = dd_mul(a.re, s); r.im = dd_mul(a.im, s); return r; }
+__device__ __forceinline__ cdd cdd_scale2(cdd a, float p2) { a.re = dd_scale2(a.re, p2); a.im = dd_scale2(a.im, p2); return a; }
+
+__device__ __forceinline__ cdd ld_cdd(const cdd *p) {
+  float4 v = *reinterpret_cast<const float4 *>(p);
+  cdd r; r.re.hi = v.x; r.re.lo = v.y; r.im.hi = v.z; r.im.lo = v.w; return r;
+}
+__device__ __forceinline__ void st_cdd(cdd *p, cdd a) {
+  *reinterpret_cast<float4 *>(p) = make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo);
+}
+
+// ------------------------------------------------------- complex float
+__device__ __forceinline__ cf cf_make(float r, float i) { cf z; z.re = r; z.im = i; return z; }
+__device__ __forceinline__ cf cf_zero() { return cf_make(0.f, 0.f); }
+__device__ __forceinline__ cf cf_add(cf a, cf b) { return cf_make(a.re + b.re, a.im + b.im); }
+__device__ __forceinline__ cf cf_sub(cf a, cf b) { return cf_make(a.re - b.re, a.im - b.im); }
+__device__ __forceinline__ cf cf_conj(cf a) { return cf_make(a.re, -a.im); }
+__device__ __forceinline__ cf cf_mul_mi(cf a) { return cf_make(a.im, -a.re); }
+__device__ __forceinline__ cf cf_mul_i(cf a) { return cf_make(-a.im, a.re); }
+__device__ __forceinline__ cf cf_mul(cf a, cf b) {
+  return cf_make(fmaf(a.re, b.re, -a.im * b.im), fmaf(a.re, b.im, a.im * b.re));
+}
+
+// --------------------------------------------- precision policies
+// Each policy names a complex type, a real type and the operations the FFT
+// engine needs, so one engine serves the df64 path and the FP32 path.
+struct PolDD {
+  typedef cdd cx;
+  typedef dd re;
+  static __device__ __forceinline__ cx zero() { return cdd_zero(); }
+  static __device__ __forceinline__ cx add(cx a, cx b) { return cdd_add(a, b); }
+  static __device__ __forceinline__ cx sub(cx a, cx b) { return cdd_sub(a, b); }
+  static __device__ __forceinline__ cx mul(cx a, cx b) { return cdd_mul(a, b); }
+  static __device__ __forceinline__ cx conj(cx a) { return cdd_conj(a); }
+  static __device__ __forceinline__ cx mul_mi(cx a) { return cdd_mul_mi(a); }
+  static __device__ __forceinline__ cx mul_i(cx a) { return cdd_mul_i(a); }
+  static __device__ __forceinline__ cx scale_re(cx a, re s) { return cdd_scale(a, s); }
+  static __device__ __forceinline__ cx scale2(cx a, float p2) { return cdd_scale2(a, p2); }
+  static __device__ __forceinline__ re re_add(re a, re b) { return dd_add(a, b); }
+  static __device__ __forceinline__ re re_sub(re a, re b) { return dd_sub(a, b); }
+  static __device__ __forceinline__ re re_mul(re a, re b) { return dd_mul(a, b); }
+  static __device__ __forceinline__ re re_zero() { return dd_zero(); }
+  static __device__ __forceinline__ cx make(re r, re i) { cx z; z.re = r; z.im = i; return z; }
+  static __device__ __forceinline__ re real(cx a) { return a.re; }
+  static __device__ __forceinline__ re imag(cx a) { return a.im; }
+};
+struct PolF {
+  typedef cf cx;
+  typedef float re;
+  static __device__ __forceinline__ cx zero() { return cf_zero(); }
+  static __device__ __forceinline__ cx add(cx a, cx b) { return cf_add(a, b); }
+  static __device__ __forceinline__ cx sub(cx a, cx b) { return cf_sub(a, b); }
+  static __device__ __forceinline__ cx mul(cx a, cx b) { return cf_mul(a, b); }
+  static __device__ __forceinline__ cx conj(cx a) { return cf_conj(a); }
+  static __device__ __forceinline__ cx mul_mi(cx a) { return cf_mul_mi(a); }
+  static __device__ __forceinline__ cx mul_i(cx a) { return cf_mul_i(a); }
+  static __device__ __forceinline__ cx scale_re(cx a, re s) { return cf_make(a.re * s, a.im * s); }
+  static __device__ __forceinline__ cx scale2(cx a, float p2) { return cf_make(a.re * p2, a.im * p2); }
+  static __device__ __forceinline__ re re_add(re a, re b) { return a + b; }
+  static __device__ __forceinline__ re re_sub(re a, re b) { return a - b; }
+  static __device__ __forceinline__ re re_mul(re a, re b) { return a * b; }
+  static __device__ __forceinline__ re re_zero() { return 0.f; }
+  static __device__ __forceinline__ cx make(re r, re i) { return cf_make(r, i); }
+  static __device__ __forceinline__ re real(cx a) { return a.re; }
+  static __device__ __forceinline__ re imag(cx a) { return a.im; }
+};
+
+// ----------------------------------- element loads/stores by format
+// real scalars
+__device__ __forceinline__ void ld_real(const double *p, dd &v) { v = dd_from_double(*p); }
+__device__ __forceinline__ void ld_real(const dd *p, dd &v) {
+  float2 t = *reinterpret_cast<const float2 *>(p); v.hi = t.x; v.lo = t.y;
+}
+__device__ __forceinline__ void ld_real(const float *p, float &v) { v = *p; }
+__device__ __forceinline__ void ld_real(const double *p, float &v) { v = __double2float_rn(*p); }
+__device__ __forceinline__ void st_real(double *p, dd v) { *p = dd_to_double(v); }
+__device__ __forceinline__ void st_real(dd *p, dd v) {
+  *reinterpret_cast<float2 *>(p) = make_float2(v.hi, v.lo);
+}
+__device__ __forceinline__ void st_real(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_real(double *p, float v) { *p = (double)v; }
+
+}  // namespace tw

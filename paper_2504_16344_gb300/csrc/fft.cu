@@ -1,0 +1,321 @@
+// fft.cu -- time-axis real FFTs and the Matern spectral filter.
+//
+// Time axis (Sec. "FFT-based Hessian matvecs", circulant embedding): a real
+// series x_0..x_{M-1} (M = Nt) zero-padded to L = 2M is transformed with one
+// complex FFT of length M on z_j = x_{2j} + i x_{2j+1} followed by the usual
+// even/odd split X_k = E_k + W_L^k O_k, k = 0..M (M+1 = Nt+1 frequencies).
+// Series are the contiguous axis of the time-major arrays ([time][series]),
+// so a CTA reads B adjacent series row by row with coalesced loads and never
+// transposes anything in HBM.
+//
+// Prior (Sec. "State of the art": block diagonal in time, each block a
+// Matern covariance): C x = IDFT2(lambda * DFT2(x)) per time step.  Two
+// time steps are packed into one complex field (C is real), and the 2D
+// transform runs as rows (contiguous), columns (strided, with the lambda
+// scaling and the inverse column transform fused), inverse rows.
+#include "kernels.h"
+
+namespace tw {
+
+namespace {
+
+// real input loaders by kind (0 double, 1 dd, 2 float)
+template <class P>
+__device__ __forceinline__ typename P::re ld_in(const void *base, int kind, long off);
+template <>
+__device__ __forceinline__ dd ld_in<PolDD>(const void *base, int kind, long off) {
+  dd v;
+  if (kind == 0) ld_real(reinterpret_cast<const double *>(base) + off, v);
+  else if (kind == 1) ld_real(reinterpret_cast<const dd *>(base) + off, v);
+  else { v.hi = reinterpret_cast<const float *>(base)[off]; v.lo = 0.f; }
+  return v;
+}
+template <>
+__device__ __forceinline__ float ld_in<PolF>(const void *base, int kind, long off) {
+  float v;
+  if (kind == 0) ld_real(reinterpret_cast<const double *>(base) + off, v);
+  else if (kind == 1) { const dd *p = reinterpret_cast<const dd *>(base) + off; v = __fadd_rn(p->hi, p->lo); }
+  else v = reinterpret_cast<const float *>(base)[off];
+  return v;
+}
+template <class P>
+__device__ __forceinline__ void st_out(void *base, int kind, long off, typename P::re v);
+template <>
+__device__ __forceinline__ void st_out<PolDD>(void *base, int kind, long off, dd v) {
+  if (kind == 0) st_real(reinterpret_cast<double *>(base) + off, v);
+  else if (kind == 1) st_real(reinterpret_cast<dd *>(base) + off, v);
+  else reinterpret_cast<float *>(base)[off] = __fadd_rn(v.hi, v.lo);
+}
+template <>
+__device__ __forceinline__ void st_out<PolF>(void *base, int kind, long off, float v) {
+  if (kind == 0) st_real(reinterpret_cast<double *>(base) + off, v);
+  else if (kind == 1) { dd t; t.hi = v; t.lo = 0.f; st_real(reinterpret_cast<dd *>(base) + off, t); }
+  else reinterpret_cast<float *>(base)[off] = v;
+}
+
+// --------------------------------------------------------- time axis
+template <class P>
+__global__ void __launch_bounds__(256)
+k_rfft_time(const void *__restrict__ in, int in_kind, long in_ld, int n_in,
+            typename P::cx *__restrict__ out, long out_ld, int N, FftPlan pl,
+            const typename P::cx *__restrict__ twM, const typename P::cx *__restrict__ twL,
+            int B) {
+  typedef typename P::cx cx;
+  typedef typename P::re re;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = pl.M;
+  cx *buf0 = reinterpret_cast<cx *>(smem_raw);
+  cx *buf1 = buf0 + (M + 1) * B;
+  const long n0 = (long)blockIdx.x * B;
+  const int nin = min(n_in, M);
+  // pack z_j = x_{2j} + i x_{2j+1}; x_t = 0 for t >= nin
+  for (int idx = threadIdx.x; idx < M * B; idx += blockDim.x) {
+    const int b = idx % B, j = idx / B;
+    const long n = n0 + b;
+    re r = P::re_zero(), im = P::re_zero();
+    if (n < N) {
+      const int t0 = 2 * j, t1 = 2 * j + 1;
+      if (t0 < nin) r = ld_in<P>(in, in_kind, (long)t0 * in_ld + n);
+      if (t1 < nin) im = ld_in<P>(in, in_kind, (long)t1 * in_ld + n);
+    }
+    buf0[j * B + b] = P::make(r, im);
+  }
+  __syncthreads();
+  cx *Z = fft_run<P, false>(buf0, buf1, twM, pl, B, B, 1, true);
+  // X_k = (Z_k + conj Z_{M-k})/2 + W_L^k (Z_k - conj Z_{M-k})/(2i)
+  for (int idx = threadIdx.x; idx < (M + 1) * B; idx += blockDim.x) {
+    const int b = idx % B, k = idx / B;
+    const long n = n0 + b;
+    if (n >= N) continue;
+    cx zk = Z[(k % M) * B + b];
+    cx zc = P::conj(Z[((M - k) % M) * B + b]);
+    cx E = P::scale2(P::add(zk, zc), 0.5f);
+    cx O = P::scale2(P::mul_mi(P::sub(zk, zc)), 0.5f);
+    cx X = P::add(E, P::mul(ld_cx<P>(twL + k), O));
+    out[(long)k * out_ld + n] = X;
+  }
+}
+
+template <class P>
+__global__ void __launch_bounds__(256)
+k_irfft_time(const typename P::cx *__restrict__ in, long in_ld, void *__restrict__ out,
+             int out_kind, long out_ld, int N, int n_keep, FftPlan pl,
+             const typename P::cx *__restrict__ twM, const typename P::cx *__restrict__ twL,
+             typename P::re invM, int B) {
+  typedef typename P::cx cx;
+  typedef typename P::re re;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = pl.M;
+  cx *buf0 = reinterpret_cast<cx *>(smem_raw);
+  cx *buf1 = buf0 + (M + 1) * B;
+  const long n0 = (long)blockIdx.x * B;
+  for (int idx = threadIdx.x; idx < (M + 1) * B; idx += blockDim.x) {
+    const int b = idx % B, k = idx / B;
+    const long n = n0 + b;
+    buf0[k * B + b] = (n < N) ? in[(long)k * in_ld + n] : P::zero();
+  }
+  __syncthreads();
+  // Z_k = E_k + i O_k, E_k = (X_k + conj X_{M-k})/2, O_k = (X_k - conj X_{M-k}) W_L^{-k} / 2
+  for (int idx = threadIdx.x; idx < M * B; idx += blockDim.x) {
+    const int b = idx % B, k = idx / B;
+    cx xk = buf0[k * B + b];
+    cx xc = P::conj(buf0[(M - k) * B + b]);
+    cx E = P::scale2(P::add(xk, xc), 0.5f);
+    cx O = P::scale2(P::mul(P::sub(xk, xc), P::conj(ld_cx<P>(twL + k))), 0.5f);
+    buf1[k * B + b] = P::add(E, P::mul_i(O));
+  }
+  __syncthreads();
+  cx *z = fft_run<P, true>(buf1, buf0, twM, pl, B, B, 1, true);
+  for (int idx = threadIdx.x; idx < M * B; idx += blockDim.x) {
+    const int b = idx % B, t = idx / B;
+    const long n = n0 + b;
+    if (n >= N) continue;
+    re v = P::re_zero();
+    if (t < n_keep) {
+      cx zz = z[(t >> 1) * B + b];
+      v = P::re_mul((t & 1) ? P::imag(zz) : P::real(zz), invM);
+    }
+    st_out<P>(out, out_kind, (long)t * out_ld + n, v);
+  }
+}
+
+// ------------------------------------------------------- Matern filter
+// rows pass: pair tp holds z = x_{2tp} + i x_{2tp+1}; FFT along b (length Ny)
+template <class P, bool INV>
+__global__ void __launch_bounds__(256)
+k_prior_rows(const void *__restrict__ x, int in_kind, void *__restrict__ y, int out_kind,
+             typename P::cx *__restrict__ work, int nt, int Nx, int Ny, FftPlan ply,
+             const typename P::cx *__restrict__ twy, int BR) {
+  typedef typename P::cx cx;
+  typedef typename P::re re;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx *buf0 = reinterpret_cast<cx *>(smem_raw);
+  cx *buf1 = buf0 + BR * Ny;
+  const int tp = blockIdx.y;
+  const int a0 = blockIdx.x * BR;
+  const int t0 = 2 * tp, t1 = 2 * tp + 1;
+  for (int idx = threadIdx.x; idx < BR * Ny; idx += blockDim.x) {
+    const int j = idx % Ny, b = idx / Ny, a = a0 + b;
+    cx v = P::zero();
+    if (a < Nx) {
+      if (!INV) {
+        re r = ld_in<P>(x, in_kind, ((long)t0 * Nx + a) * Ny + j);
+        re im = (t1 < nt) ? ld_in<P>(x, in_kind, ((long)t1 * Nx + a) * Ny + j) : P::re_zero();
+        v = P::make(r, im);
+      } else {
+        v = work[((long)tp * Nx + a) * Ny + j];
+      }
+    }
+    buf0[b * Ny + j] = v;
+  }
+  __syncthreads();
+  cx *Z = fft_run<P, INV>(buf0, buf1, twy, ply, BR, 1, Ny, false);
+  for (int idx = threadIdx.x; idx < BR * Ny; idx += blockDim.x) {
+    const int j = idx % Ny, b = idx / Ny, a = a0 + b;
+    if (a >= Nx) continue;
+    cx v = Z[b * Ny + j];
+    if (!INV) {
+      work[((long)tp * Nx + a) * Ny + j] = v;
+    } else {
+      st_out<P>(y, out_kind, ((long)t0 * Nx + a) * Ny + j, P::real(v));
+      if (t1 < nt) st_out<P>(y, out_kind, ((long)t1 * Nx + a) * Ny + j, P::imag(v));
+    }
+  }
+}
+
+// columns pass: forward FFT along a (length Nx, stride Ny), scale by lambda,
+// inverse FFT along a, in place in `work`.
+template <class P>
+__global__ void __launch_bounds__(256)
+k_prior_cols(typename P::cx *__restrict__ work, const typename P::re *__restrict__ lam, int Nx,
+             int Ny, FftPlan plx, const typename P::cx *__restrict__ twx, int BC) {
+  typedef typename P::cx cx;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx *buf0 = reinterpret_cast<cx *>(smem_raw);
+  cx *buf1 = buf0 + Nx * BC;
+  const int tp = blockIdx.y;
+  const int j0 = blockIdx.x * BC;
+  cx *wp = work + (long)tp * Nx * Ny;
+  for (int idx = threadIdx.x; idx < Nx * BC; idx += blockDim.x) {
+    const int b = idx % BC, a = idx / BC, j = j0 + b;
+    buf0[a * BC + b] = (j < Ny) ? wp[(long)a * Ny + j] : P::zero();
+  }
+  __syncthreads();
+  cx *Z = fft_run<P, false>(buf0, buf1, twx, plx, BC, BC, 1, true);
+  cx *O = (Z == buf0) ? buf1 : buf0;
+  for (int idx = threadIdx.x; idx < Nx * BC; idx += blockDim.x) {
+    const int b = idx % BC, p = idx / BC, j = j0 + b;
+    if (j < Ny) Z[p * BC + b] = P::scale_re(Z[p * BC + b], lam[(long)p * Ny + j]);
+  }
+  __syncthreads();
+  cx *Y = fft_run<P, true>(Z, O, twx, plx, BC, BC, 1, true);
+  for (int idx = threadIdx.x; idx < Nx * BC; idx += blockDim.x) {
+    const int b = idx % BC, a = idx / BC, j = j0 + b;
+    if (j < Ny) wp[(long)a * Ny + j] = Y[a * BC + b];
+  }
+}
+
+template <class KER>
+void ensure_smem(KER k, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int pick_batch(int len, size_t elem, int cap) {
+  // two ping-pong buffers of len x B elements within ~64 KB
+  int B = 1;
+  while (B * 2 <= cap && (size_t)2 * len * (B * 2) * elem <= 64 * 1024) B *= 2;
+  return B;
+}
+
+template <class P>
+cudaError_t rfft_time(const void *in, int in_kind, long in_ld, int n_in, typename P::cx *out,
+                      long out_ld, int N, const FftPlan &pl, const typename P::cx *twM,
+                      const typename P::cx *twL, cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  const int B = pick_batch(pl.M + 1, sizeof(typename P::cx), 32);
+  const size_t sm = (size_t)2 * (pl.M + 1) * B * sizeof(typename P::cx);
+  ensure_smem(k_rfft_time<P>, sm);
+  const long grid = (N + B - 1) / B;
+  k_rfft_time<P><<<(unsigned)grid, 256, sm, s>>>(in, in_kind, in_ld, n_in, out, out_ld, N, pl,
+                                                  twM, twL, B);
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t irfft_time(const typename P::cx *in, long in_ld, void *out, int out_kind, long out_ld,
+                       int N, int n_keep, const FftPlan &pl, const typename P::cx *twM,
+                       const typename P::cx *twL, typename P::re invM, cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  const int B = pick_batch(pl.M + 1, sizeof(typename P::cx), 32);
+  const size_t sm = (size_t)2 * (pl.M + 1) * B * sizeof(typename P::cx);
+  ensure_smem(k_irfft_time<P>, sm);
+  const long grid = (N + B - 1) / B;
+  k_irfft_time<P><<<(unsigned)grid, 256, sm, s>>>(in, in_ld, out, out_kind, out_ld, N, n_keep,
+                                                   pl, twM, twL, invM, B);
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t prior(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx, int Ny,
+                  typename P::cx *work, const typename P::re *lam, const FftPlan &plx,
+                  const FftPlan &ply, const typename P::cx *twx, const typename P::cx *twy,
+                  cudaStream_t s) {
+  if (nt <= 0) return cudaSuccess;
+  typedef typename P::cx cx;
+  const int np = (nt + 1) / 2;
+  int BR = 1;
+  while (BR * 2 <= 16 && (size_t)2 * (BR * 2) * Ny * sizeof(cx) <= 64 * 1024) BR *= 2;
+  int BC = 1;
+  while (BC * 2 <= 16 && (size_t)2 * (BC * 2) * Nx * sizeof(cx) <= 64 * 1024) BC *= 2;
+  const size_t smr = (size_t)2 * BR * Ny * sizeof(cx);
+  const size_t smc = (size_t)2 * BC * Nx * sizeof(cx);
+  ensure_smem(k_prior_rows<P, false>, smr);
+  ensure_smem(k_prior_rows<P, true>, smr);
+  ensure_smem(k_prior_cols<P>, smc);
+  dim3 gr((Nx + BR - 1) / BR, np), gc((Ny + BC - 1) / BC, np);
+  k_prior_rows<P, false><<<gr, 256, smr, s>>>(x, in_kind, nullptr, 0, work, nt, Nx, Ny, ply, twy, BR);
+  k_prior_cols<P><<<gc, 256, smc, s>>>(work, lam, Nx, Ny, plx, twx, BC);
+  k_prior_rows<P, true><<<gr, 256, smr, s>>>(nullptr, 0, y, out_kind, work, nt, Nx, Ny, ply, twy, BR);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_rfft_time_dd(const void *in, int in_kind, long in_ld, int n_in, cdd *out,
+                                long out_ld, int N, const FftPlan &pl, const cdd *twM,
+                                const cdd *twL, cudaStream_t s) {
+  return rfft_time<PolDD>(in, in_kind, in_ld, n_in, out, out_ld, N, pl, twM, twL, s);
+}
+cudaError_t launch_rfft_time_f(const void *in, int in_kind, long in_ld, int n_in, cf *out,
+                               long out_ld, int N, const FftPlan &pl, const cf *twM,
+                               const cf *twL, cudaStream_t s) {
+  return rfft_time<PolF>(in, in_kind, in_ld, n_in, out, out_ld, N, pl, twM, twL, s);
+}
+cudaError_t launch_irfft_time_dd(const cdd *in, long in_ld, void *out, int out_kind, long out_ld,
+                                 int N, int n_keep, const FftPlan &pl, const cdd *twM,
+                                 const cdd *twL, cudaStream_t s) {
+  // 1/M as a float pair (host double split)
+  const double inv = 1.0 / pl.M;
+  dd invM;
+  invM.hi = (float)inv;
+  invM.lo = (float)(inv - (double)invM.hi);
+  return irfft_time<PolDD>(in, in_ld, out, out_kind, out_ld, N, n_keep, pl, twM, twL, invM, s);
+}
+cudaError_t launch_irfft_time_f(const cf *in, long in_ld, void *out, int out_kind, long out_ld,
+                                int N, int n_keep, const FftPlan &pl, const cf *twM,
+                                const cf *twL, cudaStream_t s) {
+  return irfft_time<PolF>(in, in_ld, out, out_kind, out_ld, N, n_keep, pl, twM, twL,
+                          (float)(1.0 / pl.M), s);
+}
+cudaError_t launch_prior_dd(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
+                            int Ny, cdd *work, const dd *lam, const FftPlan &plx,
+                            const FftPlan &ply, const cdd *twx, const cdd *twy, cudaStream_t s) {
+  return prior<PolDD>(x, in_kind, y, out_kind, nt, Nx, Ny, work, lam, plx, ply, twx, twy, s);
+}
+cudaError_t launch_prior_f(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
+                           int Ny, cf *work, const float *lam, const FftPlan &plx,
+                           const FftPlan &ply, const cf *twx, const cf *twy, cudaStream_t s) {
+  return prior<PolF>(x, in_kind, y, out_kind, nt, Nx, Ny, work, lam, plx, ply, twx, twy, s);
+}
+
+}  // namespace tw

@@ -1,0 +1,213 @@
+// fft_engine.cuh -- batched mixed-radix complex FFT in shared memory.
+//
+// The FFT-based Toeplitz apply (Sec. "FFT-based Hessian matvecs": embed the
+// block Toeplitz matrix in a block circulant one, which the DFT
+// block-diagonalises) needs DFTs along time of length 2Nt for many series
+// at once, and the Matern prior needs 2D DFTs over the periodic grid.  This
+// engine transforms B series of length M held in shared memory with a
+// self-sorting (Stockham) sequence of radix-R passes, R in {2,3,4,5,7} with
+// specialised butterflies and any other odd R by a direct symmetric DFT.
+//
+// Pass with radix R, p = product of the earlier radices, S = M/R:
+//   for i < S:  k = i mod p,  v_j = in[i + j S] * W_M^(j k M/(p R)),
+//               u = DFT_R(v),  out[(i - k) R + k + q p] = u_q.
+// After all passes `out` holds DFT_M(in) in natural order.
+// W_M^t = exp(-2 pi i t / M) comes from a table; the inverse transform uses
+// conj(W) and is unnormalised.
+#pragma once
+#include "df64.cuh"
+
+namespace tw {
+
+#define TW_FFT_MAX_STAGES 16
+
+struct FftPlan {
+  int M;
+  int nst;
+  int R[TW_FFT_MAX_STAGES];
+};
+
+template <class P>
+__device__ __forceinline__ typename P::cx ld_cx(const typename P::cx *p);
+template <>
+__device__ __forceinline__ cdd ld_cx<PolDD>(const cdd *p) {
+  float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  cdd r; r.re.hi = v.x; r.re.lo = v.y; r.im.hi = v.z; r.im.lo = v.w; return r;
+}
+template <>
+__device__ __forceinline__ cf ld_cx<PolF>(const cf *p) {
+  float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+  return cf_make(v.x, v.y);
+}
+
+// twiddle W_M^t (forward) or its conjugate (inverse)
+template <class P, bool INV>
+__device__ __forceinline__ typename P::cx twid(const typename P::cx *tab, int t) {
+  typename P::cx w = ld_cx<P>(tab + t);
+  return INV ? P::conj(w) : w;
+}
+
+// R-point DFT of v (in registers), forward or inverse.
+template <class P, bool INV, int R>
+struct Bfly;
+
+template <class P, bool INV>
+struct Bfly<P, INV, 2> {
+  typedef typename P::cx cx;
+  static __device__ __forceinline__ void run(cx *v, const cx *, int) {
+    cx a = P::add(v[0], v[1]);
+    cx b = P::sub(v[0], v[1]);
+    v[0] = a; v[1] = b;
+  }
+};
+
+template <class P, bool INV>
+struct Bfly<P, INV, 4> {
+  typedef typename P::cx cx;
+  static __device__ __forceinline__ void run(cx *v, const cx *, int) {
+    cx s02 = P::add(v[0], v[2]), d02 = P::sub(v[0], v[2]);
+    cx s13 = P::add(v[1], v[3]), d13 = P::sub(v[1], v[3]);
+    // forward: W_4 = -i; inverse: +i
+    cx r13 = INV ? P::mul_i(d13) : P::mul_mi(d13);
+    v[0] = P::add(s02, s13);
+    v[2] = P::sub(s02, s13);
+    v[1] = P::add(d02, r13);
+    v[3] = P::sub(d02, r13);
+  }
+};
+
+// odd R: with a_j = v_j + v_{R-j}, b_j = v_j - v_{R-j} (j = 1..h, h = (R-1)/2)
+//   u_q     = v_0 + sum_j a_j cos(2 pi j q / R) -/+ i sum_j b_j sin(2 pi j q / R)
+//   u_{R-q} = v_0 + sum_j a_j cos(2 pi j q / R) +/- i sum_j b_j sin(2 pi j q / R)
+template <class P, bool INV, int R>
+struct Bfly {
+  typedef typename P::cx cx;
+  typedef typename P::re re;
+  static __device__ __forceinline__ void run(cx *v, const cx *tab, int M) {
+    constexpr int h = (R - 1) / 2;
+    cx a[h], b[h];
+#pragma unroll
+    for (int j = 1; j <= h; ++j) {
+      a[j - 1] = P::add(v[j], v[R - j]);
+      b[j - 1] = P::sub(v[j], v[R - j]);
+    }
+    cx u0 = v[0];
+#pragma unroll
+    for (int j = 0; j < h; ++j) u0 = P::add(u0, a[j]);
+    const int step = M / R;
+#pragma unroll
+    for (int q = 1; q <= h; ++q) {
+      cx c = v[0];       // v0 + sum a_j cos
+      cx s = P::zero();  // sum b_j sin
+#pragma unroll
+      for (int j = 1; j <= h; ++j) {
+        cx w = ld_cx<P>(tab + (j * q % R) * step);   // forward table: cos - i sin
+        re cs = P::real(w);
+        re sn = P::imag(w);                           // = -sin
+        c = P::add(c, P::scale_re(a[j - 1], cs));
+        s = P::add(s, P::scale_re(b[j - 1], sn));     // accumulates -sum b sin
+      }
+      // forward: u_q = c - i * sum b sin = c + i * s ; inverse: c - i * s
+      cx is = P::mul_i(s);
+      v[q] = INV ? P::sub(c, is) : P::add(c, is);
+      v[R - q] = INV ? P::add(c, is) : P::sub(c, is);
+    }
+    v[0] = u0;
+  }
+};
+
+// One pass with compile-time radix R.  Buffers: element (b, j) at b*ss + j*es.
+template <class P, bool INV, int R>
+__device__ __forceinline__ void fft_pass(const typename P::cx *src, typename P::cx *dst,
+                                         const typename P::cx *tab, int M, int p, int B,
+                                         int es, int ss, bool series_fast) {
+  typedef typename P::cx cx;
+  const int S = M / R;
+  const int tstride = M / (p * R);
+  const int total = S * B;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    int b, i;
+    if (series_fast) { b = idx % B; i = idx / B; } else { i = idx % S; b = idx / S; }
+    const int k = i % p;
+    cx v[R];
+    const cx *sb = src + b * ss;
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = sb[(i + j * S) * es];
+    if (k != 0) {
+#pragma unroll
+      for (int j = 1; j < R; ++j) v[j] = P::mul(v[j], twid<P, INV>(tab, (j * k * tstride) % M));
+    }
+    Bfly<P, INV, R>::run(v, tab, M);
+    const int base = (i - k) * R + k;
+    cx *db = dst + b * ss;
+#pragma unroll
+    for (int q = 0; q < R; ++q) db[(base + q * p) * es] = v[q];
+  }
+}
+
+// Pass with a runtime odd radix R (large prime factors): inputs are twiddled
+// in place in src (each butterfly owns its inputs), then every output is a
+// direct R-term sum.  O(R) work per output.
+template <class P, bool INV>
+__device__ void fft_pass_generic(typename P::cx *src, typename P::cx *dst,
+                                 const typename P::cx *tab, int M, int p, int R, int B,
+                                 int es, int ss, bool series_fast) {
+  typedef typename P::cx cx;
+  const int S = M / R;
+  const int tstride = M / (p * R);
+  const int total = S * B;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    int b, i;
+    if (series_fast) { b = idx % B; i = idx / B; } else { i = idx % S; b = idx / S; }
+    const int k = i % p;
+    if (k != 0) {
+      cx *sb = src + b * ss;
+      for (int j = 1; j < R; ++j) {
+        cx w = twid<P, INV>(tab, (j * k * tstride) % M);
+        sb[(i + j * S) * es] = P::mul(sb[(i + j * S) * es], w);
+      }
+    }
+  }
+  __syncthreads();
+  const int totq = S * R * B;
+  for (int idx = threadIdx.x; idx < totq; idx += blockDim.x) {
+    int b, i, q;
+    if (series_fast) { b = idx % B; int r = idx / B; i = r % S; q = r / S; }
+    else { i = idx % S; int r = idx / S; b = r % B; q = r / B; }
+    const int k = i % p;
+    const cx *sb = src + b * ss;
+    cx acc = sb[i * es];
+    for (int j = 1; j < R; ++j) {
+      cx w = twid<P, INV>(tab, ((j * q) % R) * S);
+      acc = P::add(acc, P::mul(sb[(i + j * S) * es], w));
+    }
+    dst[b * ss + ((i - k) * R + k + q * p) * es] = acc;
+  }
+}
+
+// Full transform.  Returns the buffer that holds the result (buf0 or buf1).
+template <class P, bool INV>
+__device__ typename P::cx *fft_run(typename P::cx *buf0, typename P::cx *buf1,
+                                   const typename P::cx *tab, const FftPlan &pl, int B,
+                                   int es, int ss, bool series_fast) {
+  typedef typename P::cx cx;
+  cx *src = buf0, *dst = buf1;
+  int p = 1;
+  for (int st = 0; st < pl.nst; ++st) {
+    const int R = pl.R[st];
+    switch (R) {
+      case 2: fft_pass<P, INV, 2>(src, dst, tab, pl.M, p, B, es, ss, series_fast); break;
+      case 3: fft_pass<P, INV, 3>(src, dst, tab, pl.M, p, B, es, ss, series_fast); break;
+      case 4: fft_pass<P, INV, 4>(src, dst, tab, pl.M, p, B, es, ss, series_fast); break;
+      case 5: fft_pass<P, INV, 5>(src, dst, tab, pl.M, p, B, es, ss, series_fast); break;
+      case 7: fft_pass<P, INV, 7>(src, dst, tab, pl.M, p, B, es, ss, series_fast); break;
+      default: fft_pass_generic<P, INV>(src, dst, tab, pl.M, p, R, B, es, ss, series_fast); break;
+    }
+    __syncthreads();
+    cx *t = src; src = dst; dst = t;
+    p *= R;
+  }
+  return src;
+}
+
+}  // namespace tw

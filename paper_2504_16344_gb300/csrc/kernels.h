@@ -1,0 +1,61 @@
+// kernels.h -- host-side launchers of the library's kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "fft_engine.cuh"
+
+namespace tw {
+
+// ---- operator storage formats
+enum OpFmt { FMT_DD = 0, FMT_C64 = 1, FMT_BF16X2 = 2 };
+
+// ---- time-axis real FFT (length 2M, second half zero) -------------------
+// in  [M rows][N series] real, row stride in_ld; rows >= n_in treated as 0
+// out [M+1 rows][N] complex, row stride out_ld
+// in_kind: 0 = double, 1 = dd (float2), 2 = float
+cudaError_t launch_rfft_time_dd(const void *in, int in_kind, long in_ld, int n_in,
+                                cdd *out, long out_ld, int N, const FftPlan &pl,
+                                const cdd *twM, const cdd *twL, cudaStream_t s);
+cudaError_t launch_rfft_time_f(const void *in, int in_kind, long in_ld, int n_in,
+                               cf *out, long out_ld, int N, const FftPlan &pl,
+                               const cf *twM, const cf *twL, cudaStream_t s);
+// inverse: in [M+1][N] complex -> out [M][N] real (1/(2M) applied),
+// rows t >= n_keep written as 0.  out_kind: 0 = double, 1 = dd, 2 = float
+cudaError_t launch_irfft_time_dd(const cdd *in, long in_ld, void *out, int out_kind, long out_ld,
+                                 int N, int n_keep, const FftPlan &pl, const cdd *twM,
+                                 const cdd *twL, cudaStream_t s);
+cudaError_t launch_irfft_time_f(const cf *in, long in_ld, void *out, int out_kind, long out_ld,
+                                int N, int n_keep, const FftPlan &pl, const cf *twM,
+                                const cf *twL, cudaStream_t s);
+
+// ---- Matern filter on the periodic grid: y_t = C^power x_t, t < nt -------
+// x, y: [nt][Nx][Ny] real (kind 0 double, 1 dd, 2 float); work: [ceil(nt/2)][Nx][Ny] complex
+// lam: [Nx][Ny] eigenvalues^power / (Nx Ny)
+cudaError_t launch_prior_dd(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
+                            int Ny, cdd *work, const dd *lam, const FftPlan &plx,
+                            const FftPlan &ply, const cdd *twx, const cdd *twy, cudaStream_t s);
+cudaError_t launch_prior_f(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
+                           int Ny, cf *work, const float *lam, const FftPlan &plx,
+                           const FftPlan &ply, const cf *twx, const cf *twy, cudaStream_t s);
+
+// ---- frequency-batched complex GEMV ------------------------------------
+// forward: yh[w][s] = sum_k A[w][s][k] xh[w][k]   (A: [Nf][Nr][Nm] in `fmt`)
+// partial sums per k-chunk go to `part` ([Nf][nchunk][Nr]) then are reduced.
+int gemv_fwd_nchunk(int Nm);
+cudaError_t launch_gemv_fwd_dd(const void *A, int fmt, const cdd *xh, cdd *part, cdd *yh,
+                               int Nf, int Nr, int Nm, cudaStream_t s);
+cudaError_t launch_gemv_fwd_f(const void *A, int fmt, const cf *xh, cf *part, cf *yh, int Nf,
+                              int Nr, int Nm, cudaStream_t s);
+// adjoint: xh[w][k] = sum_s conj(A[w][s][k]) yh[w][s]
+cudaError_t launch_gemv_adj_dd(const void *A, int fmt, const cdd *yh, cdd *xh, int Nf, int Nr,
+                               int Nm, cudaStream_t s);
+cudaError_t launch_gemv_adj_f(const void *A, int fmt, const cf *yh, cf *xh, int Nf, int Nr,
+                              int Nm, cudaStream_t s);
+
+// ---- operator storage conversion: dst[w][row0+r][k] from src (cdd) -----
+cudaError_t launch_convert_op(const cdd *src, long src_ld_w, void *dst, int fmt, long dst_ld_w,
+                              long n_per_w, int Nf, cudaStream_t s);
+
+}  // namespace tw

@@ -1,0 +1,346 @@
+// tw_api.cu -- context, operator set-up, Toeplitz applies and the prior.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "ctx.h"
+
+using namespace tw;
+
+namespace twh {
+
+tw_status fail(tw_ctx *c, tw_status st, const std::string &msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+tw_status cuda_fail(tw_ctx *c, cudaError_t e, const char *where) {
+  std::string m = std::string("CUDA error ") + cudaGetErrorString(e) + " in " + where;
+  return fail(c, e == cudaErrorMemoryAllocation ? TW_ERR_OOM : TW_ERR_CUDA, m);
+}
+
+void *dalloc(tw_ctx *c, size_t bytes) {
+  void *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  c->allocs.push_back(p);
+  c->bytes += bytes;
+  return p;
+}
+
+void dfree(tw_ctx *c, void *p) {
+  if (!p) return;
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+  if (it != c->allocs.end()) c->allocs.erase(it);
+  cudaFree(p);
+}
+
+// Factor M into radices: 4s first, then 2, 3, 5, 7, then remaining odd primes.
+FftPlan make_plan(int M) {
+  FftPlan p{};
+  p.M = M;
+  int m = M, n = 0;
+  const int small[5] = {4, 2, 3, 5, 7};
+  for (int r : small)
+    while (m % r == 0 && n < TW_FFT_MAX_STAGES) { p.R[n++] = r; m /= r; }
+  for (int q = 11; m > 1 && n < TW_FFT_MAX_STAGES; q += 2)
+    while (m % q == 0 && n < TW_FFT_MAX_STAGES) { p.R[n++] = q; m /= q; }
+  if (m > 1) p.R[n++] = m;  // remaining factor (only for absurd lengths)
+  p.nst = n;
+  return p;
+}
+
+}  // namespace twh
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+void split_dd(double v, dd &o) {
+  o.hi = (float)v;
+  o.lo = (float)(v - (double)o.hi);
+}
+
+// W_M^t = exp(-2 pi i t / M) for t < n (n = M, or M+1 with denominator 2M)
+tw_status upload_twiddles(tw_ctx *c, int n, double denom, cdd **out_dd, cf **out_f) {
+  std::vector<cdd> h(n);
+  std::vector<cf> hf(n);
+  for (int t = 0; t < n; ++t) {
+    const double a = -2.0 * kPi * (double)t / denom;
+    const double cr = cos(a), ci = sin(a);
+    split_dd(cr, h[t].re);
+    split_dd(ci, h[t].im);
+    hf[t].re = (float)cr;
+    hf[t].im = (float)ci;
+  }
+  *out_dd = (cdd *)twh::dalloc(c, n * sizeof(cdd));
+  *out_f = (cf *)twh::dalloc(c, n * sizeof(cf));
+  if (!*out_dd || !*out_f) return twh::fail(c, TW_ERR_OOM, "twiddle allocation");
+  TW_CUDA(c, cudaMemcpy(*out_dd, h.data(), n * sizeof(cdd), cudaMemcpyHostToDevice));
+  TW_CUDA(c, cudaMemcpy(*out_f, hf.data(), n * sizeof(cf), cudaMemcpyHostToDevice));
+  return TW_OK;
+}
+
+size_t op_elem_bytes(int fmt) { return fmt == FMT_DD ? sizeof(cdd) : 8; }
+
+int rows_of(const tw_ctx *c, int which) { return which == TW_MAP_F ? c->Nd : c->Nq; }
+
+tw_status check_ready(tw_ctx *c, int which, int fmt) {
+  if (!c) return TW_ERR_ARG;
+  if (which != TW_MAP_F && which != TW_MAP_FQ) return twh::fail(c, TW_ERR_ARG, "bad map");
+  if (fmt < 0 || fmt > 2 || !c->op[which][fmt])
+    return twh::fail(c, TW_ERR_ARG, "requested precision was not kept at tw_create");
+  for (char l : c->loaded[which])
+    if (!l) return twh::fail(c, TW_ERR_STATE, "block column not fully loaded");
+  return TW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tw_status tw_create(tw_ctx **out, int Nd, int Nq, int Nx, int Ny, int Nt, double Lx, double Ly,
+                    unsigned keep, int device) {
+  if (!out) return TW_ERR_ARG;
+  *out = nullptr;
+  if (Nd <= 0 || Nq <= 0 || Nx <= 0 || Ny <= 0 || Nt <= 0 || !(Lx > 0) || !(Ly > 0) ||
+      (keep & 7u) == 0)
+    return TW_ERR_ARG;
+  tw_ctx *c = new tw_ctx();
+  c->dev = device;
+  c->Nd = Nd; c->Nq = Nq; c->Nx = Nx; c->Ny = Ny; c->Nt = Nt;
+  c->Nm = Nx * Ny; c->Nf = Nt + 1; c->Rmax = std::max(Nd, Nq);
+  c->Lx = Lx; c->Ly = Ly; c->keep = keep;
+  c->loaded[0].assign(Nd, 0);
+  c->loaded[1].assign(Nq, 0);
+  tw_status st = TW_OK;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) { st = twh::cuda_fail(c, e, "cudaSetDevice"); delete c; return st; }
+  const size_t Nf = c->Nf, Nm = c->Nm;
+  for (int which = 0; which < 2 && st == TW_OK; ++which)
+    for (int fmt = 0; fmt < 3; ++fmt) {
+      if (!(keep & (1u << fmt))) continue;
+      const size_t b = Nf * (size_t)rows_of(c, which) * Nm * op_elem_bytes(fmt);
+      c->op[which][fmt] = twh::dalloc(c, b);
+      if (!c->op[which][fmt]) { st = twh::fail(c, TW_ERR_OOM, "operator allocation"); break; }
+    }
+  c->plT = twh::make_plan(Nt);
+  c->plX = twh::make_plan(Nx);
+  c->plY = twh::make_plan(Ny);
+  if (st == TW_OK) st = upload_twiddles(c, Nt, Nt, &c->twT, &c->twTf);
+  if (st == TW_OK) st = upload_twiddles(c, Nt + 1, 2.0 * Nt, &c->twL, &c->twLf);
+  if (st == TW_OK) st = upload_twiddles(c, Nx, Nx, &c->twX, &c->twXf);
+  if (st == TW_OK) st = upload_twiddles(c, Ny, Ny, &c->twY, &c->twYf);
+  if (st == TW_OK) {
+    const int nchunk = gemv_fwd_nchunk(c->Nm);
+    c->wf = (cdd *)twh::dalloc(c, Nf * Nm * sizeof(cdd));
+    c->wr = (cdd *)twh::dalloc(c, Nf * c->Rmax * sizeof(cdd));
+    c->part = (cdd *)twh::dalloc(c, Nf * (size_t)nchunk * c->Rmax * sizeof(cdd));
+    c->wt = (dd *)twh::dalloc(c, (size_t)Nt * Nm * sizeof(dd));
+    c->ws = (cdd *)twh::dalloc(c, (size_t)((Nt + 1) / 2) * Nm * sizeof(cdd));
+    c->d_err = (int *)twh::dalloc(c, 4 * sizeof(int));
+    if (!c->wf || !c->wr || !c->part || !c->wt || !c->ws || !c->d_err)
+      st = twh::fail(c, TW_ERR_OOM, "workspace allocation");
+    else if (cudaMemset(c->d_err, 0, 4 * sizeof(int)) != cudaSuccess)
+      st = twh::fail(c, TW_ERR_CUDA, "memset");
+  }
+  if (st != TW_OK) {
+    // keep the message for the caller: report via stderr since ctx is freed
+    fprintf(stderr, "tw_create: %s\n", c->err.c_str());
+    tw_destroy(c);
+    return st;
+  }
+  *out = c;
+  return TW_OK;
+}
+
+void tw_destroy(tw_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->dev);
+  for (void *p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+const char *tw_last_error(const tw_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+size_t tw_device_bytes(const tw_ctx *c) { return c ? c->bytes : 0; }
+
+tw_status tw_set_block_column(tw_ctx *c, tw_map which, int row0, int nrows, const double *col,
+                              void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (which != TW_MAP_F && which != TW_MAP_FQ) return twh::fail(c, TW_ERR_ARG, "bad map");
+  const int R = rows_of(c, which);
+  if (row0 < 0 || nrows <= 0 || row0 + nrows > R || !col)
+    return twh::fail(c, TW_ERR_ARG, "row range outside the map or null column");
+  cudaStream_t s = (cudaStream_t)stream;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  const long N = (long)nrows * c->Nm;                 // series in this chunk
+  const long out_ld = (long)R * c->Nm;                // frequency row stride of F^
+  cdd *dst = (cdd *)c->op[which][FMT_DD];
+  cdd *tmp = nullptr;
+  long dst_ld = out_ld;
+  if (dst) {
+    dst += (long)row0 * c->Nm;
+  } else {
+    tmp = (cdd *)twh::dalloc(c, (size_t)c->Nf * N * sizeof(cdd));
+    if (!tmp) return twh::fail(c, TW_ERR_OOM, "temporary for block column");
+    dst = tmp;
+    dst_ld = N;
+  }
+  TW_CUDA(c, launch_rfft_time_dd(col, 0, N, c->Nt, dst, dst_ld, (int)N, c->plT, c->twT, c->twL, s));
+  for (int fmt = 1; fmt < 3; ++fmt) {
+    if (!c->op[which][fmt]) continue;
+    uint8_t *d8 = (uint8_t *)c->op[which][fmt] + (size_t)row0 * c->Nm * 8;
+    TW_CUDA(c, launch_convert_op(dst, dst_ld, d8, fmt, out_ld, N, c->Nf, s));
+  }
+  if (tmp) {
+    TW_CUDA(c, cudaStreamSynchronize(s));
+    twh::dfree(c, tmp);
+    c->bytes -= (size_t)c->Nf * N * sizeof(cdd);
+  }
+  for (int r = row0; r < row0 + nrows; ++r) c->loaded[which][r] = 1;
+  return TW_OK;
+}
+
+tw_status tw_set_prior(tw_ctx *c, double nu, double ell, double var) {
+  if (!c) return TW_ERR_ARG;
+  if (!(nu > 0) || !(ell > 0) || !(var > 0)) return twh::fail(c, TW_ERR_ARG, "prior parameters must be positive");
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  const int Nx = c->Nx, Ny = c->Ny;
+  const size_t N = (size_t)Nx * Ny;
+  const double kappa = sqrt(2.0 * nu) / ell;
+  std::vector<double> s(N);
+  double ssum = 0.0;
+  for (int p = 0; p < Nx; ++p) {
+    const int pf = (p <= Nx / 2) ? p : p - Nx;          // signed frequency
+    const double kx = 2.0 * kPi * pf / c->Lx;
+    for (int q = 0; q < Ny; ++q) {
+      const int qf = (q <= Ny / 2) ? q : q - Ny;
+      const double ky = 2.0 * kPi * qf / c->Ly;
+      const double v = pow(kappa * kappa + kx * kx + ky * ky, -(nu + 1.0));
+      s[(size_t)p * Ny + q] = v;
+      ssum += v;
+    }
+  }
+  std::vector<dd> l1(N), lh(N);
+  std::vector<float> l1f(N), lhf(N);
+  for (size_t i = 0; i < N; ++i) {
+    const double lam = var * (double)N * s[i] / ssum;   // eigenvalue of C
+    const double a = lam / (double)N, b = sqrt(lam) / (double)N;   // 1/N of the inverse DFT folded in
+    split_dd(a, l1[i]);
+    split_dd(b, lh[i]);
+    l1f[i] = (float)a;
+    lhf[i] = (float)b;
+  }
+  if (!c->lam1) {
+    c->lam1 = (dd *)twh::dalloc(c, N * sizeof(dd));
+    c->lamh = (dd *)twh::dalloc(c, N * sizeof(dd));
+    c->lam1f = (float *)twh::dalloc(c, N * sizeof(float));
+    c->lamhf = (float *)twh::dalloc(c, N * sizeof(float));
+    if (!c->lam1 || !c->lamh || !c->lam1f || !c->lamhf) return twh::fail(c, TW_ERR_OOM, "prior tables");
+  }
+  TW_CUDA(c, cudaMemcpy(c->lam1, l1.data(), N * sizeof(dd), cudaMemcpyHostToDevice));
+  TW_CUDA(c, cudaMemcpy(c->lamh, lh.data(), N * sizeof(dd), cudaMemcpyHostToDevice));
+  TW_CUDA(c, cudaMemcpy(c->lam1f, l1f.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+  TW_CUDA(c, cudaMemcpy(c->lamhf, lhf.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+  c->nu = nu; c->ell = ell; c->var = var;
+  c->prior_set = true;
+  return TW_OK;
+}
+
+tw_status tw_p2o_apply(tw_ctx *c, tw_map which, tw_prec prec, int nrhs, const double *x,
+                       double *out, void *stream) {
+  tw_status st = check_ready(c, which, (int)prec);
+  if (st != TW_OK) return st;
+  if (nrhs < 0 || (nrhs > 0 && (!x || !out))) return twh::fail(c, TW_ERR_ARG, "bad rhs");
+  cudaStream_t s = (cudaStream_t)stream;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  const int R = rows_of(c, which), Nt = c->Nt, Nf = c->Nf, Nm = c->Nm;
+  const void *A = c->op[which][prec];
+  for (int r = 0; r < nrhs; ++r) {
+    const double *xr = x + (size_t)r * Nt * Nm;
+    double *outr = out + (size_t)r * Nt * R;
+    if (prec == TW_PREC_FP64) {
+      TW_CUDA(c, launch_rfft_time_dd(xr, 0, Nm, Nt, c->wf, Nm, Nm, c->plT, c->twT, c->twL, s));
+      TW_CUDA(c, launch_gemv_fwd_dd(A, FMT_DD, c->wf, c->part, c->wr, Nf, R, Nm, s));
+      TW_CUDA(c, launch_irfft_time_dd(c->wr, R, outr, 0, R, R, Nt, c->plT, c->twT, c->twL, s));
+    } else {
+      cf *wf = (cf *)c->wf, *wr = (cf *)c->wr, *part = (cf *)c->part;
+      TW_CUDA(c, launch_rfft_time_f(xr, 0, Nm, Nt, wf, Nm, Nm, c->plT, c->twTf, c->twLf, s));
+      TW_CUDA(c, launch_gemv_fwd_f(A, (int)prec, wf, part, wr, Nf, R, Nm, s));
+      TW_CUDA(c, launch_irfft_time_f(wr, R, outr, 0, R, R, Nt, c->plT, c->twTf, c->twLf, s));
+    }
+  }
+  return TW_OK;
+}
+
+tw_status tw_p2o_adjoint(tw_ctx *c, tw_map which, tw_prec prec, int nrhs, const double *y,
+                         double *x, void *stream) {
+  tw_status st = check_ready(c, which, (int)prec);
+  if (st != TW_OK) return st;
+  if (nrhs < 0 || (nrhs > 0 && (!x || !y))) return twh::fail(c, TW_ERR_ARG, "bad rhs");
+  cudaStream_t s = (cudaStream_t)stream;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  const int R = rows_of(c, which), Nt = c->Nt, Nf = c->Nf, Nm = c->Nm;
+  const void *A = c->op[which][prec];
+  for (int r = 0; r < nrhs; ++r) {
+    const double *yr = y + (size_t)r * Nt * R;
+    double *xr = x + (size_t)r * Nt * Nm;
+    if (prec == TW_PREC_FP64) {
+      TW_CUDA(c, launch_rfft_time_dd(yr, 0, R, Nt, c->wr, R, R, c->plT, c->twT, c->twL, s));
+      TW_CUDA(c, launch_gemv_adj_dd(A, FMT_DD, c->wr, c->wf, Nf, R, Nm, s));
+      TW_CUDA(c, launch_irfft_time_dd(c->wf, Nm, xr, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s));
+    } else {
+      cf *wf = (cf *)c->wf, *wr = (cf *)c->wr;
+      TW_CUDA(c, launch_rfft_time_f(yr, 0, R, Nt, wr, R, R, c->plT, c->twTf, c->twLf, s));
+      TW_CUDA(c, launch_gemv_adj_f(A, (int)prec, wr, wf, Nf, R, Nm, s));
+      TW_CUDA(c, launch_irfft_time_f(wf, Nm, xr, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s));
+    }
+  }
+  return TW_OK;
+}
+
+tw_status tw_prior_apply(tw_ctx *c, double power, int nrhs, const double *x, double *y,
+                         void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (!c->prior_set) return twh::fail(c, TW_ERR_STATE, "prior not set");
+  if (!(power == 1.0 || power == 0.5)) return twh::fail(c, TW_ERR_ARG, "power must be 1 or 0.5");
+  if (nrhs < 0 || (nrhs > 0 && (!x || !y))) return twh::fail(c, TW_ERR_ARG, "bad rhs");
+  cudaStream_t s = (cudaStream_t)stream;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  const dd *lam = power == 1.0 ? c->lam1 : c->lamh;
+  for (int r = 0; r < nrhs; ++r) {
+    const size_t off = (size_t)r * c->Nt * c->Nm;
+    TW_CUDA(c, launch_prior_dd(x + off, 0, y + off, 0, c->Nt, c->Nx, c->Ny, c->ws, lam, c->plX,
+                               c->plY, c->twX, c->twY, s));
+  }
+  return TW_OK;
+}
+
+tw_status tw_check(tw_ctx *c, void *stream) {
+  if (!c) return TW_ERR_ARG;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  TW_CUDA(c, cudaStreamSynchronize((cudaStream_t)stream));
+  int h[4] = {0, 0, 0, 0};
+  TW_CUDA(c, cudaMemcpy(h, c->d_err, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h[0] == 0) return TW_OK;
+  TW_CUDA(c, cudaMemset(c->d_err, 0, sizeof(h)));
+  char buf[160];
+  if (h[0] == TW_ERR_NOT_SPD) {
+    snprintf(buf, sizeof buf, "Cholesky: non-positive pivot at row %d", h[1]);
+    return twh::fail(c, TW_ERR_NOT_SPD, buf);
+  }
+  if (h[0] == TW_ERR_TIMEOUT) {
+    snprintf(buf, sizeof buf, "a bounded device wait ran out (site %d)", h[1]);
+    return twh::fail(c, TW_ERR_TIMEOUT, buf);
+  }
+  snprintf(buf, sizeof buf, "device error code %d info %d", h[0], h[1]);
+  return twh::fail(c, (tw_status)h[0], buf);
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+"""Thin ctypes binding of libtw.so (argument marshalling only).
+
+Every step of the online path runs in the library's CUDA kernels; this module
+only checks tensor shapes, dtypes and devices and passes raw device pointers
+and the current CUDA stream.  Importing it does not need a GPU; creating a
+Context does, and fails loudly if libtw.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libtw.so")
+
+# tw_status
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_NOT_SPD, ERR_NOT_CONVERGED, ERR_TIMEOUT = range(8)
+STATUS_NAMES = ["TW_OK", "TW_ERR_ARG", "TW_ERR_OOM", "TW_ERR_CUDA", "TW_ERR_STATE",
+                "TW_ERR_NOT_SPD", "TW_ERR_NOT_CONVERGED", "TW_ERR_TIMEOUT"]
+# tw_map
+MAP_F, MAP_FQ = 0, 1
+# tw_prec
+PREC_FP64, PREC_C64, PREC_BF16X2 = 0, 1, 2
+KEEP_FP64, KEEP_C64, KEEP_BF16X2 = 1, 2, 4
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_U = ctypes.c_uint
+_S = ctypes.c_int  # tw_status
+
+# name -> (restype, argtypes); the names are those declared in include/tw.h
+SIGNATURES = {
+    "tw_create": (_S, [ctypes.POINTER(_P), _I, _I, _I, _I, _I, _D, _D, _U, _I]),
+    "tw_destroy": (None, [_P]),
+    "tw_last_error": (ctypes.c_char_p, [_P]),
+    "tw_set_block_column": (_S, [_P, _I, _I, _I, _P, _P]),
+    "tw_set_prior": (_S, [_P, _D, _D, _D]),
+    "tw_p2o_apply": (_S, [_P, _I, _I, _I, _P, _P, _P]),
+    "tw_p2o_adjoint": (_S, [_P, _I, _I, _I, _P, _P, _P]),
+    "tw_prior_apply": (_S, [_P, _D, _I, _P, _P, _P]),
+    "tw_check": (_S, [_P, _P]),
+    "tw_device_bytes": (ctypes.c_size_t, [_P]),
+}
+
+_lib = None
+
+
+class TwError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+def lib_path() -> str:
+    return LIB_PATH
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libtw.so and declare the C signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev(t, dtype=None, shape=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """An online-inversion context on one GPU (wraps tw_ctx)."""
+
+    def __init__(self, Nd, Nq, Nx, Ny, Nt, Lx=1.0, Ly=1.0, keep=KEEP_FP64, device=0):
+        self.lib = load()
+        self.Nd, self.Nq, self.Nx, self.Ny, self.Nt = Nd, Nq, Nx, Ny, Nt
+        self.Nm = Nx * Ny
+        self.device = device
+        h = ctypes.c_void_p()
+        st = self.lib.tw_create(ctypes.byref(h), Nd, Nq, Nx, Ny, Nt, Lx, Ly, keep, device)
+        if st != OK:
+            raise TwError(st, "tw_create failed")
+        self.h = h
+
+    # ------------------------------------------------------------ util
+    def _check(self, st):
+        if st != OK:
+            raise TwError(st, self.lib.tw_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rows(self, which):
+        return self.Nd if which == MAP_F else self.Nq
+
+    def device_bytes(self) -> int:
+        return int(self.lib.tw_device_bytes(self.h))
+
+    def check(self, stream=None):
+        """Synchronise and raise on errors recorded by kernels."""
+        self._check(self.lib.tw_check(self.h, _stream_ptr(stream)))
+
+    # ----------------------------------------------------------- setup
+    def set_block_column(self, which, row0, col, stream=None):
+        import torch
+        nrows = col.shape[1]
+        p = _dev(col, torch.float64, (self.Nt, nrows, self.Nm), "col")
+        self._check(self.lib.tw_set_block_column(self.h, which, row0, nrows, p, _stream_ptr(stream)))
+
+    def set_prior(self, nu=1.0, ell=0.1, var=1.0):
+        self._check(self.lib.tw_set_prior(self.h, nu, ell, var))
+
+    # ---------------------------------------------------------- applies
+    def p2o_apply(self, which, prec, x, out=None, stream=None):
+        import torch
+        x = x if x.dim() == 3 else x.unsqueeze(0)
+        nrhs = x.shape[0]
+        px = _dev(x, torch.float64, (nrhs, self.Nt, self.Nm), "x")
+        if out is None:
+            out = torch.empty((nrhs, self.Nt, self.rows(which)), dtype=torch.float64, device=x.device)
+        po = _dev(out, torch.float64, (nrhs, self.Nt, self.rows(which)), "out")
+        self._check(self.lib.tw_p2o_apply(self.h, which, prec, nrhs, px, po, _stream_ptr(stream)))
+        return out
+
+    def p2o_adjoint(self, which, prec, y, out=None, stream=None):
+        import torch
+        y = y if y.dim() == 3 else y.unsqueeze(0)
+        nrhs = y.shape[0]
+        py = _dev(y, torch.float64, (nrhs, self.Nt, self.rows(which)), "y")
+        if out is None:
+            out = torch.empty((nrhs, self.Nt, self.Nm), dtype=torch.float64, device=y.device)
+        po = _dev(out, torch.float64, (nrhs, self.Nt, self.Nm), "out")
+        self._check(self.lib.tw_p2o_adjoint(self.h, which, prec, nrhs, py, po, _stream_ptr(stream)))
+        return out
+
+    def prior_apply(self, x, power=1.0, out=None, stream=None):
+        import torch
+        x = x if x.dim() == 3 else x.unsqueeze(0)
+        nrhs = x.shape[0]
+        px = _dev(x, torch.float64, (nrhs, self.Nt, self.Nm), "x")
+        if out is None:
+            out = torch.empty_like(x)
+        po = _dev(out, torch.float64, (nrhs, self.Nt, self.Nm), "out")
+        self._check(self.lib.tw_prior_apply(self.h, power, nrhs, px, po, _stream_ptr(stream)))
+        return out
