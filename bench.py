@@ -1,0 +1,430 @@
+#!/usr/bin/env python
+"""Benchmark of the online phase: posterior mean + forecast on one GB300.
+
+Workload (the 100-sensor case): Nd = 100 sensors, Nm = 200 x 250 = 50,000
+grid points, Nt = 400 steps, Nq = 20 forecast points; one data vector (the
+oracle-made event-0 data of tests/golden/event_c2.npy).  One step is
+
+    m = Gamma_pr F^T K^{-1} d      (tw_infer: two triangular solves, time FFT,
+                                    per-frequency GEMV^H, inverse FFT, prior)
+    q = F_q m                      (tw_forecast: time FFT, GEMV, inverse FFT)
+
+on the FP64-class path (double-float arithmetic, 16-byte operator entries).
+The same step on the mixed path (complex64 operator, FP32 factor + FP64
+refinement) is reported beside it with its error against the FP64 path.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle
+instead (bounded samples of the same step, extrapolated to a full step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "online infer+forecast ms & F/F* HBM GB/s, mixed vs FP64 at ≤1e-5 rel err"
+WORKLOAD = ("Nd=100 sensors, Nm=200x250=50,000 grid points, Nt=400 steps, Nq=20 forecast points, "
+            "one data vector, full observation window")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--small", action="store_true",
+                   help="profiling case: same shapes with Nt=40 (operator 3.3 GB)")
+    p.add_argument("--no-mixed", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback (6.8 TB/s, no MEASURED_PEAKS.json)"
+
+
+def committed_traffic(kernel_file, summary):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_2504_16344_gb300", "csrc", kernel_file), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha256") != sha:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.idx = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.idx)], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = [l.strip().split(",") for l in open(self.file.name) if l.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def rel(a, b):
+    import torch
+    return float(torch.linalg.norm((a - b).double()) / torch.linalg.norm(b.double()))
+
+
+# --------------------------------------------------------------- CPU oracle
+def oracle_sample(cfg, seed=7):
+    """Time the CPU oracle's online step on bounded samples and extrapolate.
+
+    F^T y and F_q m by the direct time-domain sums on a subset of grid
+    points (scaled by Nm / subset), the prior on a subset of time steps
+    (scaled by Nt / subset), and the two triangular solves on an n_s x n_s
+    lower-triangular stand-in factor (scaled by (n / n_s)^2).
+    Returns (extrapolated ms, description, seconds spent).
+    """
+    import numpy as np
+
+    import synth
+    from oracle import posterior as Q
+    from oracle import prior as P
+    from oracle import toeplitz as T
+
+    g = synth.rng(seed)
+    ncols = min(cfg.Nm, 4000)
+    cols = np.sort(g.choice(cfg.Nm, size=ncols, replace=False))
+    nts = min(cfg.Nt, 40)
+    n = cfg.n
+    ns = min(n, 8000)
+    Fsub = synth.block_column(cfg, "F", cols=cols)
+    Fqsub = synth.block_column(cfg, "Fq", cols=cols)
+    y = g.standard_normal((cfg.Nt, cfg.Nd))
+    msub = g.standard_normal((cfg.Nt, ncols))
+    x = g.standard_normal((nts, cfg.Nm))
+    lam = P.spectrum_for(cfg)
+    Ls = np.tril(g.standard_normal((ns, ns)) * (0.1 / np.sqrt(ns))) + 2.0 * np.eye(ns)
+    b = g.standard_normal(ns)
+    t0 = time.perf_counter()
+    T.p2o_adjoint(Fsub, y)
+    t1 = time.perf_counter()
+    P.prior_apply(x, lam)
+    t2 = time.perf_counter()
+    T.p2o_apply(Fqsub, msub)
+    t3 = time.perf_counter()
+    Q.solve_K(Ls, b)
+    t4 = time.perf_counter()
+    ms = 1e3 * ((t1 - t0) * cfg.Nm / ncols + (t2 - t1) * cfg.Nt / nts
+                + (t3 - t2) * cfg.Nm / ncols + (t4 - t3) * (n / ns) ** 2)
+    desc = (f"oracle direct-sum F^T and F_q on {ncols} of {cfg.Nm} grid points (x{cfg.Nm / ncols:.1f}), "
+            f"prior on {nts} of {cfg.Nt} steps (x{cfg.Nt / nts:.0f}), two triangular solves of a "
+            f"{ns}x{ns} factor (x{(n / ns) ** 2:.0f}); extrapolated to one full step")
+    return ms, desc, t4 - t0
+
+
+def run_reference(args):
+    import synth
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return 0
+    cfg = synth.CONFIGS[2]
+    for _ in range(args.warmup):
+        oracle_sample(cfg)
+    vals = []
+    for _ in range(args.steps):
+        ms, desc, _ = oracle_sample(cfg)
+        vals.append(ms)
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+def setup_context(cfg, dev, keep, sigma):
+    import torch
+
+    import synth
+    from paper_2504_16344_gb300 import build, tw
+    build.build()
+    ctx = tw.Context(cfg.Nd, cfg.Nq, cfg.Nx, cfg.Ny, cfg.Nt, cfg.Lx, cfg.Ly, keep=keep,
+                     device=dev.index)
+    for which, name, rows in ((tw.MAP_F, "F", cfg.Nd), (tw.MAP_FQ, "Fq", cfg.Nq)):
+        for r0 in range(0, rows, 10):
+            nr = min(10, rows - r0)
+            col = synth.block_column_torch(cfg, name, dev, r0, nr)
+            ctx.set_block_column(which, r0, col)
+            del col
+    ctx.set_prior(cfg.nu, cfg.ell, cfg.var)
+    torch.cuda.synchronize(dev)
+    if sigma is None:
+        # profiling case: noise level from the GPU's own apply (inputs only)
+        z = torch.from_numpy(synth.event_z(cfg)).to(dev)
+        m_true = ctx.prior_apply(z, 0.5)
+        dcl = ctx.p2o_apply(tw.MAP_F, tw.PREC_FP64, m_true)
+        sigma = 0.01 * float(torch.sqrt(torch.mean(dcl ** 2)))
+        d = dcl[0] + sigma * torch.from_numpy(synth.noise_z(cfg)).to(dev)
+        d = d.cpu().numpy()
+    else:
+        d = None
+    t0 = time.time()
+    ctx.factor_K(sigma ** 2)
+    return ctx, sigma, d, time.time() - t0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2504_16344_gb300 import tw
+
+    rank, world, local = rank_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if args.small:
+        cfg = synth.small_config(Nd=100, Nx=200, Ny=250, Nt=40, Nq=20, cid=2)
+        sigma, d_np = None, None
+    else:
+        cfg = synth.CONFIGS[2]
+        sigma = json.load(open(os.path.join(ROOT, "tests", "golden", "sigma_c2.json")))["sigma"]
+        d_np = np.load(os.path.join(ROOT, "tests", "golden", "event_c2.npy"))
+    keep = tw.KEEP_FP64 | (0 if args.no_mixed else tw.KEEP_C64)
+    t_setup = time.time()
+    ctx, sigma, d_gen, t_factor = setup_context(cfg, dev, keep, sigma)
+    if d_np is None:
+        d_np = d_gen
+    t_setup = time.time() - t_setup
+    d = torch.from_numpy(d_np).to(dev).unsqueeze(0).contiguous()
+    m = torch.empty((1, cfg.Nt, cfg.Nm), dtype=torch.float64, device=dev)
+    q = torch.empty((1, cfg.Nt, cfg.Nq), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(prec):
+        ctx.infer(prec, d, out=m)
+        ctx.forecast(prec, m, out=q)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(prec, steps, profile=False):
+        for _ in range(args.warmup):
+            step(prec)
+        ctx.check()
+        if profile:
+            ctx.profile_read(reset=True)
+            ctx.profile(True)
+        l0 = tw.kernel_launches()
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step(prec)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        launches = tw.kernel_launches() - l0
+        ms = e0.elapsed_time(e1) / steps
+        phases = None
+        if profile:
+            ctx.profile(False)
+            phases = ctx.profile_read(reset=True)
+        ctx.check()
+        return ms, launches, phases
+
+    dev_index = dev.index
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        dev_index = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    sampler = ClockSampler(dev_index)
+    sampler.start()
+    ms64, launches, phases = timed(tw.PREC_FP64, args.steps, profile=True)
+    clocks = sampler.stop()
+    m64, q64 = m.clone(), q.clone()
+    if world > 1:
+        t = torch.tensor([ms64], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms64 = float(t.item())
+
+    # roofline of the dominant kernel: the per-frequency GEMV^H streaming F^
+    Nf = cfg.Nt + 1
+    adj_ms, adj_calls = phases["gemv_adj"]
+    bytes_adj = 16.0 * Nf * (cfg.Nd * cfg.Nm + cfg.Nd + cfg.Nm)
+    ach = bytes_adj / (adj_ms / adj_calls * 1e-3) / 1e9
+    peak, peak_src = measured_peaks()
+    traffic = committed_traffic("gemv.cu", "gemv_adj_dd_c2.txt")
+    roofline = {"bound": "hbm", "kernel": "k_gemv_adj_dd", "achieved": round(ach, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                "traffic": traffic, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": bytes_adj,
+                "avg_launch_ms": adj_ms / adj_calls}
+    # the forward GEMV (forecast, F_q) for the F/F* GB/s pair
+    fwd_ms, fwd_calls = phases["gemv_fwd"]
+    bytes_fwd = 16.0 * Nf * (cfg.Nq * cfg.Nm + cfg.Nq + cfg.Nm)
+    phase_ms = {k: round(v[0] / max(1, args.steps), 4) for k, v in phases.items() if v[1]}
+
+    mixed = None
+    if not args.no_mixed:
+        ctx.set_refinement(3)
+        ms32, _, ph32 = timed(tw.PREC_C64, args.steps, profile=True)
+        mixed = {"prec": "complex64 operator + FP32 factor + 3 FP64-residual refinement steps",
+                 "ms_per_step": round(ms32, 4), "speedup_vs_fp64": round(ms64 / ms32, 3),
+                 "m_rel_err_vs_fp64": rel(m, m64), "q_rel_err_vs_fp64": rel(q, q64),
+                 "phases_ms": {k: round(v[0] / max(1, args.steps), 4) for k, v in ph32.items() if v[1]}}
+
+    e2e = None
+    if not args.no_e2e:
+        dh = torch.from_numpy(d_np).unsqueeze(0).contiguous().pin_memory()
+        mh = torch.empty(m.shape, dtype=torch.float64).pin_memory()
+        qh = torch.empty(q.shape, dtype=torch.float64).pin_memory()
+
+        def step_e2e():
+            d.copy_(dh, non_blocking=True)
+            ctx.infer(tw.PREC_FP64, d, out=m)
+            ctx.forecast(tw.PREC_FP64, m, out=q)
+            mh.copy_(m, non_blocking=True)
+            qh.copy_(q, non_blocking=True)
+
+        for _ in range(args.warmup):
+            step_e2e()
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_e2e()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        wall = (time.perf_counter() - t0) * 1e3 / args.steps
+        barrier()
+        e2e = {"value": round(e0.elapsed_time(e1) / args.steps, 4), "unit": "ms",
+               "h2d_bytes_per_step": int(dh.numel() * 8),
+               "d2h_bytes_per_step": int((mh.numel() + qh.numel()) * 8),
+               "host_wall_ms": round(wall, 4), "path": "tw_infer + tw_forecast through libtw.so"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu and world == 1:
+        v, desc, spent = oracle_sample(cfg)
+        cpu = {"value": round(v, 2), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": desc, "cpu_seconds": round(spent, 2)}
+
+    value = ms64 / world if world > 1 else ms64
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms64, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "df64 (FP32 pairs, 48-bit significand; FP64-class)", "data": "synthetic",
+        "config": {"workload": WORKLOAD if not args.small else WORKLOAD.replace("Nt=400", "Nt=40"),
+                   "l2": "inputs larger than L2: the 32 GB operator F^ is streamed every step",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "setup_s": round(t_setup, 1), "factor_K_s": round(t_factor, 1)},
+        "roofline": roofline,
+        "gemv_fwd_Fq_gbs": round(bytes_fwd / (fwd_ms / fwd_calls * 1e-3) / 1e9, 1),
+        "phases_ms": phase_ms,
+        "mixed": mixed,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -139,6 +139,88 @@ tw_status tw_p2o_adjoint(tw_ctx *ctx, tw_map which, tw_prec prec, int nrhs,
 tw_status tw_prior_apply(tw_ctx *ctx, double power, int nrhs, const double *x,
                          double *y, void *stream);
 
+/*
+ * tw_factor_K -- form and factor the data-space Hessian of Phase 2,
+ *   K = Gamma_n + F Gamma_pr F^T,  Gamma_n = noise_var * I,
+ * (Sec. "Real-time Bayesian inference and prediction framework": the
+ * Sherman-Morrison-Woodbury rewrite moves the inverse to data space).  K is
+ * (Nd*Nt) x (Nd*Nt), time-major (index t*Nd + sensor).  It is formed from the
+ * time-domain block column as K_(i,j) = noise_var delta_ij I +
+ * sum_{s<=min(i,j)} F_{i-s} C F_{j-s}^T (a product G G^T with
+ * G = Phi C^{1/2}, then prefix sums along block diagonals), then Cholesky-
+ * factored: in double-float if TW_KEEP_FP64 was kept, and in FP32 (plus a
+ * packed FP64 copy of K for refinement residuals) if TW_KEEP_C64 or
+ * TW_KEEP_BF16X2 was kept.  Needs tw_set_prior and the FP64 operator of F.
+ * Set-up call: allocates, synchronises `stream`, and returns TW_ERR_NOT_SPD
+ * (pivot row in tw_last_error) if K is not numerically positive definite.
+ */
+tw_status tw_factor_K(tw_ctx *ctx, double noise_var, void *stream);
+
+/* Statistics of the last right-hand side of tw_infer (optional output). */
+typedef struct {
+  int ir_iters;      /* refinement steps taken (mixed path; 0 for FP64)   */
+  double resid_rel;  /* |d' - K' y| / |d'| with the FP64 K, or -1 if no   */
+                     /* packed FP64 K is held (FP64-only contexts)        */
+} tw_infer_stats;
+
+/*
+ * tw_infer -- posterior mean (MAP point) of Phase 4 with m_prior = 0:
+ *   m = Gamma_pr F'^T (Gamma_n + F' Gamma_pr F'^T)^{-1} d'
+ * for each right-hand side r, where the observation window Nt' =
+ * nt_window[r] (host array, NULL = Nt for all) keeps the leading Nt' time
+ * blocks of the data: d' = d[r][0..Nt'-1][.], F' = the leading Nt' block
+ * rows of F, and K' = K[:Nd Nt', :Nd Nt'] (Cholesky factors nest, so the
+ * one factor serves every window).  Rows t >= Nt' of m are 0 (the prior
+ * mean; data before Nt' do not inform them).
+ * d: device [nrhs][Nt][Nd] FP64 (rows >= Nt' ignored); m: device
+ * [nrhs][Nt][Nm] FP64.  prec TW_PREC_FP64 uses the double-float factor and
+ * operator; TW_PREC_C64 / TW_PREC_BF16X2 solve with the FP32 factor, apply
+ * `refinement steps` of iterative refinement with the FP64 residual
+ * r = d' - K' y (df64 arithmetic), and use the FP32 operator for F'^T.
+ * stats may be NULL; when given, the call synchronises `stream` once.
+ */
+tw_status tw_infer(tw_ctx *ctx, tw_prec prec, int nrhs, const int *nt_window, const double *d,
+                   double *m, tw_infer_stats *stats, void *stream);
+
+/*
+ * tw_forecast -- QoI forecast q = F_q m (Phase 4, q_map = F_q m_map):
+ * m [nrhs][Nt][Nm] -> q [nrhs][Nt][Nq], the Toeplitz apply of the p2q map.
+ */
+tw_status tw_forecast(tw_ctx *ctx, tw_prec prec, int nrhs, const double *m, double *q,
+                      void *stream);
+
+/* Number of iterative-refinement steps of the mixed-precision tw_infer
+ * (default 3, range 0..50). */
+tw_status tw_set_refinement(tw_ctx *ctx, int steps);
+
+/* Phases of the online calls, for per-phase device timing. */
+typedef enum {
+  TW_PH_TRSV_FWD = 0,   /* L z = d (forward substitution, persistent kernel)  */
+  TW_PH_TRSV_BWD,       /* L^T y = z                                           */
+  TW_PH_RESIDUAL,       /* r = d - K x (refinement residual, FP64 K)           */
+  TW_PH_RFFT_DATA,      /* time FFT of a data-space vector (Nd or Nq series)   */
+  TW_PH_GEMV_ADJ,       /* x^(w) = F^(w)^H y^(w), all frequencies              */
+  TW_PH_IRFFT_PARAM,    /* inverse time FFT of a parameter vector (Nm series)  */
+  TW_PH_PRIOR,          /* Matern filter (three passes)                        */
+  TW_PH_RFFT_PARAM,     /* time FFT of a parameter vector                      */
+  TW_PH_GEMV_FWD,       /* y^(w) = F^(w) x^(w) incl. the chunk reduction       */
+  TW_PH_IRFFT_DATA,     /* inverse time FFT of a data-space vector             */
+  TW_PH_COUNT
+} tw_phase;
+
+/* Record CUDA events around every phase of later calls (on the stream the
+ * phase is launched on).  Off by default; costs two event records a phase. */
+tw_status tw_profile_enable(tw_ctx *ctx, int on);
+
+/* Synchronise on the recorded events and return, per phase, the summed
+ * device time in ms and the number of timed launches since the last reset
+ * (host arrays of TW_PH_COUNT entries; either may be NULL).  reset != 0
+ * clears the totals. */
+tw_status tw_profile_read(tw_ctx *ctx, double *ms, long long *calls, int reset);
+
+/* Number of CUDA kernels this library has enqueued in this process. */
+long long tw_kernel_launches(void);
+
 /* Synchronise `stream` and report errors recorded by kernels (TW_OK,
  * TW_ERR_NOT_SPD, TW_ERR_TIMEOUT, TW_ERR_CUDA).  Clears the record. */
 tw_status tw_check(tw_ctx *ctx, void *stream);

@@ -32,12 +32,43 @@ struct tw_ctx {
   tw::dd *wt = nullptr;     // [Nt][Nm]
   tw::cdd *ws = nullptr;    // [ceil(Nt/2)][Nm]
   int *d_err = nullptr;     // device error record: [0] code, [1] info
+  // data-space Hessian K = sigma^2 I + F Gamma_pr F^T and its factors
+  int n = 0, n_pad = 0, NB = 0;
+  double sigma2 = 0.0, shift32 = 0.0;
+  bool have64 = false, have32 = false;
+  tw::dd *Lp64 = nullptr, *inv64 = nullptr, *Kp64 = nullptr;   // packed 64x64 blocks
+  float *Lp32 = nullptr, *inv32 = nullptr;
+  // solve workspaces
+  tw::dd *vz = nullptr, *vy = nullptr, *vr = nullptr;          // [n_pad]
+  float *fz = nullptr, *fy = nullptr;                          // [n_pad]
+  int *counter = nullptr, *flagsF = nullptr, *flagsB = nullptr, *abort_flag = nullptr;
+  double *d_norm = nullptr;
+  int epoch = 0;
+  int ir_steps = 3;
+  // per-phase timing
+  struct PhaseEv { int ph; cudaEvent_t a, b; };
+  bool prof = false;
+  std::vector<PhaseEv> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[TW_PH_COUNT] = {0};
+  long long prof_calls[TW_PH_COUNT] = {0};
   size_t bytes = 0;
   std::string err;
   std::vector<void *> allocs;
+  std::vector<size_t> alloc_sizes;
 };
 
 namespace twh {
+
+// Times one phase with two events on `s` when profiling is on (RAII).
+struct Phase {
+  tw_ctx *c;
+  int ph;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  Phase(tw_ctx *c_, int ph_, cudaStream_t s_);
+  ~Phase();
+};
 
 tw_status fail(tw_ctx *c, tw_status st, const std::string &msg);
 tw_status cuda_fail(tw_ctx *c, cudaError_t e, const char *where);

@@ -1,0 +1,630 @@
+// dense.cu -- the data-space Hessian K: formation, Cholesky, triangular solves.
+//
+// Phase 2 of the paper forms K = Gamma_n + F Gamma_pr F* and Cholesky-factors
+// it; Phase 4 solves K y = d online (Sec. "Real-time Bayesian inference and
+// prediction framework").  Here K is formed from the time-domain block
+// column without unit-vector applies: with Phi the (Nd Nt) x Nm matrix whose
+// row block u is F_u and G = Phi C^{1/2},
+//   P = G G^T,  K_(i,j) = sigma^2 delta_ij I + sum_{s<=min(i,j)} P_(i-s, j-s),
+// i.e. a symmetric rank-Nm product followed by prefix sums along the Nd x Nd
+// block diagonals (time-major ordering, as in the paper's data vectors).
+//
+// All matrices use 64 x 64 tiles.  K is held in full (lower triangle used)
+// with leading dimension n_pad = 64 * ceil(n/64); the padding has an
+// identity diagonal so every tile is full.  The factor is then packed as
+// lower-triangular 64 x 64 blocks (block (I,J) at I(I+1)/2 + J), contiguous
+// for streaming, plus explicit inverses of the diagonal blocks.
+//
+// Triangular solves run as one persistent launch: CTAs take block rows in
+// order from an atomic ticket, stream their off-diagonal blocks while
+// waiting for the blocks they depend on (a flag per block row, released
+// after the block's result is stored), and finish with the inverted
+// diagonal block.  A CTA only waits on rows with earlier tickets, which are
+// held by CTAs already running, so the launch cannot deadlock; every wait is
+// bounded in time and reports TW_ERR_TIMEOUT instead of hanging.
+#include "../../include/tw.h"
+#include "dense.cuh"
+#include "dense_api.h"
+#include "kernels.h"
+
+namespace tw {
+
+namespace {
+
+template <class T> __device__ __forceinline__ T ldT(const T *p) { return *p; }
+
+__device__ __forceinline__ void record_error(int *err, int code, int info) {
+  if (atomicCAS(err, 0, code) == 0) atomicExch(err + 1, info);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <class T> __device__ __forceinline__ T ld_cg(const T *p);
+template <> __device__ __forceinline__ dd ld_cg<dd>(const dd *p) {
+  float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+  dd r; r.hi = v.x; r.lo = v.y; return r;
+}
+template <> __device__ __forceinline__ float ld_cg<float>(const float *p) { return __ldcg(p); }
+
+// -------------------------------------------------------------- GEMM NT
+// C[tile (I,J)] = (subtract ? C - S : S),  S = sum_k A[i][k] B[j][k]
+// A rows >= arows and B rows >= brows are zero.  lower: skip J > I.
+template <class T>
+__global__ void __launch_bounds__(256)
+k_gemm_nt(const T *__restrict__ A, long lda, int arows, const T *__restrict__ B, long ldb,
+          int brows, int kdim, T *__restrict__ C, long ldc, int lower, int subtract) {
+  typedef DS<T> S;
+  constexpr int KC = 16;
+  __shared__ T As[KC][NB_ + 4];
+  __shared__ T Bs[KC][NB_ + 4];
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (lower && J > I) return;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  typename S::acc acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = S::zero();
+  const int lr = tid >> 2, lk = (tid & 3) * 4;   // loader: row, first k
+  const long arow = (long)I * NB_ + lr, brow = (long)J * NB_ + lr;
+  for (int k0 = 0; k0 < kdim; k0 += KC) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = k0 + lk + q;
+      As[lk + q][lr] = (arow < arows && k < kdim) ? A[arow * lda + k] : S::zerov();
+      Bs[lk + q][lr] = (brow < brows && k < kdim) ? B[brow * ldb + k] : S::zerov();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty * 4 + u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx * 4 + v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) S::mac(acc[u][v], a[u], b[v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const long i = (long)I * NB_ + ty * 4 + u;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const long j = (long)J * NB_ + tx * 4 + v;
+      T s = S::get(acc[u][v]);
+      C[i * ldc + j] = subtract ? S::sub(C[i * ldc + j], s) : s;
+    }
+  }
+}
+
+// ------------------------------------------- K from P: block-diagonal prefix
+// K[(t+delta)Nd + a][t Nd + b] += K[(t+delta-1)Nd + a][(t-1)Nd + b], t = 1..Nt-1-delta
+__global__ void k_prefix_diag(dd *__restrict__ K, long ldk, int Nd, int Nt) {
+  const long per = (long)Nd * Nd;
+  const long total = (long)Nt * per;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int delta = (int)(idx / per);
+    const int a = (int)((idx % per) / Nd), b = (int)(idx % Nd);
+    if (delta == 0 && b > a) continue;
+    dd run = ldT(K + ((long)delta * Nd + a) * ldk + b);   // t = 0 term
+    for (int t = 1; t + delta < Nt; ++t) {
+      dd *p = K + ((long)(t + delta) * Nd + a) * ldk + (long)t * Nd + b;
+      run = dd_add(run, *p);
+      *p = run;
+    }
+  }
+}
+
+// diagonal: += sigma^2 inside, 1 on the padding
+__global__ void k_diag_set(dd *__restrict__ K, long ldk, int n, int n_pad, dd s2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_pad) return;
+  dd *p = K + (long)i * ldk + i;
+  if (i < n) *p = dd_add(*p, s2);
+  else { p->hi = 1.f; p->lo = 0.f; }
+}
+
+// ----------------------------------------------- Cholesky: diagonal block
+// Factors the 64x64 diagonal block J in place (lower) and writes the inverse
+// of the factor block to inv ([64][64], upper part zero).
+template <class T>
+__global__ void __launch_bounds__(256)
+k_potrf_diag(T *__restrict__ K, long ldk, int J, T *__restrict__ inv, int *err) {
+  typedef DS<T> S;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T(*sA)[NB_ + 1] = reinterpret_cast<T(*)[NB_ + 1]>(smem_raw);
+  T(*sX)[NB_ + 1] = sA + NB_;
+  __shared__ T sInv[NB_];
+  const int tid = threadIdx.x;
+  T *Ablk = K + (long)J * NB_ * ldk + (long)J * NB_;
+  for (int idx = tid; idx < NB_ * NB_; idx += blockDim.x) {
+    const int r = idx / NB_, c = idx % NB_;
+    sA[r][c] = (c <= r) ? Ablk[(long)r * ldk + c] : S::zerov();
+  }
+  __syncthreads();
+  for (int c = 0; c < NB_; ++c) {
+    if (tid == 0) {
+      T piv = sA[c][c];
+      if (!(S::lead(piv) > 0.f)) {   // not positive definite (or NaN)
+        record_error(err, TW_ERR_NOT_SPD, J * NB_ + c);
+        piv = S::one();
+      }
+      const T d = S::sqrtv(piv);
+      sA[c][c] = d;
+      sInv[c] = S::div(S::one(), d);
+    }
+    __syncthreads();
+    for (int r = c + 1 + tid; r < NB_; r += blockDim.x) sA[r][c] = S::mul(sA[r][c], sInv[c]);
+    __syncthreads();
+    const int m = NB_ - 1 - c;
+    const int ntri = m * (m + 1) / 2;
+    for (int idx = tid; idx < ntri; idx += blockDim.x) {
+      int rr = (int)((sqrtf(8.f * idx + 1.f) - 1.f) * 0.5f);
+      while (rr * (rr + 1) / 2 > idx) --rr;
+      while ((rr + 1) * (rr + 2) / 2 <= idx) ++rr;
+      const int kk = idx - rr * (rr + 1) / 2;
+      const int r = c + 1 + rr, k = c + 1 + kk;
+      typename S::acc a = S::zero();
+      S::mac(a, S::neg(sA[r][c]), sA[k][c]);
+      sA[r][k] = S::add(sA[r][k], S::get(a));
+    }
+    __syncthreads();
+  }
+  // write the factor block back (lower part)
+  for (int idx = tid; idx < NB_ * NB_; idx += blockDim.x) {
+    const int r = idx / NB_, c = idx % NB_;
+    if (c <= r) Ablk[(long)r * ldk + c] = sA[r][c];
+  }
+  // inverse by forward substitution, one column per thread: L X = I
+  if (tid < NB_) {
+    const int j = tid;
+    for (int r = 0; r < j; ++r) sX[r][j] = S::zerov();
+    sX[j][j] = sInv[j];
+    for (int r = j + 1; r < NB_; ++r) {
+      typename S::acc a = S::zero();
+      for (int k = j; k < r; ++k) S::mac(a, sA[r][k], sX[k][j]);
+      sX[r][j] = S::neg(S::mul(S::get(a), sInv[r]));
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < NB_ * NB_; idx += blockDim.x) {
+    const int r = idx / NB_, c = idx % NB_;
+    inv[idx] = sX[r][c];
+  }
+}
+
+// ---------------------------------------- Cholesky: panel (substitution)
+// rows of block I = J+1+blockIdx.x: X L_JJ^T = A_IJ  (one row per thread)
+template <class T>
+__global__ void __launch_bounds__(64)
+k_trsm_panel(T *__restrict__ K, long ldk, int J) {
+  typedef DS<T> S;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T(*sL)[NB_ + 1] = reinterpret_cast<T(*)[NB_ + 1]>(smem_raw);
+  T(*sX)[NB_ + 1] = sL + NB_;
+  __shared__ T sInv[NB_];
+  const int tid = threadIdx.x;
+  const int I = J + 1 + blockIdx.x;
+  const T *Lblk = K + (long)J * NB_ * ldk + (long)J * NB_;
+  T *Ablk = K + (long)I * NB_ * ldk + (long)J * NB_;
+  for (int idx = tid; idx < NB_ * NB_; idx += blockDim.x) {
+    const int r = idx / NB_, c = idx % NB_;
+    sL[r][c] = (c <= r) ? Lblk[(long)r * ldk + c] : S::zerov();
+    sX[r][c] = Ablk[(long)r * ldk + c];
+  }
+  __syncthreads();
+  sInv[tid] = S::div(S::one(), sL[tid][tid]);
+  __syncthreads();
+  const int r = tid;
+  for (int c = 0; c < NB_; ++c) {
+    typename S::acc a = S::zero();
+    for (int k = 0; k < c; ++k) S::mac(a, sX[r][k], sL[c][k]);
+    sX[r][c] = S::mul(S::sub(sX[r][c], S::get(a)), sInv[c]);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < NB_ * NB_; idx += blockDim.x) {
+    const int rr = idx / NB_, c = idx % NB_;
+    Ablk[(long)rr * ldk + c] = sX[rr][c];
+  }
+}
+
+// ---------------------------------------------------------- packing
+template <class T>
+__global__ void k_pack(const T *__restrict__ K, long ldk, T *__restrict__ P, int NB) {
+  const size_t nblk = (size_t)NB * (NB + 1) / 2;
+  for (size_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    int I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((size_t)I * (I + 1) / 2 > b) --I;
+    while ((size_t)(I + 1) * (I + 2) / 2 <= b) ++I;
+    const int J = (int)(b - (size_t)I * (I + 1) / 2);
+    const T *src = K + (long)I * NB_ * ldk + (long)J * NB_;
+    T *dst = P + b * NB_ * NB_;
+    for (int idx = threadIdx.x; idx < NB_ * NB_; idx += blockDim.x) {
+      const int r = idx / NB_, c = idx % NB_;
+      dst[idx] = (I == J && c > r) ? DS<T>::zerov() : src[(long)r * ldk + c];
+    }
+  }
+}
+
+// full dd matrix (lower tiles) -> float
+__global__ void k_lower_to_float(const dd *__restrict__ K, float *__restrict__ K32, long ld, int NB) {
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (J > I) return;
+  for (int idx = threadIdx.x; idx < NB_ * NB_; idx += blockDim.x) {
+    const int r = idx / NB_, c = idx % NB_;
+    const long o = ((long)I * NB_ + r) * ld + (long)J * NB_ + c;
+    const dd v = K[o];
+    K32[o] = __fadd_rn(v.hi, v.lo);
+  }
+}
+
+// ------------------------------------------------------ triangular solves
+// FWD: L z = b (b from `rhs`, rows >= nrows zero);  BWD: L^T x = z.
+// Lp: packed blocks; Linv: [NB][64][64] inverses of the diagonal blocks.
+template <class T> __device__ __forceinline__ T ld_rhs(const void *rhs, int kind, long i);
+template <> __device__ __forceinline__ dd ld_rhs<dd>(const void *rhs, int kind, long i) {
+  if (kind == 0) return dd_from_double(reinterpret_cast<const double *>(rhs)[i]);
+  if (kind == 1) return ld_cg(reinterpret_cast<const dd *>(rhs) + i);
+  dd r; r.hi = __ldcg(reinterpret_cast<const float *>(rhs) + i); r.lo = 0.f; return r;
+}
+template <> __device__ __forceinline__ float ld_rhs<float>(const void *rhs, int kind, long i) {
+  if (kind == 0) return __double2float_rn(reinterpret_cast<const double *>(rhs)[i]);
+  if (kind == 1) { dd v = ld_cg(reinterpret_cast<const dd *>(rhs) + i); return __fadd_rn(v.hi, v.lo); }
+  return __ldcg(reinterpret_cast<const float *>(rhs) + i);
+}
+
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s
+
+template <class T, bool FWD>
+__global__ void __launch_bounds__(256)
+k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restrict__ rhs,
+       int rhs_kind, T *__restrict__ out, int nrows, int NBw, int *counter, int *flags,
+       int epoch, int *err, int *abort_flag) {
+  typedef DS<T> S;
+  __shared__ T sv[NB_];
+  __shared__ typename S::acc sred[4][NB_];
+  __shared__ int sI, sbail;
+  const int tid = threadIdx.x;
+  // FWD mapping: row r, column quarter q (adjacent lanes share r)
+  // BWD mapping: column c, row quarter q (q = warp pair)
+  const int r_f = tid >> 2, q_f = tid & 3;
+  const int c_b = tid & 63, q_b = tid >> 6;
+  for (;;) {
+    if (tid == 0) { sI = atomicAdd(counter, 1); sbail = 0; }
+    __syncthreads();
+    const int ticket = sI;
+    if (ticket >= NBw) return;
+    const int I = FWD ? ticket : NBw - 1 - ticket;
+    typename S::acc acc = S::zero();
+    const int ndep = FWD ? I : NBw - 1 - I;
+    for (int d = 0; d < ndep; ++d) {
+      const int J = FWD ? d : NBw - 1 - d;
+      // stream this thread's 16 entries of the off-diagonal block first
+      T lv[16];
+      if (FWD) {
+        const T *blk = Lp + packed_index(I, J) * NB_ * NB_ + r_f * NB_ + q_f * 16;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) lv[u] = blk[u];
+      } else {
+        const T *blk = Lp + packed_index(J, I) * NB_ * NB_ + (q_b * 16) * NB_ + c_b;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) lv[u] = blk[u * NB_];
+      }
+      if (tid == 0) {
+        const unsigned long long t0 = global_ns();
+        while (ld_acquire(flags + J) != epoch) {
+          if (*(volatile int *)abort_flag) { sbail = 1; break; }
+          if (global_ns() - t0 > WAIT_LIMIT_NS) {
+            record_error(err, TW_ERR_TIMEOUT, FWD ? 1 : 2);
+            atomicExch(abort_flag, 1);
+            sbail = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __syncthreads();
+      if (sbail) return;
+      if (tid < NB_) sv[tid] = ld_cg(out + (long)J * NB_ + tid);
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 16; ++u) S::mac(acc, lv[u], sv[(FWD ? q_f : q_b) * 16 + u]);
+      __syncthreads();
+    }
+    // combine the four partial sums of each row (FWD) / column (BWD)
+    if (FWD) {
+      T s = S::get(acc);
+      s = S::add(s, S::shfl_xor(s, 1));
+      s = S::add(s, S::shfl_xor(s, 2));
+      if (q_f == 0) {
+        const long gi = (long)I * NB_ + r_f;
+        const T b = (gi < nrows) ? ld_rhs<T>(rhs, rhs_kind, gi) : S::zerov();
+        sv[r_f] = (gi < nrows) ? S::sub(b, s) : S::zerov();
+      }
+    } else {
+      sred[q_b][c_b] = acc;
+      __syncthreads();
+      if (tid < NB_) {
+        T s = S::get(sred[0][tid]);
+        for (int q = 1; q < 4; ++q) s = S::add(s, S::get(sred[q][tid]));
+        const long gi = (long)I * NB_ + tid;
+        const T b = (gi < nrows) ? ld_rhs<T>(rhs, rhs_kind, gi) : S::zerov();
+        sv[tid] = (gi < nrows) ? S::sub(b, s) : S::zerov();
+      }
+    }
+    __syncthreads();
+    // diagonal block: out_I = Linv v (FWD) or Linv^T v (BWD)
+    const T *iv = Linv + (size_t)I * NB_ * NB_;
+    typename S::acc a2 = S::zero();
+    if (FWD) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) S::mac(a2, iv[r_f * NB_ + q_f * 16 + u], sv[q_f * 16 + u]);
+      T s = S::get(a2);
+      s = S::add(s, S::shfl_xor(s, 1));
+      s = S::add(s, S::shfl_xor(s, 2));
+      if (q_f == 0) {
+        const long gi = (long)I * NB_ + r_f;
+        out[gi] = (gi < nrows) ? s : S::zerov();
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) S::mac(a2, iv[(q_b * 16 + u) * NB_ + c_b], sv[q_b * 16 + u]);
+      __syncthreads();
+      sred[q_b][c_b] = a2;
+      __syncthreads();
+      if (tid < NB_) {
+        T s = S::get(sred[0][tid]);
+        for (int q = 1; q < 4; ++q) s = S::add(s, S::get(sred[q][tid]));
+        const long gi = (long)I * NB_ + tid;
+        out[gi] = (gi < nrows) ? s : S::zerov();
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release(flags + I, epoch);
+  }
+}
+
+// ------------------------------------------- symmetric K x from packed lower
+// y = rhs - K x over the leading nrows (dd); one CTA per block row.
+__global__ void __launch_bounds__(256)
+k_residual(const dd *__restrict__ Kp, const dd *__restrict__ x, const double *__restrict__ d,
+           dd *__restrict__ r, int nrows, int NBw) {
+  __shared__ dd sx[NB_];
+  __shared__ dacc sred[4][NB_];
+  const int I = blockIdx.x, tid = threadIdx.x;
+  const int r_f = tid >> 2, q_f = tid & 3;     // normal blocks (J <= I)
+  const int c_b = tid & 63, q_b = tid >> 6;    // transposed blocks (J > I)
+  dacc accN = dacc_zero(), accT = dacc_zero();
+  for (int J = 0; J < NBw; ++J) {
+    __syncthreads();
+    if (tid < NB_) {
+      const long gj = (long)J * NB_ + tid;
+      sx[tid] = (gj < nrows) ? x[gj] : dd_zero();
+    }
+    __syncthreads();
+    if (J <= I) {
+      const dd *blk = Kp + packed_index(I, J) * NB_ * NB_ + r_f * NB_ + q_f * 16;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int c = q_f * 16 + u;
+        // diagonal block: the stored upper part is zero, use the lower entry instead
+        dd kv = (I == J && c > r_f) ? Kp[packed_index(I, J) * NB_ * NB_ + c * NB_ + r_f] : blk[u];
+        dacc_mac(accN, kv, sx[c]);
+      }
+    } else {
+      const dd *blk = Kp + packed_index(J, I) * NB_ * NB_ + (q_b * 16) * NB_ + c_b;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) dacc_mac(accT, blk[u * NB_], sx[q_b * 16 + u]);
+    }
+  }
+  // combine
+  dd s = dacc_get(accN);
+  s = dd_add(s, DS<dd>::shfl_xor(s, 1));
+  s = dd_add(s, DS<dd>::shfl_xor(s, 2));
+  __syncthreads();
+  sred[q_b][c_b] = accT;
+  __syncthreads();
+  __shared__ dd sN[NB_];
+  if (q_f == 0) sN[r_f] = s;
+  __syncthreads();
+  if (tid < NB_) {
+    dd t = dacc_get(sred[0][tid]);
+    for (int q = 1; q < 4; ++q) t = dd_add(t, dacc_get(sred[q][tid]));
+    t = dd_add(t, sN[tid]);
+    const long gi = (long)I * NB_ + tid;
+    r[gi] = (gi < nrows) ? dd_sub(dd_from_double(d[gi]), t) : dd_zero();
+  }
+}
+
+// x += delta (float) ; rows < nrows
+__global__ void k_axpy_dd_f(dd *__restrict__ x, const float *__restrict__ delta, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) { dd d; d.hi = delta[i]; d.lo = 0.f; x[i] = dd_add(x[i], d); }
+}
+// dd -> float copy
+__global__ void k_dd_to_f(const dd *__restrict__ a, float *__restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __fadd_rn(a[i].hi, a[i].lo);
+}
+// float -> dd copy
+__global__ void k_f_to_dd(const float *__restrict__ a, dd *__restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) { b[i].hi = a[i]; b[i].lo = 0.f; }
+}
+// sum of squares (double) of dd (kind 1) or double (kind 0) vector, atomically added
+__global__ void k_sumsq(const void *__restrict__ v, int kind, int n, double *out) {
+  double s = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double x;
+    if (kind == 0) x = reinterpret_cast<const double *>(v)[i];
+    else { const dd t = reinterpret_cast<const dd *>(v)[i]; x = (double)t.hi + (double)t.lo; }
+    s += x * x;
+  }
+  for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+template <class KER> void smem_attr(KER k, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+// ======================================================================= host
+cudaError_t launch_form_P(const dd *G, long ldg, int n, int kdim, dd *K, long ldk, int NB,
+                          cudaStream_t s) {
+  k_gemm_nt<dd><<<dim3(NB, NB), 256, 0, s>>>(G, ldg, n, G, ldg, n, kdim, K, ldk, 1, 0);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_K_from_P(dd *K, long ldk, int Nd, int Nt, int n, int n_pad, double sigma2,
+                            cudaStream_t s) {
+  const long total = (long)Nt * Nd * Nd;
+  long blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_prefix_diag<<<(unsigned)blocks, 256, 0, s>>>(K, ldk, Nd, Nt);
+  count_launches(1);
+  dd s2;
+  s2.hi = (float)sigma2;
+  s2.lo = (float)(sigma2 - (double)s2.hi);
+  k_diag_set<<<(n_pad + 255) / 256, 256, 0, s>>>(K, ldk, n, n_pad, s2);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t cholesky_t(T *K, long ldk, int NB, T *inv, int *err, cudaStream_t s) {
+  const size_t sm_potrf = 2 * NB_ * (NB_ + 1) * sizeof(T);
+  const size_t sm_trsm = 2 * NB_ * (NB_ + 1) * sizeof(T);
+  smem_attr(k_potrf_diag<T>, sm_potrf);
+  smem_attr(k_trsm_panel<T>, sm_trsm);
+  for (int J = 0; J < NB; ++J) {
+    T *diag = K + (long)J * NB_ * ldk + (long)J * NB_;
+    k_potrf_diag<T><<<1, 256, sm_potrf, s>>>(K, ldk, J, inv + (size_t)J * NB_ * NB_, err);
+    count_launches(1);
+    const int nt = NB - J - 1;
+    if (nt > 0) {
+      k_trsm_panel<T><<<nt, 64, sm_trsm, s>>>(K, ldk, J);
+      count_launches(1);
+      const T *panel = diag + (long)NB_ * ldk;               // rows (J+1)*64.., cols J*64..
+      T *trail = diag + (long)NB_ * ldk + NB_;
+      k_gemm_nt<T><<<dim3(nt, nt), 256, 0, s>>>(panel, ldk, nt * NB_, panel, ldk, nt * NB_, NB_,
+                                                trail, ldk, 1, 1);
+      count_launches(1);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_cholesky_dd(dd *K, long ldk, int NB, dd *inv, int *err, cudaStream_t s) {
+  return cholesky_t<dd>(K, ldk, NB, inv, err, s);
+}
+cudaError_t launch_cholesky_f(float *K, long ldk, int NB, float *inv, int *err, cudaStream_t s) {
+  return cholesky_t<float>(K, ldk, NB, inv, err, s);
+}
+
+cudaError_t launch_pack_dd(const dd *K, long ldk, dd *P, int NB, cudaStream_t s) {
+  k_pack<dd><<<152 * 8, 256, 0, s>>>(K, ldk, P, NB);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_pack_f(const float *K, long ldk, float *P, int NB, cudaStream_t s) {
+  k_pack<float><<<152 * 8, 256, 0, s>>>(K, ldk, P, NB);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_lower_to_float(const dd *K, float *K32, long ld, int NB, cudaStream_t s) {
+  k_lower_to_float<<<dim3(NB, NB), 256, 0, s>>>(K, K32, ld, NB);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+static int trsv_grid(int NBw) { return NBw < 152 * 4 ? NBw : 152 * 4; }
+
+cudaError_t launch_trsv_dd(const dd *Lp, const dd *Linv, const void *rhs, int rhs_kind, dd *out,
+                           int nrows, int NBw, int *counter, int *flags, int epoch, bool fwd,
+                           int *err, int *abort_flag, cudaStream_t s) {
+  if (NBw <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  if (fwd)
+    k_trsv<dd, true><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
+                                                     counter, flags, epoch, err, abort_flag);
+  else
+    k_trsv<dd, false><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
+                                                      counter, flags, epoch, err, abort_flag);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const void *rhs, int rhs_kind,
+                          float *out, int nrows, int NBw, int *counter, int *flags, int epoch,
+                          bool fwd, int *err, int *abort_flag, cudaStream_t s) {
+  if (NBw <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  if (fwd)
+    k_trsv<float, true><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
+                                                        counter, flags, epoch, err, abort_flag);
+  else
+    k_trsv<float, false><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
+                                                         counter, flags, epoch, err, abort_flag);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const dd *Kp, const dd *x, const double *d, dd *r, int nrows, int NBw,
+                            cudaStream_t s) {
+  if (NBw <= 0) return cudaSuccess;
+  k_residual<<<NBw, 256, 0, s>>>(Kp, x, d, r, nrows, NBw);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_axpy_dd_f(dd *x, const float *delta, int n, cudaStream_t s) {
+  k_axpy_dd_f<<<(n + 255) / 256, 256, 0, s>>>(x, delta, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_dd_to_f(const dd *a, float *b, int n, cudaStream_t s) {
+  k_dd_to_f<<<(n + 255) / 256, 256, 0, s>>>(a, b, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_f_to_dd(const float *a, dd *b, int n, cudaStream_t s) {
+  k_f_to_dd<<<(n + 255) / 256, 256, 0, s>>>(a, b, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_sumsq(const void *v, int kind, int n, double *out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  int blocks = (n + 255) / 256;
+  if (blocks > 152 * 4) blocks = 152 * 4;
+  if (blocks < 1) blocks = 1;
+  k_sumsq<<<blocks, 256, 0, s>>>(v, kind, n, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace tw

@@ -1,0 +1,36 @@
+// dense_api.h -- host launchers of dense.cu (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dense.cuh"
+
+namespace tw {
+
+// P = G G^T (lower 64x64 tiles) into K; G: [n][kdim] dd, row stride ldg
+cudaError_t launch_form_P(const dd *G, long ldg, int n, int kdim, dd *K, long ldk, int NB,
+                          cudaStream_t s);
+// K = sigma2 I + block-diagonal prefix sums of P (in place), identity padding
+cudaError_t launch_K_from_P(dd *K, long ldk, int Nd, int Nt, int n, int n_pad, double sigma2,
+                            cudaStream_t s);
+// blocked Cholesky in place (lower), inverses of the diagonal blocks to inv
+cudaError_t launch_cholesky_dd(dd *K, long ldk, int NB, dd *inv, int *err, cudaStream_t s);
+cudaError_t launch_cholesky_f(float *K, long ldk, int NB, float *inv, int *err, cudaStream_t s);
+cudaError_t launch_pack_dd(const dd *K, long ldk, dd *P, int NB, cudaStream_t s);
+cudaError_t launch_pack_f(const float *K, long ldk, float *P, int NB, cudaStream_t s);
+cudaError_t launch_lower_to_float(const dd *K, float *K32, long ld, int NB, cudaStream_t s);
+// triangular solves (fwd: L z = b; bwd: L^T x = z), rhs kind 0 double / 1 dd / 2 float
+cudaError_t launch_trsv_dd(const dd *Lp, const dd *Linv, const void *rhs, int rhs_kind, dd *out,
+                           int nrows, int NBw, int *counter, int *flags, int epoch, bool fwd,
+                           int *err, int *abort_flag, cudaStream_t s);
+cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const void *rhs, int rhs_kind,
+                          float *out, int nrows, int NBw, int *counter, int *flags, int epoch,
+                          bool fwd, int *err, int *abort_flag, cudaStream_t s);
+// r = d - K x (packed lower K, df64)
+cudaError_t launch_residual(const dd *Kp, const dd *x, const double *d, dd *r, int nrows, int NBw,
+                            cudaStream_t s);
+cudaError_t launch_axpy_dd_f(dd *x, const float *delta, int n, cudaStream_t s);
+cudaError_t launch_dd_to_f(const dd *a, float *b, int n, cudaStream_t s);
+cudaError_t launch_f_to_dd(const float *a, dd *b, int n, cudaStream_t s);
+cudaError_t launch_sumsq(const void *v, int kind, int n, double *out, cudaStream_t s);
+
+}  // namespace tw

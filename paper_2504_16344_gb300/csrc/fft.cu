@@ -238,6 +238,7 @@ cudaError_t rfft_time(const void *in, int in_kind, long in_ld, int n_in, typenam
   const long grid = (N + B - 1) / B;
   k_rfft_time<P><<<(unsigned)grid, 256, sm, s>>>(in, in_kind, in_ld, n_in, out, out_ld, N, pl,
                                                   twM, twL, B);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -252,6 +253,7 @@ cudaError_t irfft_time(const typename P::cx *in, long in_ld, void *out, int out_
   const long grid = (N + B - 1) / B;
   k_irfft_time<P><<<(unsigned)grid, 256, sm, s>>>(in, in_ld, out, out_kind, out_ld, N, n_keep,
                                                    pl, twM, twL, invM, B);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -274,8 +276,11 @@ cudaError_t prior(const void *x, int in_kind, void *y, int out_kind, int nt, int
   ensure_smem(k_prior_cols<P>, smc);
   dim3 gr((Nx + BR - 1) / BR, np), gc((Ny + BC - 1) / BC, np);
   k_prior_rows<P, false><<<gr, 256, smr, s>>>(x, in_kind, nullptr, 0, work, nt, Nx, Ny, ply, twy, BR);
+  count_launches(1);
   k_prior_cols<P><<<gc, 256, smc, s>>>(work, lam, Nx, Ny, plx, twx, BC);
+  count_launches(1);
   k_prior_rows<P, true><<<gr, 256, smr, s>>>(nullptr, 0, y, out_kind, work, nt, Nx, Ny, ply, twy, BR);
+  count_launches(1);
   return cudaGetLastError();
 }
 

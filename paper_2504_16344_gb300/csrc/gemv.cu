@@ -288,8 +288,10 @@ cudaError_t launch_gemv_fwd_dd(const void *A, int fmt, const cdd *xh, cdd *part,
   const int nchunk = gemv_fwd_nchunk(Nm);
   k_gemv_fwd_dd<<<dim3(nchunk, Nf), 256, 0, s>>>(reinterpret_cast<const float4 *>(A), xh, part,
                                                   Nr, Nm, nchunk);
+  count_launches(1);
   const long n = (long)Nf * Nr;
   k_gemv_reduce_dd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, yh, Nf, Nr, nchunk);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -302,8 +304,10 @@ cudaError_t launch_gemv_fwd_f(const void *A, int fmt, const cf *xh, cf *part, cf
     k_gemv_fwd_f<FMT_BF16X2><<<dim3(nchunk, Nf), 256, 0, s>>>(A, xh, part, Nr, Nm, nchunk);
   else
     return cudaErrorInvalidValue;
+  count_launches(1);
   const long n = (long)Nf * Nr;
   k_gemv_reduce_f<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, yh, Nf, Nr, nchunk);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -315,6 +319,7 @@ cudaError_t launch_gemv_adj_dd(const void *A, int fmt, const cdd *yh, cdd *xh, i
     cudaFuncSetAttribute(k_gemv_adj_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 g((Nm + 256 * ADJ_KPT - 1) / (256 * ADJ_KPT), Nf);
   k_gemv_adj_dd<<<g, 256, sm, s>>>(reinterpret_cast<const float4 *>(A), yh, xh, Nr, Nm);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -326,10 +331,12 @@ cudaError_t launch_gemv_adj_f(const void *A, int fmt, const cf *yh, cf *xh, int 
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(k_gemv_adj_f<FMT_C64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_gemv_adj_f<FMT_C64><<<g, 256, sm, s>>>(A, yh, xh, Nr, Nm);
+    count_launches(1);
   } else if (fmt == FMT_BF16X2) {
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(k_gemv_adj_f<FMT_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_gemv_adj_f<FMT_BF16X2><<<g, 256, sm, s>>>(A, yh, xh, Nr, Nm);
+    count_launches(1);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -342,6 +349,7 @@ cudaError_t launch_convert_op(const cdd *src, long src_ld_w, void *dst, int fmt,
   long blocks = (total + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   k_convert_op<<<(unsigned)blocks, 256, 0, s>>>(src, src_ld_w, dst, fmt, dst_ld_w, n_per_w, Nf);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -8,6 +8,10 @@
 
 namespace tw {
 
+// process-wide count of kernels this library has enqueued
+void count_launches(int k);
+long long launches_total();
+
 // ---- operator storage formats
 enum OpFmt { FMT_DD = 0, FMT_C64 = 1, FMT_BF16X2 = 2 };
 

@@ -4,12 +4,45 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "ctx.h"
 
 using namespace tw;
 
+namespace tw {
+static std::atomic<long long> g_launches{0};
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace tw
+
 namespace twh {
+
+static cudaEvent_t get_event(tw_ctx *c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+Phase::Phase(tw_ctx *c_, int ph_, cudaStream_t s_) : c(c_), ph(ph_), s(s_) {
+  if (c && c->prof) {
+    a = get_event(c);
+    cudaEventRecord(a, s);
+  }
+}
+
+Phase::~Phase() {
+  if (a) {
+    cudaEvent_t b = get_event(c);
+    cudaEventRecord(b, s);
+    c->prof_pending.push_back({ph, a, b});
+  }
+}
 
 tw_status fail(tw_ctx *c, tw_status st, const std::string &msg) {
   if (c) c->err = msg;
@@ -29,6 +62,7 @@ void *dalloc(tw_ctx *c, size_t bytes) {
     return nullptr;
   }
   c->allocs.push_back(p);
+  c->alloc_sizes.push_back(bytes);
   c->bytes += bytes;
   return p;
 }
@@ -36,7 +70,12 @@ void *dalloc(tw_ctx *c, size_t bytes) {
 void dfree(tw_ctx *c, void *p) {
   if (!p) return;
   auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
-  if (it != c->allocs.end()) c->allocs.erase(it);
+  if (it != c->allocs.end()) {
+    const size_t i = it - c->allocs.begin();
+    c->bytes -= c->alloc_sizes[i];
+    c->alloc_sizes.erase(c->alloc_sizes.begin() + i);
+    c->allocs.erase(it);
+  }
   cudaFree(p);
 }
 
@@ -162,6 +201,8 @@ tw_status tw_create(tw_ctx **out, int Nd, int Nq, int Nx, int Ny, int Nt, double
 void tw_destroy(tw_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->dev);
+  for (auto &pe : c->prof_pending) { cudaEventDestroy(pe.a); cudaEventDestroy(pe.b); }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void *p : c->allocs) cudaFree(p);
   delete c;
 }
@@ -201,7 +242,6 @@ tw_status tw_set_block_column(tw_ctx *c, tw_map which, int row0, int nrows, cons
   if (tmp) {
     TW_CUDA(c, cudaStreamSynchronize(s));
     twh::dfree(c, tmp);
-    c->bytes -= (size_t)c->Nf * N * sizeof(cdd);
   }
   for (int r = row0; r < row0 + nrows; ++r) c->loaded[which][r] = 1;
   return TW_OK;
@@ -266,14 +306,20 @@ tw_status tw_p2o_apply(tw_ctx *c, tw_map which, tw_prec prec, int nrhs, const do
     const double *xr = x + (size_t)r * Nt * Nm;
     double *outr = out + (size_t)r * Nt * R;
     if (prec == TW_PREC_FP64) {
-      TW_CUDA(c, launch_rfft_time_dd(xr, 0, Nm, Nt, c->wf, Nm, Nm, c->plT, c->twT, c->twL, s));
-      TW_CUDA(c, launch_gemv_fwd_dd(A, FMT_DD, c->wf, c->part, c->wr, Nf, R, Nm, s));
-      TW_CUDA(c, launch_irfft_time_dd(c->wr, R, outr, 0, R, R, Nt, c->plT, c->twT, c->twL, s));
+      { twh::Phase p(c, TW_PH_RFFT_PARAM, s);
+        TW_CUDA(c, launch_rfft_time_dd(xr, 0, Nm, Nt, c->wf, Nm, Nm, c->plT, c->twT, c->twL, s)); }
+      { twh::Phase p(c, TW_PH_GEMV_FWD, s);
+        TW_CUDA(c, launch_gemv_fwd_dd(A, FMT_DD, c->wf, c->part, c->wr, Nf, R, Nm, s)); }
+      { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
+        TW_CUDA(c, launch_irfft_time_dd(c->wr, R, outr, 0, R, R, Nt, c->plT, c->twT, c->twL, s)); }
     } else {
       cf *wf = (cf *)c->wf, *wr = (cf *)c->wr, *part = (cf *)c->part;
-      TW_CUDA(c, launch_rfft_time_f(xr, 0, Nm, Nt, wf, Nm, Nm, c->plT, c->twTf, c->twLf, s));
-      TW_CUDA(c, launch_gemv_fwd_f(A, (int)prec, wf, part, wr, Nf, R, Nm, s));
-      TW_CUDA(c, launch_irfft_time_f(wr, R, outr, 0, R, R, Nt, c->plT, c->twTf, c->twLf, s));
+      { twh::Phase p(c, TW_PH_RFFT_PARAM, s);
+        TW_CUDA(c, launch_rfft_time_f(xr, 0, Nm, Nt, wf, Nm, Nm, c->plT, c->twTf, c->twLf, s)); }
+      { twh::Phase p(c, TW_PH_GEMV_FWD, s);
+        TW_CUDA(c, launch_gemv_fwd_f(A, (int)prec, wf, part, wr, Nf, R, Nm, s)); }
+      { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
+        TW_CUDA(c, launch_irfft_time_f(wr, R, outr, 0, R, R, Nt, c->plT, c->twTf, c->twLf, s)); }
     }
   }
   return TW_OK;
@@ -292,14 +338,20 @@ tw_status tw_p2o_adjoint(tw_ctx *c, tw_map which, tw_prec prec, int nrhs, const 
     const double *yr = y + (size_t)r * Nt * R;
     double *xr = x + (size_t)r * Nt * Nm;
     if (prec == TW_PREC_FP64) {
-      TW_CUDA(c, launch_rfft_time_dd(yr, 0, R, Nt, c->wr, R, R, c->plT, c->twT, c->twL, s));
-      TW_CUDA(c, launch_gemv_adj_dd(A, FMT_DD, c->wr, c->wf, Nf, R, Nm, s));
-      TW_CUDA(c, launch_irfft_time_dd(c->wf, Nm, xr, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s));
+      { twh::Phase p(c, TW_PH_RFFT_DATA, s);
+        TW_CUDA(c, launch_rfft_time_dd(yr, 0, R, Nt, c->wr, R, R, c->plT, c->twT, c->twL, s)); }
+      { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
+        TW_CUDA(c, launch_gemv_adj_dd(A, FMT_DD, c->wr, c->wf, Nf, R, Nm, s)); }
+      { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+        TW_CUDA(c, launch_irfft_time_dd(c->wf, Nm, xr, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s)); }
     } else {
       cf *wf = (cf *)c->wf, *wr = (cf *)c->wr;
-      TW_CUDA(c, launch_rfft_time_f(yr, 0, R, Nt, wr, R, R, c->plT, c->twTf, c->twLf, s));
-      TW_CUDA(c, launch_gemv_adj_f(A, (int)prec, wr, wf, Nf, R, Nm, s));
-      TW_CUDA(c, launch_irfft_time_f(wf, Nm, xr, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s));
+      { twh::Phase p(c, TW_PH_RFFT_DATA, s);
+        TW_CUDA(c, launch_rfft_time_f(yr, 0, R, Nt, wr, R, R, c->plT, c->twTf, c->twLf, s)); }
+      { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
+        TW_CUDA(c, launch_gemv_adj_f(A, (int)prec, wr, wf, Nf, R, Nm, s)); }
+      { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+        TW_CUDA(c, launch_irfft_time_f(wf, Nm, xr, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s)); }
     }
   }
   return TW_OK;
@@ -316,11 +368,41 @@ tw_status tw_prior_apply(tw_ctx *c, double power, int nrhs, const double *x, dou
   const dd *lam = power == 1.0 ? c->lam1 : c->lamh;
   for (int r = 0; r < nrhs; ++r) {
     const size_t off = (size_t)r * c->Nt * c->Nm;
+    twh::Phase p(c, TW_PH_PRIOR, s);
     TW_CUDA(c, launch_prior_dd(x + off, 0, y + off, 0, c->Nt, c->Nx, c->Ny, c->ws, lam, c->plX,
                                c->plY, c->twX, c->twY, s));
   }
   return TW_OK;
 }
+
+tw_status tw_profile_enable(tw_ctx *c, int on) {
+  if (!c) return TW_ERR_ARG;
+  c->prof = on != 0;
+  return TW_OK;
+}
+
+tw_status tw_profile_read(tw_ctx *c, double *ms, long long *calls, int reset) {
+  if (!c) return TW_ERR_ARG;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  for (auto &pe : c->prof_pending) {
+    TW_CUDA(c, cudaEventSynchronize(pe.b));
+    float t = 0.f;
+    TW_CUDA(c, cudaEventElapsedTime(&t, pe.a, pe.b));
+    c->prof_ms[pe.ph] += t;
+    c->prof_calls[pe.ph] += 1;
+    c->ev_pool.push_back(pe.a);
+    c->ev_pool.push_back(pe.b);
+  }
+  c->prof_pending.clear();
+  for (int i = 0; i < TW_PH_COUNT; ++i) {
+    if (ms) ms[i] = c->prof_ms[i];
+    if (calls) calls[i] = c->prof_calls[i];
+    if (reset) { c->prof_ms[i] = 0.0; c->prof_calls[i] = 0; }
+  }
+  return TW_OK;
+}
+
+long long tw_kernel_launches(void) { return tw::launches_total(); }
 
 tw_status tw_check(tw_ctx *c, void *stream) {
   if (!c) return TW_ERR_ARG;
@@ -336,6 +418,7 @@ tw_status tw_check(tw_ctx *c, void *stream) {
     return twh::fail(c, TW_ERR_NOT_SPD, buf);
   }
   if (h[0] == TW_ERR_TIMEOUT) {
+    if (c->abort_flag) TW_CUDA(c, cudaMemset(c->abort_flag, 0, sizeof(int)));
     snprintf(buf, sizeof buf, "a bounded device wait ran out (site %d)", h[1]);
     return twh::fail(c, TW_ERR_TIMEOUT, buf);
   }

@@ -1,0 +1,269 @@
+// tw_solve.cu -- K formation and factorisation, posterior mean, forecast.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "ctx.h"
+#include "dense_api.h"
+
+using namespace tw;
+
+namespace {
+
+tw_status ensure_solve_workspace(tw_ctx *c) {
+  if (c->vz) return TW_OK;
+  const size_t np = c->n_pad;
+  c->vz = (dd *)twh::dalloc(c, np * sizeof(dd));
+  c->vy = (dd *)twh::dalloc(c, np * sizeof(dd));
+  c->vr = (dd *)twh::dalloc(c, np * sizeof(dd));
+  c->fz = (float *)twh::dalloc(c, np * sizeof(float));
+  c->fy = (float *)twh::dalloc(c, np * sizeof(float));
+  c->counter = (int *)twh::dalloc(c, 4 * sizeof(int));
+  c->flagsF = (int *)twh::dalloc(c, (size_t)c->NB * sizeof(int));
+  c->flagsB = (int *)twh::dalloc(c, (size_t)c->NB * sizeof(int));
+  c->abort_flag = (int *)twh::dalloc(c, sizeof(int));
+  c->d_norm = (double *)twh::dalloc(c, 2 * sizeof(double));
+  if (!c->vz || !c->vy || !c->vr || !c->fz || !c->fy || !c->counter || !c->flagsF || !c->flagsB ||
+      !c->abort_flag || !c->d_norm)
+    return twh::fail(c, TW_ERR_OOM, "solve workspace");
+  TW_CUDA(c, cudaMemset(c->vz, 0, np * sizeof(dd)));
+  TW_CUDA(c, cudaMemset(c->vy, 0, np * sizeof(dd)));
+  TW_CUDA(c, cudaMemset(c->flagsF, 0, (size_t)c->NB * sizeof(int)));
+  TW_CUDA(c, cudaMemset(c->flagsB, 0, (size_t)c->NB * sizeof(int)));
+  TW_CUDA(c, cudaMemset(c->abort_flag, 0, sizeof(int)));
+  c->epoch = 0;
+  return TW_OK;
+}
+
+// y = K^{-1} b for the leading nrows with the df64 factor.  b: double (kind 0) or dd (kind 1)
+tw_status solve64(tw_ctx *c, const void *b, int kind, int nrows, dd *y, cudaStream_t s) {
+  const int NBw = (nrows + NB_ - 1) / NB_;
+  const int e = ++c->epoch;
+  { twh::Phase p(c, TW_PH_TRSV_FWD, s);
+    TW_CUDA(c, launch_trsv_dd(c->Lp64, c->inv64, b, kind, c->vz, nrows, NBw, c->counter, c->flagsF,
+                              e, true, c->d_err, c->abort_flag, s)); }
+  twh::Phase p(c, TW_PH_TRSV_BWD, s);
+  TW_CUDA(c, launch_trsv_dd(c->Lp64, c->inv64, c->vz, 1, y, nrows, NBw, c->counter + 1,
+                            c->flagsB, e, false, c->d_err, c->abort_flag, s));
+  return TW_OK;
+}
+
+// float solve with the FP32 factor: y32 = K32^{-1} b
+tw_status solve32(tw_ctx *c, const void *b, int kind, int nrows, float *y, cudaStream_t s) {
+  const int NBw = (nrows + NB_ - 1) / NB_;
+  const int e = ++c->epoch;
+  { twh::Phase p(c, TW_PH_TRSV_FWD, s);
+    TW_CUDA(c, launch_trsv_f(c->Lp32, c->inv32, b, kind, c->fz, nrows, NBw, c->counter, c->flagsF,
+                             e, true, c->d_err, c->abort_flag, s)); }
+  twh::Phase p(c, TW_PH_TRSV_BWD, s);
+  TW_CUDA(c, launch_trsv_f(c->Lp32, c->inv32, c->fz, 2, y, nrows, NBw, c->counter + 1, c->flagsB,
+                           e, false, c->d_err, c->abort_flag, s));
+  return TW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (!(noise_var >= 0.0)) return twh::fail(c, TW_ERR_ARG, "noise variance must be >= 0");
+  if (!c->prior_set) return twh::fail(c, TW_ERR_STATE, "tw_set_prior must come before tw_factor_K");
+  if (!c->op[TW_MAP_F][FMT_DD])
+    return twh::fail(c, TW_ERR_STATE, "tw_factor_K needs the FP64 operator (TW_KEEP_FP64)");
+  for (char l : c->loaded[TW_MAP_F])
+    if (!l) return twh::fail(c, TW_ERR_STATE, "block column of F not fully loaded");
+  cudaStream_t s = (cudaStream_t)stream;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  const int Nd = c->Nd, Nt = c->Nt, Nm = c->Nm;
+  c->n = Nd * Nt;
+  c->NB = (c->n + NB_ - 1) / NB_;
+  c->n_pad = c->NB * NB_;
+  c->sigma2 = noise_var;
+  const long n = c->n, np = c->n_pad;
+  const bool want64 = (c->keep & TW_KEEP_FP64) != 0;
+  const bool want32 = (c->keep & (TW_KEEP_C64 | TW_KEEP_BF16X2)) != 0;
+  tw_status st = ensure_solve_workspace(c);
+  if (st != TW_OK) return st;
+
+  // Phi (time-domain block column, rows u*Nd + s) from F^ by the inverse time FFT
+  dd *G = (dd *)twh::dalloc(c, (size_t)n * Nm * sizeof(dd));
+  if (!G) return twh::fail(c, TW_ERR_OOM, "G = Phi C^{1/2} buffer");
+  const long ld = (long)Nd * Nm;
+  TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->op[TW_MAP_F][FMT_DD], ld, G, 1, ld, (int)ld, Nt,
+                                  c->plT, c->twT, c->twL, s));
+  // G = Phi C^{1/2}: the square-root Matern filter on every row (a spatial field)
+  const int chunk = 2 * ((Nt + 1) / 2);
+  for (long r0 = 0; r0 < n; r0 += chunk) {
+    const int nr = (int)std::min<long>(chunk, n - r0);
+    dd *g = G + r0 * Nm;
+    TW_CUDA(c, launch_prior_dd(g, 1, g, 1, nr, c->Nx, c->Ny, c->ws, c->lamh, c->plX, c->plY,
+                               c->twX, c->twY, s));
+  }
+  // P = G G^T, then K = sigma^2 I + block-diagonal prefix sums of P
+  dd *K = (dd *)twh::dalloc(c, (size_t)np * np * sizeof(dd));
+  if (!K) { twh::dfree(c, G); return twh::fail(c, TW_ERR_OOM, "K buffer"); }
+  TW_CUDA(c, cudaMemsetAsync(K, 0, (size_t)np * np * sizeof(dd), s));
+  TW_CUDA(c, launch_form_P(G, Nm, (int)n, Nm, K, np, c->NB, s));
+  TW_CUDA(c, cudaStreamSynchronize(s));
+  twh::dfree(c, G);
+  TW_CUDA(c, launch_K_from_P(K, np, Nd, Nt, (int)n, (int)np, noise_var, s));
+
+  const size_t nblk = (size_t)c->NB * (c->NB + 1) / 2;
+  const size_t blk = (size_t)NB_ * NB_;
+  // mixed path: FP64 K kept (packed) for the refinement residual; FP32 factor
+  if (want32) {
+    if (!c->Kp64) c->Kp64 = (dd *)twh::dalloc(c, nblk * blk * sizeof(dd));
+    if (!c->Lp32) c->Lp32 = (float *)twh::dalloc(c, nblk * blk * sizeof(float));
+    if (!c->inv32) c->inv32 = (float *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(float));
+    float *K32 = (float *)twh::dalloc(c, (size_t)np * np * sizeof(float));
+    if (!c->Kp64 || !c->Lp32 || !c->inv32 || !K32) {
+      twh::dfree(c, K32);
+      twh::dfree(c, K);
+      return twh::fail(c, TW_ERR_OOM, "mixed-precision factor buffers");
+    }
+    TW_CUDA(c, launch_pack_dd(K, np, c->Kp64, c->NB, s));
+    // FP32 Cholesky; if it meets a non-positive pivot, add a small diagonal shift
+    // (the refinement residual uses the unshifted FP64 K, so the solution is unchanged)
+    c->shift32 = 0.0;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      TW_CUDA(c, cudaMemsetAsync(K32, 0, (size_t)np * np * sizeof(float), s));
+      TW_CUDA(c, launch_lower_to_float(K, K32, np, c->NB, s));
+      if (c->shift32 > 0.0) {
+        // add the shift on the host-visible diagonal through a tiny kernel-free path
+        std::vector<float> diag(np);
+        TW_CUDA(c, cudaStreamSynchronize(s));
+        TW_CUDA(c, cudaMemcpy2D(diag.data(), sizeof(float), K32, (np + 1) * sizeof(float),
+                                sizeof(float), np, cudaMemcpyDeviceToHost));
+        for (long i = 0; i < n; ++i) diag[i] += (float)c->shift32;
+        TW_CUDA(c, cudaMemcpy2D(K32, (np + 1) * sizeof(float), diag.data(), sizeof(float),
+                                sizeof(float), np, cudaMemcpyHostToDevice));
+      }
+      TW_CUDA(c, launch_cholesky_f(K32, np, c->NB, c->inv32, c->d_err, s));
+      tw_status cs = tw_check(c, stream);
+      if (cs == TW_OK) break;
+      if (cs != TW_ERR_NOT_SPD || attempt == 3) { twh::dfree(c, K32); twh::dfree(c, K); return cs; }
+      // shift relative to the largest diagonal entry (read back once)
+      std::vector<dd> dg(np);
+      TW_CUDA(c, cudaMemcpy2D(dg.data(), sizeof(dd), K, (np + 1) * sizeof(dd), sizeof(dd), np,
+                              cudaMemcpyDeviceToHost));
+      double dmax = 0.0;
+      for (long i = 0; i < n; ++i) dmax = std::max(dmax, (double)dg[i].hi);
+      c->shift32 = (c->shift32 == 0.0) ? dmax * 1e-6 : c->shift32 * 10.0;
+    }
+    TW_CUDA(c, launch_pack_f(K32, np, c->Lp32, c->NB, s));
+    TW_CUDA(c, cudaStreamSynchronize(s));
+    twh::dfree(c, K32);
+    c->have32 = true;
+  }
+  if (want64) {
+    if (!c->Lp64) c->Lp64 = (dd *)twh::dalloc(c, nblk * blk * sizeof(dd));
+    if (!c->inv64) c->inv64 = (dd *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(dd));
+    if (!c->Lp64 || !c->inv64) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "factor buffers"); }
+    TW_CUDA(c, launch_cholesky_dd(K, np, c->NB, c->inv64, c->d_err, s));
+    TW_CUDA(c, launch_pack_dd(K, np, c->Lp64, c->NB, s));
+    tw_status cs = tw_check(c, stream);
+    if (cs != TW_OK) { twh::dfree(c, K); return cs; }
+    c->have64 = true;
+  }
+  TW_CUDA(c, cudaStreamSynchronize(s));
+  twh::dfree(c, K);
+  return TW_OK;
+}
+
+tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, const double *d,
+                   double *m, tw_infer_stats *stats, void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (nrhs < 0 || (nrhs > 0 && (!d || !m))) return twh::fail(c, TW_ERR_ARG, "bad rhs");
+  const bool mixed = prec != TW_PREC_FP64;
+  if (prec < 0 || prec > 2 || !c->op[TW_MAP_F][prec])
+    return twh::fail(c, TW_ERR_ARG, "requested precision was not kept at tw_create");
+  if (mixed ? !c->have32 : !c->have64)
+    return twh::fail(c, TW_ERR_STATE, "tw_factor_K must come before tw_infer");
+  cudaStream_t s = (cudaStream_t)stream;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  const int Nd = c->Nd, Nt = c->Nt, Nm = c->Nm, Nf = c->Nf;
+  const void *A = c->op[TW_MAP_F][prec];
+  if (stats) { stats->ir_iters = 0; stats->resid_rel = 0.0; }
+  for (int r = 0; r < nrhs; ++r) {
+    const int w = nt_window ? nt_window[r] : Nt;
+    if (w < 1 || w > Nt) return twh::fail(c, TW_ERR_ARG, "window must be in [1, Nt]");
+    const int nrows = Nd * w;
+    const int NBw = (nrows + NB_ - 1) / NB_;
+    const double *dr = d + (size_t)r * Nt * Nd;
+    double *mr = m + (size_t)r * Nt * Nm;
+    // 1) y = K'^{-1} d'  (leading nrows of K's factor: windows nest)
+    if (!mixed) {
+      tw_status st = solve64(c, dr, 0, nrows, c->vy, s);
+      if (st != TW_OK) return st;
+    } else {
+      // FP32 solve, then refinement with the FP64 residual r = d - K x
+      tw_status st = solve32(c, dr, 0, nrows, c->fy, s);
+      if (st != TW_OK) return st;
+      TW_CUDA(c, launch_f_to_dd(c->fy, c->vy, nrows, s));
+      for (int it = 0; it < c->ir_steps; ++it) {
+        { twh::Phase p(c, TW_PH_RESIDUAL, s);
+          TW_CUDA(c, launch_residual(c->Kp64, c->vy, dr, c->vr, nrows, NBw, s)); }
+        st = solve32(c, c->vr, 1, nrows, c->fy, s);
+        if (st != TW_OK) return st;
+        TW_CUDA(c, launch_axpy_dd_f(c->vy, c->fy, nrows, s));
+      }
+      if (stats) stats->ir_iters = c->ir_steps;
+    }
+    if (stats && r == nrhs - 1) {
+      // relative residual of the last right-hand side: |d - K y| / |d|
+      if (c->Kp64) {
+        TW_CUDA(c, launch_residual(c->Kp64, c->vy, dr, c->vr, nrows, NBw, s));
+        TW_CUDA(c, launch_sumsq(c->vr, 1, nrows, c->d_norm, s));
+        TW_CUDA(c, launch_sumsq(dr, 0, nrows, c->d_norm + 1, s));
+        double h[2];
+        TW_CUDA(c, cudaMemcpyAsync(h, c->d_norm, sizeof(h), cudaMemcpyDeviceToHost, s));
+        TW_CUDA(c, cudaStreamSynchronize(s));
+        stats->resid_rel = h[1] > 0 ? sqrt(h[0] / h[1]) : 0.0;
+      } else {
+        stats->resid_rel = -1.0;
+      }
+    }
+    // 2) x = F'^T y over the window (y rows >= w are zero), 3) m = Gamma_pr x
+    if (!mixed) {
+      { twh::Phase p(c, TW_PH_RFFT_DATA, s);
+        TW_CUDA(c, launch_rfft_time_dd(c->vy, 1, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
+      { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
+        TW_CUDA(c, launch_gemv_adj_dd(A, FMT_DD, c->wr, c->wf, Nf, Nd, Nm, s)); }
+      { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+        TW_CUDA(c, launch_irfft_time_dd(c->wf, Nm, c->wt, 1, Nm, Nm, w, c->plT, c->twT, c->twL, s)); }
+      { twh::Phase p(c, TW_PH_PRIOR, s);
+        TW_CUDA(c, launch_prior_dd(c->wt, 1, mr, 0, w, c->Nx, c->Ny, c->ws, c->lam1, c->plX, c->plY,
+                                   c->twX, c->twY, s)); }
+    } else {
+      cf *wr = (cf *)c->wr, *wf = (cf *)c->wf;
+      float *wt = (float *)c->wt;
+      { twh::Phase p(c, TW_PH_RFFT_DATA, s);
+        TW_CUDA(c, launch_rfft_time_f(c->vy, 1, Nd, w, wr, Nd, Nd, c->plT, c->twTf, c->twLf, s)); }
+      { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
+        TW_CUDA(c, launch_gemv_adj_f(A, (int)prec, wr, wf, Nf, Nd, Nm, s)); }
+      { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+        TW_CUDA(c, launch_irfft_time_f(wf, Nm, wt, 2, Nm, Nm, w, c->plT, c->twTf, c->twLf, s)); }
+      { twh::Phase p(c, TW_PH_PRIOR, s);
+        TW_CUDA(c, launch_prior_f(wt, 2, mr, 0, w, c->Nx, c->Ny, (cf *)c->ws, c->lam1f, c->plX,
+                                  c->plY, c->twXf, c->twYf, s)); }
+    }
+    if (w < Nt)
+      TW_CUDA(c, cudaMemsetAsync(mr + (size_t)w * Nm, 0, (size_t)(Nt - w) * Nm * sizeof(double), s));
+  }
+  return TW_OK;
+}
+
+tw_status tw_forecast(tw_ctx *c, tw_prec prec, int nrhs, const double *m, double *q, void *stream) {
+  return tw_p2o_apply(c, TW_MAP_FQ, prec, nrhs, m, q, stream);
+}
+
+tw_status tw_set_refinement(tw_ctx *c, int steps) {
+  if (!c) return TW_ERR_ARG;
+  if (steps < 0 || steps > 50) return twh::fail(c, TW_ERR_ARG, "refinement steps must be in [0, 50]");
+  c->ir_steps = steps;
+  return TW_OK;
+}
+
+}  // extern "C"

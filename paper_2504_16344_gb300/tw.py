@@ -17,6 +17,9 @@ LIB_PATH = os.path.join(HERE, "lib", "libtw.so")
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_NOT_SPD, ERR_NOT_CONVERGED, ERR_TIMEOUT = range(8)
 STATUS_NAMES = ["TW_OK", "TW_ERR_ARG", "TW_ERR_OOM", "TW_ERR_CUDA", "TW_ERR_STATE",
                 "TW_ERR_NOT_SPD", "TW_ERR_NOT_CONVERGED", "TW_ERR_TIMEOUT"]
+# tw_phase
+PHASES = ["trsv_fwd", "trsv_bwd", "residual", "rfft_data", "gemv_adj", "irfft_param", "prior",
+          "rfft_param", "gemv_fwd", "irfft_data"]
 # tw_map
 MAP_F, MAP_FQ = 0, 1
 # tw_prec
@@ -39,11 +42,22 @@ SIGNATURES = {
     "tw_p2o_apply": (_S, [_P, _I, _I, _I, _P, _P, _P]),
     "tw_p2o_adjoint": (_S, [_P, _I, _I, _I, _P, _P, _P]),
     "tw_prior_apply": (_S, [_P, _D, _I, _P, _P, _P]),
+    "tw_factor_K": (_S, [_P, _D, _P]),
+    "tw_infer": (_S, [_P, _I, _I, _P, _P, _P, _P, _P]),
+    "tw_forecast": (_S, [_P, _I, _I, _P, _P, _P]),
+    "tw_set_refinement": (_S, [_P, _I]),
+    "tw_profile_enable": (_S, [_P, _I]),
+    "tw_profile_read": (_S, [_P, _P, _P, _I]),
+    "tw_kernel_launches": (ctypes.c_longlong, []),
     "tw_check": (_S, [_P, _P]),
     "tw_device_bytes": (ctypes.c_size_t, [_P]),
 }
 
 _lib = None
+
+
+class InferStats(ctypes.Structure):
+    _fields_ = [("ir_iters", ctypes.c_int), ("resid_rel", ctypes.c_double)]
 
 
 class TwError(RuntimeError):
@@ -177,3 +191,58 @@ class Context:
         po = _dev(out, torch.float64, (nrhs, self.Nt, self.Nm), "out")
         self._check(self.lib.tw_prior_apply(self.h, power, nrhs, px, po, _stream_ptr(stream)))
         return out
+
+    # ------------------------------------------------------------ solve
+    def factor_K(self, noise_var, stream=None):
+        self._check(self.lib.tw_factor_K(self.h, float(noise_var), _stream_ptr(stream)))
+
+    def set_refinement(self, steps):
+        self._check(self.lib.tw_set_refinement(self.h, int(steps)))
+
+    def infer(self, prec, d, windows=None, out=None, stats=False, stream=None):
+        """Posterior mean for d [nrhs][Nt][Nd]; windows: per-rhs Nt' (None = Nt)."""
+        import torch
+        d = d if d.dim() == 3 else d.unsqueeze(0)
+        nrhs = d.shape[0]
+        pd = _dev(d, torch.float64, (nrhs, self.Nt, self.Nd), "d")
+        if out is None:
+            out = torch.empty((nrhs, self.Nt, self.Nm), dtype=torch.float64, device=d.device)
+        po = _dev(out, torch.float64, (nrhs, self.Nt, self.Nm), "m")
+        win = None
+        if windows is not None:
+            if len(windows) != nrhs:
+                raise ValueError("one window per right-hand side")
+            win = (ctypes.c_int * nrhs)(*[int(w) for w in windows])
+        st = InferStats() if stats else None
+        self._check(self.lib.tw_infer(self.h, prec, nrhs, win, pd, po,
+                                      ctypes.byref(st) if st is not None else None,
+                                      _stream_ptr(stream)))
+        return (out, st) if stats else out
+
+    def forecast(self, prec, m, out=None, stream=None):
+        import torch
+        m = m if m.dim() == 3 else m.unsqueeze(0)
+        nrhs = m.shape[0]
+        pm = _dev(m, torch.float64, (nrhs, self.Nt, self.Nm), "m")
+        if out is None:
+            out = torch.empty((nrhs, self.Nt, self.Nq), dtype=torch.float64, device=m.device)
+        po = _dev(out, torch.float64, (nrhs, self.Nt, self.Nq), "q")
+        self._check(self.lib.tw_forecast(self.h, prec, nrhs, pm, po, _stream_ptr(stream)))
+        return out
+
+    # -------------------------------------------------------- profiling
+    def profile(self, on=True):
+        self._check(self.lib.tw_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self, reset=True):
+        """{phase: (ms, launches)} of the timed phases since the last reset (synchronises)."""
+        n = len(PHASES)
+        ms = (ctypes.c_double * n)()
+        calls = (ctypes.c_longlong * n)()
+        self._check(self.lib.tw_profile_read(self.h, ms, calls, 1 if reset else 0))
+        return {PHASES[i]: (ms[i], calls[i]) for i in range(n)}
+
+
+def kernel_launches() -> int:
+    """Kernels enqueued by libtw.so in this process."""
+    return int(load().tw_kernel_launches())

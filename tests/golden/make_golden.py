@@ -1,5 +1,9 @@
 """Write tests/golden/sigma_c<N>.json: the noise level of each synthetic workload.
 
+Also writes tests/golden/event_c<N>.npy: the event-0 data
+d = F m_true + sigma z_n ([Nt][Nd] FP64) of each large workload, so GPU
+tests and the benchmark use oracle-made data without a full CPU apply.
+
 Calls only `oracle/` (and the seeded input generator `synth`).  The paper adds
 1% relative noise to its synthetic observations (Sec. "Application to the
 Cascadia subduction zone"); this build reads it as one global level,
@@ -36,9 +40,12 @@ def sigma_for(cid: int) -> dict:
 
     d_clean = T.p2o_apply(block, m_true, Nt=cfg.Nt)
     rms = float(np.sqrt(np.mean(d_clean * d_clean)))
+    sigma = Q.noise_sigma(d_clean, cfg.noise_rel)
+    if cid != 1:
+        np.save(os.path.join(HERE, f"event_c{cid}.npy"), d_clean + sigma * synth.noise_z(cfg, 0))
     return {
         "config": cid,
-        "sigma": Q.noise_sigma(d_clean, cfg.noise_rel),
+        "sigma": sigma,
         "rms_clean": rms,
         "norm_m_true": float(np.linalg.norm(m_true)),
         "recipe": "sigma = 0.01 * rms(F m_true), event 0, m_true = Gamma_pr^{1/2} z; "

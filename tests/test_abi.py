@@ -14,7 +14,7 @@ def declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"\b(tw_[a-z0-9_]+)\s*\(", text):
+        for m in re.finditer(r"\b(tw_[A-Za-z0-9_]+)\s*\(", text):
             names.add(m.group(1))
     return sorted(names)
 

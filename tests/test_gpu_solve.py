@@ -1,0 +1,129 @@
+"""GPU parity of K's factorisation, the posterior mean, windows and the forecast.
+
+The oracle forms K by the block product, factors it with LAPACK and solves;
+the GPU forms K as G G^T plus block-diagonal prefix sums, factors it in
+double-float (FP64 path) or FP32 + FP64-residual refinement (mixed path).
+Tolerances: FP64 path 1e-11 relative L2 on m and q (the oracle's own error
+against an extended-precision refinement is 3e-13 .. 3e-12 on these sizes,
+so 1e-11 leaves room for both); mixed path 1e-5.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import posterior as Q
+from oracle import prior as P
+from oracle import toeplitz as T
+
+from gpu_util import make_context, rel
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SIGMA_C1 = json.load(open(os.path.join(HERE, "golden", "sigma_c1.json")))["sigma"]
+
+CASES = {
+    "c1": synth.CONFIGS[1],
+    # n = 800: 12.5 blocks of 64 -> ragged last block
+    "mid": synth.small_config(Nd=20, Nx=40, Ny=50, Nt=40, Nq=5, cid=84),
+    # n = 2002 (odd Nt, Nd not a divisor of 64)
+    "wide": synth.small_config(Nd=26, Nx=60, Ny=75, Nt=77, Nq=3, cid=85),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    import torch
+    from paper_2504_16344_gb300 import tw
+    cfg = CASES[request.param]
+    F = synth.block_column(cfg, "F")
+    Fq = synth.block_column(cfg, "Fq")
+    lam = P.spectrum_for(cfg)
+    if request.param == "c1":
+        m_true, d, sigma = Q.synthetic_event(F, lam, synth.event_z(cfg), synth.noise_z(cfg), SIGMA_C1)
+    else:
+        m_true, d, sigma = Q.synthetic_event(F, lam, synth.event_z(cfg), synth.noise_z(cfg))
+    K = Q.form_K(F, lam, sigma ** 2)
+    L = Q.cholesky(K)
+    ctx = make_context(cfg, keep=tw.KEEP_FP64 | tw.KEEP_C64 | tw.KEEP_BF16X2)
+    ctx.factor_K(sigma ** 2)
+    yield dict(cfg=cfg, ctx=ctx, F=F, Fq=Fq, lam=lam, d=d, sigma=sigma, K=K, L=L,
+               dev=torch.device("cuda", 0))
+    ctx.close()
+
+
+def _t(a, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def test_posterior_mean_fp64_full_window(case):
+    from paper_2504_16344_gb300 import tw
+    cfg = case["cfg"]
+    m_ref, _ = Q.posterior_mean(case["F"], case["lam"], case["L"], case["d"], cfg.Nt)
+    m, st = case["ctx"].infer(tw.PREC_FP64, _t(case["d"], case["dev"]), stats=True)
+    case["ctx"].check()
+    err = rel(m[0].cpu().numpy(), m_ref)
+    print(f"{cfg.cid}: FP64 m rel err {err:.2e}")
+    assert err < 1e-11
+
+
+@pytest.mark.parametrize("frac", [0.03, 0.25, 0.5, 0.77])
+def test_posterior_mean_fp64_windows(case, frac):
+    from paper_2504_16344_gb300 import tw
+    cfg = case["cfg"]
+    w = max(1, int(round(frac * cfg.Nt)))
+    m_ref, _ = Q.posterior_mean(case["F"], case["lam"], case["L"], case["d"], cfg.Nt, nt_window=w)
+    m = case["ctx"].infer(tw.PREC_FP64, _t(case["d"], case["dev"]), windows=[w])[0].cpu().numpy()
+    case["ctx"].check()
+    assert np.all(m[w:] == 0.0)
+    assert rel(m, m_ref) < 1e-11
+
+
+def test_batched_uneven_windows_equal_single_calls(case):
+    from paper_2504_16344_gb300 import tw
+    cfg = case["cfg"]
+    ws = [cfg.Nt, max(1, cfg.Nt // 3), max(1, cfg.Nt // 2 + 1)]
+    d3 = np.stack([case["d"], case["d"] * 0.5, -case["d"]])
+    mb = case["ctx"].infer(tw.PREC_FP64, _t(d3, case["dev"]), windows=ws).cpu().numpy()
+    for r, w in enumerate(ws):
+        m_ref, _ = Q.posterior_mean(case["F"], case["lam"], case["L"], d3[r], cfg.Nt, nt_window=w)
+        assert rel(mb[r], m_ref) < 1e-11
+
+
+def test_forecast_of_posterior_mean(case):
+    from paper_2504_16344_gb300 import tw
+    cfg, ctx = case["cfg"], case["ctx"]
+    m_ref, _ = Q.posterior_mean(case["F"], case["lam"], case["L"], case["d"], cfg.Nt)
+    q_ref = Q.forecast(case["Fq"], m_ref)
+    m = ctx.infer(tw.PREC_FP64, _t(case["d"], case["dev"]))
+    q = ctx.forecast(tw.PREC_FP64, m)[0].cpu().numpy()
+    ctx.check()
+    assert rel(q, q_ref) < 1e-11
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_posterior_mean_mixed_precision_with_refinement(case, prec):
+    from paper_2504_16344_gb300 import tw
+    cfg, ctx = case["cfg"], case["ctx"]
+    m_ref, _ = Q.posterior_mean(case["F"], case["lam"], case["L"], case["d"], cfg.Nt)
+    q_ref = Q.forecast(case["Fq"], m_ref)
+    m, st = ctx.infer(prec, _t(case["d"], case["dev"]), stats=True)
+    q = ctx.forecast(prec, m)[0].cpu().numpy()
+    ctx.check()
+    em, eq = rel(m[0].cpu().numpy(), m_ref), rel(q, q_ref)
+    print(f"{cfg.cid}: prec {prec} m err {em:.2e} q err {eq:.2e} resid {st.resid_rel:.2e}")
+    assert st.resid_rel < 1e-10
+    tol = 1e-5 if prec == tw.PREC_C64 else 1e-4
+    assert em < tol and eq < tol
+
+
+def test_solve_residual_certificate_fp64(case):
+    # backward-stable solve: |d - K y| small against |K| |y|
+    from paper_2504_16344_gb300 import tw
+    cfg, ctx = case["cfg"], case["ctx"]
+    _, st = ctx.infer(tw.PREC_FP64, _t(case["d"], case["dev"]), stats=True)
+    assert 0.0 <= st.resid_rel < 1e-11
