@@ -190,8 +190,13 @@ tw_status tw_forecast(tw_ctx *ctx, tw_prec prec, int nrhs, const double *m, doub
                       void *stream);
 
 /* Number of iterative-refinement steps of the mixed-precision tw_infer
- * (default 3, range 0..50). */
+ * (range 0..50).  tw_factor_K picks it by refining a probe right-hand side
+ * until the FP64 residual stops falling; this call overrides that choice. */
 tw_status tw_set_refinement(tw_ctx *ctx, int steps);
+
+/* Refinement steps the mixed-precision tw_infer currently takes (-1 if ctx
+ * is NULL). */
+int tw_refinement_steps(const tw_ctx *ctx);
 
 /* Phases of the online calls, for per-phase device timing. */
 typedef enum {

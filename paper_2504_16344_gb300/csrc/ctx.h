@@ -41,10 +41,11 @@ struct tw_ctx {
   // solve workspaces
   tw::dd *vz = nullptr, *vy = nullptr, *vr = nullptr;          // [n_pad]
   float *fz = nullptr, *fy = nullptr;                          // [n_pad]
-  int *counter = nullptr, *flagsF = nullptr, *flagsB = nullptr, *abort_flag = nullptr;
+  int *counter = nullptr;     // [4]: forward (ticket, rows done), backward (ticket, rows done)
+  int *abort_flag = nullptr;
   double *d_norm = nullptr;
-  int epoch = 0;
   int ir_steps = 3;
+  double ir_probe_resid = 0.0;
   // per-phase timing
   struct PhaseEv { int ph; cudaEvent_t a, b; };
   bool prof = false;

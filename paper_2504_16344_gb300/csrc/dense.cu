@@ -74,10 +74,11 @@ k_gemm_nt(const T *__restrict__ A, long lda, int arows, const T *__restrict__ B,
   if (lower && J > I) return;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   typename S::acc acc[4][4];
+  T tot[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = S::zero();
+    for (int v = 0; v < 4; ++v) { acc[u][v] = S::zero(); tot[u][v] = S::zerov(); }
   const int lr = tid >> 2, lk = (tid & 3) * 4;   // loader: row, first k
   const long arow = (long)I * NB_ + lr, brow = (long)J * NB_ + lr;
   for (int k0 = 0; k0 < kdim; k0 += KC) {
@@ -100,6 +101,11 @@ k_gemm_nt(const T *__restrict__ A, long lda, int arows, const T *__restrict__ B,
 #pragma unroll
         for (int v = 0; v < 4; ++v) S::mac(acc[u][v], a[u], b[v]);
     }
+    // fold this chunk's compensated sums into the running totals
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) S::fold(tot[u][v], acc[u][v]);
     __syncthreads();
   }
 #pragma unroll
@@ -108,7 +114,7 @@ k_gemm_nt(const T *__restrict__ A, long lda, int arows, const T *__restrict__ B,
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const long j = (long)J * NB_ + tx * 4 + v;
-      T s = S::get(acc[u][v]);
+      T s = tot[u][v];
       C[i * ldc + j] = subtract ? S::sub(C[i * ldc + j], s) : s;
     }
   }
@@ -200,8 +206,13 @@ k_potrf_diag(T *__restrict__ K, long ldk, int J, T *__restrict__ inv, int *err) 
     sX[j][j] = sInv[j];
     for (int r = j + 1; r < NB_; ++r) {
       typename S::acc a = S::zero();
-      for (int k = j; k < r; ++k) S::mac(a, sA[r][k], sX[k][j]);
-      sX[r][j] = S::neg(S::mul(S::get(a), sInv[r]));
+      T t = S::zerov();
+      for (int k = j; k < r; ++k) {
+        S::mac(a, sA[r][k], sX[k][j]);
+        if (((k - j) & 15) == 15) S::fold(t, a);
+      }
+      S::fold(t, a);
+      sX[r][j] = S::neg(S::mul(t, sInv[r]));
     }
   }
   __syncthreads();
@@ -236,8 +247,13 @@ k_trsm_panel(T *__restrict__ K, long ldk, int J) {
   const int r = tid;
   for (int c = 0; c < NB_; ++c) {
     typename S::acc a = S::zero();
-    for (int k = 0; k < c; ++k) S::mac(a, sX[r][k], sL[c][k]);
-    sX[r][c] = S::mul(S::sub(sX[r][c], S::get(a)), sInv[c]);
+    T t = S::zerov();
+    for (int k = 0; k < c; ++k) {
+      S::mac(a, sX[r][k], sL[c][k]);
+      if ((k & 15) == 15) S::fold(t, a);
+    }
+    S::fold(t, a);
+    sX[r][c] = S::mul(S::sub(sX[r][c], t), sInv[c]);
   }
   __syncthreads();
   for (int idx = tid; idx < NB_ * NB_; idx += blockDim.x) {
@@ -293,65 +309,79 @@ template <> __device__ __forceinline__ float ld_rhs<float>(const void *rhs, int 
 
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s
 
+// Block rows complete strictly in dependency order (row I needs row I-1), so
+// one counter `progress` (rows finished, counted from the start for FWD and
+// from the end for BWD) tells every CTA which results are ready.  A CTA reads
+// it once, consumes every ready block without further synchronisation, and
+// only waits near the diagonal.  prog[0] = ticket, prog[1] = progress.
 template <class T, bool FWD>
 __global__ void __launch_bounds__(256)
 k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restrict__ rhs,
-       int rhs_kind, T *__restrict__ out, int nrows, int NBw, int *counter, int *flags,
-       int epoch, int *err, int *abort_flag) {
+       int rhs_kind, T *__restrict__ out, int nrows, int NBw, int *prog, int *err,
+       int *abort_flag) {
   typedef DS<T> S;
   __shared__ T sv[NB_];
-  __shared__ typename S::acc sred[4][NB_];
-  __shared__ int sI, sbail;
+  __shared__ T sred[4][NB_];
+  __shared__ int sI, sP, sbail;
   const int tid = threadIdx.x;
-  // FWD mapping: row r, column quarter q (adjacent lanes share r)
-  // BWD mapping: column c, row quarter q (q = warp pair)
+  // FWD: row r, column quarter q (the four quarters of a row are adjacent lanes)
+  // BWD: column c, row quarter q (q = pair of warps)
   const int r_f = tid >> 2, q_f = tid & 3;
   const int c_b = tid & 63, q_b = tid >> 6;
+  const int q = FWD ? q_f : q_b;
   for (;;) {
-    if (tid == 0) { sI = atomicAdd(counter, 1); sbail = 0; }
+    if (tid == 0) { sI = atomicAdd(prog, 1); sbail = 0; }
     __syncthreads();
     const int ticket = sI;
     if (ticket >= NBw) return;
     const int I = FWD ? ticket : NBw - 1 - ticket;
-    typename S::acc acc = S::zero();
-    const int ndep = FWD ? I : NBw - 1 - I;
-    for (int d = 0; d < ndep; ++d) {
-      const int J = FWD ? d : NBw - 1 - d;
-      // stream this thread's 16 entries of the off-diagonal block first
-      T lv[16];
-      if (FWD) {
-        const T *blk = Lp + packed_index(I, J) * NB_ * NB_ + r_f * NB_ + q_f * 16;
-#pragma unroll
-        for (int u = 0; u < 16; ++u) lv[u] = blk[u];
-      } else {
-        const T *blk = Lp + packed_index(J, I) * NB_ * NB_ + (q_b * 16) * NB_ + c_b;
-#pragma unroll
-        for (int u = 0; u < 16; ++u) lv[u] = blk[u * NB_];
-      }
+    const int ndep = ticket;                 // blocks this row depends on
+    T tot = S::zerov();
+    int d = 0;
+    while (d < ndep) {
       if (tid == 0) {
-        const unsigned long long t0 = global_ns();
-        while (ld_acquire(flags + J) != epoch) {
-          if (*(volatile int *)abort_flag) { sbail = 1; break; }
-          if (global_ns() - t0 > WAIT_LIMIT_NS) {
-            record_error(err, TW_ERR_TIMEOUT, FWD ? 1 : 2);
-            atomicExch(abort_flag, 1);
-            sbail = 1;
-            break;
+        int p = ld_acquire(prog + 1);
+        if (p <= d) {
+          const unsigned long long t0 = global_ns();
+          while ((p = ld_acquire(prog + 1)) <= d) {
+            if (*(volatile int *)abort_flag) { sbail = 1; break; }
+            if (global_ns() - t0 > WAIT_LIMIT_NS) {
+              record_error(err, TW_ERR_TIMEOUT, FWD ? 1 : 2);
+              atomicExch(abort_flag, 1);
+              sbail = 1;
+              break;
+            }
+            __nanosleep(32);
           }
-          __nanosleep(64);
         }
+        sP = p;
       }
       __syncthreads();
       if (sbail) return;
-      if (tid < NB_) sv[tid] = ld_cg(out + (long)J * NB_ + tid);
-      __syncthreads();
+      const int dend = min(sP, ndep);
+      for (; d < dend; ++d) {
+        const int J = FWD ? d : NBw - 1 - d;
+        const T *zj = out + (long)J * NB_ + q * 16;
+        T lv[16];
+        if (FWD) {
+          const T *blk = Lp + packed_index(I, J) * NB_ * NB_ + r_f * NB_ + q_f * 16;
 #pragma unroll
-      for (int u = 0; u < 16; ++u) S::mac(acc, lv[u], sv[(FWD ? q_f : q_b) * 16 + u]);
-      __syncthreads();
+          for (int u = 0; u < 16; ++u) lv[u] = blk[u];
+        } else {
+          const T *blk = Lp + packed_index(J, I) * NB_ * NB_ + (q_b * 16) * NB_ + c_b;
+#pragma unroll
+          for (int u = 0; u < 16; ++u) lv[u] = blk[u * NB_];
+        }
+        typename S::acc a = S::zero();
+#pragma unroll
+        for (int u = 0; u < 16; ++u) S::mac(a, lv[u], ld_cg(zj + u));
+        S::fold(tot, a);
+      }
+      __syncthreads();   // sP is rewritten next round
     }
-    // combine the four partial sums of each row (FWD) / column (BWD)
+    // sum the four partial sums of each row (FWD) / column (BWD); v = b - sum
     if (FWD) {
-      T s = S::get(acc);
+      T s = tot;
       s = S::add(s, S::shfl_xor(s, 1));
       s = S::add(s, S::shfl_xor(s, 2));
       if (q_f == 0) {
@@ -360,11 +390,10 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restr
         sv[r_f] = (gi < nrows) ? S::sub(b, s) : S::zerov();
       }
     } else {
-      sred[q_b][c_b] = acc;
+      sred[q_b][c_b] = tot;
       __syncthreads();
       if (tid < NB_) {
-        T s = S::get(sred[0][tid]);
-        for (int q = 1; q < 4; ++q) s = S::add(s, S::get(sred[q][tid]));
+        T s = S::add(S::add(sred[0][tid], sred[1][tid]), S::add(sred[2][tid], sred[3][tid]));
         const long gi = (long)I * NB_ + tid;
         const T b = (gi < nrows) ? ld_rhs<T>(rhs, rhs_kind, gi) : S::zerov();
         sv[tid] = (gi < nrows) ? S::sub(b, s) : S::zerov();
@@ -388,67 +417,67 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restr
 #pragma unroll
       for (int u = 0; u < 16; ++u) S::mac(a2, iv[(q_b * 16 + u) * NB_ + c_b], sv[q_b * 16 + u]);
       __syncthreads();
-      sred[q_b][c_b] = a2;
+      sred[q_b][c_b] = S::get(a2);
       __syncthreads();
       if (tid < NB_) {
-        T s = S::get(sred[0][tid]);
-        for (int q = 1; q < 4; ++q) s = S::add(s, S::get(sred[q][tid]));
+        T s = S::add(S::add(sred[0][tid], sred[1][tid]), S::add(sred[2][tid], sred[3][tid]));
         const long gi = (long)I * NB_ + tid;
         out[gi] = (gi < nrows) ? s : S::zerov();
       }
     }
     __threadfence();
     __syncthreads();
-    if (tid == 0) st_release(flags + I, epoch);
+    // rows finish in order, so the counter is `ticket` here; publish ticket + 1
+    if (tid == 0) st_release(prog + 1, ticket + 1);
   }
 }
 
 // ------------------------------------------- symmetric K x from packed lower
-// y = rhs - K x over the leading nrows (dd); one CTA per block row.
+// r = d - K x over the leading nrows (df64); one CTA per block row, no
+// synchronisation inside the sweep: lower blocks (J <= I) row-wise, upper
+// blocks as transposes of the stored (J, I) blocks.
 __global__ void __launch_bounds__(256)
 k_residual(const dd *__restrict__ Kp, const dd *__restrict__ x, const double *__restrict__ d,
            dd *__restrict__ r, int nrows, int NBw) {
-  __shared__ dd sx[NB_];
-  __shared__ dacc sred[4][NB_];
+  __shared__ dd sN[NB_];
+  __shared__ dd sT[4][NB_];
   const int I = blockIdx.x, tid = threadIdx.x;
-  const int r_f = tid >> 2, q_f = tid & 3;     // normal blocks (J <= I)
+  const int r_f = tid >> 2, q_f = tid & 3;     // lower blocks (J <= I)
   const int c_b = tid & 63, q_b = tid >> 6;    // transposed blocks (J > I)
-  dacc accN = dacc_zero(), accT = dacc_zero();
+  dd totN = dd_zero(), totT = dd_zero();
   for (int J = 0; J < NBw; ++J) {
-    __syncthreads();
-    if (tid < NB_) {
-      const long gj = (long)J * NB_ + tid;
-      sx[tid] = (gj < nrows) ? x[gj] : dd_zero();
-    }
-    __syncthreads();
+    dacc a = dacc_zero();
     if (J <= I) {
-      const dd *blk = Kp + packed_index(I, J) * NB_ * NB_ + r_f * NB_ + q_f * 16;
+      const dd *blk = Kp + packed_index(I, J) * NB_ * NB_;
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const int c = q_f * 16 + u;
-        // diagonal block: the stored upper part is zero, use the lower entry instead
-        dd kv = (I == J && c > r_f) ? Kp[packed_index(I, J) * NB_ * NB_ + c * NB_ + r_f] : blk[u];
-        dacc_mac(accN, kv, sx[c]);
+        // diagonal block: the stored upper part is zero, use the lower entry
+        const dd kv = (I == J && c > r_f) ? blk[c * NB_ + r_f] : blk[r_f * NB_ + c];
+        const long gj = (long)J * NB_ + c;
+        dacc_mac(a, kv, (gj < nrows) ? x[gj] : dd_zero());
       }
-    } else {
-      const dd *blk = Kp + packed_index(J, I) * NB_ * NB_ + (q_b * 16) * NB_ + c_b;
+      dacc_fold(totN, a);
+    }
+    if (J > I) {
+      const dd *blk = Kp + packed_index(J, I) * NB_ * NB_ + c_b;
 #pragma unroll
-      for (int u = 0; u < 16; ++u) dacc_mac(accT, blk[u * NB_], sx[q_b * 16 + u]);
+      for (int u = 0; u < 16; ++u) {
+        const int rr = q_b * 16 + u;
+        const long gj = (long)J * NB_ + rr;
+        dacc_mac(a, blk[rr * NB_], (gj < nrows) ? x[gj] : dd_zero());
+      }
+      dacc_fold(totT, a);
     }
   }
-  // combine
-  dd s = dacc_get(accN);
+  dd s = totN;
   s = dd_add(s, DS<dd>::shfl_xor(s, 1));
   s = dd_add(s, DS<dd>::shfl_xor(s, 2));
-  __syncthreads();
-  sred[q_b][c_b] = accT;
-  __syncthreads();
-  __shared__ dd sN[NB_];
   if (q_f == 0) sN[r_f] = s;
+  sT[q_b][c_b] = totT;
   __syncthreads();
   if (tid < NB_) {
-    dd t = dacc_get(sred[0][tid]);
-    for (int q = 1; q < 4; ++q) t = dd_add(t, dacc_get(sred[q][tid]));
+    dd t = dd_add(dd_add(sT[0][tid], sT[1][tid]), dd_add(sT[2][tid], sT[3][tid]));
     t = dd_add(t, sN[tid]);
     const long gi = (long)I * NB_ + tid;
     r[gi] = (gi < nrows) ? dd_sub(dd_from_double(d[gi]), t) : dd_zero();
@@ -564,32 +593,32 @@ cudaError_t launch_lower_to_float(const dd *K, float *K32, long ld, int NB, cuda
 static int trsv_grid(int NBw) { return NBw < 152 * 4 ? NBw : 152 * 4; }
 
 cudaError_t launch_trsv_dd(const dd *Lp, const dd *Linv, const void *rhs, int rhs_kind, dd *out,
-                           int nrows, int NBw, int *counter, int *flags, int epoch, bool fwd,
-                           int *err, int *abort_flag, cudaStream_t s) {
+                           int nrows, int NBw, int *prog, bool fwd, int *err, int *abort_flag,
+                           cudaStream_t s) {
   if (NBw <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(prog, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (fwd)
     k_trsv<dd, true><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
-                                                     counter, flags, epoch, err, abort_flag);
+                                                     prog, err, abort_flag);
   else
     k_trsv<dd, false><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
-                                                      counter, flags, epoch, err, abort_flag);
+                                                      prog, err, abort_flag);
   count_launches(1);
   return cudaGetLastError();
 }
 cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const void *rhs, int rhs_kind,
-                          float *out, int nrows, int NBw, int *counter, int *flags, int epoch,
-                          bool fwd, int *err, int *abort_flag, cudaStream_t s) {
+                          float *out, int nrows, int NBw, int *prog, bool fwd, int *err,
+                          int *abort_flag, cudaStream_t s) {
   if (NBw <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(prog, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (fwd)
     k_trsv<float, true><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
-                                                        counter, flags, epoch, err, abort_flag);
+                                                        prog, err, abort_flag);
   else
     k_trsv<float, false><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
-                                                         counter, flags, epoch, err, abort_flag);
+                                                         prog, err, abort_flag);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -13,6 +13,7 @@ template <> struct DS<dd> {
   static __device__ __forceinline__ acc zero() { return dacc_zero(); }
   static __device__ __forceinline__ void mac(acc &a, dd x, dd y) { dacc_mac(a, x, y); }
   static __device__ __forceinline__ dd get(acc a) { return dacc_get(a); }
+  static __device__ __forceinline__ void fold(dd &tot, acc &a) { dacc_fold(tot, a); }
   static __device__ __forceinline__ dd add(dd a, dd b) { return dd_add(a, b); }
   static __device__ __forceinline__ dd sub(dd a, dd b) { return dd_sub(a, b); }
   static __device__ __forceinline__ dd mul(dd a, dd b) { return dd_mul(a, b); }
@@ -33,6 +34,7 @@ template <> struct DS<float> {
   static __device__ __forceinline__ acc zero() { return 0.f; }
   static __device__ __forceinline__ void mac(acc &a, float x, float y) { a = fmaf(x, y, a); }
   static __device__ __forceinline__ float get(acc a) { return a; }
+  static __device__ __forceinline__ void fold(float &tot, acc &a) { tot += a; a = 0.f; }
   static __device__ __forceinline__ float add(float a, float b) { return a + b; }
   static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
   static __device__ __forceinline__ float mul(float a, float b) { return a * b; }

@@ -19,12 +19,13 @@ cudaError_t launch_pack_dd(const dd *K, long ldk, dd *P, int NB, cudaStream_t s)
 cudaError_t launch_pack_f(const float *K, long ldk, float *P, int NB, cudaStream_t s);
 cudaError_t launch_lower_to_float(const dd *K, float *K32, long ld, int NB, cudaStream_t s);
 // triangular solves (fwd: L z = b; bwd: L^T x = z), rhs kind 0 double / 1 dd / 2 float
+// prog: two ints (ticket, rows finished), zeroed by the launcher
 cudaError_t launch_trsv_dd(const dd *Lp, const dd *Linv, const void *rhs, int rhs_kind, dd *out,
-                           int nrows, int NBw, int *counter, int *flags, int epoch, bool fwd,
-                           int *err, int *abort_flag, cudaStream_t s);
+                           int nrows, int NBw, int *prog, bool fwd, int *err, int *abort_flag,
+                           cudaStream_t s);
 cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const void *rhs, int rhs_kind,
-                          float *out, int nrows, int NBw, int *counter, int *flags, int epoch,
-                          bool fwd, int *err, int *abort_flag, cudaStream_t s);
+                          float *out, int nrows, int NBw, int *prog, bool fwd, int *err,
+                          int *abort_flag, cudaStream_t s);
 // r = d - K x (packed lower K, df64)
 cudaError_t launch_residual(const dd *Kp, const dd *x, const double *d, dd *r, int nrows, int NBw,
                             cudaStream_t s);

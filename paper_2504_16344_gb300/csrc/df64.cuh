@@ -113,6 +113,13 @@ __device__ __forceinline__ void dacc_add(dacc &A, dd a) {
   A.t = __fadd_rn(A.t, __fadd_rn(r, a.lo));
 }
 __device__ __forceinline__ dd dacc_get(dacc A) { return dd_make(A.s, A.t); }
+// The error term t of a lazy accumulator is itself a float, so over k terms
+// it contributes O(k u^2); long sums therefore fold short runs into a
+// renormalised double-float total every few terms.
+__device__ __forceinline__ void dacc_fold(dd &tot, dacc &A) {
+  tot = dd_add(tot, dacc_get(A));
+  A = dacc_zero();
+}
 
 // ------------------------------------------------------ complex df64
 __device__ __forceinline__ cdd cdd_zero() { cdd z; z.re = dd_zero(); z.im = dd_zero(); return z; }

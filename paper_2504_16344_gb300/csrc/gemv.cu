@@ -60,10 +60,12 @@ k_gemv_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ yh, cdd *__r
   __syncthreads();
   const int kb = blockIdx.x * (256 * ADJ_KPT) + threadIdx.x;
   dacc re[ADJ_KPT], im[ADJ_KPT];
+  dd tre[ADJ_KPT], tim[ADJ_KPT];
   bool ok[ADJ_KPT];
 #pragma unroll
   for (int j = 0; j < ADJ_KPT; ++j) {
     re[j] = dacc_zero(); im[j] = dacc_zero();
+    tre[j] = dd_zero(); tim[j] = dd_zero();
     ok[j] = kb + 256 * j < Nm;
   }
   float4 cur[ADJ_KPT], nxt[ADJ_KPT];
@@ -87,15 +89,21 @@ k_gemv_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ yh, cdd *__r
       dacc_mac(im[j], ar, y.im);
       dacc_mac(im[j], dd_neg(ai), y.re);
     }
+    if ((s & 15) == 15) {
+#pragma unroll
+      for (int j = 0; j < ADJ_KPT; ++j) { dacc_fold(tre[j], re[j]); dacc_fold(tim[j], im[j]); }
+    }
 #pragma unroll
     for (int j = 0; j < ADJ_KPT; ++j) cur[j] = nxt[j];
   }
 #pragma unroll
   for (int j = 0; j < ADJ_KPT; ++j) {
     if (!ok[j]) continue;
+    dacc_fold(tre[j], re[j]);
+    dacc_fold(tim[j], im[j]);
     cdd r;
-    r.re = dacc_get(re[j]);
-    r.im = dacc_get(im[j]);
+    r.re = tre[j];
+    r.im = tim[j];
     st_cdd(xh + (size_t)w * Nm + kb + 256 * j, r);
   }
 }
@@ -162,21 +170,25 @@ k_gemv_fwd_dd(const float4 *__restrict__ A, const cdd *__restrict__ xh, cdd *__r
   for (int s = warp; s < Nr; s += 8) {
     const float4 *row = A + ((size_t)w * Nr + s) * Nm + kbase;
     dacc re = dacc_zero(), im = dacc_zero();
-#pragma unroll 8
-    for (int j = 0; j < FWD_JPL; ++j) {
-      const int kk = lane + 32 * j;
-      if (kk < nvalid) {
-        const float4 a = ld_stream4(row + kk);
-        const cdd x = sx[kk];
-        dd ar, ai;
-        ar.hi = a.x; ar.lo = a.y; ai.hi = a.z; ai.lo = a.w;
-        dacc_mac(re, ar, x.re);
-        dacc_mac(re, dd_neg(ai), x.im);
-        dacc_mac(im, ar, x.im);
-        dacc_mac(im, ai, x.re);
+    dd r = dd_zero(), i = dd_zero();
+    for (int j0 = 0; j0 < FWD_JPL; j0 += 8) {
+#pragma unroll
+      for (int j = j0; j < j0 + 8; ++j) {
+        const int kk = lane + 32 * j;
+        if (kk < nvalid) {
+          const float4 a = ld_stream4(row + kk);
+          const cdd x = sx[kk];
+          dd ar, ai;
+          ar.hi = a.x; ar.lo = a.y; ai.hi = a.z; ai.lo = a.w;
+          dacc_mac(re, ar, x.re);
+          dacc_mac(re, dd_neg(ai), x.im);
+          dacc_mac(im, ar, x.im);
+          dacc_mac(im, ai, x.re);
+        }
       }
+      dacc_fold(r, re);
+      dacc_fold(i, im);
     }
-    dd r = dacc_get(re), i = dacc_get(im);
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
       r = dd_add(r, shfl_xor_dd(r, m));

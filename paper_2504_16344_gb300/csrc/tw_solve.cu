@@ -20,45 +20,38 @@ tw_status ensure_solve_workspace(tw_ctx *c) {
   c->fz = (float *)twh::dalloc(c, np * sizeof(float));
   c->fy = (float *)twh::dalloc(c, np * sizeof(float));
   c->counter = (int *)twh::dalloc(c, 4 * sizeof(int));
-  c->flagsF = (int *)twh::dalloc(c, (size_t)c->NB * sizeof(int));
-  c->flagsB = (int *)twh::dalloc(c, (size_t)c->NB * sizeof(int));
   c->abort_flag = (int *)twh::dalloc(c, sizeof(int));
   c->d_norm = (double *)twh::dalloc(c, 2 * sizeof(double));
-  if (!c->vz || !c->vy || !c->vr || !c->fz || !c->fy || !c->counter || !c->flagsF || !c->flagsB ||
-      !c->abort_flag || !c->d_norm)
+  if (!c->vz || !c->vy || !c->vr || !c->fz || !c->fy || !c->counter || !c->abort_flag || !c->d_norm)
     return twh::fail(c, TW_ERR_OOM, "solve workspace");
   TW_CUDA(c, cudaMemset(c->vz, 0, np * sizeof(dd)));
   TW_CUDA(c, cudaMemset(c->vy, 0, np * sizeof(dd)));
-  TW_CUDA(c, cudaMemset(c->flagsF, 0, (size_t)c->NB * sizeof(int)));
-  TW_CUDA(c, cudaMemset(c->flagsB, 0, (size_t)c->NB * sizeof(int)));
+  TW_CUDA(c, cudaMemset(c->counter, 0, 4 * sizeof(int)));
   TW_CUDA(c, cudaMemset(c->abort_flag, 0, sizeof(int)));
-  c->epoch = 0;
   return TW_OK;
 }
 
 // y = K^{-1} b for the leading nrows with the df64 factor.  b: double (kind 0) or dd (kind 1)
 tw_status solve64(tw_ctx *c, const void *b, int kind, int nrows, dd *y, cudaStream_t s) {
   const int NBw = (nrows + NB_ - 1) / NB_;
-  const int e = ++c->epoch;
   { twh::Phase p(c, TW_PH_TRSV_FWD, s);
-    TW_CUDA(c, launch_trsv_dd(c->Lp64, c->inv64, b, kind, c->vz, nrows, NBw, c->counter, c->flagsF,
-                              e, true, c->d_err, c->abort_flag, s)); }
+    TW_CUDA(c, launch_trsv_dd(c->Lp64, c->inv64, b, kind, c->vz, nrows, NBw, c->counter, true,
+                              c->d_err, c->abort_flag, s)); }
   twh::Phase p(c, TW_PH_TRSV_BWD, s);
-  TW_CUDA(c, launch_trsv_dd(c->Lp64, c->inv64, c->vz, 1, y, nrows, NBw, c->counter + 1,
-                            c->flagsB, e, false, c->d_err, c->abort_flag, s));
+  TW_CUDA(c, launch_trsv_dd(c->Lp64, c->inv64, c->vz, 1, y, nrows, NBw, c->counter + 2, false,
+                            c->d_err, c->abort_flag, s));
   return TW_OK;
 }
 
 // float solve with the FP32 factor: y32 = K32^{-1} b
 tw_status solve32(tw_ctx *c, const void *b, int kind, int nrows, float *y, cudaStream_t s) {
   const int NBw = (nrows + NB_ - 1) / NB_;
-  const int e = ++c->epoch;
   { twh::Phase p(c, TW_PH_TRSV_FWD, s);
-    TW_CUDA(c, launch_trsv_f(c->Lp32, c->inv32, b, kind, c->fz, nrows, NBw, c->counter, c->flagsF,
-                             e, true, c->d_err, c->abort_flag, s)); }
+    TW_CUDA(c, launch_trsv_f(c->Lp32, c->inv32, b, kind, c->fz, nrows, NBw, c->counter, true,
+                             c->d_err, c->abort_flag, s)); }
   twh::Phase p(c, TW_PH_TRSV_BWD, s);
-  TW_CUDA(c, launch_trsv_f(c->Lp32, c->inv32, c->fz, 2, y, nrows, NBw, c->counter + 1, c->flagsB,
-                           e, false, c->d_err, c->abort_flag, s));
+  TW_CUDA(c, launch_trsv_f(c->Lp32, c->inv32, c->fz, 2, y, nrows, NBw, c->counter + 2, false,
+                           c->d_err, c->abort_flag, s));
   return TW_OK;
 }
 
@@ -156,6 +149,36 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
     TW_CUDA(c, cudaStreamSynchronize(s));
     twh::dfree(c, K32);
     c->have32 = true;
+    // choose the number of refinement steps on a probe right-hand side (all
+    // ones): iterate until the FP64 residual stops falling by 2x or reaches
+    // 1e-13 relative; online calls then run that many steps without host sync
+    std::vector<double> ones(n, 1.0);
+    double *probe = (double *)twh::dalloc(c, n * sizeof(double));
+    if (!probe) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "probe"); }
+    TW_CUDA(c, cudaMemcpy(probe, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    const int NBn = c->NB;
+    st = solve32(c, probe, 0, (int)n, c->fy, s);
+    if (st != TW_OK) { twh::dfree(c, probe); twh::dfree(c, K); return st; }
+    TW_CUDA(c, launch_f_to_dd(c->fy, c->vy, (int)n, s));
+    double prev = 1e300;
+    int steps = 0;
+    for (int it = 0; it < 30; ++it) {
+      TW_CUDA(c, launch_residual(c->Kp64, c->vy, probe, c->vr, (int)n, NBn, s));
+      TW_CUDA(c, launch_sumsq(c->vr, 1, (int)n, c->d_norm, s));
+      double h = 0.0;
+      TW_CUDA(c, cudaMemcpyAsync(&h, c->d_norm, sizeof(double), cudaMemcpyDeviceToHost, s));
+      TW_CUDA(c, cudaStreamSynchronize(s));
+      const double relr = sqrt(h / (double)n);
+      if (relr <= 1e-13 || relr > 0.5 * prev) break;
+      prev = relr;
+      st = solve32(c, c->vr, 1, (int)n, c->fy, s);
+      if (st != TW_OK) { twh::dfree(c, probe); twh::dfree(c, K); return st; }
+      TW_CUDA(c, launch_axpy_dd_f(c->vy, c->fy, (int)n, s));
+      steps = it + 1;
+    }
+    c->ir_steps = std::max(1, steps);
+    c->ir_probe_resid = prev;
+    twh::dfree(c, probe);
   }
   if (want64) {
     if (!c->Lp64) c->Lp64 = (dd *)twh::dalloc(c, nblk * blk * sizeof(dd));
@@ -265,5 +288,7 @@ tw_status tw_set_refinement(tw_ctx *c, int steps) {
   c->ir_steps = steps;
   return TW_OK;
 }
+
+int tw_refinement_steps(const tw_ctx *c) { return c ? c->ir_steps : -1; }
 
 }  // extern "C"

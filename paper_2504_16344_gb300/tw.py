@@ -46,6 +46,7 @@ SIGNATURES = {
     "tw_infer": (_S, [_P, _I, _I, _P, _P, _P, _P, _P]),
     "tw_forecast": (_S, [_P, _I, _I, _P, _P, _P]),
     "tw_set_refinement": (_S, [_P, _I]),
+    "tw_refinement_steps": (_I, [_P]),
     "tw_profile_enable": (_S, [_P, _I]),
     "tw_profile_read": (_S, [_P, _P, _P, _I]),
     "tw_kernel_launches": (ctypes.c_longlong, []),
@@ -198,6 +199,9 @@ class Context:
 
     def set_refinement(self, steps):
         self._check(self.lib.tw_set_refinement(self.h, int(steps)))
+
+    def refinement_steps(self) -> int:
+        return int(self.lib.tw_refinement_steps(self.h))
 
     def infer(self, prec, d, windows=None, out=None, stats=False, stream=None):
         """Posterior mean for d [nrhs][Nt][Nd]; windows: per-rhs Nt' (None = Nt)."""
