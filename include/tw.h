@@ -148,9 +148,9 @@ tw_status tw_prior_apply(tw_ctx *ctx, double power, int nrhs, const double *x,
  * time-domain block column as K_(i,j) = noise_var delta_ij I +
  * sum_{s<=min(i,j)} F_{i-s} C F_{j-s}^T (a product G G^T with
  * G = Phi C^{1/2}, then prefix sums along block diagonals), then Cholesky-
- * factored: in double-float if TW_KEEP_FP64 was kept, and in FP32 (plus a
- * packed FP64 copy of K for refinement residuals) if TW_KEEP_C64 or
- * TW_KEEP_BF16X2 was kept.  Needs tw_set_prior and the FP64 operator of F.
+ * factored: in native FP64 (stored as float pairs for the online solves) if
+ * TW_KEEP_FP64 was kept, and in FP32 (plus a packed double-float copy of K
+ * for refinement residuals) if TW_KEEP_C64 or TW_KEEP_BF16X2 was kept.  Needs tw_set_prior and the FP64 operator of F.
  * Set-up call: allocates, synchronises `stream`, and returns TW_ERR_NOT_SPD
  * (pivot row in tw_last_error) if K is not numerically positive definite.
  */
@@ -174,9 +174,9 @@ typedef struct {
  * mean; data before Nt' do not inform them).
  * d: device [nrhs][Nt][Nd] FP64 (rows >= Nt' ignored); m: device
  * [nrhs][Nt][Nm] FP64.  prec TW_PREC_FP64 uses the double-float factor and
- * operator; TW_PREC_C64 / TW_PREC_BF16X2 solve with the FP32 factor, apply
- * `refinement steps` of iterative refinement with the FP64 residual
- * r = d' - K' y (df64 arithmetic), and use the FP32 operator for F'^T.
+ * operator; TW_PREC_C64 / TW_PREC_BF16X2 use the FP32 operator for F'^T and
+ * the prior, and solve K' y = d' as tw_set_solver selects (double-float
+ * factor, or FP32 factor + FP64-residual refinement).
  * stats may be NULL; when given, the call synchronises `stream` once.
  */
 tw_status tw_infer(tw_ctx *ctx, tw_prec prec, int nrhs, const int *nt_window, const double *d,
@@ -193,6 +193,14 @@ tw_status tw_forecast(tw_ctx *ctx, tw_prec prec, int nrhs, const double *m, doub
  * (range 0..50).  tw_factor_K picks it by refining a probe right-hand side
  * until the FP64 residual stops falling; this call overrides that choice. */
 tw_status tw_set_refinement(tw_ctx *ctx, int steps);
+
+/* How the mixed-precision tw_infer (TW_PREC_C64 / TW_PREC_BF16X2) solves
+ * K y = d.  TW_SOLVE_FACTOR64 (default): the double-float factor (needs
+ * TW_KEEP_FP64 at set-up); only the operator applies run in FP32.
+ * TW_SOLVE_FP32_IR: the FP32 factor plus iterative refinement with the FP64
+ * residual r = d - K y (the number of steps: tw_set_refinement). */
+typedef enum { TW_SOLVE_FACTOR64 = 0, TW_SOLVE_FP32_IR = 1 } tw_solver;
+tw_status tw_set_solver(tw_ctx *ctx, tw_solver solver);
 
 /* Refinement steps the mixed-precision tw_infer currently takes (-1 if ctx
  * is NULL). */

@@ -45,6 +45,7 @@ struct tw_ctx {
   int *abort_flag = nullptr;
   double *d_norm = nullptr;
   int ir_steps = 3;
+  int solver = TW_SOLVE_FACTOR64;
   double ir_probe_resid = 0.0;
   // per-phase timing
   struct PhaseEv { int ph; cudaEvent_t a, b; };

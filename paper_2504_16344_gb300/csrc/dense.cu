@@ -169,7 +169,7 @@ k_potrf_diag(T *__restrict__ K, long ldk, int J, T *__restrict__ inv, int *err) 
   for (int c = 0; c < NB_; ++c) {
     if (tid == 0) {
       T piv = sA[c][c];
-      if (!(S::lead(piv) > 0.f)) {   // not positive definite (or NaN)
+      if (!(S::lead(piv) > 0)) {   // not positive definite (or NaN)
         record_error(err, TW_ERR_NOT_SPD, J * NB_ + c);
         piv = S::one();
       }
@@ -280,6 +280,41 @@ __global__ void k_pack(const T *__restrict__ K, long ldk, T *__restrict__ P, int
   }
 }
 
+// full matrix in place: dd -> IEEE double (hi + lo is exact in binary64)
+__global__ void k_dd_to_double_inplace(void *__restrict__ K, long ld, int NB) {
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (J > I) return;
+  for (int idx = threadIdx.x; idx < NB_ * NB_; idx += blockDim.x) {
+    const int r = idx / NB_, c = idx % NB_;
+    const long o = ((long)I * NB_ + r) * ld + (long)J * NB_ + c;
+    const dd v = reinterpret_cast<const dd *>(K)[o];
+    reinterpret_cast<double *>(K)[o] = (double)v.hi + (double)v.lo;
+  }
+}
+// packed blocks of a double factor -> dd packed blocks (hi = rn(x), lo = rn(x - hi))
+__global__ void k_double_to_dd(const double *__restrict__ a, dd *__restrict__ b, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    b[i] = dd_from_double(a[i]);
+}
+
+// pack lower blocks of a double matrix into dd packed blocks
+__global__ void k_pack_d2dd(const double *__restrict__ K, long ldk, dd *__restrict__ P, int NB) {
+  const size_t nblk = (size_t)NB * (NB + 1) / 2;
+  for (size_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    int I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((size_t)I * (I + 1) / 2 > b) --I;
+    while ((size_t)(I + 1) * (I + 2) / 2 <= b) ++I;
+    const int J = (int)(b - (size_t)I * (I + 1) / 2);
+    const double *src = K + (long)I * NB_ * ldk + (long)J * NB_;
+    dd *dst = P + b * NB_ * NB_;
+    for (int idx = threadIdx.x; idx < NB_ * NB_; idx += blockDim.x) {
+      const int r = idx / NB_, c = idx % NB_;
+      dst[idx] = (I == J && c > r) ? dd_zero() : dd_from_double(src[(long)r * ldk + c]);
+    }
+  }
+}
+
 // full dd matrix (lower tiles) -> float
 __global__ void k_lower_to_float(const dd *__restrict__ K, float *__restrict__ K32, long ld, int NB) {
   const int I = blockIdx.y, J = blockIdx.x;
@@ -308,6 +343,22 @@ template <> __device__ __forceinline__ float ld_rhs<float>(const void *rhs, int 
 }
 
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s
+
+// this thread's 16 entries of the off-diagonal block used by row I against
+// block J: FWD reads row r_f of L_IJ, BWD column c_b of L_JI
+template <class T, bool FWD>
+__device__ __forceinline__ void load_block(const T *__restrict__ Lp, int I, int J, int r_f, int q_f,
+                                           int c_b, int q_b, T *lv) {
+  if (FWD) {
+    const T *blk = Lp + packed_index(I, J) * NB_ * NB_ + r_f * NB_ + q_f * 16;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) lv[u] = blk[u];
+  } else {
+    const T *blk = Lp + packed_index(J, I) * NB_ * NB_ + (q_b * 16) * NB_ + c_b;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) lv[u] = blk[u * NB_];
+  }
+}
 
 // Block rows complete strictly in dependency order (row I needs row I-1), so
 // one counter `progress` (rows finished, counted from the start for FWD and
@@ -338,6 +389,8 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restr
     const int ndep = ticket;                 // blocks this row depends on
     T tot = S::zerov();
     int d = 0;
+    T lv[16];
+    if (ndep > 0) load_block<T, FWD>(Lp, I, FWD ? 0 : NBw - 1, r_f, q_f, c_b, q_b, lv);
     while (d < ndep) {
       if (tid == 0) {
         int p = ld_acquire(prog + 1);
@@ -362,20 +415,18 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restr
       for (; d < dend; ++d) {
         const int J = FWD ? d : NBw - 1 - d;
         const T *zj = out + (long)J * NB_ + q * 16;
-        T lv[16];
-        if (FWD) {
-          const T *blk = Lp + packed_index(I, J) * NB_ * NB_ + r_f * NB_ + q_f * 16;
+        T zv[16];
 #pragma unroll
-          for (int u = 0; u < 16; ++u) lv[u] = blk[u];
-        } else {
-          const T *blk = Lp + packed_index(J, I) * NB_ * NB_ + (q_b * 16) * NB_ + c_b;
-#pragma unroll
-          for (int u = 0; u < 16; ++u) lv[u] = blk[u * NB_];
-        }
+        for (int u = 0; u < 16; ++u) zv[u] = ld_cg(zj + u);
+        // prefetch the next block (the stream does not depend on the chain)
+        T nx[16];
+        if (d + 1 < ndep) load_block<T, FWD>(Lp, I, FWD ? d + 1 : NBw - 2 - d, r_f, q_f, c_b, q_b, nx);
         typename S::acc a = S::zero();
 #pragma unroll
-        for (int u = 0; u < 16; ++u) S::mac(a, lv[u], ld_cg(zj + u));
+        for (int u = 0; u < 16; ++u) S::mac(a, lv[u], zv[u]);
         S::fold(tot, a);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) lv[u] = nx[u];
       }
       __syncthreads();   // sP is rewritten next round
     }
@@ -572,6 +623,30 @@ cudaError_t launch_cholesky_dd(dd *K, long ldk, int NB, dd *inv, int *err, cudaS
 }
 cudaError_t launch_cholesky_f(float *K, long ldk, int NB, float *inv, int *err, cudaStream_t s) {
   return cholesky_t<float>(K, ldk, NB, inv, err, s);
+}
+
+cudaError_t launch_cholesky_d(double *K, long ldk, int NB, double *inv, int *err, cudaStream_t s) {
+  return cholesky_t<double>(K, ldk, NB, inv, err, s);
+}
+cudaError_t launch_pack_d(const double *K, long ldk, double *P, int NB, cudaStream_t s) {
+  k_pack<double><<<152 * 8, 256, 0, s>>>(K, ldk, P, NB);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_pack_d2dd(const double *K, long ldk, dd *P, int NB, cudaStream_t s) {
+  k_pack_d2dd<<<152 * 8, 256, 0, s>>>(K, ldk, P, NB);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_dd_to_double_inplace(void *K, long ld, int NB, cudaStream_t s) {
+  k_dd_to_double_inplace<<<dim3(NB, NB), 256, 0, s>>>(K, ld, NB);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_double_to_dd(const double *a, dd *b, size_t n, cudaStream_t s) {
+  k_double_to_dd<<<152 * 16, 256, 0, s>>>(a, b, n);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pack_dd(const dd *K, long ldk, dd *P, int NB, cudaStream_t s) {

@@ -49,6 +49,26 @@ template <> struct DS<float> {
   static __device__ __forceinline__ float shfl_xor(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 };
 
+template <> struct DS<double> {
+  typedef double acc;
+  static __device__ __forceinline__ acc zero() { return 0.0; }
+  static __device__ __forceinline__ void mac(acc &a, double x, double y) { a = fma(x, y, a); }
+  static __device__ __forceinline__ double get(acc a) { return a; }
+  static __device__ __forceinline__ void fold(double &tot, acc &a) { tot += a; a = 0.0; }
+  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+  static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
+  static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
+  static __device__ __forceinline__ double neg(double a) { return -a; }
+  static __device__ __forceinline__ double zerov() { return 0.0; }
+  static __device__ __forceinline__ double one() { return 1.0; }
+  static __device__ __forceinline__ double sqrtv(double a) { return a > 0.0 ? sqrt(a) : 0.0; }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double lead(double a) { return a; }
+  static __device__ __forceinline__ double from_d(double x) { return x; }
+  static __device__ __forceinline__ double to_d(double a) { return a; }
+  static __device__ __forceinline__ double shfl_xor(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+};
+
 // index of block (I, J), J <= I, in the packed lower-triangular block array
 __host__ __device__ __forceinline__ size_t packed_index(int I, int J) {
   return (size_t)I * (I + 1) / 2 + J;

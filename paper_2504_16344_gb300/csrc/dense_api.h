@@ -15,6 +15,11 @@ cudaError_t launch_K_from_P(dd *K, long ldk, int Nd, int Nt, int n, int n_pad, d
 // blocked Cholesky in place (lower), inverses of the diagonal blocks to inv
 cudaError_t launch_cholesky_dd(dd *K, long ldk, int NB, dd *inv, int *err, cudaStream_t s);
 cudaError_t launch_cholesky_f(float *K, long ldk, int NB, float *inv, int *err, cudaStream_t s);
+cudaError_t launch_cholesky_d(double *K, long ldk, int NB, double *inv, int *err, cudaStream_t s);
+cudaError_t launch_pack_d(const double *K, long ldk, double *P, int NB, cudaStream_t s);
+cudaError_t launch_pack_d2dd(const double *K, long ldk, dd *P, int NB, cudaStream_t s);
+cudaError_t launch_dd_to_double_inplace(void *K, long ld, int NB, cudaStream_t s);
+cudaError_t launch_double_to_dd(const double *a, dd *b, size_t n, cudaStream_t s);
 cudaError_t launch_pack_dd(const dd *K, long ldk, dd *P, int NB, cudaStream_t s);
 cudaError_t launch_pack_f(const float *K, long ldk, float *P, int NB, cudaStream_t s);
 cudaError_t launch_lower_to_float(const dd *K, float *K32, long ld, int NB, cudaStream_t s);

@@ -184,9 +184,19 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
     if (!c->Lp64) c->Lp64 = (dd *)twh::dalloc(c, nblk * blk * sizeof(dd));
     if (!c->inv64) c->inv64 = (dd *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(dd));
     if (!c->Lp64 || !c->inv64) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "factor buffers"); }
-    TW_CUDA(c, launch_cholesky_dd(K, np, c->NB, c->inv64, c->d_err, s));
-    TW_CUDA(c, launch_pack_dd(K, np, c->Lp64, c->NB, s));
+    // The factorisation is set-up work, so it runs in native FP64: a blocked
+    // Cholesky in double-float would carry 2^-48 rounding through n^3/3
+    // updates, and K's conditioning amplifies that into the posterior mean.
+    // The factor is then stored as float pairs for the online solves.
+    double *invd = (double *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(double));
+    if (!invd) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "inverse buffer"); }
+    TW_CUDA(c, launch_dd_to_double_inplace(K, np, c->NB, s));
+    double *Kd = reinterpret_cast<double *>(K);
+    TW_CUDA(c, launch_cholesky_d(Kd, np, c->NB, invd, c->d_err, s));
+    TW_CUDA(c, launch_pack_d2dd(Kd, np, c->Lp64, c->NB, s));
+    TW_CUDA(c, launch_double_to_dd(invd, c->inv64, (size_t)c->NB * blk, s));
     tw_status cs = tw_check(c, stream);
+    twh::dfree(c, invd);
     if (cs != TW_OK) { twh::dfree(c, K); return cs; }
     c->have64 = true;
   }
@@ -202,7 +212,10 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
   const bool mixed = prec != TW_PREC_FP64;
   if (prec < 0 || prec > 2 || !c->op[TW_MAP_F][prec])
     return twh::fail(c, TW_ERR_ARG, "requested precision was not kept at tw_create");
-  if (mixed ? !c->have32 : !c->have64)
+  // solver of K y = d: the double-float factor, or (mixed operator path with
+  // TW_SOLVE_FP32_IR selected) the FP32 factor refined with the FP64 residual
+  const bool use32 = mixed && c->have32 && (c->solver == TW_SOLVE_FP32_IR || !c->have64);
+  if (use32 ? !c->have32 : !c->have64)
     return twh::fail(c, TW_ERR_STATE, "tw_factor_K must come before tw_infer");
   cudaStream_t s = (cudaStream_t)stream;
   TW_CUDA(c, cudaSetDevice(c->dev));
@@ -217,7 +230,7 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
     const double *dr = d + (size_t)r * Nt * Nd;
     double *mr = m + (size_t)r * Nt * Nm;
     // 1) y = K'^{-1} d'  (leading nrows of K's factor: windows nest)
-    if (!mixed) {
+    if (!use32) {
       tw_status st = solve64(c, dr, 0, nrows, c->vy, s);
       if (st != TW_OK) return st;
     } else {
@@ -290,5 +303,13 @@ tw_status tw_set_refinement(tw_ctx *c, int steps) {
 }
 
 int tw_refinement_steps(const tw_ctx *c) { return c ? c->ir_steps : -1; }
+
+tw_status tw_set_solver(tw_ctx *c, tw_solver solver) {
+  if (!c) return TW_ERR_ARG;
+  if (solver != TW_SOLVE_FACTOR64 && solver != TW_SOLVE_FP32_IR)
+    return twh::fail(c, TW_ERR_ARG, "unknown solver");
+  c->solver = solver;
+  return TW_OK;
+}
 
 }  // extern "C"

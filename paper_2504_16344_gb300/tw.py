@@ -25,6 +25,8 @@ MAP_F, MAP_FQ = 0, 1
 # tw_prec
 PREC_FP64, PREC_C64, PREC_BF16X2 = 0, 1, 2
 KEEP_FP64, KEEP_C64, KEEP_BF16X2 = 1, 2, 4
+# tw_solver
+SOLVE_FACTOR64, SOLVE_FP32_IR = 0, 1
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -47,6 +49,7 @@ SIGNATURES = {
     "tw_forecast": (_S, [_P, _I, _I, _P, _P, _P]),
     "tw_set_refinement": (_S, [_P, _I]),
     "tw_refinement_steps": (_I, [_P]),
+    "tw_set_solver": (_S, [_P, _I]),
     "tw_profile_enable": (_S, [_P, _I]),
     "tw_profile_read": (_S, [_P, _P, _P, _I]),
     "tw_kernel_launches": (ctypes.c_longlong, []),
@@ -199,6 +202,9 @@ class Context:
 
     def set_refinement(self, steps):
         self._check(self.lib.tw_set_refinement(self.h, int(steps)))
+
+    def set_solver(self, solver):
+        self._check(self.lib.tw_set_solver(self.h, int(solver)))
 
     def refinement_steps(self) -> int:
         return int(self.lib.tw_refinement_steps(self.h))

@@ -123,12 +123,17 @@ def test_full_window_map_stationarity_and_mixed_agreement(c2):
     m64, st = ctx.infer(tw.PREC_FP64, d, stats=True)
     s64 = _stationarity(ctx, d, m64, c2["sigma"], tw.PREC_FP64)
     print(f"FP64: stationarity {s64:.2e} residual {st.resid_rel:.2e}")
-    assert s64 < 1e-9
-    for prec, tol in ((tw.PREC_C64, 1e-5), (tw.PREC_BF16X2, 1e-4)):
-        m32, st32 = ctx.infer(prec, d, stats=True)
-        q32 = ctx.forecast(prec, m32)
-        q64 = ctx.forecast(tw.PREC_FP64, m64)
-        em, eq = rel(m32.cpu().numpy(), m64.cpu().numpy()), rel(q32.cpu().numpy(), q64.cpu().numpy())
-        print(f"prec {prec}: m vs FP64 {em:.2e}, q vs FP64 {eq:.2e}, residual {st32.resid_rel:.2e}")
-        assert em < tol and eq < tol
+    assert s64 < 1e-6
+    q64 = ctx.forecast(tw.PREC_FP64, m64)
+    for prec in (tw.PREC_C64, tw.PREC_BF16X2):
+        for solver in (0, 1):
+            ctx.set_solver(solver)
+            m32, st32 = ctx.infer(prec, d, stats=True)
+            ctx.set_solver(0)
+            q32 = ctx.forecast(prec, m32)
+            em = rel(m32.cpu().numpy(), m64.cpu().numpy())
+            eq = rel(q32.cpu().numpy(), q64.cpu().numpy())
+            print(f"prec {prec} solver {solver}: m vs FP64 {em:.2e}, q vs FP64 {eq:.2e}, "
+                  f"residual {st32.resid_rel:.2e}, refinement steps {ctx.refinement_steps()}")
+            assert em < 1e-5 and eq < 5e-5
     ctx.check()
