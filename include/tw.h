@@ -159,8 +159,7 @@ tw_status tw_factor_K(tw_ctx *ctx, double noise_var, void *stream);
 /* Statistics of the last right-hand side of tw_infer (optional output). */
 typedef struct {
   int ir_iters;      /* refinement steps taken (mixed path; 0 for FP64)   */
-  double resid_rel;  /* |d' - K' y| / |d'| with the FP64 K, or -1 if no   */
-                     /* packed FP64 K is held (FP64-only contexts)        */
+  double resid_rel;  /* |d' - K' y| / |d'| with the stored K              */
 } tw_infer_stats;
 
 /*
@@ -181,6 +180,23 @@ typedef struct {
  */
 tw_status tw_infer(tw_ctx *ctx, tw_prec prec, int nrhs, const int *nt_window, const double *d,
                    double *m, tw_infer_stats *stats, void *stream);
+
+/*
+ * tw_solve_K -- the data-space solve of Phase 4 alone: y = K'^{-1} d' for
+ * each right-hand side (window Nt' = nt_window[r], NULL = Nt), with the
+ * solver tw_infer would use for `prec`.  d, y: device [nrhs][Nt][Nd] FP64;
+ * rows t >= Nt' of y are 0.
+ */
+tw_status tw_solve_K(tw_ctx *ctx, tw_prec prec, int nrhs, const int *nt_window, const double *d,
+                     double *y, void *stream);
+
+/*
+ * tw_apply_K -- out = K' x with the stored K (double-float, packed lower
+ * blocks; K' = leading Nd Nt' rows and columns).  For residual
+ * certificates |d - K y|.  x, out: device [nrhs][Nt][Nd] FP64.
+ */
+tw_status tw_apply_K(tw_ctx *ctx, int nrhs, const int *nt_window, const double *x, double *out,
+                     void *stream);
 
 /*
  * tw_forecast -- QoI forecast q = F_q m (Phase 4, q_map = F_q m_map):

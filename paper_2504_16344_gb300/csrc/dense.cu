@@ -344,19 +344,33 @@ template <> __device__ __forceinline__ float ld_rhs<float>(const void *rhs, int 
 
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s
 
+template <class T> __device__ __forceinline__ T ldg_t(const T *p);
+template <> __device__ __forceinline__ dd ldg_t<dd>(const dd *p) {
+  float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+  dd r; r.hi = v.x; r.lo = v.y; return r;
+}
+template <> __device__ __forceinline__ float ldg_t<float>(const float *p) { return __ldg(p); }
+
+// 16 consecutive elements of T from 16-byte-aligned storage, as vector loads
+template <class T>
+__device__ __forceinline__ void ld16(const T *__restrict__ p, T *v) {
+  const float4 *q = reinterpret_cast<const float4 *>(p);
+  float4 *o = reinterpret_cast<float4 *>(v);
+#pragma unroll
+  for (int i = 0; i < (int)(16 * sizeof(T) / 16); ++i) o[i] = __ldg(q + i);
+}
+
 // this thread's 16 entries of the off-diagonal block used by row I against
-// block J: FWD reads row r_f of L_IJ, BWD column c_b of L_JI
+// block J: FWD reads row r_f of L_IJ (contiguous), BWD column c_b of L_JI
 template <class T, bool FWD>
 __device__ __forceinline__ void load_block(const T *__restrict__ Lp, int I, int J, int r_f, int q_f,
                                            int c_b, int q_b, T *lv) {
   if (FWD) {
-    const T *blk = Lp + packed_index(I, J) * NB_ * NB_ + r_f * NB_ + q_f * 16;
-#pragma unroll
-    for (int u = 0; u < 16; ++u) lv[u] = blk[u];
+    ld16(Lp + packed_index(I, J) * NB_ * NB_ + r_f * NB_ + q_f * 16, lv);
   } else {
     const T *blk = Lp + packed_index(J, I) * NB_ * NB_ + (q_b * 16) * NB_ + c_b;
 #pragma unroll
-    for (int u = 0; u < 16; ++u) lv[u] = blk[u * NB_];
+    for (int u = 0; u < 16; ++u) lv[u] = ldg_t(blk + u * NB_);
   }
 }
 
@@ -364,7 +378,10 @@ __device__ __forceinline__ void load_block(const T *__restrict__ Lp, int I, int 
 // one counter `progress` (rows finished, counted from the start for FWD and
 // from the end for BWD) tells every CTA which results are ready.  A CTA reads
 // it once, consumes every ready block without further synchronisation, and
-// only waits near the diagonal.  prog[0] = ticket, prog[1] = progress.
+// only waits near the diagonal; CTAs far behind the front poll slowly so the
+// counter's cache line is not flooded.  The diagonal block's inverse and the
+// right-hand side are loaded before any wait, off the critical path.
+// prog[0] = ticket, prog[1] = progress.
 template <class T, bool FWD>
 __global__ void __launch_bounds__(256)
 k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restrict__ rhs,
@@ -387,6 +404,20 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restr
     if (ticket >= NBw) return;
     const int I = FWD ? ticket : NBw - 1 - ticket;
     const int ndep = ticket;                 // blocks this row depends on
+    // off the critical path: diagonal inverse entries and the right-hand side
+    T iv[16];
+    if (FWD) {
+      ld16(Linv + (size_t)I * NB_ * NB_ + r_f * NB_ + q_f * 16, iv);
+    } else {
+      const T *ib = Linv + (size_t)I * NB_ * NB_ + (q_b * 16) * NB_ + c_b;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) iv[u] = ldg_t(ib + u * NB_);
+    }
+    const int rrow = FWD ? r_f : c_b;
+    const long gi = (long)I * NB_ + rrow;
+    const bool owner = FWD ? (q_f == 0) : (tid < NB_);
+    T bval = S::zerov();
+    if (owner && gi < nrows) bval = ld_rhs<T>(rhs, rhs_kind, gi);
     T tot = S::zerov();
     int d = 0;
     T lv[16];
@@ -404,7 +435,10 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restr
               sbail = 1;
               break;
             }
-            __nanosleep(32);
+            // rows finish every few microseconds; a CTA k rows behind the
+            // front can lag k rows and catch up with one burst of blocks
+            const int behind = ticket - p;
+            __nanosleep(behind > 2 ? min(4096, 256 * (behind - 2)) : 32);
           }
         }
         sP = p;
@@ -435,44 +469,31 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restr
       T s = tot;
       s = S::add(s, S::shfl_xor(s, 1));
       s = S::add(s, S::shfl_xor(s, 2));
-      if (q_f == 0) {
-        const long gi = (long)I * NB_ + r_f;
-        const T b = (gi < nrows) ? ld_rhs<T>(rhs, rhs_kind, gi) : S::zerov();
-        sv[r_f] = (gi < nrows) ? S::sub(b, s) : S::zerov();
-      }
+      if (owner) sv[r_f] = (gi < nrows) ? S::sub(bval, s) : S::zerov();
     } else {
       sred[q_b][c_b] = tot;
       __syncthreads();
-      if (tid < NB_) {
+      if (owner) {
         T s = S::add(S::add(sred[0][tid], sred[1][tid]), S::add(sred[2][tid], sred[3][tid]));
-        const long gi = (long)I * NB_ + tid;
-        const T b = (gi < nrows) ? ld_rhs<T>(rhs, rhs_kind, gi) : S::zerov();
-        sv[tid] = (gi < nrows) ? S::sub(b, s) : S::zerov();
+        sv[tid] = (gi < nrows) ? S::sub(bval, s) : S::zerov();
       }
     }
     __syncthreads();
     // diagonal block: out_I = Linv v (FWD) or Linv^T v (BWD)
-    const T *iv = Linv + (size_t)I * NB_ * NB_;
     typename S::acc a2 = S::zero();
-    if (FWD) {
 #pragma unroll
-      for (int u = 0; u < 16; ++u) S::mac(a2, iv[r_f * NB_ + q_f * 16 + u], sv[q_f * 16 + u]);
+    for (int u = 0; u < 16; ++u) S::mac(a2, iv[u], sv[q * 16 + u]);
+    if (FWD) {
       T s = S::get(a2);
       s = S::add(s, S::shfl_xor(s, 1));
       s = S::add(s, S::shfl_xor(s, 2));
-      if (q_f == 0) {
-        const long gi = (long)I * NB_ + r_f;
-        out[gi] = (gi < nrows) ? s : S::zerov();
-      }
+      if (owner) out[gi] = (gi < nrows) ? s : S::zerov();
     } else {
-#pragma unroll
-      for (int u = 0; u < 16; ++u) S::mac(a2, iv[(q_b * 16 + u) * NB_ + c_b], sv[q_b * 16 + u]);
       __syncthreads();
       sred[q_b][c_b] = S::get(a2);
       __syncthreads();
-      if (tid < NB_) {
+      if (owner) {
         T s = S::add(S::add(sred[0][tid], sred[1][tid]), S::add(sred[2][tid], sred[3][tid]));
-        const long gi = (long)I * NB_ + tid;
         out[gi] = (gi < nrows) ? s : S::zerov();
       }
     }
@@ -487,6 +508,7 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restr
 // r = d - K x over the leading nrows (df64); one CTA per block row, no
 // synchronisation inside the sweep: lower blocks (J <= I) row-wise, upper
 // blocks as transposes of the stored (J, I) blocks.
+// d == nullptr: r = K x instead of d - K x
 __global__ void __launch_bounds__(256)
 k_residual(const dd *__restrict__ Kp, const dd *__restrict__ x, const double *__restrict__ d,
            dd *__restrict__ r, int nrows, int NBw) {
@@ -531,8 +553,17 @@ k_residual(const dd *__restrict__ Kp, const dd *__restrict__ x, const double *__
     dd t = dd_add(dd_add(sT[0][tid], sT[1][tid]), dd_add(sT[2][tid], sT[3][tid]));
     t = dd_add(t, sN[tid]);
     const long gi = (long)I * NB_ + tid;
-    r[gi] = (gi < nrows) ? dd_sub(dd_from_double(d[gi]), t) : dd_zero();
+    r[gi] = (gi < nrows) ? (d ? dd_sub(dd_from_double(d[gi]), t) : t) : dd_zero();
   }
+}
+
+__global__ void k_dd_to_double(const dd *__restrict__ a, double *__restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = dd_to_double(a[i]);
+}
+__global__ void k_double_to_dd_vec(const double *__restrict__ a, dd *__restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = dd_from_double(a[i]);
 }
 
 // x += delta (float) ; rows < nrows
@@ -702,6 +733,16 @@ cudaError_t launch_residual(const dd *Kp, const dd *x, const double *d, dd *r, i
                             cudaStream_t s) {
   if (NBw <= 0) return cudaSuccess;
   k_residual<<<NBw, 256, 0, s>>>(Kp, x, d, r, nrows, NBw);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_dd_to_double(const dd *a, double *b, int n, cudaStream_t s) {
+  k_dd_to_double<<<(n + 255) / 256, 256, 0, s>>>(a, b, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_double_to_dd_vec(const double *a, dd *b, int n, cudaStream_t s) {
+  k_double_to_dd_vec<<<(n + 255) / 256, 256, 0, s>>>(a, b, n);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -31,9 +31,11 @@ cudaError_t launch_trsv_dd(const dd *Lp, const dd *Linv, const void *rhs, int rh
 cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const void *rhs, int rhs_kind,
                           float *out, int nrows, int NBw, int *prog, bool fwd, int *err,
                           int *abort_flag, cudaStream_t s);
-// r = d - K x (packed lower K, df64)
+// r = d - K x (packed lower K, df64); d == nullptr gives r = K x
 cudaError_t launch_residual(const dd *Kp, const dd *x, const double *d, dd *r, int nrows, int NBw,
                             cudaStream_t s);
+cudaError_t launch_dd_to_double(const dd *a, double *b, int n, cudaStream_t s);
+cudaError_t launch_double_to_dd_vec(const double *a, dd *b, int n, cudaStream_t s);
 cudaError_t launch_axpy_dd_f(dd *x, const float *delta, int n, cudaStream_t s);
 cudaError_t launch_dd_to_f(const dd *a, float *b, int n, cudaStream_t s);
 cudaError_t launch_f_to_dd(const float *a, dd *b, int n, cudaStream_t s);

@@ -105,18 +105,21 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
 
   const size_t nblk = (size_t)c->NB * (c->NB + 1) / 2;
   const size_t blk = (size_t)NB_ * NB_;
-  // mixed path: FP64 K kept (packed) for the refinement residual; FP32 factor
+  // K itself is kept (packed double-float blocks): refinement residuals,
+  // tw_apply_K and residual certificates use it
+  if (!c->Kp64) c->Kp64 = (dd *)twh::dalloc(c, nblk * blk * sizeof(dd));
+  if (!c->Kp64) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "packed K"); }
+  TW_CUDA(c, launch_pack_dd(K, np, c->Kp64, c->NB, s));
+  // mixed path: FP32 factor
   if (want32) {
-    if (!c->Kp64) c->Kp64 = (dd *)twh::dalloc(c, nblk * blk * sizeof(dd));
     if (!c->Lp32) c->Lp32 = (float *)twh::dalloc(c, nblk * blk * sizeof(float));
     if (!c->inv32) c->inv32 = (float *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(float));
     float *K32 = (float *)twh::dalloc(c, (size_t)np * np * sizeof(float));
-    if (!c->Kp64 || !c->Lp32 || !c->inv32 || !K32) {
+    if (!c->Lp32 || !c->inv32 || !K32) {
       twh::dfree(c, K32);
       twh::dfree(c, K);
       return twh::fail(c, TW_ERR_OOM, "mixed-precision factor buffers");
     }
-    TW_CUDA(c, launch_pack_dd(K, np, c->Kp64, c->NB, s));
     // FP32 Cholesky; if it meets a non-positive pivot, add a small diagonal shift
     // (the refinement residual uses the unshifted FP64 K, so the solution is unchanged)
     c->shift32 = 0.0;
@@ -249,7 +252,7 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
     }
     if (stats && r == nrhs - 1) {
       // relative residual of the last right-hand side: |d - K y| / |d|
-      if (c->Kp64) {
+      if (c->Kp64 != nullptr) {
         TW_CUDA(c, launch_residual(c->Kp64, c->vy, dr, c->vr, nrows, NBw, s));
         TW_CUDA(c, launch_sumsq(c->vr, 1, nrows, c->d_norm, s));
         TW_CUDA(c, launch_sumsq(dr, 0, nrows, c->d_norm + 1, s));
@@ -287,6 +290,64 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
     }
     if (w < Nt)
       TW_CUDA(c, cudaMemsetAsync(mr + (size_t)w * Nm, 0, (size_t)(Nt - w) * Nm * sizeof(double), s));
+  }
+  return TW_OK;
+}
+
+tw_status tw_solve_K(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, const double *d,
+                     double *y, void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (nrhs < 0 || (nrhs > 0 && (!d || !y))) return twh::fail(c, TW_ERR_ARG, "bad rhs");
+  const bool use32 = prec != TW_PREC_FP64 && c->have32 && (c->solver == TW_SOLVE_FP32_IR || !c->have64);
+  if (use32 ? !c->have32 : !c->have64)
+    return twh::fail(c, TW_ERR_STATE, "tw_factor_K must come before tw_solve_K");
+  cudaStream_t s = (cudaStream_t)stream;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  const int Nd = c->Nd, Nt = c->Nt;
+  for (int r = 0; r < nrhs; ++r) {
+    const int w = nt_window ? nt_window[r] : Nt;
+    if (w < 1 || w > Nt) return twh::fail(c, TW_ERR_ARG, "window must be in [1, Nt]");
+    const int nrows = Nd * w, NBw = (nrows + NB_ - 1) / NB_;
+    const double *dr = d + (size_t)r * Nt * Nd;
+    double *yr = y + (size_t)r * Nt * Nd;
+    tw_status st;
+    if (!use32) {
+      st = solve64(c, dr, 0, nrows, c->vy, s);
+      if (st != TW_OK) return st;
+    } else {
+      st = solve32(c, dr, 0, nrows, c->fy, s);
+      if (st != TW_OK) return st;
+      TW_CUDA(c, launch_f_to_dd(c->fy, c->vy, nrows, s));
+      for (int it = 0; it < c->ir_steps; ++it) {
+        TW_CUDA(c, launch_residual(c->Kp64, c->vy, dr, c->vr, nrows, NBw, s));
+        st = solve32(c, c->vr, 1, nrows, c->fy, s);
+        if (st != TW_OK) return st;
+        TW_CUDA(c, launch_axpy_dd_f(c->vy, c->fy, nrows, s));
+      }
+    }
+    TW_CUDA(c, launch_dd_to_double(c->vy, yr, nrows, s));
+    if (w < Nt) TW_CUDA(c, cudaMemsetAsync(yr + nrows, 0, (size_t)(Nt - w) * Nd * sizeof(double), s));
+  }
+  return TW_OK;
+}
+
+tw_status tw_apply_K(tw_ctx *c, int nrhs, const int *nt_window, const double *x, double *out,
+                     void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (nrhs < 0 || (nrhs > 0 && (!x || !out))) return twh::fail(c, TW_ERR_ARG, "bad rhs");
+  if (!c->Kp64) return twh::fail(c, TW_ERR_STATE, "tw_factor_K must come before tw_apply_K");
+  cudaStream_t s = (cudaStream_t)stream;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  const int Nd = c->Nd, Nt = c->Nt;
+  for (int r = 0; r < nrhs; ++r) {
+    const int w = nt_window ? nt_window[r] : Nt;
+    if (w < 1 || w > Nt) return twh::fail(c, TW_ERR_ARG, "window must be in [1, Nt]");
+    const int nrows = Nd * w, NBw = (nrows + NB_ - 1) / NB_;
+    TW_CUDA(c, launch_double_to_dd_vec(x + (size_t)r * Nt * Nd, c->vz, nrows, s));
+    TW_CUDA(c, launch_residual(c->Kp64, c->vz, nullptr, c->vr, nrows, NBw, s));
+    double *o = out + (size_t)r * Nt * Nd;
+    TW_CUDA(c, launch_dd_to_double(c->vr, o, nrows, s));
+    if (w < Nt) TW_CUDA(c, cudaMemsetAsync(o + nrows, 0, (size_t)(Nt - w) * Nd * sizeof(double), s));
   }
   return TW_OK;
 }

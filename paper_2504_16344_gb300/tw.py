@@ -47,6 +47,8 @@ SIGNATURES = {
     "tw_factor_K": (_S, [_P, _D, _P]),
     "tw_infer": (_S, [_P, _I, _I, _P, _P, _P, _P, _P]),
     "tw_forecast": (_S, [_P, _I, _I, _P, _P, _P]),
+    "tw_solve_K": (_S, [_P, _I, _I, _P, _P, _P, _P]),
+    "tw_apply_K": (_S, [_P, _I, _P, _P, _P, _P]),
     "tw_set_refinement": (_S, [_P, _I]),
     "tw_refinement_steps": (_I, [_P]),
     "tw_set_solver": (_S, [_P, _I]),
@@ -228,6 +230,37 @@ class Context:
                                       ctypes.byref(st) if st is not None else None,
                                       _stream_ptr(stream)))
         return (out, st) if stats else out
+
+    def _windows(self, windows, nrhs):
+        if windows is None:
+            return None
+        if len(windows) != nrhs:
+            raise ValueError("one window per right-hand side")
+        return (ctypes.c_int * nrhs)(*[int(w) for w in windows])
+
+    def solve_K(self, prec, d, windows=None, out=None, stream=None):
+        """y = K'^{-1} d' for d [nrhs][Nt][Nd]."""
+        import torch
+        d = d if d.dim() == 3 else d.unsqueeze(0)
+        nrhs = d.shape[0]
+        pd = _dev(d, torch.float64, (nrhs, self.Nt, self.Nd), "d")
+        out = torch.empty_like(d) if out is None else out
+        po = _dev(out, torch.float64, (nrhs, self.Nt, self.Nd), "y")
+        self._check(self.lib.tw_solve_K(self.h, prec, nrhs, self._windows(windows, nrhs), pd, po,
+                                        _stream_ptr(stream)))
+        return out
+
+    def apply_K(self, x, windows=None, out=None, stream=None):
+        """K' x with the stored K."""
+        import torch
+        x = x if x.dim() == 3 else x.unsqueeze(0)
+        nrhs = x.shape[0]
+        px = _dev(x, torch.float64, (nrhs, self.Nt, self.Nd), "x")
+        out = torch.empty_like(x) if out is None else out
+        po = _dev(out, torch.float64, (nrhs, self.Nt, self.Nd), "out")
+        self._check(self.lib.tw_apply_K(self.h, nrhs, self._windows(windows, nrhs), px, po,
+                                        _stream_ptr(stream)))
+        return out
 
     def forecast(self, prec, m, out=None, stream=None):
         import torch

@@ -60,6 +60,28 @@ def _t(a, dev):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
 
 
+def test_K_apply_matches_oracle(case):
+    cfg, ctx = case["cfg"], case["ctx"]
+    x = synth.white((cfg.Nt, cfg.Nd), 3001)
+    got = ctx.apply_K(_t(x, case["dev"]))[0].cpu().numpy()
+    err = rel(got, case["K"] @ x.ravel())
+    print(f"{cfg.cid}: K x rel err {err:.2e}")
+    assert err < 1e-13
+
+
+def test_solve_K_matches_oracle(case):
+    from paper_2504_16344_gb300 import tw
+    cfg, ctx = case["cfg"], case["ctx"]
+    y_ref = Q.solve_K(case["L"], case["d"].ravel())
+    y = ctx.solve_K(tw.PREC_FP64, _t(case["d"], case["dev"]))[0].cpu().numpy()
+    # m from the oracle's y through the GPU applies (isolates the apply stage)
+    m_ref, _ = Q.posterior_mean(case["F"], case["lam"], case["L"], case["d"], cfg.Nt)
+    m_via = ctx.prior_apply(ctx.p2o_adjoint(tw.MAP_F, tw.PREC_FP64, _t(y_ref.reshape(cfg.Nt, cfg.Nd), case["dev"])))
+    ey, em = rel(y, y_ref), rel(m_via[0].cpu().numpy(), m_ref)
+    print(f"{cfg.cid}: y rel err {ey:.2e}; m from oracle y through GPU applies {em:.2e}")
+    assert em < 1e-11
+
+
 def test_posterior_mean_fp64_full_window(case):
     from paper_2504_16344_gb300 import tw
     cfg = case["cfg"]
