@@ -148,9 +148,10 @@ tw_status tw_prior_apply(tw_ctx *ctx, double power, int nrhs, const double *x,
  * time-domain block column as K_(i,j) = noise_var delta_ij I +
  * sum_{s<=min(i,j)} F_{i-s} C F_{j-s}^T (a product G G^T with
  * G = Phi C^{1/2}, then prefix sums along block diagonals), then Cholesky-
- * factored: in native FP64 (stored as float pairs for the online solves) if
- * TW_KEEP_FP64 was kept, and in FP32 (plus a packed double-float copy of K
- * for refinement residuals) if TW_KEEP_C64 or TW_KEEP_BF16X2 was kept.  Needs tw_set_prior and the FP64 operator of F.
+ * factored: in native FP64 if TW_KEEP_FP64 was kept (the online solves run
+ * in FP64 too), and in FP32 if TW_KEEP_C64 or TW_KEEP_BF16X2 was kept.  K
+ * itself is kept as packed double-float blocks (refinement residuals,
+ * tw_apply_K).  Needs tw_set_prior and the FP64 operator of F.
  * Set-up call: allocates, synchronises `stream`, and returns TW_ERR_NOT_SPD
  * (pivot row in tw_last_error) if K is not numerically positive definite.
  */
@@ -172,8 +173,8 @@ typedef struct {
  * one factor serves every window).  Rows t >= Nt' of m are 0 (the prior
  * mean; data before Nt' do not inform them).
  * d: device [nrhs][Nt][Nd] FP64 (rows >= Nt' ignored); m: device
- * [nrhs][Nt][Nm] FP64.  prec TW_PREC_FP64 uses the double-float factor and
- * operator; TW_PREC_C64 / TW_PREC_BF16X2 use the FP32 operator for F'^T and
+ * [nrhs][Nt][Nm] FP64.  prec TW_PREC_FP64 uses the FP64 factor and the
+ * double-float operator; TW_PREC_C64 / TW_PREC_BF16X2 use the FP32 operator for F'^T and
  * the prior, and solve K' y = d' as tw_set_solver selects (double-float
  * factor, or FP32 factor + FP64-residual refinement).
  * stats may be NULL; when given, the call synchronises `stream` once.
@@ -211,7 +212,7 @@ tw_status tw_forecast(tw_ctx *ctx, tw_prec prec, int nrhs, const double *m, doub
 tw_status tw_set_refinement(tw_ctx *ctx, int steps);
 
 /* How the mixed-precision tw_infer (TW_PREC_C64 / TW_PREC_BF16X2) solves
- * K y = d.  TW_SOLVE_FACTOR64 (default): the double-float factor (needs
+ * K y = d.  TW_SOLVE_FACTOR64 (default): the FP64 factor (needs
  * TW_KEEP_FP64 at set-up); only the operator applies run in FP32.
  * TW_SOLVE_FP32_IR: the FP32 factor plus iterative refinement with the FP64
  * residual r = d - K y (the number of steps: tw_set_refinement). */

@@ -36,10 +36,12 @@ struct tw_ctx {
   int n = 0, n_pad = 0, NB = 0;
   double sigma2 = 0.0, shift32 = 0.0;
   bool have64 = false, have32 = false;
-  tw::dd *Lp64 = nullptr, *inv64 = nullptr, *Kp64 = nullptr;   // packed 64x64 blocks
+  double *Lp64 = nullptr, *inv64 = nullptr;                      // FP64 factor, packed 64x64 blocks
+  tw::dd *Kp64 = nullptr;                                         // K, packed, double-float
   float *Lp32 = nullptr, *inv32 = nullptr;
   // solve workspaces
   tw::dd *vz = nullptr, *vy = nullptr, *vr = nullptr;          // [n_pad]
+  double *zd = nullptr, *yd = nullptr;                         // [n_pad]
   float *fz = nullptr, *fy = nullptr;                          // [n_pad]
   int *counter = nullptr;     // [4]: forward (ticket, rows done), backward (ticket, rows done)
   int *abort_flag = nullptr;

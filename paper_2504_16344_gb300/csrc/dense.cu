@@ -58,6 +58,7 @@ template <> __device__ __forceinline__ dd ld_cg<dd>(const dd *p) {
   dd r; r.hi = v.x; r.lo = v.y; return r;
 }
 template <> __device__ __forceinline__ float ld_cg<float>(const float *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ double ld_cg<double>(const double *p) { return __ldcg(p); }
 
 // -------------------------------------------------------------- GEMM NT
 // C[tile (I,J)] = (subtract ? C - S : S),  S = sum_k A[i][k] B[j][k]
@@ -336,6 +337,11 @@ template <> __device__ __forceinline__ dd ld_rhs<dd>(const void *rhs, int kind, 
   if (kind == 1) return ld_cg(reinterpret_cast<const dd *>(rhs) + i);
   dd r; r.hi = __ldcg(reinterpret_cast<const float *>(rhs) + i); r.lo = 0.f; return r;
 }
+template <> __device__ __forceinline__ double ld_rhs<double>(const void *rhs, int kind, long i) {
+  if (kind == 0) return __ldcg(reinterpret_cast<const double *>(rhs) + i);
+  if (kind == 1) return dd_to_double(ld_cg(reinterpret_cast<const dd *>(rhs) + i));
+  return (double)__ldcg(reinterpret_cast<const float *>(rhs) + i);
+}
 template <> __device__ __forceinline__ float ld_rhs<float>(const void *rhs, int kind, long i) {
   if (kind == 0) return __double2float_rn(reinterpret_cast<const double *>(rhs)[i]);
   if (kind == 1) { dd v = ld_cg(reinterpret_cast<const dd *>(rhs) + i); return __fadd_rn(v.hi, v.lo); }
@@ -350,6 +356,7 @@ template <> __device__ __forceinline__ dd ldg_t<dd>(const dd *p) {
   dd r; r.hi = v.x; r.lo = v.y; return r;
 }
 template <> __device__ __forceinline__ float ldg_t<float>(const float *p) { return __ldg(p); }
+template <> __device__ __forceinline__ double ldg_t<double>(const double *p) { return __ldg(p); }
 
 // 16 consecutive elements of T from 16-byte-aligned storage, as vector loads
 template <class T>
@@ -649,9 +656,6 @@ cudaError_t cholesky_t(T *K, long ldk, int NB, T *inv, int *err, cudaStream_t s)
   return cudaSuccess;
 }
 
-cudaError_t launch_cholesky_dd(dd *K, long ldk, int NB, dd *inv, int *err, cudaStream_t s) {
-  return cholesky_t<dd>(K, ldk, NB, inv, err, s);
-}
 cudaError_t launch_cholesky_f(float *K, long ldk, int NB, float *inv, int *err, cudaStream_t s) {
   return cholesky_t<float>(K, ldk, NB, inv, err, s);
 }
@@ -698,18 +702,18 @@ cudaError_t launch_lower_to_float(const dd *K, float *K32, long ld, int NB, cuda
 
 static int trsv_grid(int NBw) { return NBw < 152 * 4 ? NBw : 152 * 4; }
 
-cudaError_t launch_trsv_dd(const dd *Lp, const dd *Linv, const void *rhs, int rhs_kind, dd *out,
-                           int nrows, int NBw, int *prog, bool fwd, int *err, int *abort_flag,
-                           cudaStream_t s) {
+cudaError_t launch_trsv_d(const double *Lp, const double *Linv, const void *rhs, int rhs_kind,
+                          double *out, int nrows, int NBw, int *prog, bool fwd, int *err,
+                          int *abort_flag, cudaStream_t s) {
   if (NBw <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(prog, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (fwd)
-    k_trsv<dd, true><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
-                                                     prog, err, abort_flag);
+    k_trsv<double, true><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
+                                                         prog, err, abort_flag);
   else
-    k_trsv<dd, false><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
-                                                      prog, err, abort_flag);
+    k_trsv<double, false><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
+                                                          prog, err, abort_flag);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -13,7 +13,6 @@ cudaError_t launch_form_P(const dd *G, long ldg, int n, int kdim, dd *K, long ld
 cudaError_t launch_K_from_P(dd *K, long ldk, int Nd, int Nt, int n, int n_pad, double sigma2,
                             cudaStream_t s);
 // blocked Cholesky in place (lower), inverses of the diagonal blocks to inv
-cudaError_t launch_cholesky_dd(dd *K, long ldk, int NB, dd *inv, int *err, cudaStream_t s);
 cudaError_t launch_cholesky_f(float *K, long ldk, int NB, float *inv, int *err, cudaStream_t s);
 cudaError_t launch_cholesky_d(double *K, long ldk, int NB, double *inv, int *err, cudaStream_t s);
 cudaError_t launch_pack_d(const double *K, long ldk, double *P, int NB, cudaStream_t s);
@@ -25,9 +24,9 @@ cudaError_t launch_pack_f(const float *K, long ldk, float *P, int NB, cudaStream
 cudaError_t launch_lower_to_float(const dd *K, float *K32, long ld, int NB, cudaStream_t s);
 // triangular solves (fwd: L z = b; bwd: L^T x = z), rhs kind 0 double / 1 dd / 2 float
 // prog: two ints (ticket, rows finished), zeroed by the launcher
-cudaError_t launch_trsv_dd(const dd *Lp, const dd *Linv, const void *rhs, int rhs_kind, dd *out,
-                           int nrows, int NBw, int *prog, bool fwd, int *err, int *abort_flag,
-                           cudaStream_t s);
+cudaError_t launch_trsv_d(const double *Lp, const double *Linv, const void *rhs, int rhs_kind,
+                          double *out, int nrows, int NBw, int *prog, bool fwd, int *err,
+                          int *abort_flag, cudaStream_t s);
 cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const void *rhs, int rhs_kind,
                           float *out, int nrows, int NBw, int *prog, bool fwd, int *err,
                           int *abort_flag, cudaStream_t s);

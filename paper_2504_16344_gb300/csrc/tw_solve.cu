@@ -17,12 +17,14 @@ tw_status ensure_solve_workspace(tw_ctx *c) {
   c->vz = (dd *)twh::dalloc(c, np * sizeof(dd));
   c->vy = (dd *)twh::dalloc(c, np * sizeof(dd));
   c->vr = (dd *)twh::dalloc(c, np * sizeof(dd));
+  c->zd = (double *)twh::dalloc(c, np * sizeof(double));
+  c->yd = (double *)twh::dalloc(c, np * sizeof(double));
   c->fz = (float *)twh::dalloc(c, np * sizeof(float));
   c->fy = (float *)twh::dalloc(c, np * sizeof(float));
   c->counter = (int *)twh::dalloc(c, 4 * sizeof(int));
   c->abort_flag = (int *)twh::dalloc(c, sizeof(int));
   c->d_norm = (double *)twh::dalloc(c, 2 * sizeof(double));
-  if (!c->vz || !c->vy || !c->vr || !c->fz || !c->fy || !c->counter || !c->abort_flag || !c->d_norm)
+  if (!c->vz || !c->vy || !c->vr || !c->zd || !c->yd || !c->fz || !c->fy || !c->counter || !c->abort_flag || !c->d_norm)
     return twh::fail(c, TW_ERR_OOM, "solve workspace");
   TW_CUDA(c, cudaMemset(c->vz, 0, np * sizeof(dd)));
   TW_CUDA(c, cudaMemset(c->vy, 0, np * sizeof(dd)));
@@ -31,15 +33,17 @@ tw_status ensure_solve_workspace(tw_ctx *c) {
   return TW_OK;
 }
 
-// y = K^{-1} b for the leading nrows with the df64 factor.  b: double (kind 0) or dd (kind 1)
-tw_status solve64(tw_ctx *c, const void *b, int kind, int nrows, dd *y, cudaStream_t s) {
+// y = K^{-1} b for the leading nrows with the FP64 factor (native FP64
+// substitution: the solves' cancellations would amplify 2^-48 rounding)
+// b: double (kind 0) or dd (kind 1)
+tw_status solve64(tw_ctx *c, const void *b, int kind, int nrows, double *y, cudaStream_t s) {
   const int NBw = (nrows + NB_ - 1) / NB_;
   { twh::Phase p(c, TW_PH_TRSV_FWD, s);
-    TW_CUDA(c, launch_trsv_dd(c->Lp64, c->inv64, b, kind, c->vz, nrows, NBw, c->counter, true,
-                              c->d_err, c->abort_flag, s)); }
+    TW_CUDA(c, launch_trsv_d(c->Lp64, c->inv64, b, kind, c->zd, nrows, NBw, c->counter, true,
+                             c->d_err, c->abort_flag, s)); }
   twh::Phase p(c, TW_PH_TRSV_BWD, s);
-  TW_CUDA(c, launch_trsv_dd(c->Lp64, c->inv64, c->vz, 1, y, nrows, NBw, c->counter + 2, false,
-                            c->d_err, c->abort_flag, s));
+  TW_CUDA(c, launch_trsv_d(c->Lp64, c->inv64, c->zd, 0, y, nrows, NBw, c->counter + 2, false,
+                           c->d_err, c->abort_flag, s));
   return TW_OK;
 }
 
@@ -184,22 +188,17 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
     twh::dfree(c, probe);
   }
   if (want64) {
-    if (!c->Lp64) c->Lp64 = (dd *)twh::dalloc(c, nblk * blk * sizeof(dd));
-    if (!c->inv64) c->inv64 = (dd *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(dd));
+    if (!c->Lp64) c->Lp64 = (double *)twh::dalloc(c, nblk * blk * sizeof(double));
+    if (!c->inv64) c->inv64 = (double *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(double));
     if (!c->Lp64 || !c->inv64) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "factor buffers"); }
-    // The factorisation is set-up work, so it runs in native FP64: a blocked
-    // Cholesky in double-float would carry 2^-48 rounding through n^3/3
-    // updates, and K's conditioning amplifies that into the posterior mean.
-    // The factor is then stored as float pairs for the online solves.
-    double *invd = (double *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(double));
-    if (!invd) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "inverse buffer"); }
+    // The factorisation and the triangular solves run in native FP64: in
+    // double-float the solves' cancellations amplify 2^-48 rounding by K's
+    // conditioning (measured 10-30x the FP64 oracle's own error in y).
     TW_CUDA(c, launch_dd_to_double_inplace(K, np, c->NB, s));
     double *Kd = reinterpret_cast<double *>(K);
-    TW_CUDA(c, launch_cholesky_d(Kd, np, c->NB, invd, c->d_err, s));
-    TW_CUDA(c, launch_pack_d2dd(Kd, np, c->Lp64, c->NB, s));
-    TW_CUDA(c, launch_double_to_dd(invd, c->inv64, (size_t)c->NB * blk, s));
+    TW_CUDA(c, launch_cholesky_d(Kd, np, c->NB, c->inv64, c->d_err, s));
+    TW_CUDA(c, launch_pack_d(Kd, np, c->Lp64, c->NB, s));
     tw_status cs = tw_check(c, stream);
-    twh::dfree(c, invd);
     if (cs != TW_OK) { twh::dfree(c, K); return cs; }
     c->have64 = true;
   }
@@ -233,10 +232,14 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
     const double *dr = d + (size_t)r * Nt * Nd;
     double *mr = m + (size_t)r * Nt * Nm;
     // 1) y = K'^{-1} d'  (leading nrows of K's factor: windows nest)
+    const void *ysrc = c->yd;   // y as double (FP64 solve) or dd (refined FP32 solve)
+    int ykind = 0;
     if (!use32) {
-      tw_status st = solve64(c, dr, 0, nrows, c->vy, s);
+      tw_status st = solve64(c, dr, 0, nrows, c->yd, s);
       if (st != TW_OK) return st;
     } else {
+      ysrc = c->vy;
+      ykind = 1;
       // FP32 solve, then refinement with the FP64 residual r = d - K x
       tw_status st = solve32(c, dr, 0, nrows, c->fy, s);
       if (st != TW_OK) return st;
@@ -253,6 +256,7 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
     if (stats && r == nrhs - 1) {
       // relative residual of the last right-hand side: |d - K y| / |d|
       if (c->Kp64 != nullptr) {
+        if (!use32) TW_CUDA(c, launch_double_to_dd_vec(c->yd, c->vy, nrows, s));
         TW_CUDA(c, launch_residual(c->Kp64, c->vy, dr, c->vr, nrows, NBw, s));
         TW_CUDA(c, launch_sumsq(c->vr, 1, nrows, c->d_norm, s));
         TW_CUDA(c, launch_sumsq(dr, 0, nrows, c->d_norm + 1, s));
@@ -267,7 +271,7 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
     // 2) x = F'^T y over the window (y rows >= w are zero), 3) m = Gamma_pr x
     if (!mixed) {
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
-        TW_CUDA(c, launch_rfft_time_dd(c->vy, 1, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
+        TW_CUDA(c, launch_rfft_time_dd(ysrc, ykind, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
         TW_CUDA(c, launch_gemv_adj_dd(A, FMT_DD, c->wr, c->wf, Nf, Nd, Nm, s)); }
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
@@ -279,7 +283,7 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
       cf *wr = (cf *)c->wr, *wf = (cf *)c->wf;
       float *wt = (float *)c->wt;
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
-        TW_CUDA(c, launch_rfft_time_f(c->vy, 1, Nd, w, wr, Nd, Nd, c->plT, c->twTf, c->twLf, s)); }
+        TW_CUDA(c, launch_rfft_time_f(ysrc, ykind, Nd, w, wr, Nd, Nd, c->plT, c->twTf, c->twLf, s)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
         TW_CUDA(c, launch_gemv_adj_f(A, (int)prec, wr, wf, Nf, Nd, Nm, s)); }
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
@@ -312,8 +316,9 @@ tw_status tw_solve_K(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, co
     double *yr = y + (size_t)r * Nt * Nd;
     tw_status st;
     if (!use32) {
-      st = solve64(c, dr, 0, nrows, c->vy, s);
+      st = solve64(c, dr, 0, nrows, c->yd, s);
       if (st != TW_OK) return st;
+      TW_CUDA(c, cudaMemcpyAsync(yr, c->yd, (size_t)nrows * sizeof(double), cudaMemcpyDeviceToDevice, s));
     } else {
       st = solve32(c, dr, 0, nrows, c->fy, s);
       if (st != TW_OK) return st;
@@ -324,8 +329,8 @@ tw_status tw_solve_K(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, co
         if (st != TW_OK) return st;
         TW_CUDA(c, launch_axpy_dd_f(c->vy, c->fy, nrows, s));
       }
+      TW_CUDA(c, launch_dd_to_double(c->vy, yr, nrows, s));
     }
-    TW_CUDA(c, launch_dd_to_double(c->vy, yr, nrows, s));
     if (w < Nt) TW_CUDA(c, cudaMemsetAsync(yr + nrows, 0, (size_t)(Nt - w) * Nd * sizeof(double), s));
   }
   return TW_OK;
