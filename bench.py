@@ -223,13 +223,13 @@ def setup_context(cfg, dev, keep, sigma):
     build.build()
     ctx = tw.Context(cfg.Nd, cfg.Nq, cfg.Nx, cfg.Ny, cfg.Nt, cfg.Lx, cfg.Ly, keep=keep,
                      device=dev.index)
+    ctx.set_prior(cfg.nu, cfg.ell, cfg.var)
     for which, name, rows in ((tw.MAP_F, "F", cfg.Nd), (tw.MAP_FQ, "Fq", cfg.Nq)):
         for r0 in range(0, rows, 10):
             nr = min(10, rows - r0)
             col = synth.block_column_torch(cfg, name, dev, r0, nr)
             ctx.set_block_column(which, r0, col)
             del col
-    ctx.set_prior(cfg.nu, cfg.ell, cfg.var)
     torch.cuda.synchronize(dev)
     if sigma is None:
         # profiling case: noise level from the GPU's own apply (inputs only)

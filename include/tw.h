@@ -99,6 +99,10 @@ const char *tw_last_error(const tw_ctx *ctx);
  * real FFT of length 2Nt along the lag and stores them in every kept format.
  * `col` is only read during the call (stream-ordered).  Rows may be loaded
  * in any order and chunking; all rows must be loaded before an apply.
+ * When tw_set_prior came first, the call also keeps G = Phi C^{1/2} for
+ * these rows of F (computed in FP64 from `col`, Nt*nrows*Nm float pairs of
+ * device memory until tw_factor_K consumes them): K is then formed from the
+ * exact input rather than from the stored frequency-domain operator.
  */
 tw_status tw_set_block_column(tw_ctx *ctx, tw_map which, int row0, int nrows,
                               const double *col, void *stream);
@@ -154,6 +158,9 @@ tw_status tw_prior_apply(tw_ctx *ctx, double power, int nrhs, const double *x,
  * tw_apply_K).  Needs tw_set_prior and the FP64 operator of F.
  * Set-up call: allocates, synchronises `stream`, and returns TW_ERR_NOT_SPD
  * (pivot row in tw_last_error) if K is not numerically positive definite.
+ * Best accuracy: tw_set_prior, then the block column of F, then this call
+ * (G is then exact to FP64; it is released after use, so a second call, for
+ * another noise level, rebuilds Phi from the stored operator).
  */
 tw_status tw_factor_K(tw_ctx *ctx, double noise_var, void *stream);
 

@@ -20,11 +20,17 @@ struct tw_ctx {
   tw::FftPlan plT{}, plX{}, plY{};
   tw::cdd *twT = nullptr, *twL = nullptr, *twX = nullptr, *twY = nullptr;
   tw::cf *twTf = nullptr, *twLf = nullptr, *twXf = nullptr, *twYf = nullptr;
+  tw::cd *twXd = nullptr, *twYd = nullptr;      // native FP64 tables (set-up filters)
   // prior: lambda^power / N, power 1 and 1/2
   bool prior_set = false;
   double nu = 1, ell = 0.1, var = 1;
   tw::dd *lam1 = nullptr, *lamh = nullptr;
   float *lam1f = nullptr, *lamhf = nullptr;
+  double *lamhd = nullptr;                        // sqrt(lambda) / N in FP64
+  // G = Phi C^{1/2} (rows t*Nd + sensor), built in FP64 from the loaded
+  // block column when the prior is already set; consumed by tw_factor_K
+  tw::dd *G = nullptr;
+  std::vector<char> g_rows;
   // online workspaces
   tw::cdd *wf = nullptr;    // [Nf][Nm]
   tw::cdd *wr = nullptr;    // [Nf][Rmax]

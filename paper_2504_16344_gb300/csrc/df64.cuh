@@ -20,6 +20,7 @@ namespace tw {
 struct __align__(8) dd { float hi, lo; };
 struct __align__(16) cdd { dd re, im; };   // complex double-float, 16 bytes (float4 layout)
 struct __align__(8) cf { float re, im; };  // complex float, 8 bytes
+struct __align__(16) cd { double re, im; };  // complex double (set-up filters)
 
 // ---------------------------------------------------------------- basics
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -198,6 +199,30 @@ struct PolF {
   static __device__ __forceinline__ re re_mul(re a, re b) { return a * b; }
   static __device__ __forceinline__ re re_zero() { return 0.f; }
   static __device__ __forceinline__ cx make(re r, re i) { return cf_make(r, i); }
+  static __device__ __forceinline__ re real(cx a) { return a.re; }
+  static __device__ __forceinline__ re imag(cx a) { return a.im; }
+};
+
+// native FP64 policy: used at set-up, where accuracy matters and time does not
+struct PolD {
+  typedef cd cx;
+  typedef double re;
+  static __device__ __forceinline__ cx make(re r, re i) { cx z; z.re = r; z.im = i; return z; }
+  static __device__ __forceinline__ cx zero() { return make(0.0, 0.0); }
+  static __device__ __forceinline__ cx add(cx a, cx b) { return make(a.re + b.re, a.im + b.im); }
+  static __device__ __forceinline__ cx sub(cx a, cx b) { return make(a.re - b.re, a.im - b.im); }
+  static __device__ __forceinline__ cx mul(cx a, cx b) {
+    return make(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
+  }
+  static __device__ __forceinline__ cx conj(cx a) { return make(a.re, -a.im); }
+  static __device__ __forceinline__ cx mul_mi(cx a) { return make(a.im, -a.re); }
+  static __device__ __forceinline__ cx mul_i(cx a) { return make(-a.im, a.re); }
+  static __device__ __forceinline__ cx scale_re(cx a, re s) { return make(a.re * s, a.im * s); }
+  static __device__ __forceinline__ cx scale2(cx a, float p2) { return make(a.re * p2, a.im * p2); }
+  static __device__ __forceinline__ re re_add(re a, re b) { return a + b; }
+  static __device__ __forceinline__ re re_sub(re a, re b) { return a - b; }
+  static __device__ __forceinline__ re re_mul(re a, re b) { return a * b; }
+  static __device__ __forceinline__ re re_zero() { return 0.0; }
   static __device__ __forceinline__ re real(cx a) { return a.re; }
   static __device__ __forceinline__ re imag(cx a) { return a.im; }
 };

@@ -38,8 +38,20 @@ __device__ __forceinline__ float ld_in<PolF>(const void *base, int kind, long of
   else v = reinterpret_cast<const float *>(base)[off];
   return v;
 }
+template <>
+__device__ __forceinline__ double ld_in<PolD>(const void *base, int kind, long off) {
+  if (kind == 0) return reinterpret_cast<const double *>(base)[off];
+  if (kind == 1) return dd_to_double(reinterpret_cast<const dd *>(base)[off]);
+  return (double)reinterpret_cast<const float *>(base)[off];
+}
 template <class P>
 __device__ __forceinline__ void st_out(void *base, int kind, long off, typename P::re v);
+template <>
+__device__ __forceinline__ void st_out<PolD>(void *base, int kind, long off, double v) {
+  if (kind == 0) reinterpret_cast<double *>(base)[off] = v;
+  else if (kind == 1) reinterpret_cast<dd *>(base)[off] = dd_from_double(v);
+  else reinterpret_cast<float *>(base)[off] = __double2float_rn(v);
+}
 template <>
 __device__ __forceinline__ void st_out<PolDD>(void *base, int kind, long off, dd v) {
   if (kind == 0) st_real(reinterpret_cast<double *>(base) + off, v);
@@ -140,12 +152,20 @@ k_irfft_time(const typename P::cx *__restrict__ in, long in_ld, void *__restrict
 }
 
 // ------------------------------------------------------- Matern filter
+// output field of input field t: (t / per) * stride + off + t % per
+struct FieldMap {
+  int per, stride, off;
+  __device__ __forceinline__ long operator()(int t) const {
+    return (long)(t / per) * stride + off + t % per;
+  }
+};
+
 // rows pass: pair tp holds z = x_{2tp} + i x_{2tp+1}; FFT along b (length Ny)
 template <class P, bool INV>
 __global__ void __launch_bounds__(256)
 k_prior_rows(const void *__restrict__ x, int in_kind, void *__restrict__ y, int out_kind,
              typename P::cx *__restrict__ work, int nt, int Nx, int Ny, FftPlan ply,
-             const typename P::cx *__restrict__ twy, int BR) {
+             const typename P::cx *__restrict__ twy, int BR, FieldMap fm) {
   typedef typename P::cx cx;
   typedef typename P::re re;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -177,8 +197,8 @@ k_prior_rows(const void *__restrict__ x, int in_kind, void *__restrict__ y, int 
     if (!INV) {
       work[((long)tp * Nx + a) * Ny + j] = v;
     } else {
-      st_out<P>(y, out_kind, ((long)t0 * Nx + a) * Ny + j, P::real(v));
-      if (t1 < nt) st_out<P>(y, out_kind, ((long)t1 * Nx + a) * Ny + j, P::imag(v));
+      st_out<P>(y, out_kind, ((long)fm(t0) * Nx + a) * Ny + j, P::real(v));
+      if (t1 < nt) st_out<P>(y, out_kind, ((long)fm(t1) * Nx + a) * Ny + j, P::imag(v));
     }
   }
 }
@@ -261,7 +281,7 @@ template <class P>
 cudaError_t prior(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx, int Ny,
                   typename P::cx *work, const typename P::re *lam, const FftPlan &plx,
                   const FftPlan &ply, const typename P::cx *twx, const typename P::cx *twy,
-                  cudaStream_t s) {
+                  cudaStream_t s, FieldMap fm = FieldMap{1 << 30, 0, 0}) {
   if (nt <= 0) return cudaSuccess;
   typedef typename P::cx cx;
   const int np = (nt + 1) / 2;
@@ -275,11 +295,11 @@ cudaError_t prior(const void *x, int in_kind, void *y, int out_kind, int nt, int
   ensure_smem(k_prior_rows<P, true>, smr);
   ensure_smem(k_prior_cols<P>, smc);
   dim3 gr((Nx + BR - 1) / BR, np), gc((Ny + BC - 1) / BC, np);
-  k_prior_rows<P, false><<<gr, 256, smr, s>>>(x, in_kind, nullptr, 0, work, nt, Nx, Ny, ply, twy, BR);
+  k_prior_rows<P, false><<<gr, 256, smr, s>>>(x, in_kind, nullptr, 0, work, nt, Nx, Ny, ply, twy, BR, fm);
   count_launches(1);
   k_prior_cols<P><<<gc, 256, smc, s>>>(work, lam, Nx, Ny, plx, twx, BC);
   count_launches(1);
-  k_prior_rows<P, true><<<gr, 256, smr, s>>>(nullptr, 0, y, out_kind, work, nt, Nx, Ny, ply, twy, BR);
+  k_prior_rows<P, true><<<gr, 256, smr, s>>>(nullptr, 0, y, out_kind, work, nt, Nx, Ny, ply, twy, BR, fm);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -316,6 +336,13 @@ cudaError_t launch_prior_dd(const void *x, int in_kind, void *y, int out_kind, i
                             int Ny, cdd *work, const dd *lam, const FftPlan &plx,
                             const FftPlan &ply, const cdd *twx, const cdd *twy, cudaStream_t s) {
   return prior<PolDD>(x, in_kind, y, out_kind, nt, Nx, Ny, work, lam, plx, ply, twx, twy, s);
+}
+cudaError_t launch_prior_d(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
+                           int Ny, cd *work, const double *lam, const FftPlan &plx,
+                           const FftPlan &ply, const cd *twx, const cd *twy, int map_per,
+                           int map_stride, int map_off, cudaStream_t s) {
+  return prior<PolD>(x, in_kind, y, out_kind, nt, Nx, Ny, work, lam, plx, ply, twx, twy, s,
+                     FieldMap{map_per, map_stride, map_off});
 }
 cudaError_t launch_prior_f(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
                            int Ny, cf *work, const float *lam, const FftPlan &plx,

@@ -40,6 +40,12 @@ __device__ __forceinline__ cf ld_cx<PolF>(const cf *p) {
   return cf_make(v.x, v.y);
 }
 
+template <>
+__device__ __forceinline__ cd ld_cx<PolD>(const cd *p) {
+  double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+  cd r; r.re = v.x; r.im = v.y; return r;
+}
+
 // twiddle W_M^t (forward) or its conjugate (inverse)
 template <class P, bool INV>
 __device__ __forceinline__ typename P::cx twid(const typename P::cx *tab, int t) {

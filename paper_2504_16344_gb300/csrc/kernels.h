@@ -40,6 +40,11 @@ cudaError_t launch_irfft_time_f(const cf *in, long in_ld, void *out, int out_kin
 cudaError_t launch_prior_dd(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
                             int Ny, cdd *work, const dd *lam, const FftPlan &plx,
                             const FftPlan &ply, const cdd *twx, const cdd *twy, cudaStream_t s);
+// native FP64 variant (set-up); output field t goes to (t/per)*stride + off + t%per
+cudaError_t launch_prior_d(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
+                           int Ny, cd *work, const double *lam, const FftPlan &plx,
+                           const FftPlan &ply, const cd *twx, const cd *twy, int map_per,
+                           int map_stride, int map_off, cudaStream_t s);
 cudaError_t launch_prior_f(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
                            int Ny, cf *work, const float *lam, const FftPlan &plx,
                            const FftPlan &ply, const cf *twx, const cf *twy, cudaStream_t s);

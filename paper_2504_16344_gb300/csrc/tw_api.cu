@@ -125,6 +125,49 @@ tw_status upload_twiddles(tw_ctx *c, int n, double denom, cdd **out_dd, cf **out
   return TW_OK;
 }
 
+tw_status upload_twiddles_d(tw_ctx *c, int n, double denom, cd **out) {
+  std::vector<cd> h(n);
+  for (int t = 0; t < n; ++t) {
+    const double a = -2.0 * kPi * (double)t / denom;
+    h[t].re = cos(a);
+    h[t].im = sin(a);
+  }
+  *out = (cd *)twh::dalloc(c, n * sizeof(cd));
+  if (!*out) return twh::fail(c, TW_ERR_OOM, "twiddle allocation");
+  TW_CUDA(c, cudaMemcpy(*out, h.data(), n * sizeof(cd), cudaMemcpyHostToDevice));
+  return TW_OK;
+}
+
+// G rows for F's block-column rows [row0, row0+nrows): G[t*Nd + row0 + r] =
+// C^{1/2} F_t[r, :], native FP64 filter, stored as float pairs.
+tw_status build_G_rows(tw_ctx *c, int row0, int nrows, const double *col, cudaStream_t s) {
+  const int Nt = c->Nt, Nd = c->Nd, Nm = c->Nm;
+  if (!c->G) {
+    c->G = (dd *)twh::dalloc(c, (size_t)Nt * Nd * Nm * sizeof(dd));
+    if (!c->G) return twh::fail(c, TW_ERR_OOM, "G buffer (tw_set_prior before tw_set_block_column)");
+  }
+  const int cap = 2 * ((Nt + 1) / 2);    // fields the spatial workspace holds
+  if (nrows <= cap) {
+    const int lags = cap / nrows;
+    for (int u0 = 0; u0 < Nt; u0 += lags) {
+      const int nl = std::min(lags, Nt - u0);
+      TW_CUDA(c, launch_prior_d(col + (size_t)u0 * nrows * Nm, 0, c->G, 1, nl * nrows, c->Nx, c->Ny,
+                                (cd *)c->ws, c->lamhd, c->plX, c->plY, c->twXd, c->twYd, nrows,
+                                Nd, u0 * Nd + row0, s));
+    }
+  } else {
+    for (int u = 0; u < Nt; ++u)
+      for (int r0 = 0; r0 < nrows; r0 += cap) {
+        const int nr = std::min(cap, nrows - r0);
+        TW_CUDA(c, launch_prior_d(col + ((size_t)u * nrows + r0) * Nm, 0, c->G, 1, nr, c->Nx,
+                                  c->Ny, (cd *)c->ws, c->lamhd, c->plX, c->plY, c->twXd, c->twYd,
+                                  1 << 30, 0, u * Nd + row0 + r0, s));
+      }
+  }
+  for (int r = row0; r < row0 + nrows; ++r) c->g_rows[r] = 1;
+  return TW_OK;
+}
+
 size_t op_elem_bytes(int fmt) { return fmt == FMT_DD ? sizeof(cdd) : 8; }
 
 int rows_of(const tw_ctx *c, int which) { return which == TW_MAP_F ? c->Nd : c->Nq; }
@@ -175,6 +218,9 @@ tw_status tw_create(tw_ctx **out, int Nd, int Nq, int Nx, int Ny, int Nt, double
   if (st == TW_OK) st = upload_twiddles(c, Nt + 1, 2.0 * Nt, &c->twL, &c->twLf);
   if (st == TW_OK) st = upload_twiddles(c, Nx, Nx, &c->twX, &c->twXf);
   if (st == TW_OK) st = upload_twiddles(c, Ny, Ny, &c->twY, &c->twYf);
+  if (st == TW_OK) st = upload_twiddles_d(c, Nx, Nx, &c->twXd);
+  if (st == TW_OK) st = upload_twiddles_d(c, Ny, Ny, &c->twYd);
+  c->g_rows.assign(Nd, 0);
   if (st == TW_OK) {
     const int nchunk = gemv_fwd_nchunk(c->Nm);
     c->wf = (cdd *)twh::dalloc(c, Nf * Nm * sizeof(cdd));
@@ -243,6 +289,12 @@ tw_status tw_set_block_column(tw_ctx *c, tw_map which, int row0, int nrows, cons
     TW_CUDA(c, cudaStreamSynchronize(s));
     twh::dfree(c, tmp);
   }
+  // with the prior known, keep G = Phi C^{1/2} of these rows for tw_factor_K,
+  // computed in FP64 from the caller's FP64 column
+  if (which == TW_MAP_F && c->prior_set) {
+    tw_status st = build_G_rows(c, row0, nrows, col, s);
+    if (st != TW_OK) return st;
+  }
   for (int r = row0; r < row0 + nrows; ++r) c->loaded[which][r] = 1;
   return TW_OK;
 }
@@ -269,6 +321,7 @@ tw_status tw_set_prior(tw_ctx *c, double nu, double ell, double var) {
   }
   std::vector<dd> l1(N), lh(N);
   std::vector<float> l1f(N), lhf(N);
+  std::vector<double> lhd(N);
   for (size_t i = 0; i < N; ++i) {
     const double lam = var * (double)N * s[i] / ssum;   // eigenvalue of C
     const double a = lam / (double)N, b = sqrt(lam) / (double)N;   // 1/N of the inverse DFT folded in
@@ -276,14 +329,20 @@ tw_status tw_set_prior(tw_ctx *c, double nu, double ell, double var) {
     split_dd(b, lh[i]);
     l1f[i] = (float)a;
     lhf[i] = (float)b;
+    lhd[i] = b;
   }
   if (!c->lam1) {
     c->lam1 = (dd *)twh::dalloc(c, N * sizeof(dd));
     c->lamh = (dd *)twh::dalloc(c, N * sizeof(dd));
     c->lam1f = (float *)twh::dalloc(c, N * sizeof(float));
     c->lamhf = (float *)twh::dalloc(c, N * sizeof(float));
-    if (!c->lam1 || !c->lamh || !c->lam1f || !c->lamhf) return twh::fail(c, TW_ERR_OOM, "prior tables");
+    c->lamhd = (double *)twh::dalloc(c, N * sizeof(double));
+    if (!c->lam1 || !c->lamh || !c->lam1f || !c->lamhf || !c->lamhd)
+      return twh::fail(c, TW_ERR_OOM, "prior tables");
   }
+  TW_CUDA(c, cudaMemcpy(c->lamhd, lhd.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+  // a new prior invalidates any G built with the old one
+  std::fill(c->g_rows.begin(), c->g_rows.end(), 0);
   TW_CUDA(c, cudaMemcpy(c->lam1, l1.data(), N * sizeof(dd), cudaMemcpyHostToDevice));
   TW_CUDA(c, cudaMemcpy(c->lamh, lh.data(), N * sizeof(dd), cudaMemcpyHostToDevice));
   TW_CUDA(c, cudaMemcpy(c->lam1f, l1f.data(), N * sizeof(float), cudaMemcpyHostToDevice));

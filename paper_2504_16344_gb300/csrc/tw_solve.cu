@@ -84,20 +84,29 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
   tw_status st = ensure_solve_workspace(c);
   if (st != TW_OK) return st;
 
-  // Phi (time-domain block column, rows u*Nd + s) from F^ by the inverse time FFT
-  dd *G = (dd *)twh::dalloc(c, (size_t)n * Nm * sizeof(dd));
-  if (!G) return twh::fail(c, TW_ERR_OOM, "G = Phi C^{1/2} buffer");
-  const long ld = (long)Nd * Nm;
-  TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->op[TW_MAP_F][FMT_DD], ld, G, 1, ld, (int)ld, Nt,
-                                  c->plT, c->twT, c->twL, s));
-  // G = Phi C^{1/2}: the square-root Matern filter on every row (a spatial field)
-  const int chunk = 2 * ((Nt + 1) / 2);
-  for (long r0 = 0; r0 < n; r0 += chunk) {
-    const int nr = (int)std::min<long>(chunk, n - r0);
-    dd *g = G + r0 * Nm;
-    TW_CUDA(c, launch_prior_dd(g, 1, g, 1, nr, c->Nx, c->Ny, c->ws, c->lamh, c->plX, c->plY,
-                               c->twX, c->twY, s));
+  // G = Phi C^{1/2}, rows u*Nd + s.  Normally built in FP64 while the block
+  // column was loaded (tw_set_prior first); otherwise Phi is recovered from
+  // the stored operator by the inverse time FFT (K then carries ~1e-14
+  // relative error from the double-float operator and filter).
+  bool have_G = c->G != nullptr;
+  for (char g : c->g_rows) have_G = have_G && g;
+  dd *G = c->G;
+  if (!have_G) {
+    if (!G) G = (dd *)twh::dalloc(c, (size_t)n * Nm * sizeof(dd));
+    if (!G) return twh::fail(c, TW_ERR_OOM, "G = Phi C^{1/2} buffer");
+    const long ld = (long)Nd * Nm;
+    TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->op[TW_MAP_F][FMT_DD], ld, G, 1, ld, (int)ld, Nt,
+                                    c->plT, c->twT, c->twL, s));
+    const int chunk = 2 * ((Nt + 1) / 2);
+    for (long r0 = 0; r0 < n; r0 += chunk) {
+      const int nr = (int)std::min<long>(chunk, n - r0);
+      dd *g = G + r0 * Nm;
+      TW_CUDA(c, launch_prior_dd(g, 1, g, 1, nr, c->Nx, c->Ny, c->ws, c->lamh, c->plX, c->plY,
+                                 c->twX, c->twY, s));
+    }
   }
+  c->G = nullptr;                       // consumed below
+  std::fill(c->g_rows.begin(), c->g_rows.end(), 0);
   // P = G G^T, then K = sigma^2 I + block-diagonal prefix sums of P
   dd *K = (dd *)twh::dalloc(c, (size_t)np * np * sizeof(dd));
   if (!K) { twh::dfree(c, G); return twh::fail(c, TW_ERR_OOM, "K buffer"); }
@@ -214,7 +223,7 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
   const bool mixed = prec != TW_PREC_FP64;
   if (prec < 0 || prec > 2 || !c->op[TW_MAP_F][prec])
     return twh::fail(c, TW_ERR_ARG, "requested precision was not kept at tw_create");
-  // solver of K y = d: the double-float factor, or (mixed operator path with
+  // solver of K y = d: the FP64 factor, or (mixed operator path with
   // TW_SOLVE_FP32_IR selected) the FP32 factor refined with the FP64 residual
   const bool use32 = mixed && c->have32 && (c->solver == TW_SOLVE_FP32_IR || !c->have64);
   if (use32 ? !c->have32 : !c->have64)

@@ -23,6 +23,9 @@ def make_context(cfg, keep=None, on_device_columns=False, chunk_rows=None, prior
     keep = tw.KEEP_FP64 if keep is None else keep
     ctx = tw.Context(cfg.Nd, cfg.Nq, cfg.Nx, cfg.Ny, cfg.Nt, cfg.Lx, cfg.Ly, keep=keep)
     dev = torch.device("cuda", ctx.device)
+    if prior:
+        # prior first: the context then forms K's factor G from the exact column
+        ctx.set_prior(cfg.nu, cfg.ell, cfg.var)
     for which, name, rows in ((tw.MAP_F, "F", cfg.Nd), (tw.MAP_FQ, "Fq", cfg.Nq)):
         step = chunk_rows or rows
         for r0 in range(0, rows, step):
@@ -33,7 +36,5 @@ def make_context(cfg, keep=None, on_device_columns=False, chunk_rows=None, prior
                 col = torch.from_numpy(synth.block_column(cfg, name, rows=range(r0, r0 + nr))).to(dev)
             ctx.set_block_column(which, r0, col)
             del col
-    if prior:
-        ctx.set_prior(cfg.nu, cfg.ell, cfg.var)
     torch.cuda.synchronize()
     return ctx

@@ -130,7 +130,7 @@ def test_forecast_of_posterior_mean(case):
 @pytest.mark.parametrize("solver", [0, 1])
 @pytest.mark.parametrize("prec", [1, 2])
 def test_posterior_mean_mixed_precision(case, prec, solver):
-    # solver 0: double-float factor; 1: FP32 factor + FP64-residual refinement
+    # solver 0: FP64 factor; 1: FP32 factor + FP64-residual refinement
     from paper_2504_16344_gb300 import tw
     cfg, ctx = case["cfg"], case["ctx"]
     m_ref, _ = Q.posterior_mean(case["F"], case["lam"], case["L"], case["d"], cfg.Nt)
