@@ -7,8 +7,8 @@
 //   * TwoSum (Knuth, TAOCP vol. 2): s + e == a + b exactly;
 //   * FastTwoSum (Dekker 1971): same when |a| >= |b|;
 //   * TwoProd via FMA: p + e == a * b exactly;
-//   * Dot2-style lazy accumulation (Ogita, Rump & Oishi 2005): a running
-//     float sum plus a float that collects the exact rounding errors.
+//   * running sums kept as renormalised float pairs, fed with exact
+//     products (the double-length accumulation of Dekker 1971).
 // The `_rn` intrinsics keep the compiler from fusing or reordering these.
 #pragma once
 #include <cuda_runtime.h>
@@ -92,31 +92,31 @@ __device__ __forceinline__ dd dd_from_double(double x) {
 }
 __device__ __forceinline__ double dd_to_double(dd a) { return (double)a.hi + (double)a.lo; }
 
-// ------------------------------------------------- lazy accumulation
-// value = s + t; t collects the exact rounding errors of the running sum.
+// ------------------------------------------------- accumulation
+// value = s + t, renormalised after every step (|t| <= ulp(s)/2), so each
+// step rounds at the 2^-48 level of the running sum; a float error term
+// that is left to grow would instead lose O(k^1.5 u^2) over k terms.
 struct dacc { float s, t; };
 __device__ __forceinline__ dacc dacc_zero() { dacc a; a.s = 0.f; a.t = 0.f; return a; }
-// A += sgn * a * b   (sgn = +1 or -1, folded into the operand signs)
+// A += a * b   (a sign is folded into the operands by the caller)
 __device__ __forceinline__ void dacc_mac(dacc &A, dd a, dd b) {
   float p = __fmul_rn(a.hi, b.hi);
-  float e = fmaf(a.hi, b.hi, -p);
+  float e = fmaf(a.hi, b.hi, -p);     // exact error of the leading product
   e = fmaf(a.hi, b.lo, e);
   e = fmaf(a.lo, b.hi, e);
   float s, r;
   two_sum(A.s, p, s, r);
-  A.s = s;
-  A.t = __fadd_rn(A.t, __fadd_rn(r, e));
+  r = __fadd_rn(r, __fadd_rn(A.t, e));
+  fast_two_sum(s, r, A.s, A.t);
 }
 __device__ __forceinline__ void dacc_add(dacc &A, dd a) {
   float s, r;
   two_sum(A.s, a.hi, s, r);
-  A.s = s;
-  A.t = __fadd_rn(A.t, __fadd_rn(r, a.lo));
+  r = __fadd_rn(r, __fadd_rn(A.t, a.lo));
+  fast_two_sum(s, r, A.s, A.t);
 }
-__device__ __forceinline__ dd dacc_get(dacc A) { return dd_make(A.s, A.t); }
-// The error term t of a lazy accumulator is itself a float, so over k terms
-// it contributes O(k u^2); long sums therefore fold short runs into a
-// renormalised double-float total every few terms.
+__device__ __forceinline__ dd dacc_get(dacc A) { dd r; r.hi = A.s; r.lo = A.t; return r; }
+// fold a partial sum into a double-float total and restart it
 __device__ __forceinline__ void dacc_fold(dd &tot, dacc &A) {
   tot = dd_add(tot, dacc_get(A));
   A = dacc_zero();

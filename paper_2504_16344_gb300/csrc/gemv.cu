@@ -59,8 +59,8 @@ k_gemv_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ yh, cdd *__r
   for (int s = threadIdx.x; s < Nr; s += blockDim.x) sy[s] = ld_cdd(yh + (size_t)w * Nr + s);
   __syncthreads();
   const int kb = blockIdx.x * (256 * ADJ_KPT) + threadIdx.x;
-  // Nr (<= a few hundred) terms per sum: the lazy accumulator's O(Nr u^2)
-  // error stays near 1e-13, so no folding here (it would cost occupancy)
+  // Nr (<= a few hundred) terms per sum: the renormalised accumulator
+  // needs no extra folding here (it would only cost registers)
   dacc re[ADJ_KPT], im[ADJ_KPT];
   bool ok[ADJ_KPT];
 #pragma unroll
