@@ -113,6 +113,15 @@ def test_prior_matches_library_fft2():
         assert _rel(P.prior_apply(x, lam, power), ref.reshape(x.shape)) < 1e-13
 
 
+def test_prior_matches_library_fft2_at_full_grid_to_rounding():
+    # the 200 x 250 grid of the 100-sensor workload: agreement to FP64 rounding
+    cfg = synth.CONFIGS[2]
+    lam = P.spectrum_for(cfg)
+    x = synth.white((2, cfg.Nm), 24)
+    ref = np.fft.ifft2(np.fft.fft2(x.reshape(-1, cfg.Nx, cfg.Ny)) * lam).real.reshape(x.shape)
+    assert _rel(P.prior_apply(x, lam), ref) < 2e-15
+
+
 def test_prior_dense_circulant_variance_and_spd(c1):
     lam = c1["lam"]
     C = P.dense_prior(lam)
