@@ -258,6 +258,25 @@ tw_status tw_profile_read(tw_ctx *ctx, double *ms, long long *calls, int reset);
 /* Number of CUDA kernels this library has enqueued in this process. */
 long long tw_kernel_launches(void);
 
+/*
+ * tw_p2o_apply_noalloc -- the same result as tw_p2o_apply, from a call that
+ * allocates nothing (the paper has no counterpart: this serves callers that
+ * must not allocate device memory after start-up, such as a real-time loop
+ * with a fixed footprint).  The per-chunk partial sums of the frequency GEMV,
+ * which tw_p2o_apply keeps in the context, live in a fixed 32 MiB device
+ * array inside the library; every GPU that loads the library holds it until
+ * the process exits.  Sizes whose partial sums exceed it,
+ * (Nt+1) * ceil(Nm/1024) * rows * (16 bytes FP64 path, 8 bytes FP32 paths),
+ * return TW_ERR_ARG with a message.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Nothing in the array needs clearing between
+ * calls; each call overwrites what it reads.
+ */
+tw_status tw_p2o_apply_noalloc(tw_ctx *ctx, tw_map which, tw_prec prec, int nrhs,
+                               const double *x, double *out, void *stream);
+
 /* Synchronise `stream` and report errors recorded by kernels (TW_OK,
  * TW_ERR_NOT_SPD, TW_ERR_TIMEOUT, TW_ERR_CUDA).  Clears the record. */
 tw_status tw_check(tw_ctx *ctx, void *stream);

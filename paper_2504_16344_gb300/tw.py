@@ -55,6 +55,7 @@ SIGNATURES = {
     "tw_profile_enable": (_S, [_P, _I]),
     "tw_profile_read": (_S, [_P, _P, _P, _I]),
     "tw_kernel_launches": (ctypes.c_longlong, []),
+    "tw_p2o_apply_noalloc": (_S, [_P, _I, _I, _I, _P, _P, _P]),
     "tw_check": (_S, [_P, _P]),
     "tw_device_bytes": (ctypes.c_size_t, [_P]),
 }
@@ -174,6 +175,19 @@ class Context:
             out = torch.empty((nrhs, self.Nt, self.rows(which)), dtype=torch.float64, device=x.device)
         po = _dev(out, torch.float64, (nrhs, self.Nt, self.rows(which)), "out")
         self._check(self.lib.tw_p2o_apply(self.h, which, prec, nrhs, px, po, _stream_ptr(stream)))
+        return out
+
+    def p2o_apply_noalloc(self, which, prec, x, out, stream=None):
+        """F x like p2o_apply, through the entry point that allocates nothing.
+
+        `out` must be given: this call path creates no tensors either.
+        """
+        import torch
+        nrhs = x.shape[0]
+        px = _dev(x, torch.float64, (nrhs, self.Nt, self.Nm), "x")
+        po = _dev(out, torch.float64, (nrhs, self.Nt, self.rows(which)), "out")
+        self._check(self.lib.tw_p2o_apply_noalloc(self.h, which, prec, nrhs, px, po,
+                                                  _stream_ptr(stream)))
         return out
 
     def p2o_adjoint(self, which, prec, y, out=None, stream=None):
