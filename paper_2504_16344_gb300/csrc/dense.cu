@@ -63,10 +63,25 @@ template <> __device__ __forceinline__ double ld_cg<double>(const double *p) { r
 // -------------------------------------------------------------- GEMM NT
 // C[tile (I,J)] = (subtract ? C - S : S),  S = sum_k A[i][k] B[j][k]
 // A rows >= arows and B rows >= brows are zero.  lower: skip J > I.
-template <class T>
+// Products accumulate in T over chunks of 16 and the chunk sums are added
+// into totals of type TC: for K's formation T = dd (double-float products,
+// FP32 pipe) and TC = double, so the long sum over Nm rounds at FP64's 2^-53
+// rather than at double-float's 2^-48 of the running total.
+template <class T, class TC> struct Fold;
+template <class T> struct Fold<T, T> {
+  static __device__ __forceinline__ void run(T &tot, typename DS<T>::acc &a) { DS<T>::fold(tot, a); }
+};
+template <> struct Fold<dd, double> {
+  static __device__ __forceinline__ void run(double &tot, dacc &a) {
+    tot += (double)a.s + (double)a.t;
+    a = dacc_zero();
+  }
+};
+
+template <class T, class TC = T>
 __global__ void __launch_bounds__(256)
 k_gemm_nt(const T *__restrict__ A, long lda, int arows, const T *__restrict__ B, long ldb,
-          int brows, int kdim, T *__restrict__ C, long ldc, int lower, int subtract) {
+          int brows, int kdim, TC *__restrict__ C, long ldc, int lower, int subtract) {
   typedef DS<T> S;
   constexpr int KC = 16;
   __shared__ T As[KC][NB_ + 4];
@@ -75,11 +90,11 @@ k_gemm_nt(const T *__restrict__ A, long lda, int arows, const T *__restrict__ B,
   if (lower && J > I) return;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   typename S::acc acc[4][4];
-  T tot[4][4];
+  TC tot[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) { acc[u][v] = S::zero(); tot[u][v] = S::zerov(); }
+    for (int v = 0; v < 4; ++v) { acc[u][v] = S::zero(); tot[u][v] = DS<TC>::zerov(); }
   const int lr = tid >> 2, lk = (tid & 3) * 4;   // loader: row, first k
   const long arow = (long)I * NB_ + lr, brow = (long)J * NB_ + lr;
   for (int k0 = 0; k0 < kdim; k0 += KC) {
@@ -106,7 +121,7 @@ k_gemm_nt(const T *__restrict__ A, long lda, int arows, const T *__restrict__ B,
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) S::fold(tot[u][v], acc[u][v]);
+      for (int v = 0; v < 4; ++v) Fold<T, TC>::run(tot[u][v], acc[u][v]);
     __syncthreads();
   }
 #pragma unroll
@@ -115,15 +130,15 @@ k_gemm_nt(const T *__restrict__ A, long lda, int arows, const T *__restrict__ B,
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const long j = (long)J * NB_ + tx * 4 + v;
-      T s = tot[u][v];
-      C[i * ldc + j] = subtract ? S::sub(C[i * ldc + j], s) : s;
+      TC s = tot[u][v];
+      C[i * ldc + j] = subtract ? DS<TC>::sub(C[i * ldc + j], s) : s;
     }
   }
 }
 
 // ------------------------------------------- K from P: block-diagonal prefix
 // K[(t+delta)Nd + a][t Nd + b] += K[(t+delta-1)Nd + a][(t-1)Nd + b], t = 1..Nt-1-delta
-__global__ void k_prefix_diag(dd *__restrict__ K, long ldk, int Nd, int Nt) {
+__global__ void k_prefix_diag(double *__restrict__ K, long ldk, int Nd, int Nt) {
   const long per = (long)Nd * Nd;
   const long total = (long)Nt * per;
   for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -131,22 +146,21 @@ __global__ void k_prefix_diag(dd *__restrict__ K, long ldk, int Nd, int Nt) {
     const int delta = (int)(idx / per);
     const int a = (int)((idx % per) / Nd), b = (int)(idx % Nd);
     if (delta == 0 && b > a) continue;
-    dd run = ldT(K + ((long)delta * Nd + a) * ldk + b);   // t = 0 term
+    double run = ldT(K + ((long)delta * Nd + a) * ldk + b);   // t = 0 term
     for (int t = 1; t + delta < Nt; ++t) {
-      dd *p = K + ((long)(t + delta) * Nd + a) * ldk + (long)t * Nd + b;
-      run = dd_add(run, *p);
+      double *p = K + ((long)(t + delta) * Nd + a) * ldk + (long)t * Nd + b;
+      run += *p;
       *p = run;
     }
   }
 }
 
 // diagonal: += sigma^2 inside, 1 on the padding
-__global__ void k_diag_set(dd *__restrict__ K, long ldk, int n, int n_pad, dd s2) {
+__global__ void k_diag_set(double *__restrict__ K, long ldk, int n, int n_pad, double s2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_pad) return;
-  dd *p = K + (long)i * ldk + i;
-  if (i < n) *p = dd_add(*p, s2);
-  else { p->hi = 1.f; p->lo = 0.f; }
+  double *p = K + (long)i * ldk + i;
+  *p = (i < n) ? *p + s2 : 1.0;
 }
 
 // ----------------------------------------------- Cholesky: diagonal block
@@ -281,17 +295,6 @@ __global__ void k_pack(const T *__restrict__ K, long ldk, T *__restrict__ P, int
   }
 }
 
-// full matrix in place: dd -> IEEE double (hi + lo is exact in binary64)
-__global__ void k_dd_to_double_inplace(void *__restrict__ K, long ld, int NB) {
-  const int I = blockIdx.y, J = blockIdx.x;
-  if (J > I) return;
-  for (int idx = threadIdx.x; idx < NB_ * NB_; idx += blockDim.x) {
-    const int r = idx / NB_, c = idx % NB_;
-    const long o = ((long)I * NB_ + r) * ld + (long)J * NB_ + c;
-    const dd v = reinterpret_cast<const dd *>(K)[o];
-    reinterpret_cast<double *>(K)[o] = (double)v.hi + (double)v.lo;
-  }
-}
 // packed blocks of a double factor -> dd packed blocks (hi = rn(x), lo = rn(x - hi))
 __global__ void k_double_to_dd(const double *__restrict__ a, dd *__restrict__ b, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -317,14 +320,13 @@ __global__ void k_pack_d2dd(const double *__restrict__ K, long ldk, dd *__restri
 }
 
 // full dd matrix (lower tiles) -> float
-__global__ void k_lower_to_float(const dd *__restrict__ K, float *__restrict__ K32, long ld, int NB) {
+__global__ void k_lower_to_float(const double *__restrict__ K, float *__restrict__ K32, long ld, int NB) {
   const int I = blockIdx.y, J = blockIdx.x;
   if (J > I) return;
   for (int idx = threadIdx.x; idx < NB_ * NB_; idx += blockDim.x) {
     const int r = idx / NB_, c = idx % NB_;
     const long o = ((long)I * NB_ + r) * ld + (long)J * NB_ + c;
-    const dd v = K[o];
-    K32[o] = __fadd_rn(v.hi, v.lo);
+    K32[o] = __double2float_rn(K[o]);
   }
 }
 
@@ -608,24 +610,21 @@ template <class KER> void smem_attr(KER k, size_t bytes) {
 }  // namespace
 
 // ======================================================================= host
-cudaError_t launch_form_P(const dd *G, long ldg, int n, int kdim, dd *K, long ldk, int NB,
+cudaError_t launch_form_P(const dd *G, long ldg, int n, int kdim, double *K, long ldk, int NB,
                           cudaStream_t s) {
-  k_gemm_nt<dd><<<dim3(NB, NB), 256, 0, s>>>(G, ldg, n, G, ldg, n, kdim, K, ldk, 1, 0);
+  k_gemm_nt<dd, double><<<dim3(NB, NB), 256, 0, s>>>(G, ldg, n, G, ldg, n, kdim, K, ldk, 1, 0);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_K_from_P(dd *K, long ldk, int Nd, int Nt, int n, int n_pad, double sigma2,
+cudaError_t launch_K_from_P(double *K, long ldk, int Nd, int Nt, int n, int n_pad, double sigma2,
                             cudaStream_t s) {
   const long total = (long)Nt * Nd * Nd;
   long blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   k_prefix_diag<<<(unsigned)blocks, 256, 0, s>>>(K, ldk, Nd, Nt);
   count_launches(1);
-  dd s2;
-  s2.hi = (float)sigma2;
-  s2.lo = (float)(sigma2 - (double)s2.hi);
-  k_diag_set<<<(n_pad + 255) / 256, 256, 0, s>>>(K, ldk, n, n_pad, s2);
+  k_diag_set<<<(n_pad + 255) / 256, 256, 0, s>>>(K, ldk, n, n_pad, sigma2);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -673,11 +672,6 @@ cudaError_t launch_pack_d2dd(const double *K, long ldk, dd *P, int NB, cudaStrea
   count_launches(1);
   return cudaGetLastError();
 }
-cudaError_t launch_dd_to_double_inplace(void *K, long ld, int NB, cudaStream_t s) {
-  k_dd_to_double_inplace<<<dim3(NB, NB), 256, 0, s>>>(K, ld, NB);
-  count_launches(1);
-  return cudaGetLastError();
-}
 cudaError_t launch_double_to_dd(const double *a, dd *b, size_t n, cudaStream_t s) {
   k_double_to_dd<<<152 * 16, 256, 0, s>>>(a, b, n);
   count_launches(1);
@@ -694,7 +688,7 @@ cudaError_t launch_pack_f(const float *K, long ldk, float *P, int NB, cudaStream
   count_launches(1);
   return cudaGetLastError();
 }
-cudaError_t launch_lower_to_float(const dd *K, float *K32, long ld, int NB, cudaStream_t s) {
+cudaError_t launch_lower_to_float(const double *K, float *K32, long ld, int NB, cudaStream_t s) {
   k_lower_to_float<<<dim3(NB, NB), 256, 0, s>>>(K, K32, ld, NB);
   count_launches(1);
   return cudaGetLastError();

@@ -6,22 +6,21 @@
 
 namespace tw {
 
-// P = G G^T (lower 64x64 tiles) into K; G: [n][kdim] dd, row stride ldg
-cudaError_t launch_form_P(const dd *G, long ldg, int n, int kdim, dd *K, long ldk, int NB,
+// P = G G^T (lower 64x64 tiles) into K (FP64); G: [n][kdim] dd, row stride ldg
+cudaError_t launch_form_P(const dd *G, long ldg, int n, int kdim, double *K, long ldk, int NB,
                           cudaStream_t s);
-// K = sigma2 I + block-diagonal prefix sums of P (in place), identity padding
-cudaError_t launch_K_from_P(dd *K, long ldk, int Nd, int Nt, int n, int n_pad, double sigma2,
+// K = sigma2 I + block-diagonal prefix sums of P (in place, FP64), identity padding
+cudaError_t launch_K_from_P(double *K, long ldk, int Nd, int Nt, int n, int n_pad, double sigma2,
                             cudaStream_t s);
 // blocked Cholesky in place (lower), inverses of the diagonal blocks to inv
 cudaError_t launch_cholesky_f(float *K, long ldk, int NB, float *inv, int *err, cudaStream_t s);
 cudaError_t launch_cholesky_d(double *K, long ldk, int NB, double *inv, int *err, cudaStream_t s);
 cudaError_t launch_pack_d(const double *K, long ldk, double *P, int NB, cudaStream_t s);
 cudaError_t launch_pack_d2dd(const double *K, long ldk, dd *P, int NB, cudaStream_t s);
-cudaError_t launch_dd_to_double_inplace(void *K, long ld, int NB, cudaStream_t s);
 cudaError_t launch_double_to_dd(const double *a, dd *b, size_t n, cudaStream_t s);
 cudaError_t launch_pack_dd(const dd *K, long ldk, dd *P, int NB, cudaStream_t s);
 cudaError_t launch_pack_f(const float *K, long ldk, float *P, int NB, cudaStream_t s);
-cudaError_t launch_lower_to_float(const dd *K, float *K32, long ld, int NB, cudaStream_t s);
+cudaError_t launch_lower_to_float(const double *K, float *K32, long ld, int NB, cudaStream_t s);
 // triangular solves (fwd: L z = b; bwd: L^T x = z), rhs kind 0 double / 1 dd / 2 float
 // prog: two ints (ticket, rows finished), zeroed by the launcher
 cudaError_t launch_trsv_d(const double *Lp, const double *Linv, const void *rhs, int rhs_kind,

@@ -108,9 +108,9 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
   c->G = nullptr;                       // consumed below
   std::fill(c->g_rows.begin(), c->g_rows.end(), 0);
   // P = G G^T, then K = sigma^2 I + block-diagonal prefix sums of P
-  dd *K = (dd *)twh::dalloc(c, (size_t)np * np * sizeof(dd));
+  double *K = (double *)twh::dalloc(c, (size_t)np * np * sizeof(double));
   if (!K) { twh::dfree(c, G); return twh::fail(c, TW_ERR_OOM, "K buffer"); }
-  TW_CUDA(c, cudaMemsetAsync(K, 0, (size_t)np * np * sizeof(dd), s));
+  TW_CUDA(c, cudaMemsetAsync(K, 0, (size_t)np * np * sizeof(double), s));
   TW_CUDA(c, launch_form_P(G, Nm, (int)n, Nm, K, np, c->NB, s));
   TW_CUDA(c, cudaStreamSynchronize(s));
   twh::dfree(c, G);
@@ -122,7 +122,7 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
   // tw_apply_K and residual certificates use it
   if (!c->Kp64) c->Kp64 = (dd *)twh::dalloc(c, nblk * blk * sizeof(dd));
   if (!c->Kp64) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "packed K"); }
-  TW_CUDA(c, launch_pack_dd(K, np, c->Kp64, c->NB, s));
+  TW_CUDA(c, launch_pack_d2dd(K, np, c->Kp64, c->NB, s));
   // mixed path: FP32 factor
   if (want32) {
     if (!c->Lp32) c->Lp32 = (float *)twh::dalloc(c, nblk * blk * sizeof(float));
@@ -154,11 +154,11 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
       if (cs == TW_OK) break;
       if (cs != TW_ERR_NOT_SPD || attempt == 3) { twh::dfree(c, K32); twh::dfree(c, K); return cs; }
       // shift relative to the largest diagonal entry (read back once)
-      std::vector<dd> dg(np);
-      TW_CUDA(c, cudaMemcpy2D(dg.data(), sizeof(dd), K, (np + 1) * sizeof(dd), sizeof(dd), np,
-                              cudaMemcpyDeviceToHost));
+      std::vector<double> dg(np);
+      TW_CUDA(c, cudaMemcpy2D(dg.data(), sizeof(double), K, (np + 1) * sizeof(double),
+                              sizeof(double), np, cudaMemcpyDeviceToHost));
       double dmax = 0.0;
-      for (long i = 0; i < n; ++i) dmax = std::max(dmax, (double)dg[i].hi);
+      for (long i = 0; i < n; ++i) dmax = std::max(dmax, dg[i]);
       c->shift32 = (c->shift32 == 0.0) ? dmax * 1e-6 : c->shift32 * 10.0;
     }
     TW_CUDA(c, launch_pack_f(K32, np, c->Lp32, c->NB, s));
@@ -203,10 +203,8 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
     // The factorisation and the triangular solves run in native FP64: in
     // double-float the solves' cancellations amplify 2^-48 rounding by K's
     // conditioning (measured 10-30x the FP64 oracle's own error in y).
-    TW_CUDA(c, launch_dd_to_double_inplace(K, np, c->NB, s));
-    double *Kd = reinterpret_cast<double *>(K);
-    TW_CUDA(c, launch_cholesky_d(Kd, np, c->NB, c->inv64, c->d_err, s));
-    TW_CUDA(c, launch_pack_d(Kd, np, c->Lp64, c->NB, s));
+    TW_CUDA(c, launch_cholesky_d(K, np, c->NB, c->inv64, c->d_err, s));
+    TW_CUDA(c, launch_pack_d(K, np, c->Lp64, c->NB, s));
     tw_status cs = tw_check(c, stream);
     if (cs != TW_OK) { twh::dfree(c, K); return cs; }
     c->have64 = true;
