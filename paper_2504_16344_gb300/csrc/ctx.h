@@ -43,8 +43,10 @@ struct tw_ctx {
   double sigma2 = 0.0, shift32 = 0.0;
   bool have64 = false, have32 = false;
   double *Lp64 = nullptr, *inv64 = nullptr;                      // FP64 factor, packed 64x64 blocks
+  double *chF64 = nullptr, *chB64 = nullptr;                      // chain blocks of the solves
   tw::dd *Kp64 = nullptr;                                         // K, packed, double-float
   float *Lp32 = nullptr, *inv32 = nullptr;
+  float *chF32 = nullptr, *chB32 = nullptr;
   // solve workspaces
   tw::dd *vz = nullptr, *vy = nullptr, *vr = nullptr;          // [n_pad]
   double *zd = nullptr, *yd = nullptr;                         // [n_pad]

@@ -63,9 +63,9 @@ template <> __device__ __forceinline__ double ld_cg<double>(const double *p) { r
 // -------------------------------------------------------------- GEMM NT
 // C[tile (I,J)] = (subtract ? C - S : S),  S = sum_k A[i][k] B[j][k]
 // A rows >= arows and B rows >= brows are zero.  lower: skip J > I.
-// Products accumulate in T over chunks of 16 and the chunk sums are added
-// into totals of type TC: for K's formation T = dd (double-float products,
-// FP32 pipe) and TC = double, so the long sum over Nm rounds at FP64's 2^-53
+// Products accumulate in T over runs of 32 and the run sums are added into
+// totals of type TC: for K's formation T = dd (double-float products, FP32
+// pipe) and TC = double, so the long sum over Nm rounds at FP64's 2^-53
 // rather than at double-float's 2^-48 of the running total.
 template <class T, class TC> struct Fold;
 template <class T> struct Fold<T, T> {
@@ -117,11 +117,14 @@ k_gemm_nt(const T *__restrict__ A, long lda, int arows, const T *__restrict__ B,
 #pragma unroll
         for (int v = 0; v < 4; ++v) S::mac(acc[u][v], a[u], b[v]);
     }
-    // fold this chunk's compensated sums into the running totals
+    // fold the compensated chunk sums into the running totals every 32
+    // products (and after the last chunk)
+    if (((k0 / KC) & 1) || k0 + KC >= kdim) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) Fold<T, TC>::run(tot[u][v], acc[u][v]);
+        for (int v = 0; v < 4; ++v) Fold<T, TC>::run(tot[u][v], acc[u][v]);
+    }
     __syncthreads();
   }
 #pragma unroll
@@ -361,12 +364,37 @@ template <> __device__ __forceinline__ float ldg_t<float>(const float *p) { retu
 template <> __device__ __forceinline__ double ldg_t<double>(const double *p) { return __ldg(p); }
 
 // 16 consecutive elements of T from 16-byte-aligned storage, as vector loads
-template <class T>
-__device__ __forceinline__ void ld16(const T *__restrict__ p, T *v) {
-  const float4 *q = reinterpret_cast<const float4 *>(p);
-  float4 *o = reinterpret_cast<float4 *>(v);
+// (elements assigned one by one so the array stays in registers)
+template <class T> __device__ __forceinline__ void ld16(const T *__restrict__ p, T *v);
+template <> __device__ __forceinline__ void ld16<double>(const double *__restrict__ p, double *v) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
 #pragma unroll
-  for (int i = 0; i < (int)(16 * sizeof(T) / 16); ++i) o[i] = __ldg(q + i);
+  for (int i = 0; i < 8; ++i) { const double2 t = __ldg(q + i); v[2 * i] = t.x; v[2 * i + 1] = t.y; }
+}
+template <> __device__ __forceinline__ void ld16<float>(const float *__restrict__ p, float *v) {
+  const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 t = __ldg(q + i);
+    v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+  }
+}
+template <> __device__ __forceinline__ void ld16<dd>(const dd *__restrict__ p, dd *v) {
+  const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 t = __ldg(q + i);
+    v[2 * i].hi = t.x; v[2 * i].lo = t.y; v[2 * i + 1].hi = t.z; v[2 * i + 1].lo = t.w;
+  }
+}
+
+// column-wise slice of packed block (R, C): entries [q*16+u][c], u < 16
+template <class T>
+__device__ __forceinline__ void load_colslice(const T *__restrict__ Lp, int R, int C, int c, int q,
+                                              T *lv) {
+  const T *blk = Lp + packed_index(R, C) * NB_ * NB_ + (q * 16) * NB_ + c;
+#pragma unroll
+  for (int u = 0; u < 16; ++u) lv[u] = ldg_t(blk + u * NB_);
 }
 
 // this thread's 16 entries of the off-diagonal block used by row I against
@@ -387,17 +415,24 @@ __device__ __forceinline__ void load_block(const T *__restrict__ Lp, int I, int 
 // one counter `progress` (rows finished, counted from the start for FWD and
 // from the end for BWD) tells every CTA which results are ready.  A CTA reads
 // it once, consumes every ready block without further synchronisation, and
-// only waits near the diagonal; CTAs far behind the front poll slowly so the
-// counter's cache line is not flooded.  The diagonal block's inverse and the
-// right-hand side are loaded before any wait, off the critical path.
-// prog[0] = ticket, prog[1] = progress.
+// waits only for its last dependency; CTAs far behind the front poll slowly
+// so the counter's cache line is not flooded.
+//
+// The chain step is a single 64x64 product: with the diagonal inverse
+// applied ahead of time,
+//   FWD  z_I = Linv_I (b_I - sum_{J<I-1} L_IJ z_J)  -  M_I z_{I-1},
+//        M_I = Linv_I L_{I,I-1}
+//   BWD  x_I = Linv_I^T (y_I - sum_{J>I+1} L_JI^T x_J)  -  N_I^T-form x_{I+1},
+//        stored as C_I = L_{I+1,I} Linv_I so that x_I[c] -= sum_r C_I[r][c] x_{I+1}[r]
+// (M_I and C_I are formed at factor time).  prog[0] = ticket, prog[1] = progress.
 template <class T, bool FWD>
 __global__ void __launch_bounds__(256)
-k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restrict__ rhs,
-       int rhs_kind, T *__restrict__ out, int nrows, int NBw, int *prog, int *err,
-       int *abort_flag) {
+k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const T *__restrict__ Lchain,
+       const void *__restrict__ rhs, int rhs_kind, T *__restrict__ out, int nrows, int NBw,
+       int *prog, int *err, int *abort_flag) {
   typedef DS<T> S;
   __shared__ T sv[NB_];
+  __shared__ T sw[NB_];
   __shared__ T sred[4][NB_];
   __shared__ int sI, sP, sbail;
   const int tid = threadIdx.x;
@@ -413,25 +448,24 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restr
     if (ticket >= NBw) return;
     const int I = FWD ? ticket : NBw - 1 - ticket;
     const int ndep = ticket;                 // blocks this row depends on
-    // off the critical path: diagonal inverse entries and the right-hand side
-    T iv[16];
-    if (FWD) {
-      ld16(Linv + (size_t)I * NB_ * NB_ + r_f * NB_ + q_f * 16, iv);
-    } else {
-      const T *ib = Linv + (size_t)I * NB_ * NB_ + (q_b * 16) * NB_ + c_b;
-#pragma unroll
-      for (int u = 0; u < 16; ++u) iv[u] = ldg_t(ib + u * NB_);
-    }
     const int rrow = FWD ? r_f : c_b;
     const long gi = (long)I * NB_ + rrow;
     const bool owner = FWD ? (q_f == 0) : (tid < NB_);
     T bval = S::zerov();
     if (owner && gi < nrows) bval = ld_rhs<T>(rhs, rhs_kind, gi);
-    T tot = S::zerov();
+    // ---- bulk: every dependency but the last.  Both sweeps read blocks column-
+    // wise (for each u a warp reads 32 consecutive elements of row q*16+u):
+    //   FWD: acc[u] += L_IJ[q*16+u][c] z_J[c]        (16 row sums per thread)
+    //   BWD: acc    += L_JI[q*16+u][c] x_J[q*16+u]   (one column sum per thread)
+    T accs[FWD ? 16 : 1];
+#pragma unroll
+    for (int u = 0; u < (FWD ? 16 : 1); ++u) accs[u] = S::zerov();
+    const int nbulk = ndep > 0 ? ndep - 1 : 0;
     int d = 0;
     T lv[16];
-    if (ndep > 0) load_block<T, FWD>(Lp, I, FWD ? 0 : NBw - 1, r_f, q_f, c_b, q_b, lv);
-    while (d < ndep) {
+    // dependency d is block (I, d) for FWD and block (NBw-1-d, I) for BWD
+    if (nbulk > 0) load_colslice(Lp, FWD ? I : NBw - 1, FWD ? 0 : I, c_b, q_b, lv);
+    while (d < nbulk) {
       if (tid == 0) {
         int p = ld_acquire(prog + 1);
         if (p <= d) {
@@ -454,33 +488,45 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restr
       }
       __syncthreads();
       if (sbail) return;
-      const int dend = min(sP, ndep);
+      const int dend = min(sP, nbulk);
       for (; d < dend; ++d) {
         const int J = FWD ? d : NBw - 1 - d;
-        const T *zj = out + (long)J * NB_ + q * 16;
-        T zv[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) zv[u] = ld_cg(zj + u);
         // prefetch the next block (the stream does not depend on the chain)
         T nx[16];
-        if (d + 1 < ndep) load_block<T, FWD>(Lp, I, FWD ? d + 1 : NBw - 2 - d, r_f, q_f, c_b, q_b, nx);
-        typename S::acc a = S::zero();
+        if (d + 1 < nbulk) load_colslice(Lp, FWD ? I : NBw - 2 - d, FWD ? d + 1 : I, c_b, q_b, nx);
+        if (FWD) {
+          const T zc = ld_cg(out + (long)J * NB_ + c_b);
 #pragma unroll
-        for (int u = 0; u < 16; ++u) S::mac(a, lv[u], zv[u]);
-        S::fold(tot, a);
+          for (int u = 0; u < 16; ++u) accs[u] = S::add(accs[u], S::mul(lv[u], zc));
+        } else {
+          const T *zj = out + (long)J * NB_ + q_b * 16;
+          typename S::acc a = S::zero();
+#pragma unroll
+          for (int u = 0; u < 16; ++u) S::mac(a, lv[u], ld_cg(zj + u));
+          S::fold(accs[0], a);
+        }
 #pragma unroll
         for (int u = 0; u < 16; ++u) lv[u] = nx[u];
       }
       __syncthreads();   // sP is rewritten next round
     }
-    // sum the four partial sums of each row (FWD) / column (BWD); v = b - sum
+    // ---- v = b - bulk sum, w = Linv v (or Linv^T v): before the last dependency
     if (FWD) {
-      T s = tot;
-      s = S::add(s, S::shfl_xor(s, 1));
-      s = S::add(s, S::shfl_xor(s, 2));
-      if (owner) sv[r_f] = (gi < nrows) ? S::sub(bval, s) : S::zerov();
+      // row r = q*16+u: sum the 64 column partials (warp tree, then two warps per q)
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        T v = accs[u];
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) v = S::add(v, S::shfl_xor(v, m));
+        if ((tid & 31) == 0) sred[(tid >> 5) & 1][q_b * 16 + u] = v;
+      }
+      __syncthreads();
+      if (owner) {
+        const T s = S::add(sred[0][r_f], sred[1][r_f]);
+        sv[r_f] = (gi < nrows) ? S::sub(bval, s) : S::zerov();
+      }
     } else {
-      sred[q_b][c_b] = tot;
+      sred[q_b][c_b] = accs[0];
       __syncthreads();
       if (owner) {
         T s = S::add(S::add(sred[0][tid], sred[1][tid]), S::add(sred[2][tid], sred[3][tid]));
@@ -488,28 +534,116 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const void *__restr
       }
     }
     __syncthreads();
-    // diagonal block: out_I = Linv v (FWD) or Linv^T v (BWD)
-    typename S::acc a2 = S::zero();
+    {
+      // diagonal inverse entries: loaded here, after the bulk loop, to keep
+      // registers free while the off-diagonal blocks stream
+      T iv[16];
+      if (FWD) {
+        ld16(Linv + (size_t)I * NB_ * NB_ + r_f * NB_ + q_f * 16, iv);
+      } else {
+        const T *ib = Linv + (size_t)I * NB_ * NB_ + (q_b * 16) * NB_ + c_b;
 #pragma unroll
-    for (int u = 0; u < 16; ++u) S::mac(a2, iv[u], sv[q * 16 + u]);
-    if (FWD) {
-      T s = S::get(a2);
-      s = S::add(s, S::shfl_xor(s, 1));
-      s = S::add(s, S::shfl_xor(s, 2));
-      if (owner) out[gi] = (gi < nrows) ? s : S::zerov();
-    } else {
-      __syncthreads();
-      sred[q_b][c_b] = S::get(a2);
-      __syncthreads();
-      if (owner) {
-        T s = S::add(S::add(sred[0][tid], sred[1][tid]), S::add(sred[2][tid], sred[3][tid]));
-        out[gi] = (gi < nrows) ? s : S::zerov();
+        for (int u = 0; u < 16; ++u) iv[u] = ldg_t(ib + u * NB_);
+      }
+      typename S::acc a2 = S::zero();
+#pragma unroll
+      for (int u = 0; u < 16; ++u) S::mac(a2, iv[u], sv[q * 16 + u]);
+      if (FWD) {
+        T s = S::get(a2);
+        s = S::add(s, S::shfl_xor(s, 1));
+        s = S::add(s, S::shfl_xor(s, 2));
+        if (owner) sw[r_f] = s;
+      } else {
+        __syncthreads();
+        sred[q_b][c_b] = S::get(a2);
+        __syncthreads();
+        if (owner) sw[tid] = S::add(S::add(sred[0][tid], sred[1][tid]), S::add(sred[2][tid], sred[3][tid]));
       }
     }
+    // ---- the last dependency: one product with the chain block
+    T corr = S::zerov();
+    if (ndep > 0) {
+      // chain block entries: issued before the wait so they arrive during it
+      T cv[16];
+      if (FWD) {
+        ld16(Lchain + (size_t)I * NB_ * NB_ + r_f * NB_ + q_f * 16, cv);
+      } else {
+        const T *cb = Lchain + (size_t)I * NB_ * NB_ + (q_b * 16) * NB_ + c_b;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) cv[u] = ldg_t(cb + u * NB_);
+      }
+      if (tid == 0) {
+        const unsigned long long t0 = global_ns();
+        int p;
+        while ((p = ld_acquire(prog + 1)) < ndep) {
+          if (*(volatile int *)abort_flag) { sbail = 1; break; }
+          if (global_ns() - t0 > WAIT_LIMIT_NS) {
+            record_error(err, TW_ERR_TIMEOUT, FWD ? 3 : 4);
+            atomicExch(abort_flag, 1);
+            sbail = 1;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __syncthreads();
+      if (sbail) return;
+      const int J = FWD ? I - 1 : I + 1;
+      const T *zj = out + (long)J * NB_ + q * 16;
+      typename S::acc a3 = S::zero();
+#pragma unroll
+      for (int u = 0; u < 16; ++u) S::mac(a3, cv[u], ld_cg(zj + u));
+      if (FWD) {
+        T s = S::get(a3);
+        s = S::add(s, S::shfl_xor(s, 1));
+        s = S::add(s, S::shfl_xor(s, 2));
+        corr = s;
+      } else {
+        sred[q_b][c_b] = S::get(a3);
+        __syncthreads();
+        if (owner) corr = S::add(S::add(sred[0][tid], sred[1][tid]), S::add(sred[2][tid], sred[3][tid]));
+      }
+    } else {
+      __syncthreads();
+    }
+    if (owner) out[gi] = (gi < nrows) ? S::sub(sw[rrow], corr) : S::zerov();
     __threadfence();
     __syncthreads();
     // rows finish in order, so the counter is `ticket` here; publish ticket + 1
     if (tid == 0) st_release(prog + 1, ticket + 1);
+  }
+}
+
+// Chain blocks of the solves (formed once per factorisation):
+//   M_I = Linv_I L_{I,I-1}  (I >= 1)     C_I = L_{I+1,I} Linv_I  (I <= NB-2)
+template <class T>
+__global__ void __launch_bounds__(256)
+k_chain_blocks(const T *__restrict__ Lp, const T *__restrict__ Linv, T *__restrict__ Mf,
+               T *__restrict__ Cb, int NB) {
+  typedef DS<T> S;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T(*sA)[NB_ + 1] = reinterpret_cast<T(*)[NB_ + 1]>(smem_raw);
+  T(*sB)[NB_ + 1] = sA + NB_;
+  const int I = blockIdx.x, tid = threadIdx.x;
+  for (int which = 0; which < 2; ++which) {
+    const bool fwd = which == 0;
+    if (fwd ? I < 1 : I > NB - 2) continue;
+    const T *Lb = fwd ? Lp + packed_index(I, I - 1) * NB_ * NB_ : Lp + packed_index(I + 1, I) * NB_ * NB_;
+    const T *Iv = Linv + (size_t)I * NB_ * NB_;
+    __syncthreads();
+    for (int idx = tid; idx < NB_ * NB_; idx += blockDim.x) {
+      const int r = idx / NB_, c = idx % NB_;
+      sA[r][c] = fwd ? Iv[idx] : Lb[idx];     // left factor
+      sB[r][c] = fwd ? Lb[idx] : Iv[idx];     // right factor
+    }
+    __syncthreads();
+    T *dst = (fwd ? Mf : Cb) + (size_t)I * NB_ * NB_;
+    for (int idx = tid; idx < NB_ * NB_; idx += blockDim.x) {
+      const int r = idx / NB_, c = idx % NB_;
+      typename S::acc a = S::zero();
+      for (int k = 0; k < NB_; ++k) S::mac(a, sA[r][k], sB[k][c]);
+      dst[idx] = S::get(a);
+    }
   }
 }
 
@@ -696,37 +830,53 @@ cudaError_t launch_lower_to_float(const double *K, float *K32, long ld, int NB, 
 
 static int trsv_grid(int NBw) { return NBw < 152 * 4 ? NBw : 152 * 4; }
 
-cudaError_t launch_trsv_d(const double *Lp, const double *Linv, const void *rhs, int rhs_kind,
-                          double *out, int nrows, int NBw, int *prog, bool fwd, int *err,
-                          int *abort_flag, cudaStream_t s) {
+cudaError_t launch_trsv_d(const double *Lp, const double *Linv, const double *Lchain,
+                          const void *rhs, int rhs_kind, double *out, int nrows, int NBw,
+                          int *prog, bool fwd, int *err, int *abort_flag, cudaStream_t s) {
   if (NBw <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(prog, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (fwd)
-    k_trsv<double, true><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
-                                                         prog, err, abort_flag);
+    k_trsv<double, true><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, out,
+                                                         nrows, NBw, prog, err, abort_flag);
   else
-    k_trsv<double, false><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
-                                                          prog, err, abort_flag);
+    k_trsv<double, false><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, out,
+                                                          nrows, NBw, prog, err, abort_flag);
   count_launches(1);
   return cudaGetLastError();
 }
-cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const void *rhs, int rhs_kind,
-                          float *out, int nrows, int NBw, int *prog, bool fwd, int *err,
-                          int *abort_flag, cudaStream_t s) {
+cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const float *Lchain,
+                          const void *rhs, int rhs_kind, float *out, int nrows, int NBw, int *prog,
+                          bool fwd, int *err, int *abort_flag, cudaStream_t s) {
   if (NBw <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(prog, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   if (fwd)
-    k_trsv<float, true><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
-                                                        prog, err, abort_flag);
+    k_trsv<float, true><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, out,
+                                                        nrows, NBw, prog, err, abort_flag);
   else
-    k_trsv<float, false><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, rhs, rhs_kind, out, nrows, NBw,
-                                                         prog, err, abort_flag);
+    k_trsv<float, false><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, out,
+                                                         nrows, NBw, prog, err, abort_flag);
   count_launches(1);
   return cudaGetLastError();
 }
 
+cudaError_t launch_chain_blocks_d(const double *Lp, const double *Linv, double *Mf, double *Cb,
+                                  int NB, cudaStream_t s) {
+  const size_t sm = 2 * NB_ * (NB_ + 1) * sizeof(double);
+  smem_attr(k_chain_blocks<double>, sm);
+  k_chain_blocks<double><<<NB, 256, sm, s>>>(Lp, Linv, Mf, Cb, NB);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_chain_blocks_f(const float *Lp, const float *Linv, float *Mf, float *Cb, int NB,
+                                  cudaStream_t s) {
+  const size_t sm = 2 * NB_ * (NB_ + 1) * sizeof(float);
+  smem_attr(k_chain_blocks<float>, sm);
+  k_chain_blocks<float><<<NB, 256, sm, s>>>(Lp, Linv, Mf, Cb, NB);
+  count_launches(1);
+  return cudaGetLastError();
+}
 cudaError_t launch_residual(const dd *Kp, const dd *x, const double *d, dd *r, int nrows, int NBw,
                             cudaStream_t s) {
   if (NBw <= 0) return cudaSuccess;

@@ -23,12 +23,17 @@ cudaError_t launch_pack_f(const float *K, long ldk, float *P, int NB, cudaStream
 cudaError_t launch_lower_to_float(const double *K, float *K32, long ld, int NB, cudaStream_t s);
 // triangular solves (fwd: L z = b; bwd: L^T x = z), rhs kind 0 double / 1 dd / 2 float
 // prog: two ints (ticket, rows finished), zeroed by the launcher
-cudaError_t launch_trsv_d(const double *Lp, const double *Linv, const void *rhs, int rhs_kind,
-                          double *out, int nrows, int NBw, int *prog, bool fwd, int *err,
-                          int *abort_flag, cudaStream_t s);
-cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const void *rhs, int rhs_kind,
-                          float *out, int nrows, int NBw, int *prog, bool fwd, int *err,
-                          int *abort_flag, cudaStream_t s);
+// Lchain: M_I = Linv_I L_{I,I-1} (fwd) or C_I = L_{I+1,I} Linv_I (bwd), [NB][64][64]
+cudaError_t launch_trsv_d(const double *Lp, const double *Linv, const double *Lchain,
+                          const void *rhs, int rhs_kind, double *out, int nrows, int NBw,
+                          int *prog, bool fwd, int *err, int *abort_flag, cudaStream_t s);
+cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const float *Lchain,
+                          const void *rhs, int rhs_kind, float *out, int nrows, int NBw, int *prog,
+                          bool fwd, int *err, int *abort_flag, cudaStream_t s);
+cudaError_t launch_chain_blocks_d(const double *Lp, const double *Linv, double *Mf, double *Cb,
+                                  int NB, cudaStream_t s);
+cudaError_t launch_chain_blocks_f(const float *Lp, const float *Linv, float *Mf, float *Cb, int NB,
+                                  cudaStream_t s);
 // r = d - K x (packed lower K, df64); d == nullptr gives r = K x
 cudaError_t launch_residual(const dd *Kp, const dd *x, const double *d, dd *r, int nrows, int NBw,
                             cudaStream_t s);

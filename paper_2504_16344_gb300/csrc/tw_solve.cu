@@ -39,11 +39,11 @@ tw_status ensure_solve_workspace(tw_ctx *c) {
 tw_status solve64(tw_ctx *c, const void *b, int kind, int nrows, double *y, cudaStream_t s) {
   const int NBw = (nrows + NB_ - 1) / NB_;
   { twh::Phase p(c, TW_PH_TRSV_FWD, s);
-    TW_CUDA(c, launch_trsv_d(c->Lp64, c->inv64, b, kind, c->zd, nrows, NBw, c->counter, true,
-                             c->d_err, c->abort_flag, s)); }
+    TW_CUDA(c, launch_trsv_d(c->Lp64, c->inv64, c->chF64, b, kind, c->zd, nrows, NBw, c->counter,
+                             true, c->d_err, c->abort_flag, s)); }
   twh::Phase p(c, TW_PH_TRSV_BWD, s);
-  TW_CUDA(c, launch_trsv_d(c->Lp64, c->inv64, c->zd, 0, y, nrows, NBw, c->counter + 2, false,
-                           c->d_err, c->abort_flag, s));
+  TW_CUDA(c, launch_trsv_d(c->Lp64, c->inv64, c->chB64, c->zd, 0, y, nrows, NBw, c->counter + 2,
+                           false, c->d_err, c->abort_flag, s));
   return TW_OK;
 }
 
@@ -51,11 +51,11 @@ tw_status solve64(tw_ctx *c, const void *b, int kind, int nrows, double *y, cuda
 tw_status solve32(tw_ctx *c, const void *b, int kind, int nrows, float *y, cudaStream_t s) {
   const int NBw = (nrows + NB_ - 1) / NB_;
   { twh::Phase p(c, TW_PH_TRSV_FWD, s);
-    TW_CUDA(c, launch_trsv_f(c->Lp32, c->inv32, b, kind, c->fz, nrows, NBw, c->counter, true,
-                             c->d_err, c->abort_flag, s)); }
+    TW_CUDA(c, launch_trsv_f(c->Lp32, c->inv32, c->chF32, b, kind, c->fz, nrows, NBw, c->counter,
+                             true, c->d_err, c->abort_flag, s)); }
   twh::Phase p(c, TW_PH_TRSV_BWD, s);
-  TW_CUDA(c, launch_trsv_f(c->Lp32, c->inv32, c->fz, 2, y, nrows, NBw, c->counter + 2, false,
-                           c->d_err, c->abort_flag, s));
+  TW_CUDA(c, launch_trsv_f(c->Lp32, c->inv32, c->chB32, c->fz, 2, y, nrows, NBw, c->counter + 2,
+                           false, c->d_err, c->abort_flag, s));
   return TW_OK;
 }
 
@@ -162,6 +162,10 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
       c->shift32 = (c->shift32 == 0.0) ? dmax * 1e-6 : c->shift32 * 10.0;
     }
     TW_CUDA(c, launch_pack_f(K32, np, c->Lp32, c->NB, s));
+    if (!c->chF32) c->chF32 = (float *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(float));
+    if (!c->chB32) c->chB32 = (float *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(float));
+    if (!c->chF32 || !c->chB32) { twh::dfree(c, K32); twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "chain blocks"); }
+    TW_CUDA(c, launch_chain_blocks_f(c->Lp32, c->inv32, c->chF32, c->chB32, c->NB, s));
     TW_CUDA(c, cudaStreamSynchronize(s));
     twh::dfree(c, K32);
     c->have32 = true;
@@ -205,6 +209,10 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
     // conditioning (measured 10-30x the FP64 oracle's own error in y).
     TW_CUDA(c, launch_cholesky_d(K, np, c->NB, c->inv64, c->d_err, s));
     TW_CUDA(c, launch_pack_d(K, np, c->Lp64, c->NB, s));
+    if (!c->chF64) c->chF64 = (double *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(double));
+    if (!c->chB64) c->chB64 = (double *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(double));
+    if (!c->chF64 || !c->chB64) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "chain blocks"); }
+    TW_CUDA(c, launch_chain_blocks_d(c->Lp64, c->inv64, c->chF64, c->chB64, c->NB, s));
     tw_status cs = tw_check(c, stream);
     if (cs != TW_OK) { twh::dfree(c, K); return cs; }
     c->have64 = true;
