@@ -207,6 +207,23 @@ tw_status tw_apply_K(tw_ctx *ctx, int nrhs, const int *nt_window, const double *
                      void *stream);
 
 /*
+ * tw_sample_posterior -- posterior samples by perturb-then-condition, exact
+ * for the linear-Gaussian model: for each sample k with window Nt'
+ * (nt_window[k], NULL = Nt),
+ *   m_pr = Gamma_pr^{1/2} z_m,
+ *   s    = m_pr + Gamma_pr F'^T K'^{-1} (d' - F' m_pr - sigma z_n),
+ * whose covariance is Gamma_post = Gamma_pr - G* K^{-1} G (the Woodbury form
+ * of Phase 2) and whose mean is the posterior mean; this realises the paper's
+ * Gamma_post^{1/2} z draws.  The random draws are inputs: z_m [ns][Nt][Nm]
+ * and z_n [ns][Nt][Nd] (rows >= Nt' unused), d [ns][Nt][Nd] the data of each
+ * sample (rows >= Nt' unused), sigma the noise standard deviation used in K.
+ * samples [ns][Nt][Nm]; rows t >= Nt' hold the prior draw m_pr.  FP64 path.
+ */
+tw_status tw_sample_posterior(tw_ctx *ctx, int ns, const int *nt_window, const double *d,
+                              const double *z_m, const double *z_n, double sigma,
+                              double *samples, void *stream);
+
+/*
  * tw_forecast -- QoI forecast q = F_q m (Phase 4, q_map = F_q m_map):
  * m [nrhs][Nt][Nm] -> q [nrhs][Nt][Nq], the Toeplitz apply of the p2q map.
  */

@@ -49,7 +49,7 @@ struct tw_ctx {
   float *chF32 = nullptr, *chB32 = nullptr;
   // solve workspaces
   tw::dd *vz = nullptr, *vy = nullptr, *vr = nullptr;          // [n_pad]
-  double *zd = nullptr, *yd = nullptr;                         // [n_pad]
+  double *zd = nullptr, *yd = nullptr, *rd = nullptr, *ad = nullptr;   // [n_pad]
   float *fz = nullptr, *fy = nullptr;                          // [n_pad]
   int *counter = nullptr;     // [4]: forward (ticket, rows done), backward (ticket, rows done)
   int *abort_flag = nullptr;

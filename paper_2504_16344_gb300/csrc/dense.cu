@@ -388,6 +388,17 @@ template <> __device__ __forceinline__ void ld16<dd>(const dd *__restrict__ p, d
   }
 }
 
+// 4 x 4 tile of packed block (R, C): rows 4g..4g+3, columns 4h..4h+3 (row-major in v)
+template <class T>
+__device__ __forceinline__ void load_tile44(const T *__restrict__ Lp, int R, int C, int g, int h,
+                                            T *v) {
+  const T *blk = Lp + packed_index(R, C) * NB_ * NB_ + (g * 4) * NB_ + h * 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[i * 4 + j] = ldg_t(blk + i * NB_ + j);
+}
+
 // column-wise slice of packed block (R, C): entries [q*16+u][c], u < 16
 template <class T>
 __device__ __forceinline__ void load_colslice(const T *__restrict__ Lp, int R, int C, int c, int q,
@@ -434,6 +445,7 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const T *__restrict
   __shared__ T sv[NB_];
   __shared__ T sw[NB_];
   __shared__ T sred[4][NB_];
+  __shared__ T spart[16][NB_ + 1];
   __shared__ int sI, sP, sbail;
   const int tid = threadIdx.x;
   // FWD: row r, column quarter q (the four quarters of a row are adjacent lanes)
@@ -453,18 +465,24 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const T *__restrict
     const bool owner = FWD ? (q_f == 0) : (tid < NB_);
     T bval = S::zerov();
     if (owner && gi < nrows) bval = ld_rhs<T>(rhs, rhs_kind, gi);
-    // ---- bulk: every dependency but the last.  Both sweeps read blocks column-
-    // wise (for each u a warp reads 32 consecutive elements of row q*16+u):
-    //   FWD: acc[u] += L_IJ[q*16+u][c] z_J[c]        (16 row sums per thread)
-    //   BWD: acc    += L_JI[q*16+u][c] x_J[q*16+u]   (one column sum per thread)
-    T accs[FWD ? 16 : 1];
+    // ---- bulk: every dependency but the last.
+    //   FWD: thread (row group g = tid/16, column group h = tid%16) sums rows
+    //        4g..4g+3 of L_IJ over columns 4h..4h+3 (16 partials per row; each
+    //        half-warp reads whole 512-byte rows)
+    //   BWD: thread (column c, row quarter q): sum_u L_JI[q*16+u][c] x_J[q*16+u]
+    //        (for each u a warp reads 32 consecutive elements)
+    const int g_f = tid >> 4, h_f = tid & 15;
+    T accs[FWD ? 4 : 1];
 #pragma unroll
-    for (int u = 0; u < (FWD ? 16 : 1); ++u) accs[u] = S::zerov();
+    for (int u = 0; u < (FWD ? 4 : 1); ++u) accs[u] = S::zerov();
     const int nbulk = ndep > 0 ? ndep - 1 : 0;
     int d = 0;
     T lv[16];
     // dependency d is block (I, d) for FWD and block (NBw-1-d, I) for BWD
-    if (nbulk > 0) load_colslice(Lp, FWD ? I : NBw - 1, FWD ? 0 : I, c_b, q_b, lv);
+    if (nbulk > 0) {
+      if (FWD) load_tile44(Lp, I, 0, g_f, h_f, lv);
+      else load_colslice(Lp, NBw - 1, I, c_b, q_b, lv);
+    }
     while (d < nbulk) {
       if (tid == 0) {
         int p = ld_acquire(prog + 1);
@@ -493,11 +511,19 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const T *__restrict
         const int J = FWD ? d : NBw - 1 - d;
         // prefetch the next block (the stream does not depend on the chain)
         T nx[16];
-        if (d + 1 < nbulk) load_colslice(Lp, FWD ? I : NBw - 2 - d, FWD ? d + 1 : I, c_b, q_b, nx);
+        if (d + 1 < nbulk) {
+          if (FWD) load_tile44(Lp, I, d + 1, g_f, h_f, nx);
+          else load_colslice(Lp, NBw - 2 - d, I, c_b, q_b, nx);
+        }
         if (FWD) {
-          const T zc = ld_cg(out + (long)J * NB_ + c_b);
+          const T *zj = out + (long)J * NB_ + h_f * 4;
+          T zc[4];
 #pragma unroll
-          for (int u = 0; u < 16; ++u) accs[u] = S::add(accs[u], S::mul(lv[u], zc));
+          for (int j = 0; j < 4; ++j) zc[j] = ld_cg(zj + j);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) accs[i] = S::add(accs[i], S::mul(lv[i * 4 + j], zc[j]));
         } else {
           const T *zj = out + (long)J * NB_ + q_b * 16;
           typename S::acc a = S::zero();
@@ -512,17 +538,14 @@ k_trsv(const T *__restrict__ Lp, const T *__restrict__ Linv, const T *__restrict
     }
     // ---- v = b - bulk sum, w = Linv v (or Linv^T v): before the last dependency
     if (FWD) {
-      // row r = q*16+u: sum the 64 column partials (warp tree, then two warps per q)
+      // row r: sum its 16 column-group partials through shared memory
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        T v = accs[u];
-#pragma unroll
-        for (int m = 16; m >= 1; m >>= 1) v = S::add(v, S::shfl_xor(v, m));
-        if ((tid & 31) == 0) sred[(tid >> 5) & 1][q_b * 16 + u] = v;
-      }
+      for (int i = 0; i < 4; ++i) spart[h_f][g_f * 4 + i] = accs[i];
       __syncthreads();
       if (owner) {
-        const T s = S::add(sred[0][r_f], sred[1][r_f]);
+        T s = spart[0][r_f];
+#pragma unroll
+        for (int h = 1; h < 16; ++h) s = S::add(s, spart[h][r_f]);
         sv[r_f] = (gi < nrows) ? S::sub(bval, s) : S::zerov();
       }
     } else {
@@ -709,6 +732,19 @@ __global__ void k_double_to_dd_vec(const double *__restrict__ a, dd *__restrict_
   if (i < n) b[i] = dd_from_double(a[i]);
 }
 
+// r[i] = d[i] - a[i] - sigma z[i] for i < n (time-major data vectors, the
+// leading n = Nd Nt' rows; the rest of r is left alone)
+__global__ void k_sample_rhs(const double *__restrict__ d, const double *__restrict__ a,
+                             const double *__restrict__ z, double sigma, double *__restrict__ r, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = d[i] - a[i] - sigma * z[i];
+}
+// s[i] += x[i] (x double-float) for i < n
+__global__ void k_add_dd(double *__restrict__ s, const dd *__restrict__ x, long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) s[i] += dd_to_double(x[i]);
+}
+
 // x += delta (float) ; rows < nrows
 __global__ void k_axpy_dd_f(dd *__restrict__ x, const float *__restrict__ delta, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -891,6 +927,19 @@ cudaError_t launch_dd_to_double(const dd *a, double *b, int n, cudaStream_t s) {
 }
 cudaError_t launch_double_to_dd_vec(const double *a, dd *b, int n, cudaStream_t s) {
   k_double_to_dd_vec<<<(n + 255) / 256, 256, 0, s>>>(a, b, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_sample_rhs(const double *d, const double *a, const double *z, double sigma,
+                              double *r, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_sample_rhs<<<(n + 255) / 256, 256, 0, s>>>(d, a, z, sigma, r, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_add_dd(double *sv, const dd *x, long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_add_dd<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sv, x, n);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -39,6 +39,9 @@ cudaError_t launch_residual(const dd *Kp, const dd *x, const double *d, dd *r, i
                             cudaStream_t s);
 cudaError_t launch_dd_to_double(const dd *a, double *b, int n, cudaStream_t s);
 cudaError_t launch_double_to_dd_vec(const double *a, dd *b, int n, cudaStream_t s);
+cudaError_t launch_sample_rhs(const double *d, const double *a, const double *z, double sigma,
+                              double *r, int n, cudaStream_t s);
+cudaError_t launch_add_dd(double *sv, const dd *x, long n, cudaStream_t s);
 cudaError_t launch_axpy_dd_f(dd *x, const float *delta, int n, cudaStream_t s);
 cudaError_t launch_dd_to_f(const dd *a, float *b, int n, cudaStream_t s);
 cudaError_t launch_f_to_dd(const float *a, dd *b, int n, cudaStream_t s);

@@ -19,12 +19,14 @@ tw_status ensure_solve_workspace(tw_ctx *c) {
   c->vr = (dd *)twh::dalloc(c, np * sizeof(dd));
   c->zd = (double *)twh::dalloc(c, np * sizeof(double));
   c->yd = (double *)twh::dalloc(c, np * sizeof(double));
+  c->rd = (double *)twh::dalloc(c, np * sizeof(double));
+  c->ad = (double *)twh::dalloc(c, np * sizeof(double));
   c->fz = (float *)twh::dalloc(c, np * sizeof(float));
   c->fy = (float *)twh::dalloc(c, np * sizeof(float));
   c->counter = (int *)twh::dalloc(c, 4 * sizeof(int));
   c->abort_flag = (int *)twh::dalloc(c, sizeof(int));
   c->d_norm = (double *)twh::dalloc(c, 2 * sizeof(double));
-  if (!c->vz || !c->vy || !c->vr || !c->zd || !c->yd || !c->fz || !c->fy || !c->counter || !c->abort_flag || !c->d_norm)
+  if (!c->vz || !c->vy || !c->vr || !c->zd || !c->yd || !c->rd || !c->ad || !c->fz || !c->fy || !c->counter || !c->abort_flag || !c->d_norm)
     return twh::fail(c, TW_ERR_OOM, "solve workspace");
   TW_CUDA(c, cudaMemset(c->vz, 0, np * sizeof(dd)));
   TW_CUDA(c, cudaMemset(c->vy, 0, np * sizeof(dd)));
@@ -368,6 +370,55 @@ tw_status tw_apply_K(tw_ctx *c, int nrhs, const int *nt_window, const double *x,
     double *o = out + (size_t)r * Nt * Nd;
     TW_CUDA(c, launch_dd_to_double(c->vr, o, nrows, s));
     if (w < Nt) TW_CUDA(c, cudaMemsetAsync(o + nrows, 0, (size_t)(Nt - w) * Nd * sizeof(double), s));
+  }
+  return TW_OK;
+}
+
+tw_status tw_sample_posterior(tw_ctx *c, int ns, const int *nt_window, const double *d,
+                              const double *z_m, const double *z_n, double sigma, double *samples,
+                              void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (ns < 0 || (ns > 0 && (!d || !z_m || !z_n || !samples)))
+    return twh::fail(c, TW_ERR_ARG, "bad sample arguments");
+  if (!(sigma >= 0.0)) return twh::fail(c, TW_ERR_ARG, "sigma must be >= 0");
+  if (!c->have64 || !c->op[TW_MAP_F][FMT_DD])
+    return twh::fail(c, TW_ERR_STATE, "tw_sample_posterior needs the FP64 factor and operator");
+  cudaStream_t s = (cudaStream_t)stream;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  const int Nd = c->Nd, Nt = c->Nt, Nm = c->Nm, Nf = c->Nf;
+  const void *A = c->op[TW_MAP_F][FMT_DD];
+  for (int k = 0; k < ns; ++k) {
+    const int w = nt_window ? nt_window[k] : Nt;
+    if (w < 1 || w > Nt) return twh::fail(c, TW_ERR_ARG, "window must be in [1, Nt]");
+    const int nrows = Nd * w;
+    const size_t off_m = (size_t)k * Nt * Nm, off_d = (size_t)k * Nt * Nd;
+    double *sk = samples + off_m;
+    // m_pr = Gamma_pr^{1/2} z_m  (written to the output, which accumulates the sample)
+    { twh::Phase p(c, TW_PH_PRIOR, s);
+      TW_CUDA(c, launch_prior_dd(z_m + off_m, 0, sk, 0, Nt, c->Nx, c->Ny, c->ws, c->lamh, c->plX,
+                                 c->plY, c->twX, c->twY, s)); }
+    // a = F' m_pr (leading w blocks: they depend on m_pr[0..w-1] only)
+    { twh::Phase p(c, TW_PH_RFFT_PARAM, s);
+      TW_CUDA(c, launch_rfft_time_dd(sk, 0, Nm, w, c->wf, Nm, Nm, c->plT, c->twT, c->twL, s)); }
+    { twh::Phase p(c, TW_PH_GEMV_FWD, s);
+      TW_CUDA(c, launch_gemv_fwd_dd(A, FMT_DD, c->wf, c->part, c->wr, Nf, Nd, Nm, s)); }
+    { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
+      TW_CUDA(c, launch_irfft_time_dd(c->wr, Nd, c->ad, 0, Nd, Nd, w, c->plT, c->twT, c->twL, s)); }
+    // r = d' - F' m_pr - sigma z_n,  y = K'^{-1} r
+    TW_CUDA(c, launch_sample_rhs(d + off_d, c->ad, z_n + off_d, sigma, c->rd, nrows, s));
+    tw_status st = solve64(c, c->rd, 0, nrows, c->yd, s);
+    if (st != TW_OK) return st;
+    // s = m_pr + Gamma_pr F'^T y  (rows t >= w keep the prior draw)
+    { twh::Phase p(c, TW_PH_RFFT_DATA, s);
+      TW_CUDA(c, launch_rfft_time_dd(c->yd, 0, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
+    { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
+      TW_CUDA(c, launch_gemv_adj_dd(A, FMT_DD, c->wr, c->wf, Nf, Nd, Nm, s)); }
+    { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+      TW_CUDA(c, launch_irfft_time_dd(c->wf, Nm, c->wt, 1, Nm, Nm, w, c->plT, c->twT, c->twL, s)); }
+    { twh::Phase p(c, TW_PH_PRIOR, s);
+      TW_CUDA(c, launch_prior_dd(c->wt, 1, c->wt, 1, w, c->Nx, c->Ny, c->ws, c->lam1, c->plX,
+                                 c->plY, c->twX, c->twY, s)); }
+    TW_CUDA(c, launch_add_dd(sk, c->wt, (long)w * Nm, s));
   }
   return TW_OK;
 }

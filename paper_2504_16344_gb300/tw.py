@@ -49,6 +49,7 @@ SIGNATURES = {
     "tw_forecast": (_S, [_P, _I, _I, _P, _P, _P]),
     "tw_solve_K": (_S, [_P, _I, _I, _P, _P, _P, _P]),
     "tw_apply_K": (_S, [_P, _I, _P, _P, _P, _P]),
+    "tw_sample_posterior": (_S, [_P, _I, _P, _P, _P, _P, _D, _P, _P]),
     "tw_set_refinement": (_S, [_P, _I]),
     "tw_refinement_steps": (_I, [_P]),
     "tw_set_solver": (_S, [_P, _I]),
@@ -274,6 +275,19 @@ class Context:
         po = _dev(out, torch.float64, (nrhs, self.Nt, self.Nd), "out")
         self._check(self.lib.tw_apply_K(self.h, nrhs, self._windows(windows, nrhs), px, po,
                                         _stream_ptr(stream)))
+        return out
+
+    def sample_posterior(self, d, z_m, z_n, sigma, windows=None, out=None, stream=None):
+        """Perturb-then-condition posterior samples; d, z_n [ns][Nt][Nd], z_m [ns][Nt][Nm]."""
+        import torch
+        ns = z_m.shape[0]
+        pd = _dev(d, torch.float64, (ns, self.Nt, self.Nd), "d")
+        pzm = _dev(z_m, torch.float64, (ns, self.Nt, self.Nm), "z_m")
+        pzn = _dev(z_n, torch.float64, (ns, self.Nt, self.Nd), "z_n")
+        out = torch.empty_like(z_m) if out is None else out
+        po = _dev(out, torch.float64, (ns, self.Nt, self.Nm), "samples")
+        self._check(self.lib.tw_sample_posterior(self.h, ns, self._windows(windows, ns), pd, pzm,
+                                                 pzn, float(sigma), po, _stream_ptr(stream)))
         return out
 
     def forecast(self, prec, m, out=None, stream=None):

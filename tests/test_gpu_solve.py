@@ -158,3 +158,25 @@ def test_solve_residual_certificate_fp64(case):
     _, st = ctx.infer(tw.PREC_FP64, _t(case["d"], case["dev"]), stats=True)
     print(f"{cfg.cid}: FP64 residual {st.resid_rel:.2e}")
     assert 0.0 <= st.resid_rel < 1e-11
+
+
+@pytest.mark.parametrize("frac", [1.0, 0.4])
+def test_posterior_samples_match_oracle(case, frac):
+    # same draws on both sides: the perturb-then-condition sample is deterministic given z
+    cfg, ctx = case["cfg"], case["ctx"]
+    w = max(1, int(round(frac * cfg.Nt)))
+    zs = [synth.sample_z(cfg, k, cfg.Nt) for k in range(2)]
+    z_m = np.stack([z[0] for z in zs])
+    z_n = np.stack([z[1] for z in zs])
+    d2 = np.stack([case["d"], case["d"]])
+    got = ctx.sample_posterior(_t(d2, case["dev"]), _t(z_m, case["dev"]), _t(z_n, case["dev"]),
+                               case["sigma"], windows=[w, w]).cpu().numpy()
+    ctx.check()
+    for k in range(2):
+        ref = Q.posterior_sample(case["F"], case["lam"], case["L"], case["sigma"], case["d"],
+                                 z_m[k], z_n[k], w)
+        m_pr = P.prior_apply(z_m[k], case["lam"], 0.5)
+        err = rel(got[k], ref)
+        err_c = rel(got[k] - m_pr, ref - m_pr)      # the conditioning update alone
+        print(f"{cfg.cid}: sample {k} window {w} rel err {err:.2e}, update {err_c:.2e}")
+        assert err < 1e-11 and err_c < 1e-10
