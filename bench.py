@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--batch-steps", type=int, default=3)
     return p.parse_args()
 
 
@@ -246,6 +248,105 @@ def setup_context(cfg, dev, keep, sigma):
     return ctx, sigma, d, time.time() - t0
 
 
+def run_batch(args, ctx, cfg, sigma, d0, dev, barrier):
+    """The batched workload on the same operator: 64 events with uneven windows
+    (uniform on {100, 150, ..., 400}) plus 32 posterior samples of event 0 at
+    its window, one CUDA graph per precision; inputs made on the device."""
+    import torch
+
+    import synth
+    from paper_2504_16344_gb300 import tw
+
+    c4 = synth.CONFIGS[4]
+    E, S = c4.events, c4.samples
+    ws = [int(w) for w in synth.batch_windows(c4)]
+    ctx.reserve_batch(max(E, S))
+    # event data: d_e = F Gamma^{1/2} z_e + sigma z_n,e (event 0: the fixed data vector)
+    d = torch.empty((E, cfg.Nt, cfg.Nd), dtype=torch.float64, device=dev)
+    d[0] = d0[0]
+    for e in range(1, E):
+        z = torch.from_numpy(synth.event_z(c4, e)).to(dev)
+        dcl = ctx.p2o_apply(tw.MAP_F, tw.PREC_FP64, ctx.prior_apply(z, 0.5))[0]
+        d[e] = dcl + sigma * torch.from_numpy(synth.noise_z(c4, e)).to(dev)
+    zm = torch.empty((S, cfg.Nt, cfg.Nm), dtype=torch.float64, device=dev)
+    zn = torch.empty((S, cfg.Nt, cfg.Nd), dtype=torch.float64, device=dev)
+    for k in range(S):
+        a, b = synth.sample_z(c4, k, cfg.Nt)
+        zm[k] = torch.from_numpy(a).to(dev)
+        zn[k] = torch.from_numpy(b).to(dev)
+    ds = d[:1].expand(S, -1, -1).contiguous()
+    win_e = torch.tensor(ws, dtype=torch.int32, device=dev)
+    win_s = torch.full((S,), ws[0], dtype=torch.int32, device=dev)
+    m = torch.empty((E, cfg.Nt, cfg.Nm), dtype=torch.float64, device=dev)
+    q = torch.empty((E, cfg.Nt, cfg.Nq), dtype=torch.float64, device=dev)
+    smp = torch.empty((S, cfg.Nt, cfg.Nm), dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    out = {"workload": (f"{E} events, windows uniform on {{100,150,...,{cfg.Nt}}} (mean "
+                        f"{sum(ws) / len(ws):.0f} steps), + {S} posterior samples of event 0 at "
+                        f"window {ws[0]}; posterior means and forecasts of every event; operator of "
+                        "the 100-sensor 200x250-grid case"),
+           "right_hand_sides": E + S}
+    results = {}
+    for name, prec in (("fp64", tw.PREC_FP64), ("mixed_c64", tw.PREC_C64)):
+        if not ctx_has(ctx, prec):
+            continue
+        with torch.cuda.stream(stream):
+            def body():
+                ctx.infer_batch(prec, d, win_e, m, q, stream=stream)
+                ctx.sample_posterior_batch(prec, ds, zm, zn, sigma, win_s, out=smp, stream=stream)
+            body()                               # sets kernel attributes before capture
+            stream.synchronize()
+            with ctx.capture(stream) as cap:
+                body()
+            g = cap.graph
+            for _ in range(max(1, args.warmup // 3)):
+                g.launch(stream)
+            stream.synchronize()
+            ctx.check(stream)
+            ctx.profile_read(reset=True)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            l0 = tw.kernel_launches()
+            e0.record(stream)
+            for _ in range(args.batch_steps):
+                g.launch(stream)
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / args.batch_steps
+            # per-phase device times: one profiled uncaptured pass
+            ctx.profile(True)
+            body()
+            stream.synchronize()
+            ctx.profile(False)
+            ph = ctx.profile_read(reset=True)
+            ctx.check(stream)
+        results[name] = {"ms_per_batch": round(ms, 2),
+                         "ms_per_rhs": round(ms / (E + S), 3),
+                         "graph_kernels": g.kernel_count(),
+                         "phases_ms": {k: round(v[0], 2) for k, v in ph.items() if v[1]}}
+        g.close()
+        if name == "fp64":
+            m64, q64, s64 = m.clone(), q.clone(), smp.clone()
+        else:
+            results[name]["m_max_rel_err_vs_fp64"] = max(rel(m[e], m64[e]) for e in range(E))
+            results[name]["q_max_rel_err_vs_fp64"] = max(rel(q[e], q64[e]) for e in range(E))
+            results[name]["sample_max_rel_err_vs_fp64"] = max(rel(smp[k], s64[k]) for k in range(S))
+    out.update(results)
+    if "fp64" in results and "mixed_c64" in results:
+        out["mixed_speedup"] = round(results["fp64"]["ms_per_batch"] /
+                                     results["mixed_c64"]["ms_per_batch"], 3)
+    del m, q, smp, zm, zn, d, ds
+    ctx.reserve_batch(0)
+    torch.cuda.empty_cache()
+    return out
+
+
+def ctx_has(ctx, prec):
+    from paper_2504_16344_gb300 import tw
+    return prec == tw.PREC_FP64 or ctx.keep & tw.KEEP_C64
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -398,6 +499,10 @@ def run_ours(args):
                "d2h_bytes_per_step": int((mh.numel() + qh.numel()) * 8),
                "host_wall_ms": round(wall, 4), "path": "tw_infer + tw_forecast through libtw.so"}
 
+    batch = None
+    if not args.no_batch and not args.small:
+        batch = run_batch(args, ctx, cfg, sigma, d, dev, barrier)
+
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
         v, desc, spent = oracle_sample(cfg)
@@ -418,6 +523,7 @@ def run_ours(args):
         "gemv_fwd_Fq_gbs": round(bytes_fwd / (fwd_ms / fwd_calls * 1e-3) / 1e9, 1),
         "phases_ms": phase_ms,
         "mixed": mixed,
+        "batch": batch,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -294,6 +294,71 @@ long long tw_kernel_launches(void);
 tw_status tw_p2o_apply_noalloc(tw_ctx *ctx, tw_map which, tw_prec prec, int nrhs,
                                const double *x, double *out, void *stream);
 
+/*
+ * ---- Batches of right-hand sides (Phase 4 serving many events and
+ * posterior samples at once).  With B right-hand sides the solves become
+ * block products L_IJ x Z_J(64 x 8 columns) and each frequency's product
+ * F^(w)^H Y^(w) a matrix-matrix product, so the factor and the operator
+ * are streamed once per column slice instead of once per right-hand side.
+ *
+ * tw_reserve_batch -- allocate the workspaces of batches of up to bmax
+ * right-hand sides (about bmax * (Nt+1) * Nm * 16 bytes, plus a float-pair
+ * copy of the factor when an FP32 operator is kept); bmax = 0 frees them.
+ * Needs tw_factor_K (the FP64 factor); a later tw_factor_K refreshes the
+ * copy.  Set-up call: synchronises the device.  Once a batch is reserved,
+ * tw_infer (FP64 path, or mixed path with TW_SOLVE_FACTOR64), tw_forecast and
+ * tw_sample_posterior with several right-hand sides run as batches of up to
+ * bmax columns.
+ */
+tw_status tw_reserve_batch(tw_ctx *ctx, int bmax);
+
+/* Reserved batch size (0 if none, -1 if ctx is NULL). */
+int tw_batch_capacity(const tw_ctx *ctx);
+
+/*
+ * tw_infer_batch -- posterior means of nrhs <= bmax right-hand sides, and
+ * their forecasts when q != NULL, with the windows in DEVICE memory:
+ * nt_window_dev[r] in [0, Nt] (0: an empty slot, m and q come out zero).
+ * d [nrhs][Nt][Nd], m [nrhs][Nt][Nm], q [nrhs][Nt][Nq]; same results as
+ * tw_infer / tw_forecast.  prec TW_PREC_FP64 solves with the FP64 factor;
+ * the mixed precisions solve with its float-pair copy (48-bit), whatever
+ * tw_set_solver selected.  The call allocates nothing and never
+ * synchronises: it can be captured into a CUDA graph (tw_capture_begin)
+ * and relaunched after new data and windows are written to the same
+ * buffers.
+ */
+tw_status tw_infer_batch(tw_ctx *ctx, tw_prec prec, int nrhs, const int *nt_window_dev,
+                         const double *d, double *m, double *q, void *stream);
+
+/* tw_sample_posterior for ns <= bmax samples with windows in DEVICE memory
+ * (values in [0, Nt]); prec as tw_infer_batch.  No allocation, no
+ * synchronisation (capturable). */
+tw_status tw_sample_posterior_batch(tw_ctx *ctx, tw_prec prec, int ns, const int *nt_window_dev,
+                                    const double *d, const double *z_m, const double *z_n,
+                                    double sigma, double *samples, void *stream);
+
+/* q = F_q m for nrhs <= bmax parameter vectors; rows t >= nt_window_dev[r]
+ * of m are taken as zero (NULL: all rows).  Capturable. */
+tw_status tw_forecast_batch(tw_ctx *ctx, tw_prec prec, int nrhs, const int *nt_window_dev,
+                            const double *m, double *q, void *stream);
+
+/*
+ * CUDA graphs of batched calls.  tw_capture_begin starts capturing `stream`
+ * (a created stream, not NULL); the batched calls above then only record
+ * their work; tw_capture_end ends the capture and instantiates the graph.
+ * tw_graph_launch replays it on any stream: the recorded calls run again
+ * with whatever the captured buffers (data, windows) hold at that time.
+ * Make one uncaptured call of the same kind first, so every kernel's
+ * shared-memory attribute is already set.
+ */
+typedef struct tw_graph tw_graph;
+tw_status tw_capture_begin(tw_ctx *ctx, void *stream);
+tw_status tw_capture_end(tw_ctx *ctx, void *stream, tw_graph **out);
+tw_status tw_graph_launch(tw_graph *graph, void *stream);
+/* Kernel nodes in the graph (-1 on error). */
+int tw_graph_kernel_count(const tw_graph *graph);
+void tw_graph_destroy(tw_graph *graph);
+
 /* Synchronise `stream` and report errors recorded by kernels (TW_OK,
  * TW_ERR_NOT_SPD, TW_ERR_TIMEOUT, TW_ERR_CUDA).  Clears the record. */
 tw_status tw_check(tw_ctx *ctx, void *stream);

@@ -57,6 +57,17 @@ struct tw_ctx {
   int ir_steps = 3;
   int solver = TW_SOLVE_FACTOR64;
   double ir_probe_resid = 0.0;
+  // batched right-hand sides (tw_reserve_batch): RHS-major workspaces
+  int bmax = 0;
+  int *win_dev = nullptr;            // [bmax] windows of host-window batched calls
+  int *trsm_prog = nullptr;          // [2][trsm_prog_ints(bmax)] solve counters
+  double *bz = nullptr, *by = nullptr;      // [bmax][n_pad] FP64 solves
+  tw::dd *bzd = nullptr, *byd = nullptr;    // [bmax][n_pad] float-pair solves (mixed)
+  double *brd = nullptr;             // [bmax][Nt][Nd] data-side scratch (samples)
+  void *byh = nullptr;               // [bmax][Nf][Rmax] data-side spectra (16-byte entries)
+  void *bxh = nullptr;               // [bmax][Nf][Nm] parameter-side spectra / prior work
+  void *bpart = nullptr;             // [bmax][Nf][nchunk][Rmax] forward-product partial sums
+  tw::dd *Lp_dd = nullptr, *inv_dd = nullptr, *chF_dd = nullptr, *chB_dd = nullptr;
   // per-phase timing
   struct PhaseEv { int ph; cudaEvent_t a, b; };
   bool prof = false;
@@ -87,8 +98,21 @@ tw_status cuda_fail(tw_ctx *c, cudaError_t e, const char *where);
 void *dalloc(tw_ctx *c, size_t bytes);   // tracked cudaMalloc; nullptr on failure
 void dfree(tw_ctx *c, void *p);
 tw::FftPlan make_plan(int M);
+// float-pair copy of the FP64 factor for mixed batched solves (no-op unless reserved)
+tw_status refresh_dd_factor(tw_ctx *c, cudaStream_t s);
 
 }  // namespace twh
+
+// host-window calls routed to the batched path (tw_batch.cu)
+namespace twb {
+tw_status infer_host_windows(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window,
+                             const double *d, double *m, cudaStream_t s);
+tw_status sample_host_windows(tw_ctx *c, int ns, const int *nt_window, const double *d,
+                              const double *z_m, const double *z_n, double sigma, double *samples,
+                              cudaStream_t s);
+tw_status forecast_full(tw_ctx *c, tw_prec prec, int nrhs, const double *m, double *q,
+                        cudaStream_t s);
+}  // namespace twb
 
 #define TW_CUDA(c, call)                                             \
   do {                                                               \

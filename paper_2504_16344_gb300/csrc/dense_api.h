@@ -30,6 +30,18 @@ cudaError_t launch_trsv_d(const double *Lp, const double *Linv, const double *Lc
 cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const float *Lchain,
                           const void *rhs, int rhs_kind, float *out, int nrows, int NBw, int *prog,
                           bool fwd, int *err, int *abort_flag, cudaStream_t s);
+// batched solves (B right-hand sides, column b at rhs + b*rhs_bstride /
+// out + b*out_bstride, window win[b] time steps in device memory); prog:
+// trsm_prog_ints(B) ints, zeroed by the launcher
+int trsm_prog_ints(int B);
+cudaError_t launch_trsm_d(const double *Lp, const double *Linv, const double *Lchain,
+                          const void *rhs, int rhs_kind, long rhs_bstride, double *out,
+                          long out_bstride, const int *win, int Nd, int Nt, int B, int NB,
+                          int *prog, bool fwd, int *err, int *abort_flag, cudaStream_t s);
+cudaError_t launch_trsm_dd(const dd *Lp, const dd *Linv, const dd *Lchain, const void *rhs,
+                           int rhs_kind, long rhs_bstride, dd *out, long out_bstride,
+                           const int *win, int Nd, int Nt, int B, int NB, int *prog, bool fwd,
+                           int *err, int *abort_flag, cudaStream_t s);
 cudaError_t launch_chain_blocks_d(const double *Lp, const double *Linv, double *Mf, double *Cb,
                                   int NB, cudaStream_t s);
 cudaError_t launch_chain_blocks_f(const float *Lp, const float *Linv, float *Mf, float *Cb, int NB,

@@ -65,13 +65,40 @@ __device__ __forceinline__ void st_out<PolF>(void *base, int kind, long off, flo
   else reinterpret_cast<float *>(base)[off] = v;
 }
 
+// y[off] += v (the prior's accumulate mode; double and dd outputs)
+template <class P>
+__device__ __forceinline__ void add_out(void *base, int kind, long off, typename P::re v);
+template <>
+__device__ __forceinline__ void add_out<PolDD>(void *base, int kind, long off, dd v) {
+  if (kind == 0) {
+    double *p = reinterpret_cast<double *>(base) + off;
+    *p = *p + dd_to_double(v);
+  } else if (kind == 1) {
+    dd *p = reinterpret_cast<dd *>(base) + off;
+    *p = dd_add(*p, v);
+  } else {
+    float *p = reinterpret_cast<float *>(base) + off;
+    *p = *p + __fadd_rn(v.hi, v.lo);
+  }
+}
+template <>
+__device__ __forceinline__ void add_out<PolF>(void *base, int kind, long off, float v) {
+  if (kind == 0) { double *p = reinterpret_cast<double *>(base) + off; *p = *p + (double)v; }
+  else if (kind == 1) { dd *p = reinterpret_cast<dd *>(base) + off; dd t; t.hi = v; t.lo = 0.f; *p = dd_add(*p, t); }
+  else { float *p = reinterpret_cast<float *>(base) + off; *p = *p + v; }
+}
+template <>
+__device__ __forceinline__ void add_out<PolD>(void *base, int kind, long off, double v) {
+  if (kind == 0) { double *p = reinterpret_cast<double *>(base) + off; *p = *p + v; }
+}
+
 // --------------------------------------------------------- time axis
 template <class P>
 __global__ void __launch_bounds__(256)
 k_rfft_time(const void *__restrict__ in, int in_kind, long in_ld, int n_in,
             typename P::cx *__restrict__ out, long out_ld, int N, FftPlan pl,
             const typename P::cx *__restrict__ twM, const typename P::cx *__restrict__ twL,
-            int B) {
+            int B, BatchArg ba) {
   typedef typename P::cx cx;
   typedef typename P::re re;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -79,7 +106,10 @@ k_rfft_time(const void *__restrict__ in, int in_kind, long in_ld, int n_in,
   cx *buf0 = reinterpret_cast<cx *>(smem_raw);
   cx *buf1 = buf0 + (M + 1) * B;
   const long n0 = (long)blockIdx.x * B;
-  const int nin = min(n_in, M);
+  const int bz = blockIdx.y;
+  const int nin = min(ba.window(bz, n_in), M);
+  const long ioff = bz * ba.in_stride;
+  out += bz * ba.out_stride;
   // pack z_j = x_{2j} + i x_{2j+1}; x_t = 0 for t >= nin
   for (int idx = threadIdx.x; idx < M * B; idx += blockDim.x) {
     const int b = idx % B, j = idx / B;
@@ -87,8 +117,8 @@ k_rfft_time(const void *__restrict__ in, int in_kind, long in_ld, int n_in,
     re r = P::re_zero(), im = P::re_zero();
     if (n < N) {
       const int t0 = 2 * j, t1 = 2 * j + 1;
-      if (t0 < nin) r = ld_in<P>(in, in_kind, (long)t0 * in_ld + n);
-      if (t1 < nin) im = ld_in<P>(in, in_kind, (long)t1 * in_ld + n);
+      if (t0 < nin) r = ld_in<P>(in, in_kind, ioff + (long)t0 * in_ld + n);
+      if (t1 < nin) im = ld_in<P>(in, in_kind, ioff + (long)t1 * in_ld + n);
     }
     buf0[j * B + b] = P::make(r, im);
   }
@@ -113,7 +143,7 @@ __global__ void __launch_bounds__(256)
 k_irfft_time(const typename P::cx *__restrict__ in, long in_ld, void *__restrict__ out,
              int out_kind, long out_ld, int N, int n_keep, FftPlan pl,
              const typename P::cx *__restrict__ twM, const typename P::cx *__restrict__ twL,
-             typename P::re invM, int B) {
+             typename P::re invM, int B, BatchArg ba) {
   typedef typename P::cx cx;
   typedef typename P::re re;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -121,6 +151,10 @@ k_irfft_time(const typename P::cx *__restrict__ in, long in_ld, void *__restrict
   cx *buf0 = reinterpret_cast<cx *>(smem_raw);
   cx *buf1 = buf0 + (M + 1) * B;
   const long n0 = (long)blockIdx.x * B;
+  const int bz = blockIdx.y;
+  in += bz * ba.in_stride;
+  const long ooff = bz * ba.out_stride;
+  const int nkeep = ba.window(bz, n_keep);
   for (int idx = threadIdx.x; idx < (M + 1) * B; idx += blockDim.x) {
     const int b = idx % B, k = idx / B;
     const long n = n0 + b;
@@ -143,11 +177,11 @@ k_irfft_time(const typename P::cx *__restrict__ in, long in_ld, void *__restrict
     const long n = n0 + b;
     if (n >= N) continue;
     re v = P::re_zero();
-    if (t < n_keep) {
+    if (t < nkeep) {
       cx zz = z[(t >> 1) * B + b];
       v = P::re_mul((t & 1) ? P::imag(zz) : P::real(zz), invM);
     }
-    st_out<P>(out, out_kind, (long)t * out_ld + n, v);
+    st_out<P>(out, out_kind, ooff + (long)t * out_ld + n, v);
   }
 }
 
@@ -165,7 +199,7 @@ template <class P, bool INV>
 __global__ void __launch_bounds__(256)
 k_prior_rows(const void *__restrict__ x, int in_kind, void *__restrict__ y, int out_kind,
              typename P::cx *__restrict__ work, int nt, int Nx, int Ny, FftPlan ply,
-             const typename P::cx *__restrict__ twy, int BR, FieldMap fm) {
+             const typename P::cx *__restrict__ twy, int BR, FieldMap fm, BatchArg ba, int accum) {
   typedef typename P::cx cx;
   typedef typename P::re re;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -174,13 +208,29 @@ k_prior_rows(const void *__restrict__ x, int in_kind, void *__restrict__ y, int 
   const int tp = blockIdx.y;
   const int a0 = blockIdx.x * BR;
   const int t0 = 2 * tp, t1 = 2 * tp + 1;
+  const int bz = blockIdx.z;
+  // fields t >= ntb of this batch entry are zero (input) / written as zero
+  const int ntb = ba.window(bz, nt);
+  const long xoff = bz * ba.in_stride, yoff = bz * ba.out_stride;
+  work += bz * ba.work_stride;
+  if (t0 >= ntb) {
+    if (INV && !accum) {
+      for (int idx = threadIdx.x; idx < BR * Ny; idx += blockDim.x) {
+        const int j = idx % Ny, b = idx / Ny, a = a0 + b;
+        if (a >= Nx) continue;
+        st_out<P>(y, out_kind, yoff + ((long)fm(t0) * Nx + a) * Ny + j, P::re_zero());
+        if (t1 < nt) st_out<P>(y, out_kind, yoff + ((long)fm(t1) * Nx + a) * Ny + j, P::re_zero());
+      }
+    }
+    return;
+  }
   for (int idx = threadIdx.x; idx < BR * Ny; idx += blockDim.x) {
     const int j = idx % Ny, b = idx / Ny, a = a0 + b;
     cx v = P::zero();
     if (a < Nx) {
       if (!INV) {
-        re r = ld_in<P>(x, in_kind, ((long)t0 * Nx + a) * Ny + j);
-        re im = (t1 < nt) ? ld_in<P>(x, in_kind, ((long)t1 * Nx + a) * Ny + j) : P::re_zero();
+        re r = ld_in<P>(x, in_kind, xoff + ((long)t0 * Nx + a) * Ny + j);
+        re im = (t1 < ntb) ? ld_in<P>(x, in_kind, xoff + ((long)t1 * Nx + a) * Ny + j) : P::re_zero();
         v = P::make(r, im);
       } else {
         v = work[((long)tp * Nx + a) * Ny + j];
@@ -197,8 +247,15 @@ k_prior_rows(const void *__restrict__ x, int in_kind, void *__restrict__ y, int 
     if (!INV) {
       work[((long)tp * Nx + a) * Ny + j] = v;
     } else {
-      st_out<P>(y, out_kind, ((long)fm(t0) * Nx + a) * Ny + j, P::real(v));
-      if (t1 < nt) st_out<P>(y, out_kind, ((long)fm(t1) * Nx + a) * Ny + j, P::imag(v));
+      const long o0 = yoff + ((long)fm(t0) * Nx + a) * Ny + j;
+      const long o1 = yoff + ((long)fm(t1) * Nx + a) * Ny + j;
+      if (accum) {
+        add_out<P>(y, out_kind, o0, P::real(v));
+        if (t1 < ntb) add_out<P>(y, out_kind, o1, P::imag(v));
+      } else {
+        st_out<P>(y, out_kind, o0, P::real(v));
+        if (t1 < nt) st_out<P>(y, out_kind, o1, t1 < ntb ? P::imag(v) : P::re_zero());
+      }
     }
   }
 }
@@ -208,14 +265,17 @@ k_prior_rows(const void *__restrict__ x, int in_kind, void *__restrict__ y, int 
 template <class P>
 __global__ void __launch_bounds__(256)
 k_prior_cols(typename P::cx *__restrict__ work, const typename P::re *__restrict__ lam, int Nx,
-             int Ny, FftPlan plx, const typename P::cx *__restrict__ twx, int BC) {
+             int Ny, FftPlan plx, const typename P::cx *__restrict__ twx, int BC, int nt,
+             BatchArg ba) {
   typedef typename P::cx cx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx *buf0 = reinterpret_cast<cx *>(smem_raw);
   cx *buf1 = buf0 + Nx * BC;
   const int tp = blockIdx.y;
   const int j0 = blockIdx.x * BC;
-  cx *wp = work + (long)tp * Nx * Ny;
+  const int bz = blockIdx.z;
+  if (2 * tp >= ba.window(bz, nt)) return;
+  cx *wp = work + bz * ba.work_stride + (long)tp * Nx * Ny;
   for (int idx = threadIdx.x; idx < Nx * BC; idx += blockDim.x) {
     const int b = idx % BC, a = idx / BC, j = j0 + b;
     buf0[a * BC + b] = (j < Ny) ? wp[(long)a * Ny + j] : P::zero();
@@ -250,14 +310,14 @@ int pick_batch(int len, size_t elem, int cap) {
 template <class P>
 cudaError_t rfft_time(const void *in, int in_kind, long in_ld, int n_in, typename P::cx *out,
                       long out_ld, int N, const FftPlan &pl, const typename P::cx *twM,
-                      const typename P::cx *twL, cudaStream_t s) {
-  if (N <= 0) return cudaSuccess;
+                      const typename P::cx *twL, cudaStream_t s, BatchArg ba = BatchArg{}) {
+  if (N <= 0 || ba.count <= 0) return cudaSuccess;
   const int B = pick_batch(pl.M + 1, sizeof(typename P::cx), 32);
   const size_t sm = (size_t)2 * (pl.M + 1) * B * sizeof(typename P::cx);
   ensure_smem(k_rfft_time<P>, sm);
-  const long grid = (N + B - 1) / B;
-  k_rfft_time<P><<<(unsigned)grid, 256, sm, s>>>(in, in_kind, in_ld, n_in, out, out_ld, N, pl,
-                                                  twM, twL, B);
+  const dim3 grid((unsigned)((N + B - 1) / B), (unsigned)ba.count);
+  k_rfft_time<P><<<grid, 256, sm, s>>>(in, in_kind, in_ld, n_in, out, out_ld, N, pl, twM, twL, B,
+                                       ba);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -265,14 +325,15 @@ cudaError_t rfft_time(const void *in, int in_kind, long in_ld, int n_in, typenam
 template <class P>
 cudaError_t irfft_time(const typename P::cx *in, long in_ld, void *out, int out_kind, long out_ld,
                        int N, int n_keep, const FftPlan &pl, const typename P::cx *twM,
-                       const typename P::cx *twL, typename P::re invM, cudaStream_t s) {
-  if (N <= 0) return cudaSuccess;
+                       const typename P::cx *twL, typename P::re invM, cudaStream_t s,
+                       BatchArg ba = BatchArg{}) {
+  if (N <= 0 || ba.count <= 0) return cudaSuccess;
   const int B = pick_batch(pl.M + 1, sizeof(typename P::cx), 32);
   const size_t sm = (size_t)2 * (pl.M + 1) * B * sizeof(typename P::cx);
   ensure_smem(k_irfft_time<P>, sm);
-  const long grid = (N + B - 1) / B;
-  k_irfft_time<P><<<(unsigned)grid, 256, sm, s>>>(in, in_ld, out, out_kind, out_ld, N, n_keep,
-                                                   pl, twM, twL, invM, B);
+  const dim3 grid((unsigned)((N + B - 1) / B), (unsigned)ba.count);
+  k_irfft_time<P><<<grid, 256, sm, s>>>(in, in_ld, out, out_kind, out_ld, N, n_keep, pl, twM, twL,
+                                        invM, B, ba);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -281,8 +342,9 @@ template <class P>
 cudaError_t prior(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx, int Ny,
                   typename P::cx *work, const typename P::re *lam, const FftPlan &plx,
                   const FftPlan &ply, const typename P::cx *twx, const typename P::cx *twy,
-                  cudaStream_t s, FieldMap fm = FieldMap{1 << 30, 0, 0}) {
-  if (nt <= 0) return cudaSuccess;
+                  cudaStream_t s, FieldMap fm = FieldMap{1 << 30, 0, 0}, BatchArg ba = BatchArg{},
+                  int accum = 0) {
+  if (nt <= 0 || ba.count <= 0) return cudaSuccess;
   typedef typename P::cx cx;
   const int np = (nt + 1) / 2;
   int BR = 1;
@@ -294,12 +356,14 @@ cudaError_t prior(const void *x, int in_kind, void *y, int out_kind, int nt, int
   ensure_smem(k_prior_rows<P, false>, smr);
   ensure_smem(k_prior_rows<P, true>, smr);
   ensure_smem(k_prior_cols<P>, smc);
-  dim3 gr((Nx + BR - 1) / BR, np), gc((Ny + BC - 1) / BC, np);
-  k_prior_rows<P, false><<<gr, 256, smr, s>>>(x, in_kind, nullptr, 0, work, nt, Nx, Ny, ply, twy, BR, fm);
+  dim3 gr((Nx + BR - 1) / BR, np, ba.count), gc((Ny + BC - 1) / BC, np, ba.count);
+  k_prior_rows<P, false><<<gr, 256, smr, s>>>(x, in_kind, nullptr, 0, work, nt, Nx, Ny, ply, twy, BR,
+                                              fm, ba, 0);
   count_launches(1);
-  k_prior_cols<P><<<gc, 256, smc, s>>>(work, lam, Nx, Ny, plx, twx, BC);
+  k_prior_cols<P><<<gc, 256, smc, s>>>(work, lam, Nx, Ny, plx, twx, BC, nt, ba);
   count_launches(1);
-  k_prior_rows<P, true><<<gr, 256, smr, s>>>(nullptr, 0, y, out_kind, work, nt, Nx, Ny, ply, twy, BR, fm);
+  k_prior_rows<P, true><<<gr, 256, smr, s>>>(nullptr, 0, y, out_kind, work, nt, Nx, Ny, ply, twy, BR,
+                                             fm, ba, accum);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -308,34 +372,36 @@ cudaError_t prior(const void *x, int in_kind, void *y, int out_kind, int nt, int
 
 cudaError_t launch_rfft_time_dd(const void *in, int in_kind, long in_ld, int n_in, cdd *out,
                                 long out_ld, int N, const FftPlan &pl, const cdd *twM,
-                                const cdd *twL, cudaStream_t s) {
-  return rfft_time<PolDD>(in, in_kind, in_ld, n_in, out, out_ld, N, pl, twM, twL, s);
+                                const cdd *twL, cudaStream_t s, const BatchArg &ba) {
+  return rfft_time<PolDD>(in, in_kind, in_ld, n_in, out, out_ld, N, pl, twM, twL, s, ba);
 }
 cudaError_t launch_rfft_time_f(const void *in, int in_kind, long in_ld, int n_in, cf *out,
                                long out_ld, int N, const FftPlan &pl, const cf *twM,
-                               const cf *twL, cudaStream_t s) {
-  return rfft_time<PolF>(in, in_kind, in_ld, n_in, out, out_ld, N, pl, twM, twL, s);
+                               const cf *twL, cudaStream_t s, const BatchArg &ba) {
+  return rfft_time<PolF>(in, in_kind, in_ld, n_in, out, out_ld, N, pl, twM, twL, s, ba);
 }
 cudaError_t launch_irfft_time_dd(const cdd *in, long in_ld, void *out, int out_kind, long out_ld,
                                  int N, int n_keep, const FftPlan &pl, const cdd *twM,
-                                 const cdd *twL, cudaStream_t s) {
+                                 const cdd *twL, cudaStream_t s, const BatchArg &ba) {
   // 1/M as a float pair (host double split)
   const double inv = 1.0 / pl.M;
   dd invM;
   invM.hi = (float)inv;
   invM.lo = (float)(inv - (double)invM.hi);
-  return irfft_time<PolDD>(in, in_ld, out, out_kind, out_ld, N, n_keep, pl, twM, twL, invM, s);
+  return irfft_time<PolDD>(in, in_ld, out, out_kind, out_ld, N, n_keep, pl, twM, twL, invM, s, ba);
 }
 cudaError_t launch_irfft_time_f(const cf *in, long in_ld, void *out, int out_kind, long out_ld,
                                 int N, int n_keep, const FftPlan &pl, const cf *twM,
-                                const cf *twL, cudaStream_t s) {
+                                const cf *twL, cudaStream_t s, const BatchArg &ba) {
   return irfft_time<PolF>(in, in_ld, out, out_kind, out_ld, N, n_keep, pl, twM, twL,
-                          (float)(1.0 / pl.M), s);
+                          (float)(1.0 / pl.M), s, ba);
 }
 cudaError_t launch_prior_dd(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
                             int Ny, cdd *work, const dd *lam, const FftPlan &plx,
-                            const FftPlan &ply, const cdd *twx, const cdd *twy, cudaStream_t s) {
-  return prior<PolDD>(x, in_kind, y, out_kind, nt, Nx, Ny, work, lam, plx, ply, twx, twy, s);
+                            const FftPlan &ply, const cdd *twx, const cdd *twy, cudaStream_t s,
+                            const BatchArg &ba, int accum) {
+  return prior<PolDD>(x, in_kind, y, out_kind, nt, Nx, Ny, work, lam, plx, ply, twx, twy, s,
+                      FieldMap{1 << 30, 0, 0}, ba, accum);
 }
 cudaError_t launch_prior_d(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
                            int Ny, cd *work, const double *lam, const FftPlan &plx,
@@ -346,8 +412,10 @@ cudaError_t launch_prior_d(const void *x, int in_kind, void *y, int out_kind, in
 }
 cudaError_t launch_prior_f(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
                            int Ny, cf *work, const float *lam, const FftPlan &plx,
-                           const FftPlan &ply, const cf *twx, const cf *twy, cudaStream_t s) {
-  return prior<PolF>(x, in_kind, y, out_kind, nt, Nx, Ny, work, lam, plx, ply, twx, twy, s);
+                           const FftPlan &ply, const cf *twx, const cf *twy, cudaStream_t s,
+                           const BatchArg &ba, int accum) {
+  return prior<PolF>(x, in_kind, y, out_kind, nt, Nx, Ny, work, lam, plx, ply, twx, twy, s,
+                     FieldMap{1 << 30, 0, 0}, ba, accum);
 }
 
 }  // namespace tw

@@ -1,0 +1,426 @@
+// gemm.cu -- the per-frequency products for a batch of right-hand sides.
+//
+// With B right-hand sides the block-diagonal-in-frequency form of the
+// Toeplitz maps (Sec. "FFT-based Hessian matvecs") turns each frequency's
+// matrix-vector product into a matrix-matrix product:
+//   adjoint  X^(w) = F^(w)^H Y^(w)      (Nm x Nr) (Nr x B)
+//   forward  Y^(w) = F^(w)   X^(w)      (Nr x Nm) (Nm x B)
+// The operator is read once per CTA column slice instead of once per
+// right-hand side, so the cost moves from HBM to the arithmetic units.
+//
+// Batched arrays are RHS-major: entry b of Y is at Y + b * y_bstride and
+// holds [Nf][Nr] complex values (X: [Nf][Nm]).
+//
+//  * adjoint: a CTA owns 128 grid points of one frequency and a slice of
+//    right-hand sides; its slice of Y^(w) sits in shared memory, each warp
+//    keeps 4 right-hand sides x 4 grid points of accumulators and walks the
+//    Nr rows (no cross-thread reduction).
+//  * forward: a CTA owns a range of grid points of one frequency and 32
+//    right-hand sides (lane = right-hand side); each warp keeps RPW rows of
+//    accumulators, reads F^(w) entries once (broadcast to the warp) and the
+//    X^(w) tile from shared memory.  The per-range partial sums are added by
+//    a second kernel in a fixed order.
+//
+// FP64-class path: float-pair operands, exact products, renormalised
+// running sums (as the single-vector kernels); FP32 path: complex64 or
+// bf16 hi+lo operator, FP32 FMA.
+#include "kernels.h"
+
+namespace tw {
+
+namespace {
+
+constexpr int GA_K = 128;      // grid points per CTA (adjoint)
+constexpr int GF_K = 128;      // grid points per shared tile (forward)
+constexpr int GF_TILES = 32;   // tiles per CTA: a CTA sums 4096 grid points
+
+__device__ __forceinline__ float bf16lo(unsigned w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
+
+template <int FMT> __device__ __forceinline__ cf ld_opf(const void *A, size_t i);
+template <> __device__ __forceinline__ cf ld_opf<FMT_C64>(const void *A, size_t i) {
+  float2 v = __ldg(reinterpret_cast<const float2 *>(A) + i);
+  return cf_make(v.x, v.y);
+}
+template <> __device__ __forceinline__ cf ld_opf<FMT_BF16X2>(const void *A, size_t i) {
+  uint2 v = __ldg(reinterpret_cast<const uint2 *>(A) + i);
+  return cf_make(bf16lo(v.x) + bf16hi(v.x), bf16lo(v.y) + bf16hi(v.y));
+}
+
+// ------------------------------------------------------------ adjoint, df64
+// grid (ceil(Nm/128), Nf, ceil(B/32)); 8 warps x 4 right-hand sides each
+__global__ void __launch_bounds__(256, 2)
+k_gemm_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ Y, long y_bstride,
+              cdd *__restrict__ X, long x_bstride, int Nr, int Nm, int B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cdd *sy = reinterpret_cast<cdd *>(smem_raw);   // [32][Nr]
+  const int w = blockIdx.y;
+  const int b0 = blockIdx.z * 32;
+  const int nb = min(32, B - b0);
+  for (int idx = threadIdx.x; idx < 32 * Nr; idx += blockDim.x) {
+    const int bl = idx / Nr, sr = idx % Nr;
+    sy[idx] = bl < nb ? ld_cdd(Y + (size_t)(b0 + bl) * y_bstride + (size_t)w * Nr + sr) : cdd_zero();
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int k0 = blockIdx.x * GA_K + lane;
+  const float4 *Aw = A + (size_t)w * Nr * Nm;
+  dacc re[4][4], im[4][4];   // [rhs][point]
+  bool ok[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) ok[j] = k0 + 32 * j < Nm;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { re[i][j] = dacc_zero(); im[i][j] = dacc_zero(); }
+  float4 cur[4], nxt[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) cur[j] = ok[j] ? __ldg(Aw + k0 + 32 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const cdd *syg = sy + (grp * 4) * Nr;
+  for (int s = 0; s < Nr; ++s) {
+    if (s + 1 < Nr) {
+      const float4 *row = Aw + (size_t)(s + 1) * Nm + k0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) nxt[j] = ok[j] ? __ldg(row + 32 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const cdd y = syg[i * Nr + s];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        dd ar, ai;
+        ar.hi = cur[j].x; ar.lo = cur[j].y; ai.hi = cur[j].z; ai.lo = cur[j].w;
+        // conj(a) y = (ar yr + ai yi) + i (ar yi - ai yr)
+        dacc_mac(re[i][j], ar, y.re);
+        dacc_mac(re[i][j], ai, y.im);
+        dacc_mac(im[i][j], ar, y.im);
+        dacc_mac(im[i][j], dd_neg(ai), y.re);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cur[j] = nxt[j];
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int bl = grp * 4 + i;
+    if (bl >= nb) continue;
+    cdd *xo = X + (size_t)(b0 + bl) * x_bstride + (size_t)w * Nm;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!ok[j]) continue;
+      cdd r;
+      r.re = dacc_get(re[i][j]);
+      r.im = dacc_get(im[i][j]);
+      st_cdd(xo + k0 + 32 * j, r);
+    }
+  }
+}
+
+// ------------------------------------------------------------ adjoint, FP32
+// grid (ceil(Nm/128), Nf, ceil(B/64)); 8 warps x 8 right-hand sides each
+template <int FMT>
+__global__ void __launch_bounds__(256, 2)
+k_gemm_adj_f(const void *__restrict__ A, const cf *__restrict__ Y, long y_bstride,
+             cf *__restrict__ X, long x_bstride, int Nr, int Nm, int B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cf *sy = reinterpret_cast<cf *>(smem_raw);   // [64][Nr]
+  const int w = blockIdx.y;
+  const int b0 = blockIdx.z * 64;
+  const int nb = min(64, B - b0);
+  for (int idx = threadIdx.x; idx < 64 * Nr; idx += blockDim.x) {
+    const int bl = idx / Nr, sr = idx % Nr;
+    sy[idx] = bl < nb ? Y[(size_t)(b0 + bl) * y_bstride + (size_t)w * Nr + sr] : cf_zero();
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int k0 = blockIdx.x * GA_K + lane;
+  const size_t base = (size_t)w * Nr * Nm;
+  float re[8][4], im[8][4];
+  bool ok[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) ok[j] = k0 + 32 * j < Nm;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { re[i][j] = 0.f; im[i][j] = 0.f; }
+  cf cur[4], nxt[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) cur[j] = ok[j] ? ld_opf<FMT>(A, base + k0 + 32 * j) : cf_zero();
+  const cf *syg = sy + (grp * 8) * Nr;
+  for (int s = 0; s < Nr; ++s) {
+    if (s + 1 < Nr) {
+      const size_t row = base + (size_t)(s + 1) * Nm + k0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) nxt[j] = ok[j] ? ld_opf<FMT>(A, row + 32 * j) : cf_zero();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const cf y = syg[i * Nr + s];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        re[i][j] = fmaf(cur[j].re, y.re, fmaf(cur[j].im, y.im, re[i][j]));
+        im[i][j] = fmaf(cur[j].re, y.im, fmaf(-cur[j].im, y.re, im[i][j]));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cur[j] = nxt[j];
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int bl = grp * 8 + i;
+    if (bl >= nb) continue;
+    cf *xo = X + (size_t)(b0 + bl) * x_bstride + (size_t)w * Nm;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (ok[j]) xo[k0 + 32 * j] = cf_make(re[i][j], im[i][j]);
+  }
+}
+
+// ------------------------------------------------------------ forward, df64
+// grid (nchunk, Nf, ceil(B/32)); lane = right-hand side, warp = RPW rows per
+// pass, passes cover all Nr rows; partial sums to part[b][w][chunk][r]
+template <int RPW>
+__global__ void __launch_bounds__(256)
+k_gemm_fwd_dd(const float4 *__restrict__ A, const cdd *__restrict__ X, long x_bstride,
+              cdd *__restrict__ part, int nchunk, int Nr, int Nm, int B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cdd *sx = reinterpret_cast<cdd *>(smem_raw);   // [32][GF_K + 1]
+  const int w = blockIdx.y, chunk = blockIdx.x;
+  const int b0 = blockIdx.z * 32;
+  const int nb = min(32, B - b0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int kbeg = chunk * GF_K * GF_TILES;
+  const int kend = min(Nm, kbeg + GF_K * GF_TILES);
+  const float4 *Aw = A + (size_t)w * Nr * Nm;
+  const int npass = (Nr + 8 * RPW - 1) / (8 * RPW);
+  for (int pass = 0; pass < npass; ++pass) {   // uniform over the CTA (barriers inside)
+    const int r0 = pass * 8 * RPW + warp * RPW;
+    dacc re[RPW], im[RPW];
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) { re[i] = dacc_zero(); im[i] = dacc_zero(); }
+    for (int kt = kbeg; kt < kend; kt += GF_K) {
+      const int nk = min(GF_K, kend - kt);
+      __syncthreads();   // previous tile consumed
+      for (int idx = threadIdx.x; idx < 32 * GF_K; idx += blockDim.x) {
+        const int bl = idx / GF_K, kk = idx % GF_K;
+        sx[bl * (GF_K + 1) + kk] = (bl < nb && kk < nk)
+            ? ld_cdd(X + (size_t)(b0 + bl) * x_bstride + (size_t)w * Nm + kt + kk)
+            : cdd_zero();
+      }
+      __syncthreads();
+      const cdd *xs = sx + lane * (GF_K + 1);
+      for (int kk = 0; kk < nk; ++kk) {
+        const cdd x = xs[kk];
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+          const int r = r0 + i;
+          if (r >= Nr) continue;
+          const float4 a = __ldg(Aw + (size_t)r * Nm + kt + kk);
+          dd ar, ai;
+          ar.hi = a.x; ar.lo = a.y; ai.hi = a.z; ai.lo = a.w;
+          // a x = (ar xr - ai xi) + i (ar xi + ai xr)
+          dacc_mac(re[i], ar, x.re);
+          dacc_mac(re[i], dd_neg(ai), x.im);
+          dacc_mac(im[i], ar, x.im);
+          dacc_mac(im[i], ai, x.re);
+        }
+      }
+    }
+    if (lane < nb) {
+#pragma unroll
+      for (int i = 0; i < RPW; ++i) {
+        const int r = r0 + i;
+        if (r >= Nr) continue;
+        cdd v;
+        v.re = dacc_get(re[i]);
+        v.im = dacc_get(im[i]);
+        st_cdd(part + (((size_t)(b0 + lane) * gridDim.y + w) * nchunk + chunk) * Nr + r, v);
+      }
+    }
+  }
+}
+
+template <int RPW, int FMT>
+__global__ void __launch_bounds__(256)
+k_gemm_fwd_f(const void *__restrict__ A, const cf *__restrict__ X, long x_bstride,
+             cf *__restrict__ part, int nchunk, int Nr, int Nm, int B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cf *sx = reinterpret_cast<cf *>(smem_raw);   // [32][GF_K + 1]
+  const int w = blockIdx.y, chunk = blockIdx.x;
+  const int b0 = blockIdx.z * 32;
+  const int nb = min(32, B - b0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int kbeg = chunk * GF_K * GF_TILES;
+  const int kend = min(Nm, kbeg + GF_K * GF_TILES);
+  const size_t base = (size_t)w * Nr * Nm;
+  const int npass = (Nr + 8 * RPW - 1) / (8 * RPW);
+  for (int pass = 0; pass < npass; ++pass) {   // uniform over the CTA (barriers inside)
+    const int r0 = pass * 8 * RPW + warp * RPW;
+    float re[RPW], im[RPW];
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) { re[i] = 0.f; im[i] = 0.f; }
+    for (int kt = kbeg; kt < kend; kt += GF_K) {
+      const int nk = min(GF_K, kend - kt);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < 32 * GF_K; idx += blockDim.x) {
+        const int bl = idx / GF_K, kk = idx % GF_K;
+        sx[bl * (GF_K + 1) + kk] = (bl < nb && kk < nk)
+            ? X[(size_t)(b0 + bl) * x_bstride + (size_t)w * Nm + kt + kk]
+            : cf_zero();
+      }
+      __syncthreads();
+      const cf *xs = sx + lane * (GF_K + 1);
+      // a fresh sum per tile, added to the running total: FP32 rounding then
+      // grows with GF_K + the tile count instead of the chunk length
+      float tre[RPW], tim[RPW];
+#pragma unroll
+      for (int i = 0; i < RPW; ++i) { tre[i] = 0.f; tim[i] = 0.f; }
+      for (int kk = 0; kk < nk; ++kk) {
+        const cf x = xs[kk];
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+          const int r = r0 + i;
+          if (r >= Nr) continue;
+          const cf a = ld_opf<FMT>(A, base + (size_t)r * Nm + kt + kk);
+          tre[i] = fmaf(a.re, x.re, fmaf(-a.im, x.im, tre[i]));
+          tim[i] = fmaf(a.re, x.im, fmaf(a.im, x.re, tim[i]));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < RPW; ++i) { re[i] += tre[i]; im[i] += tim[i]; }
+    }
+    if (lane < nb) {
+#pragma unroll
+      for (int i = 0; i < RPW; ++i) {
+        const int r = r0 + i;
+        if (r >= Nr) continue;
+        part[(((size_t)(b0 + lane) * gridDim.y + w) * nchunk + chunk) * Nr + r] = cf_make(re[i], im[i]);
+      }
+    }
+  }
+}
+
+// out[b][w][r] = sum over chunks (ascending) of part[b][w][chunk][r]
+__global__ void k_gemm_fwd_reduce_dd(const cdd *__restrict__ part, cdd *__restrict__ Yo,
+                                     long y_bstride, int nchunk, int Nf, int Nr, int B) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long total = (long)B * Nf * Nr;
+  if (i >= total) return;
+  const int r = (int)(i % Nr);
+  const long bw = i / Nr;
+  const int w = (int)(bw % Nf), b = (int)(bw / Nf);
+  const cdd *p = part + (size_t)bw * nchunk * Nr + r;
+  cdd acc = cdd_zero();
+  for (int c = 0; c < nchunk; ++c) acc = cdd_add(acc, ld_cdd(p + (size_t)c * Nr));
+  st_cdd(Yo + (size_t)b * y_bstride + (size_t)w * Nr + r, acc);
+}
+__global__ void k_gemm_fwd_reduce_f(const cf *__restrict__ part, cf *__restrict__ Yo,
+                                    long y_bstride, int nchunk, int Nf, int Nr, int B) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long total = (long)B * Nf * Nr;
+  if (i >= total) return;
+  const int r = (int)(i % Nr);
+  const long bw = i / Nr;
+  const int w = (int)(bw % Nf), b = (int)(bw / Nf);
+  const cf *p = part + (size_t)bw * nchunk * Nr + r;
+  cf acc = cf_zero();
+  for (int c = 0; c < nchunk; ++c) acc = cf_add(acc, p[(size_t)c * Nr]);
+  Yo[(size_t)b * y_bstride + (size_t)w * Nr + r] = acc;
+}
+
+template <class KER>
+void ensure_smem_g(KER k, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+int gemm_fwd_nchunk(int Nm) { return (Nm + GF_K * GF_TILES - 1) / (GF_K * GF_TILES); }
+
+size_t gemm_adj_smem(int prec_fp32, int Nr) {
+  return prec_fp32 ? (size_t)64 * Nr * sizeof(cf) : (size_t)32 * Nr * sizeof(cdd);
+}
+
+cudaError_t launch_gemm_adj_dd(const void *A, const cdd *Y, long y_bstride, cdd *X, long x_bstride,
+                               int Nf, int Nr, int Nm, int B, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const size_t sm = gemm_adj_smem(0, Nr);
+  ensure_smem_g(k_gemm_adj_dd, sm);
+  dim3 grid((Nm + GA_K - 1) / GA_K, Nf, (B + 31) / 32);
+  k_gemm_adj_dd<<<grid, 256, sm, s>>>(reinterpret_cast<const float4 *>(A), Y, y_bstride, X,
+                                      x_bstride, Nr, Nm, B);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_adj_f(const void *A, int fmt, const cf *Y, long y_bstride, cf *X,
+                              long x_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const size_t sm = gemm_adj_smem(1, Nr);
+  dim3 grid((Nm + GA_K - 1) / GA_K, Nf, (B + 63) / 64);
+  if (fmt == FMT_C64) {
+    ensure_smem_g(k_gemm_adj_f<FMT_C64>, sm);
+    k_gemm_adj_f<FMT_C64><<<grid, 256, sm, s>>>(A, Y, y_bstride, X, x_bstride, Nr, Nm, B);
+  } else {
+    ensure_smem_g(k_gemm_adj_f<FMT_BF16X2>, sm);
+    k_gemm_adj_f<FMT_BF16X2><<<grid, 256, sm, s>>>(A, Y, y_bstride, X, x_bstride, Nr, Nm, B);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// rows per warp: enough that one pass covers up to 8*RPW rows
+template <int RPW>
+static cudaError_t gemm_fwd_dd_rpw(const void *A, const cdd *X, long x_bstride, cdd *part,
+                                   cdd *Yo, long y_bstride, int Nf, int Nr, int Nm, int B,
+                                   cudaStream_t s) {
+  const int nchunk = gemm_fwd_nchunk(Nm);
+  const size_t sm = (size_t)32 * (GF_K + 1) * sizeof(cdd);
+  ensure_smem_g(k_gemm_fwd_dd<RPW>, sm);
+  dim3 grid(nchunk, Nf, (B + 31) / 32);
+  k_gemm_fwd_dd<RPW><<<grid, 256, sm, s>>>(reinterpret_cast<const float4 *>(A), X, x_bstride, part,
+                                           nchunk, Nr, Nm, B);
+  count_launches(1);
+  const long total = (long)B * Nf * Nr;
+  k_gemm_fwd_reduce_dd<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, Yo, y_bstride, nchunk,
+                                                                      Nf, Nr, B);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_fwd_dd(const void *A, const cdd *X, long x_bstride, cdd *part, cdd *Yo,
+                               long y_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  if (Nr <= 24) return gemm_fwd_dd_rpw<3>(A, X, x_bstride, part, Yo, y_bstride, Nf, Nr, Nm, B, s);
+  return gemm_fwd_dd_rpw<7>(A, X, x_bstride, part, Yo, y_bstride, Nf, Nr, Nm, B, s);
+}
+
+template <int RPW, int FMT>
+static cudaError_t gemm_fwd_f_rpw(const void *A, const cf *X, long x_bstride, cf *part, cf *Yo,
+                                  long y_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s) {
+  const int nchunk = gemm_fwd_nchunk(Nm);
+  const size_t sm = (size_t)32 * (GF_K + 1) * sizeof(cf);
+  ensure_smem_g(k_gemm_fwd_f<RPW, FMT>, sm);
+  dim3 grid(nchunk, Nf, (B + 31) / 32);
+  k_gemm_fwd_f<RPW, FMT><<<grid, 256, sm, s>>>(A, X, x_bstride, part, nchunk, Nr, Nm, B);
+  count_launches(1);
+  const long total = (long)B * Nf * Nr;
+  k_gemm_fwd_reduce_f<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, Yo, y_bstride, nchunk,
+                                                                     Nf, Nr, B);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_fwd_f(const void *A, int fmt, const cf *X, long x_bstride, cf *part,
+                              cf *Yo, long y_bstride, int Nf, int Nr, int Nm, int B,
+                              cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  if (fmt == FMT_C64) {
+    if (Nr <= 24) return gemm_fwd_f_rpw<3, FMT_C64>(A, X, x_bstride, part, Yo, y_bstride, Nf, Nr, Nm, B, s);
+    return gemm_fwd_f_rpw<13, FMT_C64>(A, X, x_bstride, part, Yo, y_bstride, Nf, Nr, Nm, B, s);
+  }
+  if (Nr <= 24) return gemm_fwd_f_rpw<3, FMT_BF16X2>(A, X, x_bstride, part, Yo, y_bstride, Nf, Nr, Nm, B, s);
+  return gemm_fwd_f_rpw<13, FMT_BF16X2>(A, X, x_bstride, part, Yo, y_bstride, Nf, Nr, Nm, B, s);
+}
+
+}  // namespace tw

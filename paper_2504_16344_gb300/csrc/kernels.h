@@ -12,6 +12,19 @@ namespace tw {
 void count_launches(int k);
 long long launches_total();
 
+// ---- batches of right-hand sides ----------------------------------------
+// Entry b of a batch is at base + b * stride (elements of the array's type);
+// its window (time steps kept, rows read) is win[b] when win != nullptr,
+// capped by the call's scalar window.  win lives in device memory.
+struct BatchArg {
+  int count = 1;
+  long in_stride = 0, out_stride = 0, work_stride = 0;
+  const int *win = nullptr;
+  __device__ __forceinline__ int window(int b, int cap) const {
+    return win ? min(max(win[b], 0), cap) : cap;
+  }
+};
+
 // ---- operator storage formats
 enum OpFmt { FMT_DD = 0, FMT_C64 = 1, FMT_BF16X2 = 2 };
 
@@ -21,25 +34,30 @@ enum OpFmt { FMT_DD = 0, FMT_C64 = 1, FMT_BF16X2 = 2 };
 // in_kind: 0 = double, 1 = dd (float2), 2 = float
 cudaError_t launch_rfft_time_dd(const void *in, int in_kind, long in_ld, int n_in,
                                 cdd *out, long out_ld, int N, const FftPlan &pl,
-                                const cdd *twM, const cdd *twL, cudaStream_t s);
+                                const cdd *twM, const cdd *twL, cudaStream_t s,
+                                const BatchArg &ba = BatchArg{});
 cudaError_t launch_rfft_time_f(const void *in, int in_kind, long in_ld, int n_in,
                                cf *out, long out_ld, int N, const FftPlan &pl,
-                               const cf *twM, const cf *twL, cudaStream_t s);
+                               const cf *twM, const cf *twL, cudaStream_t s,
+                               const BatchArg &ba = BatchArg{});
 // inverse: in [M+1][N] complex -> out [M][N] real (1/(2M) applied),
 // rows t >= n_keep written as 0.  out_kind: 0 = double, 1 = dd, 2 = float
 cudaError_t launch_irfft_time_dd(const cdd *in, long in_ld, void *out, int out_kind, long out_ld,
                                  int N, int n_keep, const FftPlan &pl, const cdd *twM,
-                                 const cdd *twL, cudaStream_t s);
+                                 const cdd *twL, cudaStream_t s, const BatchArg &ba = BatchArg{});
 cudaError_t launch_irfft_time_f(const cf *in, long in_ld, void *out, int out_kind, long out_ld,
                                 int N, int n_keep, const FftPlan &pl, const cf *twM,
-                                const cf *twL, cudaStream_t s);
+                                const cf *twL, cudaStream_t s, const BatchArg &ba = BatchArg{});
 
 // ---- Matern filter on the periodic grid: y_t = C^power x_t, t < nt -------
 // x, y: [nt][Nx][Ny] real (kind 0 double, 1 dd, 2 float); work: [ceil(nt/2)][Nx][Ny] complex
 // lam: [Nx][Ny] eigenvalues^power / (Nx Ny)
+// batched: entry b reads x + b*ba.in_stride, writes y + b*ba.out_stride, uses
+// work + b*ba.work_stride; accum != 0 adds the result to y instead of storing it
 cudaError_t launch_prior_dd(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
                             int Ny, cdd *work, const dd *lam, const FftPlan &plx,
-                            const FftPlan &ply, const cdd *twx, const cdd *twy, cudaStream_t s);
+                            const FftPlan &ply, const cdd *twx, const cdd *twy, cudaStream_t s,
+                            const BatchArg &ba = BatchArg{}, int accum = 0);
 // native FP64 variant (set-up); output field t goes to (t/per)*stride + off + t%per
 cudaError_t launch_prior_d(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
                            int Ny, cd *work, const double *lam, const FftPlan &plx,
@@ -47,7 +65,8 @@ cudaError_t launch_prior_d(const void *x, int in_kind, void *y, int out_kind, in
                            int map_stride, int map_off, cudaStream_t s);
 cudaError_t launch_prior_f(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
                            int Ny, cf *work, const float *lam, const FftPlan &plx,
-                           const FftPlan &ply, const cf *twx, const cf *twy, cudaStream_t s);
+                           const FftPlan &ply, const cf *twx, const cf *twy, cudaStream_t s,
+                           const BatchArg &ba = BatchArg{}, int accum = 0);
 
 // ---- frequency-batched complex GEMV ------------------------------------
 // forward: yh[w][s] = sum_k A[w][s][k] xh[w][k]   (A: [Nf][Nr][Nm] in `fmt`)
@@ -62,6 +81,20 @@ cudaError_t launch_gemv_adj_dd(const void *A, int fmt, const cdd *yh, cdd *xh, i
                                int Nm, cudaStream_t s);
 cudaError_t launch_gemv_adj_f(const void *A, int fmt, const cf *yh, cf *xh, int Nf, int Nr,
                               int Nm, cudaStream_t s);
+
+// ---- batched per-frequency products (gemm.cu) ----------------------------
+// adjoint: X[b][w][k] = sum_s conj(A[w][s][k]) Y[b][w][s]
+// forward: Yo[b][w][r] = sum_k A[w][r][k] X[b][w][k]; part: B*Nf*nchunk*Nr entries
+int gemm_fwd_nchunk(int Nm);
+cudaError_t launch_gemm_adj_dd(const void *A, const cdd *Y, long y_bstride, cdd *X, long x_bstride,
+                               int Nf, int Nr, int Nm, int B, cudaStream_t s);
+cudaError_t launch_gemm_adj_f(const void *A, int fmt, const cf *Y, long y_bstride, cf *X,
+                              long x_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s);
+cudaError_t launch_gemm_fwd_dd(const void *A, const cdd *X, long x_bstride, cdd *part, cdd *Yo,
+                               long y_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s);
+cudaError_t launch_gemm_fwd_f(const void *A, int fmt, const cf *X, long x_bstride, cf *part,
+                              cf *Yo, long y_bstride, int Nf, int Nr, int Nm, int B,
+                              cudaStream_t s);
 
 // ---- operator storage conversion: dst[w][row0+r][k] from src (cdd) -----
 cudaError_t launch_convert_op(const cdd *src, long src_ld_w, void *dst, int fmt, long dst_ld_w,

@@ -1,0 +1,385 @@
+// tw_batch.cu -- batches of right-hand sides with per-RHS observation windows.
+//
+// Phase 4 serves many events and posterior samples at once; with B
+// right-hand sides the online path becomes
+//   batched triangular solves  Z = L^-1 D,  Y = L^-T Z      (trsm.cu)
+//   batched time FFTs, per-frequency products F^(w)^H Y^(w) (gemm.cu),
+//   inverse FFTs and the prior filter                         (fft.cu)
+// with every factor block and operator entry read once per column slice
+// rather than once per right-hand side.  Windows live in device memory, so
+// the calls below neither allocate nor synchronise and can be captured into
+// one CUDA graph that is relaunched with new data and windows.
+#include <algorithm>
+
+#include "ctx.h"
+#include "dense_api.h"
+
+using namespace tw;
+
+namespace {
+
+// r[i] = d[i] - a[i] - sigma z[i] over B * n entries
+__global__ void k_sample_rhs_b(const double *__restrict__ d, const double *__restrict__ a,
+                               const double *__restrict__ z, double sigma, double *__restrict__ r,
+                               long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = d[i] - a[i] - sigma * z[i];
+}
+
+// windows from a host array into device memory (stream-ordered copy of a
+// pageable buffer: the host array may be reused once the call returns)
+tw_status upload_windows(tw_ctx *c, const int *nt_window, int nrhs, cudaStream_t s) {
+  std::vector<int> w(nrhs);
+  for (int r = 0; r < nrhs; ++r) {
+    w[r] = nt_window ? nt_window[r] : c->Nt;
+    if (w[r] < 1 || w[r] > c->Nt) return twh::fail(c, TW_ERR_ARG, "window must be in [1, Nt]");
+  }
+  TW_CUDA(c, cudaMemcpyAsync(c->win_dev, w.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+  return TW_OK;
+}
+
+tw_status check_batch(tw_ctx *c, tw_prec prec, int nrhs, const int *win) {
+  if (prec < 0 || prec > 2 || !c->op[TW_MAP_F][prec])
+    return twh::fail(c, TW_ERR_ARG, "requested precision was not kept at tw_create");
+  if (c->bmax <= 0) return twh::fail(c, TW_ERR_STATE, "tw_reserve_batch must come first");
+  if (nrhs > c->bmax) return twh::fail(c, TW_ERR_ARG, "more right-hand sides than reserved");
+  if (nrhs > 0 && !win) return twh::fail(c, TW_ERR_ARG, "windows (device array) required");
+  if (prec == TW_PREC_FP64 ? !c->have64 : !c->Lp_dd)
+    return twh::fail(c, TW_ERR_STATE, "batched solves need the FP64 factor (tw_factor_K)");
+  return TW_OK;
+}
+
+// q = F_q m for B right-hand sides; rows t >= win[b] of m are taken as zero
+tw_status forecast_core(tw_ctx *c, tw_prec prec, int B, const int *win, const double *m,
+                        double *q, cudaStream_t s) {
+  const int Nt = c->Nt, Nm = c->Nm, Nf = c->Nf, Nq = c->Nq;
+  const void *Aq = c->op[TW_MAP_FQ][prec];
+  const BatchArg ba_m{B, (long)Nt * Nm, (long)Nf * Nm, 0, win};
+  const BatchArg ba_q{B, (long)Nf * Nq, (long)Nt * Nq, 0, nullptr};
+  if (prec == TW_PREC_FP64) {
+    { twh::Phase p(c, TW_PH_RFFT_PARAM, s);
+      TW_CUDA(c, launch_rfft_time_dd(m, 0, Nm, Nt, (cdd *)c->bxh, Nm, Nm, c->plT, c->twT, c->twL, s, ba_m)); }
+    { twh::Phase p(c, TW_PH_GEMV_FWD, s);
+      TW_CUDA(c, launch_gemm_fwd_dd(Aq, (const cdd *)c->bxh, (long)Nf * Nm, (cdd *)c->bpart,
+                                    (cdd *)c->byh, (long)Nf * Nq, Nf, Nq, Nm, B, s)); }
+    { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
+      TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->byh, Nq, q, 0, Nq, Nq, Nt, c->plT, c->twT, c->twL, s, ba_q)); }
+  } else {
+    { twh::Phase p(c, TW_PH_RFFT_PARAM, s);
+      TW_CUDA(c, launch_rfft_time_f(m, 0, Nm, Nt, (cf *)c->bxh, Nm, Nm, c->plT, c->twTf, c->twLf, s, ba_m)); }
+    { twh::Phase p(c, TW_PH_GEMV_FWD, s);
+      TW_CUDA(c, launch_gemm_fwd_f(Aq, (int)prec, (const cf *)c->bxh, (long)Nf * Nm, (cf *)c->bpart,
+                                   (cf *)c->byh, (long)Nf * Nq, Nf, Nq, Nm, B, s)); }
+    { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
+      TW_CUDA(c, launch_irfft_time_f((const cf *)c->byh, Nq, q, 0, Nq, Nq, Nt, c->plT, c->twTf, c->twLf, s, ba_q)); }
+  }
+  return TW_OK;
+}
+
+// m = Gamma_pr F'^T K'^{-1} d' per right-hand side (window win[b]); rhs
+// column b at rhs + b * rhs_bstride (FP64, [Nt][Nd]); q = F_q m if q != NULL
+tw_status infer_core(tw_ctx *c, tw_prec prec, int B, const int *win, const double *rhs,
+                     long rhs_bstride, double *m, double *q, cudaStream_t s) {
+  const int Nd = c->Nd, Nt = c->Nt, Nm = c->Nm, Nf = c->Nf;
+  const long np = c->n_pad;
+  const void *A = c->op[TW_MAP_F][prec];
+  int *prog_f = c->trsm_prog, *prog_b = c->trsm_prog + trsm_prog_ints(c->bmax);
+  const BatchArg ba_y{B, np, (long)Nf * Nd, 0, win};
+  const BatchArg ba_x{B, (long)Nf * Nm, (long)Nt * Nm, 0, win};
+  const BatchArg ba_p{B, (long)Nt * Nm, (long)Nt * Nm, (long)((Nt + 1) / 2) * Nm, win};
+  if (prec == TW_PREC_FP64) {
+    { twh::Phase p(c, TW_PH_TRSV_FWD, s);
+      TW_CUDA(c, launch_trsm_d(c->Lp64, c->inv64, c->chF64, rhs, 0, rhs_bstride, c->bz, np, win, Nd,
+                               Nt, B, c->NB, prog_f, true, c->d_err, c->abort_flag, s)); }
+    { twh::Phase p(c, TW_PH_TRSV_BWD, s);
+      TW_CUDA(c, launch_trsm_d(c->Lp64, c->inv64, c->chB64, c->bz, 0, np, c->by, np, win, Nd, Nt, B,
+                               c->NB, prog_b, false, c->d_err, c->abort_flag, s)); }
+    { twh::Phase p(c, TW_PH_RFFT_DATA, s);
+      TW_CUDA(c, launch_rfft_time_dd(c->by, 0, Nd, Nt, (cdd *)c->byh, Nd, Nd, c->plT, c->twT, c->twL, s, ba_y)); }
+    { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
+      TW_CUDA(c, launch_gemm_adj_dd(A, (const cdd *)c->byh, (long)Nf * Nd, (cdd *)c->bxh, (long)Nf * Nm,
+                                    Nf, Nd, Nm, B, s)); }
+    { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+      TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s, ba_x)); }
+    { twh::Phase p(c, TW_PH_PRIOR, s);
+      TW_CUDA(c, launch_prior_dd(m, 0, m, 0, Nt, c->Nx, c->Ny, (cdd *)c->bxh, c->lam1, c->plX, c->plY,
+                                 c->twX, c->twY, s, ba_p, 0)); }
+  } else {
+    { twh::Phase p(c, TW_PH_TRSV_FWD, s);
+      TW_CUDA(c, launch_trsm_dd(c->Lp_dd, c->inv_dd, c->chF_dd, rhs, 0, rhs_bstride, c->bzd, np, win,
+                                Nd, Nt, B, c->NB, prog_f, true, c->d_err, c->abort_flag, s)); }
+    { twh::Phase p(c, TW_PH_TRSV_BWD, s);
+      TW_CUDA(c, launch_trsm_dd(c->Lp_dd, c->inv_dd, c->chB_dd, c->bzd, 1, np, c->byd, np, win, Nd, Nt,
+                                B, c->NB, prog_b, false, c->d_err, c->abort_flag, s)); }
+    { twh::Phase p(c, TW_PH_RFFT_DATA, s);
+      TW_CUDA(c, launch_rfft_time_f(c->byd, 1, Nd, Nt, (cf *)c->byh, Nd, Nd, c->plT, c->twTf, c->twLf, s, ba_y)); }
+    { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
+      TW_CUDA(c, launch_gemm_adj_f(A, (int)prec, (const cf *)c->byh, (long)Nf * Nd, (cf *)c->bxh,
+                                   (long)Nf * Nm, Nf, Nd, Nm, B, s)); }
+    { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+      TW_CUDA(c, launch_irfft_time_f((const cf *)c->bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s, ba_x)); }
+    { twh::Phase p(c, TW_PH_PRIOR, s);
+      TW_CUDA(c, launch_prior_f(m, 0, m, 0, Nt, c->Nx, c->Ny, (cf *)c->bxh, c->lam1f, c->plX, c->plY,
+                                c->twXf, c->twYf, s, ba_p, 0)); }
+  }
+  if (q) return forecast_core(c, prec, B, win, m, q, s);
+  return TW_OK;
+}
+
+// s = m_pr + Gamma_pr F'^T K'^{-1} (d' - F' m_pr - sigma z_n), m_pr = Gamma_pr^{1/2} z_m
+tw_status sample_core(tw_ctx *c, tw_prec prec, int B, const int *win, const double *d,
+                      const double *z_m, const double *z_n, double sigma, double *samples,
+                      cudaStream_t s) {
+  const int Nd = c->Nd, Nt = c->Nt, Nm = c->Nm, Nf = c->Nf;
+  const void *A = c->op[TW_MAP_F][prec];
+  const BatchArg ba_full{B, (long)Nt * Nm, (long)Nt * Nm, (long)((Nt + 1) / 2) * Nm, nullptr};
+  const BatchArg ba_m{B, (long)Nt * Nm, (long)Nf * Nm, 0, win};
+  const BatchArg ba_d{B, (long)Nf * Nd, (long)Nt * Nd, 0, win};
+  const bool f64 = prec == TW_PREC_FP64;
+  // m_pr into the output
+  { twh::Phase p(c, TW_PH_PRIOR, s);
+    if (f64) TW_CUDA(c, launch_prior_dd(z_m, 0, samples, 0, Nt, c->Nx, c->Ny, (cdd *)c->bxh, c->lamh,
+                                        c->plX, c->plY, c->twX, c->twY, s, ba_full, 0));
+    else TW_CUDA(c, launch_prior_f(z_m, 0, samples, 0, Nt, c->Nx, c->Ny, (cf *)c->bxh, c->lamhf,
+                                   c->plX, c->plY, c->twXf, c->twYf, s, ba_full, 0)); }
+  // a = F' m_pr (the leading window blocks depend on m_pr's leading blocks only)
+  if (f64) {
+    { twh::Phase p(c, TW_PH_RFFT_PARAM, s);
+      TW_CUDA(c, launch_rfft_time_dd(samples, 0, Nm, Nt, (cdd *)c->bxh, Nm, Nm, c->plT, c->twT, c->twL, s, ba_m)); }
+    { twh::Phase p(c, TW_PH_GEMV_FWD, s);
+      TW_CUDA(c, launch_gemm_fwd_dd(A, (const cdd *)c->bxh, (long)Nf * Nm, (cdd *)c->bpart, (cdd *)c->byh,
+                                    (long)Nf * Nd, Nf, Nd, Nm, B, s)); }
+    { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
+      TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->byh, Nd, c->brd, 0, Nd, Nd, Nt, c->plT, c->twT, c->twL, s, ba_d)); }
+  } else {
+    { twh::Phase p(c, TW_PH_RFFT_PARAM, s);
+      TW_CUDA(c, launch_rfft_time_f(samples, 0, Nm, Nt, (cf *)c->bxh, Nm, Nm, c->plT, c->twTf, c->twLf, s, ba_m)); }
+    { twh::Phase p(c, TW_PH_GEMV_FWD, s);
+      TW_CUDA(c, launch_gemm_fwd_f(A, (int)prec, (const cf *)c->bxh, (long)Nf * Nm, (cf *)c->bpart,
+                                   (cf *)c->byh, (long)Nf * Nd, Nf, Nd, Nm, B, s)); }
+    { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
+      TW_CUDA(c, launch_irfft_time_f((const cf *)c->byh, Nd, c->brd, 0, Nd, Nd, Nt, c->plT, c->twTf, c->twLf, s, ba_d)); }
+  }
+  const long nd = (long)B * Nt * Nd;
+  k_sample_rhs_b<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(d, c->brd, z_n, sigma, c->brd, nd);
+  count_launches(1);
+  TW_CUDA(c, cudaGetLastError());
+  tw_status st = infer_core(c, prec, B, win, c->brd, (long)Nt * Nd, samples, nullptr, s);
+  if (st != TW_OK) return st;
+  // add m_pr back (recomputed: no second parameter-sized buffer is needed)
+  twh::Phase p(c, TW_PH_PRIOR, s);
+  if (f64) TW_CUDA(c, launch_prior_dd(z_m, 0, samples, 0, Nt, c->Nx, c->Ny, (cdd *)c->bxh, c->lamh,
+                                      c->plX, c->plY, c->twX, c->twY, s, ba_full, 1));
+  else TW_CUDA(c, launch_prior_f(z_m, 0, samples, 0, Nt, c->Nx, c->Ny, (cf *)c->bxh, c->lamhf,
+                                 c->plX, c->plY, c->twXf, c->twYf, s, ba_full, 1));
+  return TW_OK;
+}
+
+void free_batch(tw_ctx *c) {
+  void **bufs[] = {(void **)&c->win_dev, (void **)&c->trsm_prog, (void **)&c->bz, (void **)&c->by,
+                   (void **)&c->bzd, (void **)&c->byd, (void **)&c->brd, &c->byh, &c->bxh,
+                   &c->bpart, (void **)&c->Lp_dd, (void **)&c->inv_dd, (void **)&c->chF_dd,
+                   (void **)&c->chB_dd};
+  for (void **b : bufs) { twh::dfree(c, *b); *b = nullptr; }
+  c->bmax = 0;
+}
+
+}  // namespace
+
+tw_status twh::refresh_dd_factor(tw_ctx *c, cudaStream_t s) {
+  if (!c->Lp_dd || !c->have64) return TW_OK;
+  const size_t blk = (size_t)NB_ * NB_;
+  const size_t nblk = (size_t)c->NB * (c->NB + 1) / 2;
+  TW_CUDA(c, launch_double_to_dd(c->Lp64, c->Lp_dd, nblk * blk, s));
+  TW_CUDA(c, launch_double_to_dd(c->inv64, c->inv_dd, (size_t)c->NB * blk, s));
+  TW_CUDA(c, launch_double_to_dd(c->chF64, c->chF_dd, (size_t)c->NB * blk, s));
+  TW_CUDA(c, launch_double_to_dd(c->chB64, c->chB_dd, (size_t)c->NB * blk, s));
+  TW_CUDA(c, cudaStreamSynchronize(s));
+  return TW_OK;
+}
+
+extern "C" {
+
+tw_status tw_reserve_batch(tw_ctx *c, int bmax) {
+  if (!c) return TW_ERR_ARG;
+  if (bmax < 0) return twh::fail(c, TW_ERR_ARG, "bmax must be >= 0");
+  if (!c->have64) return twh::fail(c, TW_ERR_STATE, "tw_factor_K (FP64 factor) must come first");
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  TW_CUDA(c, cudaDeviceSynchronize());
+  free_batch(c);
+  if (bmax == 0) return TW_OK;
+  const size_t B = bmax, np = c->n_pad, Nt = c->Nt, Nf = c->Nf, Nm = c->Nm, R = c->Rmax;
+  const bool mixed = c->op[TW_MAP_F][TW_PREC_C64] || c->op[TW_MAP_F][TW_PREC_BF16X2];
+  const size_t blk = (size_t)NB_ * NB_;
+  const size_t nblk = (size_t)c->NB * (c->NB + 1) / 2;
+  bool ok = true;
+  auto take = [&](size_t bytes) -> void * {
+    void *p = twh::dalloc(c, bytes);
+    ok = ok && p;
+    return p;
+  };
+  c->win_dev = (int *)take(B * sizeof(int));
+  c->trsm_prog = (int *)take(2 * (size_t)trsm_prog_ints(bmax) * sizeof(int));
+  c->bz = (double *)take(B * np * sizeof(double));
+  c->by = (double *)take(B * np * sizeof(double));
+  c->brd = (double *)take(B * Nt * c->Nd * sizeof(double));
+  c->byh = take(B * Nf * R * sizeof(cdd));
+  c->bxh = take(B * Nf * Nm * sizeof(cdd));   // >= B * ceil(Nt/2) * Nm: also the prior's work
+  c->bpart = take(B * Nf * (size_t)gemm_fwd_nchunk(c->Nm) * R * sizeof(cdd));
+  if (mixed) {
+    c->bzd = (dd *)take(B * np * sizeof(dd));
+    c->byd = (dd *)take(B * np * sizeof(dd));
+    c->Lp_dd = (dd *)take(nblk * blk * sizeof(dd));
+    c->inv_dd = (dd *)take(c->NB * blk * sizeof(dd));
+    c->chF_dd = (dd *)take(c->NB * blk * sizeof(dd));
+    c->chB_dd = (dd *)take(c->NB * blk * sizeof(dd));
+  }
+  if (!ok) {
+    free_batch(c);
+    return twh::fail(c, TW_ERR_OOM, "batch workspaces");
+  }
+  c->bmax = bmax;
+  TW_CUDA(c, cudaMemset(c->win_dev, 0, B * sizeof(int)));
+  return twh::refresh_dd_factor(c, 0);
+}
+
+int tw_batch_capacity(const tw_ctx *c) { return c ? c->bmax : -1; }
+
+tw_status tw_infer_batch(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window_dev,
+                         const double *d, double *m, double *q, void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (nrhs < 0 || (nrhs > 0 && (!d || !m))) return twh::fail(c, TW_ERR_ARG, "bad rhs");
+  tw_status st = check_batch(c, prec, nrhs, nt_window_dev);
+  if (st != TW_OK || nrhs == 0) return st;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  return infer_core(c, prec, nrhs, nt_window_dev, d, (long)c->Nt * c->Nd, m, q, (cudaStream_t)stream);
+}
+
+tw_status tw_sample_posterior_batch(tw_ctx *c, tw_prec prec, int ns, const int *nt_window_dev,
+                                    const double *d, const double *z_m, const double *z_n,
+                                    double sigma, double *samples, void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (ns < 0 || (ns > 0 && (!d || !z_m || !z_n || !samples)))
+    return twh::fail(c, TW_ERR_ARG, "bad sample arguments");
+  if (!(sigma >= 0.0)) return twh::fail(c, TW_ERR_ARG, "sigma must be >= 0");
+  tw_status st = check_batch(c, prec, ns, nt_window_dev);
+  if (st != TW_OK || ns == 0) return st;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  return sample_core(c, prec, ns, nt_window_dev, d, z_m, z_n, sigma, samples, (cudaStream_t)stream);
+}
+
+tw_status tw_forecast_batch(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window_dev,
+                            const double *m, double *q, void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (nrhs < 0 || (nrhs > 0 && (!m || !q))) return twh::fail(c, TW_ERR_ARG, "bad rhs");
+  if (prec < 0 || prec > 2 || !c->op[TW_MAP_FQ][prec])
+    return twh::fail(c, TW_ERR_ARG, "requested precision was not kept at tw_create");
+  if (c->bmax <= 0) return twh::fail(c, TW_ERR_STATE, "tw_reserve_batch must come first");
+  if (nrhs > c->bmax) return twh::fail(c, TW_ERR_ARG, "more right-hand sides than reserved");
+  if (nrhs == 0) return TW_OK;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  return forecast_core(c, prec, nrhs, nt_window_dev, m, q, (cudaStream_t)stream);
+}
+
+// ---- CUDA graphs of batched calls
+struct tw_graph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t x = nullptr;
+};
+
+tw_status tw_capture_begin(tw_ctx *c, void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (!stream) return twh::fail(c, TW_ERR_ARG, "capture needs a created stream (not the default)");
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  TW_CUDA(c, cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeRelaxed));
+  return TW_OK;
+}
+
+tw_status tw_capture_end(tw_ctx *c, void *stream, tw_graph **out) {
+  if (!c || !out) return TW_ERR_ARG;
+  *out = nullptr;
+  cudaGraph_t g = nullptr;
+  TW_CUDA(c, cudaStreamEndCapture((cudaStream_t)stream, &g));
+  tw_graph *h = new tw_graph;
+  h->g = g;
+  cudaError_t e = cudaGraphInstantiate(&h->x, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    delete h;
+    return twh::cuda_fail(c, e, "cudaGraphInstantiate");
+  }
+  *out = h;
+  return TW_OK;
+}
+
+tw_status tw_graph_launch(tw_graph *h, void *stream) {
+  if (!h || !h->x) return TW_ERR_ARG;
+  return cudaGraphLaunch(h->x, (cudaStream_t)stream) == cudaSuccess ? TW_OK : TW_ERR_CUDA;
+}
+
+int tw_graph_kernel_count(const tw_graph *h) {
+  if (!h || !h->g) return -1;
+  size_t n = 0;
+  if (cudaGraphGetNodes(h->g, nullptr, &n) != cudaSuccess) return -1;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(h->g, nodes.data(), &n) != cudaSuccess) return -1;
+  int k = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
+void tw_graph_destroy(tw_graph *h) {
+  if (!h) return;
+  if (h->x) cudaGraphExecDestroy(h->x);
+  if (h->g) cudaGraphDestroy(h->g);
+  delete h;
+}
+
+}  // extern "C"
+
+// host-window entry points route here when a batch is reserved
+namespace twb {
+
+tw_status infer_host_windows(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window,
+                             const double *d, double *m, cudaStream_t s) {
+  for (int r0 = 0; r0 < nrhs; r0 += c->bmax) {
+    const int nb = std::min(c->bmax, nrhs - r0);
+    tw_status st = upload_windows(c, nt_window ? nt_window + r0 : nullptr, nb, s);
+    if (st != TW_OK) return st;
+    st = infer_core(c, prec, nb, c->win_dev, d + (size_t)r0 * c->Nt * c->Nd, (long)c->Nt * c->Nd,
+                    m + (size_t)r0 * c->Nt * c->Nm, nullptr, s);
+    if (st != TW_OK) return st;
+  }
+  return TW_OK;
+}
+
+tw_status sample_host_windows(tw_ctx *c, int ns, const int *nt_window, const double *d,
+                              const double *z_m, const double *z_n, double sigma, double *samples,
+                              cudaStream_t s) {
+  const size_t pm = (size_t)c->Nt * c->Nm, pd = (size_t)c->Nt * c->Nd;
+  for (int k0 = 0; k0 < ns; k0 += c->bmax) {
+    const int nb = std::min(c->bmax, ns - k0);
+    tw_status st = upload_windows(c, nt_window ? nt_window + k0 : nullptr, nb, s);
+    if (st != TW_OK) return st;
+    st = sample_core(c, TW_PREC_FP64, nb, c->win_dev, d + k0 * pd, z_m + k0 * pm, z_n + k0 * pd,
+                     sigma, samples + k0 * pm, s);
+    if (st != TW_OK) return st;
+  }
+  return TW_OK;
+}
+
+tw_status forecast_full(tw_ctx *c, tw_prec prec, int nrhs, const double *m, double *q,
+                        cudaStream_t s) {
+  const size_t pm = (size_t)c->Nt * c->Nm, pq = (size_t)c->Nt * c->Nq;
+  for (int r0 = 0; r0 < nrhs; r0 += c->bmax) {
+    const int nb = std::min(c->bmax, nrhs - r0);
+    tw_status st = forecast_core(c, prec, nb, nullptr, m + r0 * pm, q + r0 * pq, s);
+    if (st != TW_OK) return st;
+  }
+  return TW_OK;
+}
+
+}  // namespace twb

@@ -59,6 +59,16 @@ SIGNATURES = {
     "tw_p2o_apply_noalloc": (_S, [_P, _I, _I, _I, _P, _P, _P]),
     "tw_check": (_S, [_P, _P]),
     "tw_device_bytes": (ctypes.c_size_t, [_P]),
+    "tw_reserve_batch": (_S, [_P, _I]),
+    "tw_batch_capacity": (_I, [_P]),
+    "tw_infer_batch": (_S, [_P, _I, _I, _P, _P, _P, _P, _P]),
+    "tw_sample_posterior_batch": (_S, [_P, _I, _I, _P, _P, _P, _P, _D, _P, _P]),
+    "tw_forecast_batch": (_S, [_P, _I, _I, _P, _P, _P, _P]),
+    "tw_capture_begin": (_S, [_P, _P]),
+    "tw_capture_end": (_S, [_P, _P, ctypes.POINTER(_P)]),
+    "tw_graph_launch": (_S, [_P, _P]),
+    "tw_graph_kernel_count": (_I, [_P]),
+    "tw_graph_destroy": (None, [_P]),
 }
 
 _lib = None
@@ -124,6 +134,7 @@ class Context:
         self.Nd, self.Nq, self.Nx, self.Ny, self.Nt = Nd, Nq, Nx, Ny, Nt
         self.Nm = Nx * Ny
         self.device = device
+        self.keep = keep
         h = ctypes.c_void_p()
         st = self.lib.tw_create(ctypes.byref(h), Nd, Nq, Nx, Ny, Nt, Lx, Ly, keep, device)
         if st != OK:
@@ -301,6 +312,59 @@ class Context:
         self._check(self.lib.tw_forecast(self.h, prec, nrhs, pm, po, _stream_ptr(stream)))
         return out
 
+    # -------------------------------------------------------- batches
+    def reserve_batch(self, bmax: int):
+        """Workspaces for batches of up to bmax right-hand sides (after factor_K)."""
+        self._check(self.lib.tw_reserve_batch(self.h, int(bmax)))
+
+    def batch_capacity(self) -> int:
+        return int(self.lib.tw_batch_capacity(self.h))
+
+    def infer_batch(self, prec, d, windows_dev, m=None, q=None, forecast=True, stream=None):
+        """Posterior means (and forecasts) of d [B][Nt][Nd]; windows_dev: int32 CUDA tensor [B]."""
+        import torch
+        B = d.shape[0]
+        pd = _dev(d, torch.float64, (B, self.Nt, self.Nd), "d")
+        pw = _dev(windows_dev, torch.int32, (B,), "windows")
+        if m is None:
+            m = torch.empty((B, self.Nt, self.Nm), dtype=torch.float64, device=d.device)
+        pm = _dev(m, torch.float64, (B, self.Nt, self.Nm), "m")
+        pq = None
+        if forecast:
+            if q is None:
+                q = torch.empty((B, self.Nt, self.Nq), dtype=torch.float64, device=d.device)
+            pq = _dev(q, torch.float64, (B, self.Nt, self.Nq), "q")
+        self._check(self.lib.tw_infer_batch(self.h, prec, B, pw, pd, pm, pq, _stream_ptr(stream)))
+        return (m, q) if forecast else m
+
+    def sample_posterior_batch(self, prec, d, z_m, z_n, sigma, windows_dev, out=None, stream=None):
+        import torch
+        ns = z_m.shape[0]
+        pd = _dev(d, torch.float64, (ns, self.Nt, self.Nd), "d")
+        pzm = _dev(z_m, torch.float64, (ns, self.Nt, self.Nm), "z_m")
+        pzn = _dev(z_n, torch.float64, (ns, self.Nt, self.Nd), "z_n")
+        pw = _dev(windows_dev, torch.int32, (ns,), "windows")
+        out = torch.empty_like(z_m) if out is None else out
+        po = _dev(out, torch.float64, (ns, self.Nt, self.Nm), "samples")
+        self._check(self.lib.tw_sample_posterior_batch(self.h, prec, ns, pw, pd, pzm, pzn,
+                                                       float(sigma), po, _stream_ptr(stream)))
+        return out
+
+    def forecast_batch(self, prec, m, windows_dev=None, out=None, stream=None):
+        import torch
+        B = m.shape[0]
+        pm = _dev(m, torch.float64, (B, self.Nt, self.Nm), "m")
+        pw = None if windows_dev is None else _dev(windows_dev, torch.int32, (B,), "windows")
+        if out is None:
+            out = torch.empty((B, self.Nt, self.Nq), dtype=torch.float64, device=m.device)
+        po = _dev(out, torch.float64, (B, self.Nt, self.Nq), "q")
+        self._check(self.lib.tw_forecast_batch(self.h, prec, B, pw, pm, po, _stream_ptr(stream)))
+        return out
+
+    def capture(self, stream):
+        """Context manager: batched calls on `stream` inside it are recorded into a Graph."""
+        return _Capture(self, stream)
+
     # -------------------------------------------------------- profiling
     def profile(self, on=True):
         self._check(self.lib.tw_profile_enable(self.h, 1 if on else 0))
@@ -312,6 +376,51 @@ class Context:
         calls = (ctypes.c_longlong * n)()
         self._check(self.lib.tw_profile_read(self.h, ms, calls, 1 if reset else 0))
         return {PHASES[i]: (ms[i], calls[i]) for i in range(n)}
+
+
+class Graph:
+    """An instantiated CUDA graph of batched calls (tw_graph)."""
+
+    def __init__(self, lib, handle):
+        self.lib, self.h = lib, handle
+
+    def launch(self, stream=None):
+        st = self.lib.tw_graph_launch(self.h, _stream_ptr(stream))
+        if st != OK:
+            raise TwError(st, "tw_graph_launch failed")
+
+    def kernel_count(self) -> int:
+        return int(self.lib.tw_graph_kernel_count(self.h))
+
+    def close(self):
+        if self.h:
+            self.lib.tw_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Capture:
+    def __init__(self, ctx, stream):
+        self.ctx, self.stream, self.graph = ctx, stream, None
+
+    def __enter__(self):
+        self.ctx._check(self.ctx.lib.tw_capture_begin(self.ctx.h, _stream_ptr(self.stream)))
+        return self
+
+    def __exit__(self, et, ev, tb):
+        h = ctypes.c_void_p()
+        st = self.ctx.lib.tw_capture_end(self.ctx.h, _stream_ptr(self.stream), ctypes.byref(h))
+        if et is None:
+            self.ctx._check(st)
+            self.graph = Graph(self.ctx.lib, h)
+        elif h:
+            self.ctx.lib.tw_graph_destroy(h)
+        return False
 
 
 def kernel_launches() -> int:
