@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-steps", type=int, default=3)
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--requests", type=int, default=1000,
+                   help="requests of the serving trace (Poisson 200/s)")
     return p.parse_args()
 
 
@@ -262,12 +265,7 @@ def run_batch(args, ctx, cfg, sigma, d0, dev, barrier):
     ws = [int(w) for w in synth.batch_windows(c4)]
     ctx.reserve_batch(max(E, S))
     # event data: d_e = F Gamma^{1/2} z_e + sigma z_n,e (event 0: the fixed data vector)
-    d = torch.empty((E, cfg.Nt, cfg.Nd), dtype=torch.float64, device=dev)
-    d[0] = d0[0]
-    for e in range(1, E):
-        z = torch.from_numpy(synth.event_z(c4, e)).to(dev)
-        dcl = ctx.p2o_apply(tw.MAP_F, tw.PREC_FP64, ctx.prior_apply(z, 0.5))[0]
-        d[e] = dcl + sigma * torch.from_numpy(synth.noise_z(c4, e)).to(dev)
+    d = event_bank(ctx, cfg, c4, E, sigma, d0, dev)
     zm = torch.empty((S, cfg.Nt, cfg.Nm), dtype=torch.float64, device=dev)
     zn = torch.empty((S, cfg.Nt, cfg.Nd), dtype=torch.float64, device=dev)
     for k in range(S):
@@ -340,6 +338,72 @@ def run_batch(args, ctx, cfg, sigma, d0, dev, barrier):
     ctx.reserve_batch(0)
     torch.cuda.empty_cache()
     return out
+
+
+def event_bank(ctx, cfg, src_cfg, n, sigma, d0, dev):
+    """Data vectors of events 0..n-1: d_e = F Gamma^{1/2} z_e + sigma z_n,e (event 0 given)."""
+    import torch
+
+    import synth
+    from paper_2504_16344_gb300 import tw
+    d = torch.empty((n, cfg.Nt, cfg.Nd), dtype=torch.float64, device=dev)
+    d[0] = d0[0]
+    for e in range(1, n):
+        z = torch.from_numpy(synth.event_z(src_cfg, e)).to(dev)
+        dcl = ctx.p2o_apply(tw.MAP_F, tw.PREC_FP64, ctx.prior_apply(z, 0.5))[0]
+        d[e] = dcl + sigma * torch.from_numpy(synth.noise_z(src_cfg, e)).to(dev)
+    return d
+
+
+def run_serve(args, ctx, cfg, sigma, d0, dev):
+    """Serving: the request recipe of the 16-event serving workload (Poisson
+    arrivals at 200/s, event uniform, window uniform in [60, Nt]) replayed in
+    real time on this operator, FP64 path and mixed path on the same trace."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2504_16344_gb300 import tw
+
+    # the serving recipe's seeds (events, trace) at this operator's shapes
+    c5 = dataclass_replace(synth.CONFIGS[5], Nd=cfg.Nd, Nx=cfg.Nx, Ny=cfg.Ny, Nt=cfg.Nt, Nq=cfg.Nq)
+    reqs = synth.request_trace(c5, n=args.requests)
+    arr = np.array([r.t_arrival for r in reqs])
+    ev = np.array([r.event for r in reqs], dtype=np.int32)
+    win = np.array([r.window for r in reqs], dtype=np.int32)
+    bmax = 64
+    ctx.reserve_batch(bmax)
+    bank = event_bank(ctx, cfg, c5, c5.events, sigma, d0, dev)
+    stream = torch.cuda.Stream(device=dev)
+    out = {"workload": (f"{len(reqs)} requests, Poisson arrivals at 200/s over {arr[-1]:.1f} s, "
+                        f"event uniform over {c5.events}, window uniform in [60, {cfg.Nt}]; "
+                        "each request: posterior mean + forecast, forecast copied to host; "
+                        "operator of the 100-sensor 200x250-grid case"),
+           "max_batch": bmax}
+    for name, prec in (("fp64", tw.PREC_FP64), ("mixed_c64", tw.PREC_C64)):
+        if not ctx_has(ctx, prec):
+            continue
+        ctx.serve_replay(prec, arr[:8] - arr[0], ev[:8], win[:8], bank, bmax, stream, q_out=False)
+        lat, _, _, st = ctx.serve_replay(prec, arr, ev, win, bank, bmax, stream, q_out=False)
+        out[name] = {"p50_ms": round(float(np.percentile(lat, 50)), 2),
+                     "p99_ms": round(float(np.percentile(lat, 99)), 2),
+                     "max_ms": round(float(lat.max()), 2),
+                     "solves_per_s": round(len(reqs) / st.makespan_s, 1),
+                     "capacity_solves_per_s": round(len(reqs) / st.busy_s, 1),
+                     "batches": st.batches, "mean_batch": round(st.mean_batch, 2),
+                     "max_batch": st.max_batch}
+    if "fp64" in out and "mixed_c64" in out:
+        out["mixed_capacity_ratio"] = round(out["mixed_c64"]["capacity_solves_per_s"] /
+                                            out["fp64"]["capacity_solves_per_s"], 3)
+    ctx.reserve_batch(0)
+    del bank
+    torch.cuda.empty_cache()
+    return out
+
+
+def dataclass_replace(cfg, **kw):
+    import dataclasses
+    return dataclasses.replace(cfg, **kw)
 
 
 def ctx_has(ctx, prec):
@@ -503,6 +567,10 @@ def run_ours(args):
     if not args.no_batch and not args.small:
         batch = run_batch(args, ctx, cfg, sigma, d, dev, barrier)
 
+    serve = None
+    if not args.no_serve and not args.small:
+        serve = run_serve(args, ctx, cfg, sigma, d, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
         v, desc, spent = oracle_sample(cfg)
@@ -524,6 +592,7 @@ def run_ours(args):
         "phases_ms": phase_ms,
         "mixed": mixed,
         "batch": batch,
+        "serve": serve,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),

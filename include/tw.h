@@ -359,6 +359,50 @@ tw_status tw_graph_launch(tw_graph *graph, void *stream);
 int tw_graph_kernel_count(const tw_graph *graph);
 void tw_graph_destroy(tw_graph *graph);
 
+/*
+ * ---- Serving (Phase 4 under a stream of requests).
+ * A request names an event (a data vector in a device-resident bank) and an
+ * observation window Nt'; it is served when its posterior mean and
+ * forecast are computed and the forecast is in host memory.  Admission:
+ * requests queue in arrival order; whenever the device is idle and requests
+ * wait, the oldest min(waiting, max_batch) start as one batch
+ * (work-conserving continuous batching; max_batch <= the reserved batch,
+ * which tw_reserve_batch sized from device memory).
+ */
+typedef struct {
+  int batches;         /* batches launched                                   */
+  int max_batch;       /* largest batch                                      */
+  double mean_batch;   /* requests per batch                                 */
+  double makespan_s;   /* first arrival to last completion                   */
+  double busy_s;       /* summed device time of the batches                  */
+} tw_serve_stats;
+
+/*
+ * tw_serve_replay -- replay a trace in real time: request i arrives
+ * arrival_s[i] seconds (host, sorted) after the call starts its clock,
+ * with event[i] in [0, nevents) and window[i] in [1, Nt] (host arrays).
+ * event_data: device [nevents][Nt][Nd].  Outputs (host): latency_ms[i] =
+ * completion - arrival; q_out [nreq][Nt][Nq] and m_out [nreq][Nt][Nm]
+ * (either may be NULL; copying m_out is outside the timed path but slows
+ * the replay).  stats may be NULL.  Needs tw_reserve_batch; allocates its
+ * slot buffers (max_batch x (Nt Nm + Nt Nd + Nt Nq) doubles) before the clock
+ * starts and frees them on return.  `stream` must be a created stream.
+ */
+tw_status tw_serve_replay(tw_ctx *ctx, tw_prec prec, int nreq, const double *arrival_s,
+                          const int *event, const int *window, int nevents,
+                          const double *event_data, int max_batch, double *latency_ms,
+                          double *q_out, double *m_out, tw_serve_stats *stats, void *stream);
+
+/*
+ * tw_serve_simulate -- the same admission policy on a virtual clock with a
+ * modelled batch time of cost_ms + cost_ms_per_req * batch size (host
+ * only, no device use): latency_ms[i] and the batch index batch_of[i]
+ * (may be NULL) of each request.  Returns TW_ERR_ARG for unsorted arrivals,
+ * max_batch < 1 or NULL arrays.
+ */
+tw_status tw_serve_simulate(int nreq, const double *arrival_s, int max_batch, double cost_ms,
+                            double cost_ms_per_req, double *latency_ms, int *batch_of);
+
 /* Synchronise `stream` and report errors recorded by kernels (TW_OK,
  * TW_ERR_NOT_SPD, TW_ERR_TIMEOUT, TW_ERR_CUDA).  Clears the record. */
 tw_status tw_check(tw_ctx *ctx, void *stream);

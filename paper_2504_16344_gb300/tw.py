@@ -69,6 +69,8 @@ SIGNATURES = {
     "tw_graph_launch": (_S, [_P, _P]),
     "tw_graph_kernel_count": (_I, [_P]),
     "tw_graph_destroy": (None, [_P]),
+    "tw_serve_replay": (_S, [_P, _I, _I, _P, _P, _P, _I, _P, _I, _P, _P, _P, _P, _P]),
+    "tw_serve_simulate": (_S, [_I, _P, _I, _D, _D, _P, _P]),
 }
 
 _lib = None
@@ -76,6 +78,12 @@ _lib = None
 
 class InferStats(ctypes.Structure):
     _fields_ = [("ir_iters", ctypes.c_int), ("resid_rel", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("mean_batch", ctypes.c_double), ("makespan_s", ctypes.c_double),
+                ("busy_s", ctypes.c_double)]
 
 
 class TwError(RuntimeError):
@@ -361,6 +369,29 @@ class Context:
         self._check(self.lib.tw_forecast_batch(self.h, prec, B, pw, pm, po, _stream_ptr(stream)))
         return out
 
+    def serve_replay(self, prec, arrival_s, event, window, event_data, max_batch, stream,
+                     q_out=True, m_out=False):
+        """Replay a request trace (host arrays) with continuous batching.
+
+        Returns (latency_ms [n], q [n][Nt][Nq] or None, m [n][Nt][Nm] or None, ServeStats)."""
+        import numpy as np
+        import torch
+        n = len(arrival_s)
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        ev = np.ascontiguousarray(event, dtype=np.int32)
+        win = np.ascontiguousarray(window, dtype=np.int32)
+        ne = event_data.shape[0]
+        pe = _dev(event_data, torch.float64, (ne, self.Nt, self.Nd), "event_data")
+        lat = np.zeros(n, dtype=np.float64)
+        q = np.zeros((n, self.Nt, self.Nq), dtype=np.float64) if q_out else None
+        m = np.zeros((n, self.Nt, self.Nm), dtype=np.float64) if m_out else None
+        st = ServeStats()
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+        self._check(self.lib.tw_serve_replay(self.h, prec, n, ptr(arr), ptr(ev), ptr(win), ne, pe,
+                                             int(max_batch), ptr(lat), ptr(q), ptr(m),
+                                             ctypes.byref(st), _stream_ptr(stream)))
+        return lat, q, m, st
+
     def capture(self, stream):
         """Context manager: batched calls on `stream` inside it are recorded into a Graph."""
         return _Capture(self, stream)
@@ -421,6 +452,22 @@ class _Capture:
         elif h:
             self.ctx.lib.tw_graph_destroy(h)
         return False
+
+
+def serve_simulate(arrival_s, max_batch, cost_ms, cost_ms_per_req):
+    """The serving policy on a virtual clock: (latency_ms [n], batch index [n]). Host only."""
+    import numpy as np
+    arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    n = len(arr)
+    lat = np.zeros(n, dtype=np.float64)
+    bid = np.zeros(n, dtype=np.int32)
+    st = load().tw_serve_simulate(n, arr.ctypes.data_as(ctypes.c_void_p), int(max_batch),
+                                  float(cost_ms), float(cost_ms_per_req),
+                                  lat.ctypes.data_as(ctypes.c_void_p),
+                                  bid.ctypes.data_as(ctypes.c_void_p))
+    if st != OK:
+        raise TwError(st, "tw_serve_simulate failed")
+    return lat, bid
 
 
 def kernel_launches() -> int:
