@@ -44,6 +44,16 @@ struct tw_ctx {
   bool have64 = false, have32 = false;
   double *Lp64 = nullptr, *inv64 = nullptr;                      // FP64 factor, packed 64x64 blocks
   double *chF64 = nullptr, *chB64 = nullptr;                      // chain blocks of the solves
+  // single-vector FP64 solves (trsv64.cu): block-scaled factor and scheduling state
+  double *Lf64 = nullptr, *Lb64 = nullptr;                        // packed, like Lp64
+  double *band1 = nullptr, *band2 = nullptr;                      // [NB][64][64]
+  int2 *tasks = nullptr;                                          // worker task table
+  std::vector<int> task_prefix;                                   // tasks of rows < u: task_prefix[u]
+  double *tpart = nullptr;                                        // [NB][maxk][64]
+  int tmaxk = 0;
+  int *tcnt = nullptr;                                            // [NB]
+  double *wbuf64 = nullptr;                                       // [n_pad]
+  int *wflag = nullptr;                                           // [NB]
   tw::dd *Kp64 = nullptr;                                         // K, packed, double-float
   float *Lp32 = nullptr, *inv32 = nullptr;
   float *chF32 = nullptr, *chB32 = nullptr;

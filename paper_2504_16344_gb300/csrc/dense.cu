@@ -1,3 +1,4 @@
+#include <algorithm>
 // dense.cu -- the data-space Hessian K: formation, Cholesky, triangular solves.
 //
 // Phase 2 of the paper forms K = Gamma_n + F Gamma_pr F* and Cholesky-factors
@@ -874,10 +875,10 @@ cudaError_t launch_trsv_d(const double *Lp, const double *Linv, const double *Lc
   if (e != cudaSuccess) return e;
   if (fwd)
     k_trsv<double, true><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, out,
-                                                         nrows, NBw, prog, err, abort_flag);
+                                                                nrows, NBw, prog, err, abort_flag);
   else
     k_trsv<double, false><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, out,
-                                                          nrows, NBw, prog, err, abort_flag);
+                                                                 nrows, NBw, prog, err, abort_flag);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -889,10 +890,10 @@ cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const float *Lchai
   if (e != cudaSuccess) return e;
   if (fwd)
     k_trsv<float, true><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, out,
-                                                        nrows, NBw, prog, err, abort_flag);
+                                                               nrows, NBw, prog, err, abort_flag);
   else
     k_trsv<float, false><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, out,
-                                                         nrows, NBw, prog, err, abort_flag);
+                                                                nrows, NBw, prog, err, abort_flag);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "dense.cuh"
 
 namespace tw {
@@ -27,6 +29,29 @@ cudaError_t launch_lower_to_float(const double *K, float *K32, long ld, int NB, 
 cudaError_t launch_trsv_d(const double *Lp, const double *Linv, const double *Lchain,
                           const void *rhs, int rhs_kind, double *out, int nrows, int NBw,
                           int *prog, bool fwd, int *err, int *abort_flag, cudaStream_t s);
+
+// FP64 solves of one right-hand side with the block-scaled factor (trsv64.cu)
+struct Trsv64Args {
+  const double *Lf, *Lb;            // packed Linv_I L_IJ and L_IJ Linv_J (J < I)
+  const double *Linv;               // [NB][64][64] diagonal-block inverses
+  const double *band1, *band2;      // forward chain blocks, transposed: Lf_{I,I-1}^T, Lf_{I,I-2}^T
+  const void *rhs;                  // kind 0 double, 1 float pairs
+  int rhs_kind;
+  double *out;
+  int nrows, NBw;
+  const int2 *tasks;                // (row, chunk) in row order; tasks of rows < NBw form a prefix
+  int ntasks;
+  double *part;                     // [NB][maxk][64] partial sums
+  int maxk;
+  int *cnt, *wflag;                 // [NB] each, zeroed by the launcher
+  double *wbuf;                     // [n_pad]
+  int *prog, *err, *abort_flag;     // prog: 2 ints, zeroed by the launcher
+};
+int trsv64_max_tasks_per_row(int NB);
+void trsv64_task_table(int NB, std::vector<int> &tab, std::vector<int> &prefix);
+cudaError_t launch_trsv64_setup(const double *Lp, const double *Linv, double *Lf, double *Lb,
+                                double *band1, double *band2, int NB, cudaStream_t s);
+cudaError_t launch_trsv64(const Trsv64Args &a, bool fwd, cudaStream_t s);
 cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const float *Lchain,
                           const void *rhs, int rhs_kind, float *out, int nrows, int NBw, int *prog,
                           bool fwd, int *err, int *abort_flag, cudaStream_t s);

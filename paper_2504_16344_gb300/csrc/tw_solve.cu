@@ -40,12 +40,17 @@ tw_status ensure_solve_workspace(tw_ctx *c) {
 // b: double (kind 0) or dd (kind 1)
 tw_status solve64(tw_ctx *c, const void *b, int kind, int nrows, double *y, cudaStream_t s) {
   const int NBw = (nrows + NB_ - 1) / NB_;
+  Trsv64Args a{};
+  a.Lf = c->Lf64; a.Lb = c->Lb64; a.Linv = c->inv64; a.band1 = c->band1; a.band2 = c->band2;
+  a.nrows = nrows; a.NBw = NBw; a.tasks = c->tasks; a.ntasks = c->task_prefix[NBw];
+  a.part = c->tpart; a.maxk = c->tmaxk; a.cnt = c->tcnt; a.wflag = c->wflag; a.wbuf = c->wbuf64;
+  a.err = c->d_err; a.abort_flag = c->abort_flag;
   { twh::Phase p(c, TW_PH_TRSV_FWD, s);
-    TW_CUDA(c, launch_trsv_d(c->Lp64, c->inv64, c->chF64, b, kind, c->zd, nrows, NBw, c->counter,
-                             true, c->d_err, c->abort_flag, s)); }
+    a.rhs = b; a.rhs_kind = kind; a.out = c->zd; a.prog = c->counter;
+    TW_CUDA(c, launch_trsv64(a, true, s)); }
   twh::Phase p(c, TW_PH_TRSV_BWD, s);
-  TW_CUDA(c, launch_trsv_d(c->Lp64, c->inv64, c->chB64, c->zd, 0, y, nrows, NBw, c->counter + 2,
-                           false, c->d_err, c->abort_flag, s));
+  a.rhs = c->zd; a.rhs_kind = 0; a.out = y; a.prog = c->counter + 2;
+  TW_CUDA(c, launch_trsv64(a, false, s));
   return TW_OK;
 }
 
@@ -215,6 +220,26 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
     if (!c->chB64) c->chB64 = (double *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(double));
     if (!c->chF64 || !c->chB64) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "chain blocks"); }
     TW_CUDA(c, launch_chain_blocks_d(c->Lp64, c->inv64, c->chF64, c->chB64, c->NB, s));
+    // single-vector solves: block-scaled factor, chain bands, task table
+    {
+      std::vector<int> tab;
+      trsv64_task_table(c->NB, tab, c->task_prefix);
+      c->tmaxk = trsv64_max_tasks_per_row(c->NB);
+      auto need = [&](void *&p, size_t bytes) { if (!p) p = twh::dalloc(c, bytes); return p != nullptr; };
+      bool ok = need((void *&)c->Lf64, nblk * blk * sizeof(double)) &&
+                need((void *&)c->Lb64, nblk * blk * sizeof(double)) &&
+                need((void *&)c->band1, (size_t)c->NB * blk * sizeof(double)) &&
+                need((void *&)c->band2, (size_t)c->NB * blk * sizeof(double)) &&
+                need((void *&)c->tasks, tab.size() / 2 * sizeof(int2)) &&
+                need((void *&)c->tpart, (size_t)c->NB * c->tmaxk * NB_ * sizeof(double)) &&
+                need((void *&)c->tcnt, (size_t)c->NB * sizeof(int)) &&
+                need((void *&)c->wbuf64, (size_t)np * sizeof(double)) &&
+                need((void *&)c->wflag, (size_t)c->NB * sizeof(int));
+      if (!ok) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "single-vector solve buffers"); }
+      TW_CUDA(c, cudaMemcpyAsync(c->tasks, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      TW_CUDA(c, launch_trsv64_setup(c->Lp64, c->inv64, c->Lf64, c->Lb64, c->band1, c->band2, c->NB, s));
+      TW_CUDA(c, cudaStreamSynchronize(s));
+    }
     tw_status cs = tw_check(c, stream);
     if (cs != TW_OK) { twh::dfree(c, K); return cs; }
     c->have64 = true;
