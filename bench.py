@@ -285,7 +285,8 @@ def run_batch(args, ctx, cfg, sigma, d0, dev, barrier):
                         "the 100-sensor 200x250-grid case"),
            "right_hand_sides": E + S}
     results = {}
-    for name, prec in (("fp64", tw.PREC_FP64), ("mixed_c64", tw.PREC_C64)):
+    for name, prec in (("fp64", tw.PREC_FP64), ("mixed_c64", tw.PREC_C64),
+                       ("mixed_bf16x2_tensorcore", tw.PREC_BF16X2)):
         if not ctx_has(ctx, prec):
             continue
         with torch.cuda.stream(stream):
@@ -331,9 +332,10 @@ def run_batch(args, ctx, cfg, sigma, d0, dev, barrier):
             results[name]["q_max_rel_err_vs_fp64"] = max(rel(q[e], q64[e]) for e in range(E))
             results[name]["sample_max_rel_err_vs_fp64"] = max(rel(smp[k], s64[k]) for k in range(S))
     out.update(results)
-    if "fp64" in results and "mixed_c64" in results:
-        out["mixed_speedup"] = round(results["fp64"]["ms_per_batch"] /
-                                     results["mixed_c64"]["ms_per_batch"], 3)
+    for name in ("mixed_c64", "mixed_bf16x2_tensorcore"):
+        if "fp64" in results and name in results:
+            results[name]["speedup_vs_fp64"] = round(results["fp64"]["ms_per_batch"] /
+                                                     results[name]["ms_per_batch"], 3)
     del m, q, smp, zm, zn, d, ds
     ctx.reserve_batch(0)
     torch.cuda.empty_cache()
@@ -408,7 +410,9 @@ def dataclass_replace(cfg, **kw):
 
 def ctx_has(ctx, prec):
     from paper_2504_16344_gb300 import tw
-    return prec == tw.PREC_FP64 or ctx.keep & tw.KEEP_C64
+    if prec == tw.PREC_FP64:
+        return True
+    return bool(ctx.keep & (tw.KEEP_C64 if prec == tw.PREC_C64 else tw.KEEP_BF16X2))
 
 
 def run_ours(args):
@@ -431,7 +435,7 @@ def run_ours(args):
         cfg = synth.CONFIGS[2]
         sigma = json.load(open(os.path.join(ROOT, "tests", "golden", "sigma_c2.json")))["sigma"]
         d_np = np.load(os.path.join(ROOT, "tests", "golden", "event_c2.npy"))
-    keep = tw.KEEP_FP64 | (0 if args.no_mixed else tw.KEEP_C64)
+    keep = tw.KEEP_FP64 | (0 if args.no_mixed else tw.KEEP_C64 | tw.KEEP_BF16X2)
     t_setup = time.time()
     ctx, sigma, d_gen, t_factor = setup_context(cfg, dev, keep, sigma)
     if d_np is None:

@@ -78,6 +78,8 @@ struct tw_ctx {
   void *bxh = nullptr;               // [bmax][Nf][Nm] parameter-side spectra / prior work
   void *bpart = nullptr;             // [bmax][Nf][nchunk][Rmax] forward-product partial sums
   tw::dd *Lp_dd = nullptr, *inv_dd = nullptr, *chF_dd = nullptr, *chB_dd = nullptr;
+  void *op_tc = nullptr;             // F^ as tensor-core tiles (bf16 hi/lo, swizzled), BF16X2 kept
+  void *btc = nullptr;               // B' tiles of one 128-column slice
   // per-phase timing
   struct PhaseEv { int ph; cudaEvent_t a, b; };
   bool prof = false;

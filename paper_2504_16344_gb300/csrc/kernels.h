@@ -96,6 +96,17 @@ cudaError_t launch_gemm_fwd_f(const void *A, int fmt, const cf *X, long x_bstrid
                               cf *Yo, long y_bstride, int Nf, int Nr, int Nm, int B,
                               cudaStream_t s);
 
+// ---- tensor-core adjoint product (gemm_tc.cu), bf16 hi/lo operator --------
+int gemm_tc_nka(int Nr);
+int gemm_tc_nmt(int Nm);
+size_t gemm_tc_op_bytes(int Nf, int Nr, int Nm);
+size_t gemm_tc_b_bytes(int Nf, int Nr);
+cudaError_t launch_optc_build(const void *op_bf16x2, void *tc, int Nf, int Nr, int Nm,
+                              cudaStream_t s);
+cudaError_t launch_gemm_adj_tc(const void *op_tc, const cf *Y, long y_bstride, cf *X,
+                               long x_bstride, int Nf, int Nr, int Nm, int B, void *btc, int *err,
+                               cudaStream_t s);
+
 // ---- operator storage conversion: dst[w][row0+r][k] from src (cdd) -----
 cudaError_t launch_convert_op(const cdd *src, long src_ld_w, void *dst, int fmt, long dst_ld_w,
                               long n_per_w, int Nf, cudaStream_t s);

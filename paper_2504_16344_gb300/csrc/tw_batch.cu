@@ -114,8 +114,12 @@ tw_status infer_core(tw_ctx *c, tw_prec prec, int B, const int *win, const doubl
     { twh::Phase p(c, TW_PH_RFFT_DATA, s);
       TW_CUDA(c, launch_rfft_time_f(c->byd, 1, Nd, Nt, (cf *)c->byh, Nd, Nd, c->plT, c->twTf, c->twLf, s, ba_y)); }
     { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-      TW_CUDA(c, launch_gemm_adj_f(A, (int)prec, (const cf *)c->byh, (long)Nf * Nd, (cf *)c->bxh,
-                                   (long)Nf * Nm, Nf, Nd, Nm, B, s)); }
+      if (prec == TW_PREC_BF16X2 && c->op_tc)   // tensor cores (tcgen05)
+        TW_CUDA(c, launch_gemm_adj_tc(c->op_tc, (const cf *)c->byh, (long)Nf * Nd, (cf *)c->bxh,
+                                      (long)Nf * Nm, Nf, Nd, Nm, B, c->btc, c->d_err, s));
+      else
+        TW_CUDA(c, launch_gemm_adj_f(A, (int)prec, (const cf *)c->byh, (long)Nf * Nd, (cf *)c->bxh,
+                                     (long)Nf * Nm, Nf, Nd, Nm, B, s)); }
     { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
       TW_CUDA(c, launch_irfft_time_f((const cf *)c->bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s, ba_x)); }
     { twh::Phase p(c, TW_PH_PRIOR, s);
@@ -179,7 +183,7 @@ void free_batch(tw_ctx *c) {
   void **bufs[] = {(void **)&c->win_dev, (void **)&c->trsm_prog, (void **)&c->bz, (void **)&c->by,
                    (void **)&c->bzd, (void **)&c->byd, (void **)&c->brd, &c->byh, &c->bxh,
                    &c->bpart, (void **)&c->Lp_dd, (void **)&c->inv_dd, (void **)&c->chF_dd,
-                   (void **)&c->chB_dd};
+                   (void **)&c->chB_dd, &c->op_tc, &c->btc};
   for (void **b : bufs) { twh::dfree(c, *b); *b = nullptr; }
   c->bmax = 0;
 }
@@ -234,9 +238,17 @@ tw_status tw_reserve_batch(tw_ctx *c, int bmax) {
     c->chF_dd = (dd *)take(c->NB * blk * sizeof(dd));
     c->chB_dd = (dd *)take(c->NB * blk * sizeof(dd));
   }
+  if (c->op[TW_MAP_F][TW_PREC_BF16X2]) {
+    c->op_tc = take(gemm_tc_op_bytes(c->Nf, c->Nd, c->Nm));
+    c->btc = take(gemm_tc_b_bytes(c->Nf, c->Nd));
+  }
   if (!ok) {
     free_batch(c);
     return twh::fail(c, TW_ERR_OOM, "batch workspaces");
+  }
+  if (c->op_tc) {
+    TW_CUDA(c, launch_optc_build(c->op[TW_MAP_F][TW_PREC_BF16X2], c->op_tc, c->Nf, c->Nd, c->Nm, 0));
+    TW_CUDA(c, cudaDeviceSynchronize());
   }
   c->bmax = bmax;
   TW_CUDA(c, cudaMemset(c->win_dev, 0, B * sizeof(int)));
