@@ -18,9 +18,12 @@ paper (arXiv 2504.16344):
   Cholesky factor, the posterior mean m = Gamma_pr F* K^{-1} d and forecast
   q = F_q m (Phase 4 of Sec. "Real-time Bayesian inference and prediction
   framework"), the parameter-space MAP system of Eq. (mmap-problem) for
-  cross-checks, observation windows and posterior samples.
+  cross-checks, observation windows and posterior samples;
+* `qoi`      -- Phase 3: the data-to-QoI map Q = F_q Gamma_post F* Gamma_n^{-1}
+  and the QoI posterior covariance F_q Gamma_post F_q*, formed from QoI unit
+  vectors, and their dense parameter-space definitions for tiny cases.
 
 Library primitives used as single steps: numpy matmul, numpy.linalg.cholesky
 and scipy.linalg.solve_triangular.  No FFT library is used by the oracle.
 """
-from . import toeplitz, prior, posterior  # noqa: F401
+from . import toeplitz, prior, posterior, qoi  # noqa: F401

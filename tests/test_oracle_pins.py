@@ -268,3 +268,52 @@ def test_forecast_matches_dense_p2q(c1):
     q = Q.forecast(c1["Fq"], m)
     assert _rel(q, T.dense_p2o(c1["Fq"]) @ m.reshape(-1)) < 1e-14
     assert q.shape == (C1.Nt, C1.Nq)
+
+
+# ------------------------------------------------------- Phase 3: QoI map and covariance
+
+from oracle import qoi as QO  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def tiny_qoi():
+    cfg = synth.small_config(Nd=4, Nx=8, Ny=8, Nt=8, Nq=2, cid=92)
+    F = synth.block_column(cfg, "F")
+    Fq = synth.block_column(cfg, "Fq")
+    lam = P.spectrum_for(cfg)
+    _, d, sigma = Q.synthetic_event(F, lam, synth.event_z(cfg), synth.noise_z(cfg))
+    L = Q.cholesky(Q.form_K(F, lam, sigma ** 2))
+    return dict(cfg=cfg, F=F, Fq=Fq, lam=lam, d=d, sigma=sigma, L=L)
+
+
+def test_qoi_map_reproduces_forecast_of_posterior_mean(c1):
+    # Phase 4: q_map = F_q m_map = Q d, for the event and for an unrelated data vector
+    F, Fq, lam, sigma = c1["F"], c1["Fq"], c1["lam"], c1["sigma"]
+    L = Q.cholesky(Q.form_K(F, lam, sigma ** 2))
+    Qm = QO.qoi_map(F, Fq, lam, L)
+    for d in (c1["d"], synth.white((C1.Nt, C1.Nd), 4242)):
+        m, _ = Q.posterior_mean(F, lam, L, d, C1.Nt)
+        assert _rel(Qm @ d.ravel(), Q.forecast(Fq, m).ravel()) < 1e-11
+
+
+def test_qoi_map_equals_parameter_space_definition(tiny_qoi):
+    t = tiny_qoi
+    Qd = QO.qoi_map(t["F"], t["Fq"], t["lam"], t["L"])
+    Qp = QO.qoi_map_dense(t["F"], t["Fq"], t["lam"], t["sigma"] ** 2)
+    assert _rel(Qd, Qp) < 1e-9
+
+
+def test_qoi_covariance_equals_parameter_space_definition(tiny_qoi):
+    t = tiny_qoi
+    Cd = QO.qoi_covariance(t["F"], t["Fq"], t["lam"], t["L"])
+    Cp = QO.qoi_covariance_dense(t["F"], t["Fq"], t["lam"], t["sigma"] ** 2)
+    assert _rel(Cd, Cp) < 1e-8
+
+
+def test_qoi_covariance_symmetric_positive_and_below_prior(tiny_qoi):
+    t = tiny_qoi
+    W, Y, C = QO.qoi_columns(t["F"], t["Fq"], t["lam"], t["L"])
+    G = C - W @ Y.T
+    assert _rel(G, G.T) < 1e-10
+    assert np.linalg.eigvalsh(0.5 * (G + G.T)).min() > 0.0
+    assert np.all(np.diag(G) <= np.diag(C) * (1 + 1e-12))     # data never add variance
