@@ -403,6 +403,35 @@ tw_status tw_serve_replay(tw_ctx *ctx, tw_prec prec, int nreq, const double *arr
 tw_status tw_serve_simulate(int nreq, const double *arrival_s, int max_batch, double cost_ms,
                             double cost_ms_per_req, double *latency_ms, int *batch_of);
 
+/*
+ * ---- Phase 3 / Phase 4 for the QoI (Sec. "Real-time Bayesian inference and
+ * prediction framework").  Phase 3 precomputes, from Nq*Nt actions on QoI
+ * unit vectors e_j (QoI entry j = t*Nq + i),
+ *   the data-to-QoI map       Q = F_q Gamma_post F^T Gamma_n^{-1} = F_q Gamma_pr F^T K^{-1}
+ *   the QoI posterior covariance  F_q Gamma_post F_q^T = C - W^T K^{-1} W,
+ *     C = F_q Gamma_pr F_q^T, W = F Gamma_pr F_q^T,
+ * so that Phase 4 forecasts q = Q d directly from data (full observation
+ * window; windowed forecasts go through tw_infer + tw_forecast).
+ *
+ * tw_qoi_build -- the Phase 3 pass (FP64 path: double-float applies, FP64
+ * factor), in batches of min(32, reserved batch) unit vectors; needs
+ * tw_reserve_batch.  Keeps Q and W ((Nq Nt) x (Nd Nt) doubles each), C and
+ * the variances on the device.  Set-up call: allocates, synchronises.
+ */
+tw_status tw_qoi_build(tw_ctx *ctx, void *stream);
+
+/* q = Q d for nrhs data vectors: d device [nrhs][Nt][Nd], q device
+ * [nrhs][Nt][Nq] (FP64).  Equals tw_forecast of the full-window tw_infer. */
+tw_status tw_qoi_apply(tw_ctx *ctx, int nrhs, const double *d, double *q, void *stream);
+
+/* Variances of the QoI posterior (diagonal of F_q Gamma_post F_q^T), device
+ * [Nt][Nq]; the 95% credible interval of q_j is q_j +- 1.96 sqrt(var_j). */
+tw_status tw_qoi_variance(tw_ctx *ctx, double *var, void *stream);
+
+/* The dense QoI posterior covariance, device [Nq Nt][Nq Nt] (row-major),
+ * C - W^T (K^{-1} W) as one FP64 GEMM over Nd*Nt terms. */
+tw_status tw_qoi_covariance(tw_ctx *ctx, double *cov, void *stream);
+
 /* Synchronise `stream` and report errors recorded by kernels (TW_OK,
  * TW_ERR_NOT_SPD, TW_ERR_TIMEOUT, TW_ERR_CUDA).  Clears the record. */
 tw_status tw_check(tw_ctx *ctx, void *stream);

@@ -79,6 +79,11 @@ struct tw_ctx {
   void *bpart = nullptr;             // [bmax][Nf][nchunk][Rmax] forward-product partial sums
   tw::dd *Lp_dd = nullptr, *inv_dd = nullptr, *chF_dd = nullptr, *chB_dd = nullptr;
   void *op_tc = nullptr;             // F^ as tensor-core tiles (bf16 hi/lo, swizzled), BF16X2 kept
+  // Phase 3 QoI precomputations (tw_qoi_build): rows indexed by QoI entry t*Nq + i
+  double *Qmap = nullptr, *Wmap = nullptr;   // [Nq Nt][Nd Nt]: Q = F_q Gamma_pr F^T K^-1, W = (F Gamma_pr F_q^T)^T
+  double *Cqq = nullptr;                     // [Nq Nt][Nq Nt]: F_q Gamma_pr F_q^T
+  double *qvar = nullptr;                    // [Nq Nt]: diagonal of the QoI posterior covariance
+  bool have_qoi = false;
   void *btc = nullptr;               // B' tiles of one 128-column slice
   // per-phase timing
   struct PhaseEv { int ph; cudaEvent_t a, b; };

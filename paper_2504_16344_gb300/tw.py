@@ -71,6 +71,10 @@ SIGNATURES = {
     "tw_graph_destroy": (None, [_P]),
     "tw_serve_replay": (_S, [_P, _I, _I, _P, _P, _P, _I, _P, _I, _P, _P, _P, _P, _P]),
     "tw_serve_simulate": (_S, [_I, _P, _I, _D, _D, _P, _P]),
+    "tw_qoi_build": (_S, [_P, _P]),
+    "tw_qoi_apply": (_S, [_P, _I, _P, _P, _P]),
+    "tw_qoi_variance": (_S, [_P, _P, _P]),
+    "tw_qoi_covariance": (_S, [_P, _P, _P]),
 }
 
 _lib = None
@@ -391,6 +395,36 @@ class Context:
                                              int(max_batch), ptr(lat), ptr(q), ptr(m),
                                              ctypes.byref(st), _stream_ptr(stream)))
         return lat, q, m, st
+
+    # -------------------------------------------------------- QoI (Phase 3 / 4)
+    def qoi_build(self, stream=None):
+        """Precompute the data-to-QoI map, W, C and the QoI posterior variances."""
+        self._check(self.lib.tw_qoi_build(self.h, _stream_ptr(stream)))
+
+    def qoi_apply(self, d, out=None, stream=None):
+        """q = Q d for d [nrhs][Nt][Nd]."""
+        import torch
+        d = d if d.dim() == 3 else d.unsqueeze(0)
+        nrhs = d.shape[0]
+        pd = _dev(d, torch.float64, (nrhs, self.Nt, self.Nd), "d")
+        if out is None:
+            out = torch.empty((nrhs, self.Nt, self.Nq), dtype=torch.float64, device=d.device)
+        po = _dev(out, torch.float64, (nrhs, self.Nt, self.Nq), "q")
+        self._check(self.lib.tw_qoi_apply(self.h, nrhs, pd, po, _stream_ptr(stream)))
+        return out
+
+    def qoi_variance(self, stream=None):
+        import torch
+        out = torch.empty((self.Nt, self.Nq), dtype=torch.float64, device=torch.device("cuda", self.device))
+        self._check(self.lib.tw_qoi_variance(self.h, _dev(out, torch.float64), _stream_ptr(stream)))
+        return out
+
+    def qoi_covariance(self, stream=None):
+        import torch
+        nq = self.Nq * self.Nt
+        out = torch.empty((nq, nq), dtype=torch.float64, device=torch.device("cuda", self.device))
+        self._check(self.lib.tw_qoi_covariance(self.h, _dev(out, torch.float64), _stream_ptr(stream)))
+        return out
 
     def capture(self, stream):
         """Context manager: batched calls on `stream` inside it are recorded into a Graph."""
