@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-steps", type=int, default=3)
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--qoi", action="store_true",
+                   help="also time the Phase 3 QoI build (about two minutes) and q = Q d")
     p.add_argument("--requests", type=int, default=1000,
                    help="requests of the serving trace (Poisson 200/s)")
     return p.parse_args()
@@ -346,6 +348,44 @@ def run_batch(args, ctx, cfg, sigma, d0, dev, barrier):
     return out
 
 
+def run_qoi(args, ctx, cfg, d, q_ref, dev):
+    """Phase 3 (data-to-QoI map Q, QoI posterior variances) then Phase 4 q = Q d."""
+    import torch
+
+    from paper_2504_16344_gb300 import tw
+    ctx.reserve_batch(96)
+    torch.cuda.synchronize(dev)
+    t0 = time.time()
+    ctx.qoi_build()
+    build_s = time.time() - t0
+    stream = torch.cuda.current_stream(dev)
+    q = torch.empty((1, cfg.Nt, cfg.Nq), dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        ctx.qoi_apply(d, out=q)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.qoi_apply(d, out=q)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    var = ctx.qoi_variance()
+    ctx.check()
+    nq, n = cfg.Nq * cfg.Nt, cfg.Nd * cfg.Nt
+    peak, _ = measured_peaks()
+    gbs = 8.0 * nq * n / (ms * 1e-3) / 1e9
+    out = {"build_s": round(build_s, 1), "unit_vectors": nq,
+           "q_from_d_ms": round(ms, 4),
+           "q_from_d_gbs": round(gbs, 1), "q_from_d_frac_of_hbm": round(gbs / peak, 3),
+           "q_rel_err_vs_infer_forecast": rel(q, q_ref),
+           "min_posterior_std": float(torch.sqrt(var.min())),
+           "note": "Q is (Nq Nt) x (Nd Nt) FP64 (2.56 GB), read once per q = Q d"}
+    ctx.reserve_batch(0)
+    return out
+
+
 def event_bank(ctx, cfg, src_cfg, n, sigma, d0, dev):
     """Data vectors of events 0..n-1: d_e = F Gamma^{1/2} z_e + sigma z_n,e (event 0 given)."""
     import torch
@@ -575,6 +615,10 @@ def run_ours(args):
     if not args.no_batch:
         batch = run_batch(args, ctx, cfg, sigma, d, dev, barrier)
 
+    qoi = None
+    if args.qoi:
+        qoi = run_qoi(args, ctx, cfg, d, q64, dev)
+
     serve = None
     if not args.no_serve and not args.small:
         serve = run_serve(args, ctx, cfg, sigma, d, dev)
@@ -601,6 +645,7 @@ def run_ours(args):
         "mixed": mixed,
         "batch": batch,
         "serve": serve,
+        "qoi": qoi,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),

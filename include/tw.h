@@ -414,7 +414,7 @@ tw_status tw_serve_simulate(int nreq, const double *arrival_s, int max_batch, do
  * window; windowed forecasts go through tw_infer + tw_forecast).
  *
  * tw_qoi_build -- the Phase 3 pass (FP64 path: double-float applies, FP64
- * factor), in batches of min(32, reserved batch) unit vectors; needs
+ * factor), in batches of min(96, reserved batch) unit vectors; needs
  * tw_reserve_batch.  Keeps Q and W ((Nq Nt) x (Nd Nt) doubles each), C and
  * the variances on the device.  Set-up call: allocates, synchronises.
  */

@@ -13,7 +13,7 @@
 //   c_j = F_q u_j,  w_j = F u_j  (one time FFT of u_j feeds both products)
 //   y_j = K^{-1} w_j             (batched triangular solves)
 // and keeps Q (row j = y_j), W (row j = w_j), C (row j = c_j) and the
-// variances C_jj - w_j . y_j.  FP64 path throughout (double-float applies,
+// variances C_jj - w_j . y_j (batches of up to 96).  FP64 path throughout (double-float applies,
 // FP64 factor); the full covariance is one FP64 GEMM on request.
 #include <algorithm>
 #include <vector>
@@ -55,27 +55,40 @@ __global__ void k_qoi_var(const double *__restrict__ cq, const double *__restric
   }
 }
 
-// q[r][j] = sum_i Q[j][i] d[r][i]: one warp per row j, up to 8 right-hand sides per pass
+// q[r][j] = sum_i Q[j][i] d[r][i]: one warp per row j, up to 4 right-hand
+// sides per pass; eight independent loads per lane in flight (the row is
+// streamed once per pass, FP64 FMA)
 __global__ void __launch_bounds__(256)
 k_qoi_apply(const double *__restrict__ Qm, const double *__restrict__ d, double *__restrict__ q,
             int nq, int n, int nrhs) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= nq) return;
   const double *row = Qm + (size_t)warp * n;
-  for (int r0 = 0; r0 < nrhs; r0 += 8) {
-    const int nr = min(8, nrhs - r0);
-    double acc[8];
+  for (int r0 = 0; r0 < nrhs; r0 += 4) {
+    const int nr = min(4, nrhs - r0);
+    double acc[4][2];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) acc[r] = 0.0;
-    for (int i = lane; i < n; i += 32) {
-      const double a = __ldg(row + i);
+    for (int r = 0; r < 4; ++r) { acc[r][0] = 0.0; acc[r][1] = 0.0; }
+    int i = lane;
+    for (; i + 7 * 32 < n; i += 8 * 32) {
+      double a[8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
-        if (r < nr) acc[r] = fma(a, __ldg(d + (size_t)(r0 + r) * n + i), acc[r]);
+      for (int k = 0; k < 8; ++k) a[k] = __ldcs(row + i + 32 * k);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (r >= nr) break;
+        const double *dr = d + (size_t)(r0 + r) * n + i;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[r][k & 1] = fma(a[k], __ldg(dr + 32 * k), acc[r][k & 1]);
+      }
+    }
+    for (; i < n; i += 32) {
+      const double a = __ldcs(row + i);
+      for (int r = 0; r < nr; ++r) acc[r][0] = fma(a, __ldg(d + (size_t)(r0 + r) * n + i), acc[r][0]);
     }
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      double v = acc[r];
+    for (int r = 0; r < 4; ++r) {
+      double v = acc[r][0] + acc[r][1];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == 0 && r < nr) q[(size_t)(r0 + r) * nq + warp] = v;
     }
@@ -135,7 +148,7 @@ tw_status tw_qoi_build(tw_ctx *c, void *stream) {
   const int Nd = c->Nd, Nq = c->Nq, Nt = c->Nt, Nm = c->Nm, Nf = c->Nf;
   const int nq = Nq * Nt, n = Nd * Nt;
   const long np = c->n_pad;
-  const int Bq = std::min(c->bmax, 32);
+  const int Bq = std::min(c->bmax, 96);
   auto need = [&](void *&p, size_t bytes) { if (!p) p = twh::dalloc(c, bytes); return p != nullptr; };
   bool ok = need((void *&)c->Qmap, (size_t)nq * n * sizeof(double)) &&
             need((void *&)c->Wmap, (size_t)nq * n * sizeof(double)) &&

@@ -58,7 +58,7 @@ def _t(a, dev):
 
 def test_q_map_apply_matches_oracle(case):
     """Model data (events): 1e-11.  A white vector, which is not data of the model,
-    makes Q d cancel; it is held to 1e-12 of |Q| |d| (entrywise) instead."""
+    makes Q d cancel; it is held entrywise to kappa(K) u of |Q| |d| instead."""
     cfg, ctx = case["cfg"], case["ctx"]
     F, lam = case["F"], case["lam"]
     sigma = case["sigma"]
@@ -75,10 +75,13 @@ def test_q_map_apply_matches_oracle(case):
         e1, e2 = rel(q[r], ref), rel(q[r], ref2)
         print(f"{cfg.cid}: event {r}: q = Q d rel err vs oracle Q d {e1:.2e}, vs F_q m_map {e2:.2e}")
         assert e1 < 1e-11 and e2 < 1e-11
+    # two backward-stable FP64 solvers of K may differ by ~kappa(K) u entrywise
+    kappa = Q.condition_number_K(Q.form_K(F, lam, sigma ** 2))
     scale = np.abs(case["Y"]) @ np.abs(white.ravel())
     ew = np.max(np.abs(q[-1].ravel() - case["Y"] @ white.ravel()) / scale)
-    print(f"{cfg.cid}: white vector: error / (|Q||d|) {ew:.2e}")
-    assert ew < 1e-12
+    bound = max(1e-12, kappa * 2.0 ** -53)
+    print(f"{cfg.cid}: white vector: error / (|Q||d|) {ew:.2e}, kappa(K) u = {kappa * 2.0 ** -53:.1e}")
+    assert ew < bound
 
 
 
