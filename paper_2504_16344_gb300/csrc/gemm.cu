@@ -24,6 +24,9 @@
 // FP64-class path: float-pair operands, exact products, renormalised
 // running sums (as the single-vector kernels); FP32 path: complex64 or
 // bf16 hi+lo operator, FP32 FMA.
+#include <algorithm>
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace tw {
@@ -176,76 +179,56 @@ k_gemm_adj_f(const void *__restrict__ A, const cf *__restrict__ Y, long y_bstrid
   }
 }
 
-// ------------------------------------------------------------ forward, df64
-// grid (nchunk, Nf, ceil(B/32)); lane = right-hand side, warp = RPW rows per
-// pass, passes cover all Nr rows; partial sums to part[b][w][chunk][r]
-template <int RPW>
-__global__ void __launch_bounds__(256)
-k_gemm_fwd_dd(const float4 *__restrict__ A, const cdd *__restrict__ X, long x_bstride,
-              cdd *__restrict__ part, int nchunk, int Nr, int Nm, int B) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cdd *sx = reinterpret_cast<cdd *>(smem_raw);   // [32][GF_K + 1]
-  const int w = blockIdx.y, chunk = blockIdx.x;
-  const int b0 = blockIdx.z * 32;
-  const int nb = min(32, B - b0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int kbeg = chunk * GF_K * GF_TILES;
-  const int kend = min(Nm, kbeg + GF_K * GF_TILES);
-  const float4 *Aw = A + (size_t)w * Nr * Nm;
-  const int npass = (Nr + 8 * RPW - 1) / (8 * RPW);
-  for (int pass = 0; pass < npass; ++pass) {   // uniform over the CTA (barriers inside)
-    const int r0 = pass * 8 * RPW + warp * RPW;
-    dacc re[RPW], im[RPW];
-#pragma unroll
-    for (int i = 0; i < RPW; ++i) { re[i] = dacc_zero(); im[i] = dacc_zero(); }
-    for (int kt = kbeg; kt < kend; kt += GF_K) {
-      const int nk = min(GF_K, kend - kt);
-      __syncthreads();   // previous tile consumed
-      for (int idx = threadIdx.x; idx < 32 * GF_K; idx += blockDim.x) {
-        const int bl = idx / GF_K, kk = idx % GF_K;
-        sx[bl * (GF_K + 1) + kk] = (bl < nb && kk < nk)
-            ? ld_cdd(X + (size_t)(b0 + bl) * x_bstride + (size_t)w * Nm + kt + kk)
-            : cdd_zero();
-      }
-      __syncthreads();
-      const cdd *xs = sx + lane * (GF_K + 1);
-      for (int kk = 0; kk < nk; ++kk) {
-        const cdd x = xs[kk];
-#pragma unroll
-        for (int i = 0; i < RPW; ++i) {
-          const int r = r0 + i;
-          if (r >= Nr) continue;
-          const float4 a = __ldg(Aw + (size_t)r * Nm + kt + kk);
-          dd ar, ai;
-          ar.hi = a.x; ar.lo = a.y; ai.hi = a.z; ai.lo = a.w;
-          // a x = (ar xr - ai xi) + i (ar xi + ai xr)
-          dacc_mac(re[i], ar, x.re);
-          dacc_mac(re[i], dd_neg(ai), x.im);
-          dacc_mac(im[i], ar, x.im);
-          dacc_mac(im[i], ai, x.re);
-        }
-      }
-    }
-    if (lane < nb) {
-#pragma unroll
-      for (int i = 0; i < RPW; ++i) {
-        const int r = r0 + i;
-        if (r >= Nr) continue;
-        cdd v;
-        v.re = dacc_get(re[i]);
-        v.im = dacc_get(im[i]);
-        st_cdd(part + (((size_t)(b0 + lane) * gridDim.y + w) * nchunk + chunk) * Nr + r, v);
-      }
-    }
+// ------------------------------------------------------------ forward
+// grid (nchunk, Nf, ceil(B/32)); a CTA sums 4096 grid points of one
+// frequency for 32 right-hand sides (lane = right-hand side) and all Nr rows
+// (warp w owns rows w, w+8, ..., RPW of them per pass).  Each GK-wide k
+// tile stages X^ [32][GK] and the operator rows [Nr][GK] in shared memory;
+// the inner loop reads the operator entry as a warp broadcast and X^ per
+// lane, both from shared memory.  Partial sums per chunk go to
+// part[b][w][chunk][r].
+template <class CX> struct FwdT;
+template <> struct FwdT<cdd> {
+  typedef dacc acc;
+  static __device__ __forceinline__ void zero(acc &re, acc &im) { re = dacc_zero(); im = dacc_zero(); }
+  // (re, im) += a x
+  static __device__ __forceinline__ void mac(acc &re, acc &im, const cdd &a, const cdd &x) {
+    dacc_mac(re, a.re, x.re);
+    dacc_mac(re, dd_neg(a.im), x.im);
+    dacc_mac(im, a.re, x.im);
+    dacc_mac(im, a.im, x.re);
   }
-}
+  static __device__ __forceinline__ cdd get(const acc &re, const acc &im) {
+    cdd r; r.re = dacc_get(re); r.im = dacc_get(im); return r;
+  }
+  static __device__ __forceinline__ cdd zx() { return cdd_zero(); }
+};
+template <> struct FwdT<cf> {
+  typedef float acc;
+  static __device__ __forceinline__ void zero(acc &re, acc &im) { re = 0.f; im = 0.f; }
+  static __device__ __forceinline__ void mac(acc &re, acc &im, const cf &a, const cf &x) {
+    re = fmaf(a.re, x.re, fmaf(-a.im, x.im, re));
+    im = fmaf(a.re, x.im, fmaf(a.im, x.re, im));
+  }
+  static __device__ __forceinline__ cf get(const acc &re, const acc &im) { return cf_make(re, im); }
+  static __device__ __forceinline__ cf zx() { return cf_zero(); }
+};
 
-template <int RPW, int FMT>
-__global__ void __launch_bounds__(256)
-k_gemm_fwd_f(const void *__restrict__ A, const cf *__restrict__ X, long x_bstride,
-             cf *__restrict__ part, int nchunk, int Nr, int Nm, int B) {
+// operator entry (complex) from the stored formats
+__device__ __forceinline__ cdd ld_op(const cdd *, const void *A, size_t i) {
+  return ld_cdd(reinterpret_cast<const cdd *>(A) + i);
+}
+template <int FMT>
+__device__ __forceinline__ cf ld_op_fmt(const void *A, size_t i) { return ld_opf<FMT>(A, i); }
+
+template <class CX, int RPW, int GK, int FMT>
+__global__ void __launch_bounds__(256, 2)
+k_gemm_fwd(const void *__restrict__ A, const CX *__restrict__ X, long x_bstride,
+           CX *__restrict__ part, int nchunk, int Nr, int Nm, int B) {
+  typedef FwdT<CX> T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cf *sx = reinterpret_cast<cf *>(smem_raw);   // [32][GF_K + 1]
+  CX *sx = reinterpret_cast<CX *>(smem_raw);          // [32][GK + 1]
+  CX *sa = sx + 32 * (GK + 1);                        // [Nr][GK]
   const int w = blockIdx.y, chunk = blockIdx.x;
   const int b0 = blockIdx.z * 32;
   const int nb = min(32, B - b0);
@@ -254,47 +237,67 @@ k_gemm_fwd_f(const void *__restrict__ A, const cf *__restrict__ X, long x_bstrid
   const int kend = min(Nm, kbeg + GF_K * GF_TILES);
   const size_t base = (size_t)w * Nr * Nm;
   const int npass = (Nr + 8 * RPW - 1) / (8 * RPW);
-  for (int pass = 0; pass < npass; ++pass) {   // uniform over the CTA (barriers inside)
-    const int r0 = pass * 8 * RPW + warp * RPW;
-    float re[RPW], im[RPW];
+  for (int pass = 0; pass < npass; ++pass) {
+    const int r0 = pass * 8 * RPW;
+    const int nrp = min(8 * RPW, Nr - r0);           // rows staged this pass
+    typename T::acc re[RPW], im[RPW];
 #pragma unroll
-    for (int i = 0; i < RPW; ++i) { re[i] = 0.f; im[i] = 0.f; }
-    for (int kt = kbeg; kt < kend; kt += GF_K) {
-      const int nk = min(GF_K, kend - kt);
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < 32 * GF_K; idx += blockDim.x) {
-        const int bl = idx / GF_K, kk = idx % GF_K;
-        sx[bl * (GF_K + 1) + kk] = (bl < nb && kk < nk)
-            ? X[(size_t)(b0 + bl) * x_bstride + (size_t)w * Nm + kt + kk]
-            : cf_zero();
+    for (int i = 0; i < RPW; ++i) T::zero(re[i], im[i]);
+    for (int kt = kbeg; kt < kend; kt += GK) {
+      const int nk = min(GK, kend - kt);
+      __syncthreads();   // previous tile consumed
+      for (int idx = threadIdx.x; idx < 32 * GK; idx += blockDim.x) {
+        const int bl = idx / GK, kk = idx % GK;
+        sx[bl * (GK + 1) + kk] = (bl < nb && kk < nk)
+            ? X[(size_t)(b0 + bl) * x_bstride + (size_t)w * Nm + kt + kk] : T::zx();
+      }
+      for (int idx = threadIdx.x; idx < nrp * GK; idx += blockDim.x) {
+        const int rl = idx / GK, kk = idx % GK;
+        CX v = T::zx();
+        if (kk < nk) {
+          const size_t gi = base + (size_t)(r0 + rl) * Nm + kt + kk;
+          if constexpr (FMT == FMT_DD) v = ld_op((const cdd *)nullptr, A, gi);
+          else v = ld_op_fmt<FMT>(A, gi);
+        }
+        sa[rl * GK + kk] = v;
       }
       __syncthreads();
-      const cf *xs = sx + lane * (GF_K + 1);
-      // a fresh sum per tile, added to the running total: FP32 rounding then
-      // grows with GF_K + the tile count instead of the chunk length
-      float tre[RPW], tim[RPW];
+      const CX *xs = sx + lane * (GK + 1);
+      if constexpr (std::is_same<CX, cf>::value) {
+        // FP32: a fresh sum per tile, added to the running total, so rounding
+        // grows with GK + the tile count rather than the chunk length
+        float tre[RPW], tim[RPW];
 #pragma unroll
-      for (int i = 0; i < RPW; ++i) { tre[i] = 0.f; tim[i] = 0.f; }
-      for (int kk = 0; kk < nk; ++kk) {
-        const cf x = xs[kk];
+        for (int i = 0; i < RPW; ++i) { tre[i] = 0.f; tim[i] = 0.f; }
+#pragma unroll 4
+        for (int kk = 0; kk < nk; ++kk) {
+          const CX x = xs[kk];
 #pragma unroll
-        for (int i = 0; i < RPW; ++i) {
-          const int r = r0 + i;
-          if (r >= Nr) continue;
-          const cf a = ld_opf<FMT>(A, base + (size_t)r * Nm + kt + kk);
-          tre[i] = fmaf(a.re, x.re, fmaf(-a.im, x.im, tre[i]));
-          tim[i] = fmaf(a.re, x.im, fmaf(a.im, x.re, tim[i]));
+          for (int i = 0; i < RPW; ++i) {
+            const int rl = warp * RPW + i;
+            if (rl < nrp) T::mac(tre[i], tim[i], sa[rl * GK + kk], x);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) { re[i] += tre[i]; im[i] += tim[i]; }
+      } else {
+#pragma unroll 4
+        for (int kk = 0; kk < nk; ++kk) {
+          const CX x = xs[kk];
+#pragma unroll
+          for (int i = 0; i < RPW; ++i) {
+            const int rl = warp * RPW + i;
+            if (rl < nrp) T::mac(re[i], im[i], sa[rl * GK + kk], x);
+          }
         }
       }
-#pragma unroll
-      for (int i = 0; i < RPW; ++i) { re[i] += tre[i]; im[i] += tim[i]; }
     }
     if (lane < nb) {
 #pragma unroll
       for (int i = 0; i < RPW; ++i) {
-        const int r = r0 + i;
-        if (r >= Nr) continue;
-        part[(((size_t)(b0 + lane) * gridDim.y + w) * nchunk + chunk) * Nr + r] = cf_make(re[i], im[i]);
+        const int rl = warp * RPW + i;
+        if (rl >= nrp) continue;
+        part[(((size_t)(b0 + lane) * gridDim.y + w) * nchunk + chunk) * Nr + r0 + rl] = T::get(re[i], im[i]);
       }
     }
   }
@@ -369,21 +372,16 @@ cudaError_t launch_gemm_adj_f(const void *A, int fmt, const cf *Y, long y_bstrid
   return cudaGetLastError();
 }
 
-// rows per warp: enough that one pass covers up to 8*RPW rows
-template <int RPW>
-static cudaError_t gemm_fwd_dd_rpw(const void *A, const cdd *X, long x_bstride, cdd *part,
-                                   cdd *Yo, long y_bstride, int Nf, int Nr, int Nm, int B,
-                                   cudaStream_t s) {
+// rows per warp: one pass covers up to 8*RPW rows
+template <class CX, int RPW, int GK, int FMT>
+static cudaError_t gemm_fwd_run(const void *A, const CX *X, long x_bstride, CX *part, int Nf, int Nr,
+                                int Nm, int B, cudaStream_t s) {
   const int nchunk = gemm_fwd_nchunk(Nm);
-  const size_t sm = (size_t)32 * (GF_K + 1) * sizeof(cdd);
-  ensure_smem_g(k_gemm_fwd_dd<RPW>, sm);
+  const int rows = std::min(Nr, 8 * RPW);
+  const size_t sm = (size_t)(32 * (GK + 1) + rows * GK) * sizeof(CX);
+  ensure_smem_g(k_gemm_fwd<CX, RPW, GK, FMT>, sm);
   dim3 grid(nchunk, Nf, (B + 31) / 32);
-  k_gemm_fwd_dd<RPW><<<grid, 256, sm, s>>>(reinterpret_cast<const float4 *>(A), X, x_bstride, part,
-                                           nchunk, Nr, Nm, B);
-  count_launches(1);
-  const long total = (long)B * Nf * Nr;
-  k_gemm_fwd_reduce_dd<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, Yo, y_bstride, nchunk,
-                                                                      Nf, Nr, B);
+  k_gemm_fwd<CX, RPW, GK, FMT><<<grid, 256, sm, s>>>(A, X, x_bstride, part, nchunk, Nr, Nm, B);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -391,22 +389,13 @@ static cudaError_t gemm_fwd_dd_rpw(const void *A, const cdd *X, long x_bstride, 
 cudaError_t launch_gemm_fwd_dd(const void *A, const cdd *X, long x_bstride, cdd *part, cdd *Yo,
                                long y_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  if (Nr <= 24) return gemm_fwd_dd_rpw<3>(A, X, x_bstride, part, Yo, y_bstride, Nf, Nr, Nm, B, s);
-  return gemm_fwd_dd_rpw<7>(A, X, x_bstride, part, Yo, y_bstride, Nf, Nr, Nm, B, s);
-}
-
-template <int RPW, int FMT>
-static cudaError_t gemm_fwd_f_rpw(const void *A, const cf *X, long x_bstride, cf *part, cf *Yo,
-                                  long y_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s) {
+  cudaError_t e = Nr <= 24 ? gemm_fwd_run<cdd, 3, 32, FMT_DD>(A, X, x_bstride, part, Nf, Nr, Nm, B, s)
+                           : gemm_fwd_run<cdd, 13, 32, FMT_DD>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+  if (e != cudaSuccess) return e;
   const int nchunk = gemm_fwd_nchunk(Nm);
-  const size_t sm = (size_t)32 * (GF_K + 1) * sizeof(cf);
-  ensure_smem_g(k_gemm_fwd_f<RPW, FMT>, sm);
-  dim3 grid(nchunk, Nf, (B + 31) / 32);
-  k_gemm_fwd_f<RPW, FMT><<<grid, 256, sm, s>>>(A, X, x_bstride, part, nchunk, Nr, Nm, B);
-  count_launches(1);
   const long total = (long)B * Nf * Nr;
-  k_gemm_fwd_reduce_f<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, Yo, y_bstride, nchunk,
-                                                                     Nf, Nr, B);
+  k_gemm_fwd_reduce_dd<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, Yo, y_bstride, nchunk,
+                                                                      Nf, Nr, B);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -415,12 +404,20 @@ cudaError_t launch_gemm_fwd_f(const void *A, int fmt, const cf *X, long x_bstrid
                               cf *Yo, long y_bstride, int Nf, int Nr, int Nm, int B,
                               cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  if (fmt == FMT_C64) {
-    if (Nr <= 24) return gemm_fwd_f_rpw<3, FMT_C64>(A, X, x_bstride, part, Yo, y_bstride, Nf, Nr, Nm, B, s);
-    return gemm_fwd_f_rpw<13, FMT_C64>(A, X, x_bstride, part, Yo, y_bstride, Nf, Nr, Nm, B, s);
-  }
-  if (Nr <= 24) return gemm_fwd_f_rpw<3, FMT_BF16X2>(A, X, x_bstride, part, Yo, y_bstride, Nf, Nr, Nm, B, s);
-  return gemm_fwd_f_rpw<13, FMT_BF16X2>(A, X, x_bstride, part, Yo, y_bstride, Nf, Nr, Nm, B, s);
+  cudaError_t e;
+  if (fmt == FMT_C64)
+    e = Nr <= 24 ? gemm_fwd_run<cf, 3, 64, FMT_C64>(A, X, x_bstride, part, Nf, Nr, Nm, B, s)
+                 : gemm_fwd_run<cf, 13, 64, FMT_C64>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+  else
+    e = Nr <= 24 ? gemm_fwd_run<cf, 3, 64, FMT_BF16X2>(A, X, x_bstride, part, Nf, Nr, Nm, B, s)
+                 : gemm_fwd_run<cf, 13, 64, FMT_BF16X2>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+  if (e != cudaSuccess) return e;
+  const int nchunk = gemm_fwd_nchunk(Nm);
+  const long total = (long)B * Nf * Nr;
+  k_gemm_fwd_reduce_f<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, Yo, y_bstride, nchunk,
+                                                                     Nf, Nr, B);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 }  // namespace tw
