@@ -71,6 +71,15 @@ typedef enum { TW_PREC_FP64 = 0, TW_PREC_C64 = 1, TW_PREC_BF16X2 = 2 } tw_prec;
 #define TW_KEEP_FP64   1u
 #define TW_KEEP_C64    2u
 #define TW_KEEP_BF16X2 4u
+/* TW_KEEP_G: tw_factor_K also forms G^ = F^ C per frequency in every kept
+ * format -- the block Toeplitz G* = Gamma_pr F* of Phase 2 (Sec. "Real-time
+ * Bayesian inference and prediction framework") -- and tw_infer's adjoint
+ * applies use it, so the online posterior mean needs no prior filter.
+ * Formed in the FP64 and complex64 storages (bf16 hi+lo would round G^ at
+ * 2^-18, which reaches m unsmoothed: the TW_PREC_BF16X2 path keeps F^ and
+ * the prior filter).  Adds the storage of F's FP64 and complex64 operators;
+ * needs TW_KEEP_FP64. */
+#define TW_KEEP_G      8u
 
 /*
  * tw_create -- allocate a context for Nd sensors, Nq forecast points, an

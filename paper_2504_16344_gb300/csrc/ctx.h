@@ -15,6 +15,9 @@ struct tw_ctx {
   unsigned keep = 0;
   // frequency-domain operators op[which][fmt], [Nf][rows][Nm]
   void *op[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  // G^ = F^ C per frequency (the paper's G* = Gamma_pr F* of Phase 2), per kept
+  // format, when TW_KEEP_G: the adjoint applies of tw_infer then need no prior filter
+  void *opG[3] = {nullptr, nullptr, nullptr};
   std::vector<char> loaded[2];     // per row: loaded?
   // FFT plans and twiddle tables (df64 and float)
   tw::FftPlan plT{}, plX{}, plY{};
@@ -27,6 +30,7 @@ struct tw_ctx {
   tw::dd *lam1 = nullptr, *lamh = nullptr;
   float *lam1f = nullptr, *lamhf = nullptr;
   double *lamhd = nullptr;                        // sqrt(lambda) / N in FP64
+  double *lam1d = nullptr;                        // lambda / N in FP64 (forming G^)
   // G = Phi C^{1/2} (rows t*Nd + sensor), built in FP64 from the loaded
   // block column when the prior is already set; consumed by tw_factor_K
   tw::dd *G = nullptr;
@@ -115,7 +119,8 @@ tw_status cuda_fail(tw_ctx *c, cudaError_t e, const char *where);
 void *dalloc(tw_ctx *c, size_t bytes);   // tracked cudaMalloc; nullptr on failure
 void dfree(tw_ctx *c, void *p);
 tw::FftPlan make_plan(int M);
-// float-pair copy of the FP64 factor for mixed batched solves (no-op unless reserved)
+// batch copies after a factorisation: the float-pair factor for mixed batched
+// solves and the tensor-core operator tiles (no-op unless reserved)
 tw_status refresh_dd_factor(tw_ctx *c, cudaStream_t s);
 
 }  // namespace twh

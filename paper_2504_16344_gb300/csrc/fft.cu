@@ -13,6 +13,8 @@
 // time steps are packed into one complex field (C is real), and the 2D
 // transform runs as rows (contiguous), columns (strided, with the lambda
 // scaling and the inverse column transform fused), inverse rows.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace tw {
@@ -295,6 +297,48 @@ k_prior_cols(typename P::cx *__restrict__ work, const typename P::re *__restrict
   }
 }
 
+// Complex fields, FP64 (set-up): rows pass of C applied to x[f] (cdd storage)
+// for fields f in [0, nf); forward: x -> work (cd), inverse: work -> x.
+template <bool INV>
+__global__ void __launch_bounds__(256)
+k_cfield_rows(cdd *__restrict__ x, cd *__restrict__ work, int Nx, int Ny, FftPlan ply,
+              const cd *__restrict__ twy, int BR) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cd *buf0 = reinterpret_cast<cd *>(smem_raw);
+  cd *buf1 = buf0 + BR * Ny;
+  const int f = blockIdx.y, a0 = blockIdx.x * BR;
+  cdd *xf = x + (long)f * Nx * Ny;
+  cd *wf = work + (long)f * Nx * Ny;
+  for (int idx = threadIdx.x; idx < BR * Ny; idx += blockDim.x) {
+    const int j = idx % Ny, b = idx / Ny, a = a0 + b;
+    cd v = PolD::zero();
+    if (a < Nx) {
+      if (!INV) {
+        const cdd z = ld_cdd(xf + (long)a * Ny + j);
+        v = PolD::make(dd_to_double(z.re), dd_to_double(z.im));
+      } else {
+        v = wf[(long)a * Ny + j];
+      }
+    }
+    buf0[b * Ny + j] = v;
+  }
+  __syncthreads();
+  cd *Z = fft_run<PolD, INV>(buf0, buf1, twy, ply, BR, 1, Ny, false);
+  for (int idx = threadIdx.x; idx < BR * Ny; idx += blockDim.x) {
+    const int j = idx % Ny, b = idx / Ny, a = a0 + b;
+    if (a >= Nx) continue;
+    const cd v = Z[b * Ny + j];
+    if (!INV) {
+      wf[(long)a * Ny + j] = v;
+    } else {
+      cdd z;
+      z.re = dd_from_double(v.re);
+      z.im = dd_from_double(v.im);
+      st_cdd(xf + (long)a * Ny + j, z);
+    }
+  }
+}
+
 template <class KER>
 void ensure_smem(KER k, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -410,6 +454,33 @@ cudaError_t launch_prior_d(const void *x, int in_kind, void *y, int out_kind, in
   return prior<PolD>(x, in_kind, y, out_kind, nt, Nx, Ny, work, lam, plx, ply, twx, twy, s,
                      FieldMap{map_per, map_stride, map_off});
 }
+// x[f] <- C x[f] for complex fields f < nf (cdd storage, FP64 arithmetic);
+// lam: eigenvalues / (Nx Ny) in FP64; work: nf_chunk fields of cd
+cudaError_t launch_prior_cfields_d(cdd *x, long nf, int Nx, int Ny, cd *work, long nf_chunk,
+                                   const double *lam, const FftPlan &plx, const FftPlan &ply,
+                                   const cd *twx, const cd *twy, cudaStream_t s) {
+  int BR = 1;
+  while (BR * 2 <= 16 && (size_t)2 * (BR * 2) * Ny * sizeof(cd) <= 64 * 1024) BR *= 2;
+  int BC = 1;
+  while (BC * 2 <= 16 && (size_t)2 * (BC * 2) * Nx * sizeof(cd) <= 64 * 1024) BC *= 2;
+  const size_t smr = (size_t)2 * BR * Ny * sizeof(cd), smc = (size_t)2 * BC * Nx * sizeof(cd);
+  ensure_smem(k_cfield_rows<false>, smr);
+  ensure_smem(k_cfield_rows<true>, smr);
+  ensure_smem(k_prior_cols<PolD>, smc);
+  for (long f0 = 0; f0 < nf; f0 += nf_chunk) {
+    const int nc = (int)std::min<long>(nf_chunk, nf - f0);
+    cdd *xc = x + f0 * Nx * Ny;
+    dim3 gr((Nx + BR - 1) / BR, nc), gc((Ny + BC - 1) / BC, nc);
+    k_cfield_rows<false><<<gr, 256, smr, s>>>(xc, work, Nx, Ny, ply, twy, BR);
+    k_prior_cols<PolD><<<gc, 256, smc, s>>>(work, lam, Nx, Ny, plx, twx, BC, 2 * nc, BatchArg{});
+    k_cfield_rows<true><<<gr, 256, smr, s>>>(xc, work, Nx, Ny, ply, twy, BR);
+    count_launches(3);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_prior_f(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
                            int Ny, cf *work, const float *lam, const FftPlan &plx,
                            const FftPlan &ply, const cf *twx, const cf *twy, cudaStream_t s,

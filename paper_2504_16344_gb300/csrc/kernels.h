@@ -63,6 +63,11 @@ cudaError_t launch_prior_d(const void *x, int in_kind, void *y, int out_kind, in
                            int Ny, cd *work, const double *lam, const FftPlan &plx,
                            const FftPlan &ply, const cd *twx, const cd *twy, int map_per,
                            int map_stride, int map_off, cudaStream_t s);
+// x[f] <- C x[f] for complex fields f < nf (cdd storage, FP64 arithmetic, set-up);
+// lam: eigenvalues / (Nx Ny) in FP64; work: nf_chunk fields of cd
+cudaError_t launch_prior_cfields_d(cdd *x, long nf, int Nx, int Ny, cd *work, long nf_chunk,
+                                   const double *lam, const FftPlan &plx, const FftPlan &ply,
+                                   const cd *twx, const cd *twy, cudaStream_t s);
 cudaError_t launch_prior_f(const void *x, int in_kind, void *y, int out_kind, int nt, int Nx,
                            int Ny, cf *work, const float *lam, const FftPlan &plx,
                            const FftPlan &ply, const cf *twx, const cf *twy, cudaStream_t s,

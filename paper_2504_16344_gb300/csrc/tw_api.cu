@@ -321,7 +321,7 @@ tw_status tw_set_prior(tw_ctx *c, double nu, double ell, double var) {
   }
   std::vector<dd> l1(N), lh(N);
   std::vector<float> l1f(N), lhf(N);
-  std::vector<double> lhd(N);
+  std::vector<double> lhd(N), l1d(N);
   for (size_t i = 0; i < N; ++i) {
     const double lam = var * (double)N * s[i] / ssum;   // eigenvalue of C
     const double a = lam / (double)N, b = sqrt(lam) / (double)N;   // 1/N of the inverse DFT folded in
@@ -330,6 +330,7 @@ tw_status tw_set_prior(tw_ctx *c, double nu, double ell, double var) {
     l1f[i] = (float)a;
     lhf[i] = (float)b;
     lhd[i] = b;
+    l1d[i] = a;
   }
   if (!c->lam1) {
     c->lam1 = (dd *)twh::dalloc(c, N * sizeof(dd));
@@ -337,10 +338,12 @@ tw_status tw_set_prior(tw_ctx *c, double nu, double ell, double var) {
     c->lam1f = (float *)twh::dalloc(c, N * sizeof(float));
     c->lamhf = (float *)twh::dalloc(c, N * sizeof(float));
     c->lamhd = (double *)twh::dalloc(c, N * sizeof(double));
-    if (!c->lam1 || !c->lamh || !c->lam1f || !c->lamhf || !c->lamhd)
+    c->lam1d = (double *)twh::dalloc(c, N * sizeof(double));
+    if (!c->lam1 || !c->lamh || !c->lam1f || !c->lamhf || !c->lamhd || !c->lam1d)
       return twh::fail(c, TW_ERR_OOM, "prior tables");
   }
   TW_CUDA(c, cudaMemcpy(c->lamhd, lhd.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+  TW_CUDA(c, cudaMemcpy(c->lam1d, l1d.data(), N * sizeof(double), cudaMemcpyHostToDevice));
   // a new prior invalidates any G built with the old one
   std::fill(c->g_rows.begin(), c->g_rows.end(), 0);
   TW_CUDA(c, cudaMemcpy(c->lam1, l1.data(), N * sizeof(dd), cudaMemcpyHostToDevice));

@@ -82,7 +82,9 @@ tw_status infer_core(tw_ctx *c, tw_prec prec, int B, const int *win, const doubl
                      long rhs_bstride, double *m, double *q, cudaStream_t s) {
   const int Nd = c->Nd, Nt = c->Nt, Nm = c->Nm, Nf = c->Nf;
   const long np = c->n_pad;
-  const void *A = c->op[TW_MAP_F][prec];
+  // with G^ = F^ C kept the adjoint gives m directly (no prior filter)
+  const bool useG = c->opG[prec] != nullptr;
+  const void *A = useG ? c->opG[prec] : c->op[TW_MAP_F][prec];
   int *prog_f = c->trsm_prog, *prog_b = c->trsm_prog + trsm_prog_ints(c->bmax);
   const BatchArg ba_y{B, np, (long)Nf * Nd, 0, win};
   const BatchArg ba_x{B, (long)Nf * Nm, (long)Nt * Nm, 0, win};
@@ -101,9 +103,11 @@ tw_status infer_core(tw_ctx *c, tw_prec prec, int B, const int *win, const doubl
                                     Nf, Nd, Nm, B, s)); }
     { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
       TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s, ba_x)); }
-    { twh::Phase p(c, TW_PH_PRIOR, s);
+    if (!useG) {
+      twh::Phase p(c, TW_PH_PRIOR, s);
       TW_CUDA(c, launch_prior_dd(m, 0, m, 0, Nt, c->Nx, c->Ny, (cdd *)c->bxh, c->lam1, c->plX, c->plY,
-                                 c->twX, c->twY, s, ba_p, 0)); }
+                                 c->twX, c->twY, s, ba_p, 0));
+    }
   } else {
     { twh::Phase p(c, TW_PH_TRSV_FWD, s);
       TW_CUDA(c, launch_trsm_dd(c->Lp_dd, c->inv_dd, c->chF_dd, rhs, 0, rhs_bstride, c->bzd, np, win,
@@ -122,9 +126,11 @@ tw_status infer_core(tw_ctx *c, tw_prec prec, int B, const int *win, const doubl
                                      (long)Nf * Nm, Nf, Nd, Nm, B, s)); }
     { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
       TW_CUDA(c, launch_irfft_time_f((const cf *)c->bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s, ba_x)); }
-    { twh::Phase p(c, TW_PH_PRIOR, s);
+    if (!useG) {
+      twh::Phase p(c, TW_PH_PRIOR, s);
       TW_CUDA(c, launch_prior_f(m, 0, m, 0, Nt, c->Nx, c->Ny, (cf *)c->bxh, c->lam1f, c->plX, c->plY,
-                                c->twXf, c->twYf, s, ba_p, 0)); }
+                                c->twXf, c->twYf, s, ba_p, 0));
+    }
   }
   if (q) return forecast_core(c, prec, B, win, m, q, s);
   return TW_OK;
@@ -191,6 +197,11 @@ void free_batch(tw_ctx *c) {
 }  // namespace
 
 tw_status twh::refresh_dd_factor(tw_ctx *c, cudaStream_t s) {
+  if (c->op_tc) {   // tensor-core tiles of the adjoint operator (G^ when kept)
+    const void *src = c->opG[TW_PREC_BF16X2] ? c->opG[TW_PREC_BF16X2] : c->op[TW_MAP_F][TW_PREC_BF16X2];
+    TW_CUDA(c, launch_optc_build(src, c->op_tc, c->Nf, c->Nd, c->Nm, s));
+    TW_CUDA(c, cudaStreamSynchronize(s));
+  }
   if (!c->Lp_dd || !c->have64) return TW_OK;
   const size_t blk = (size_t)NB_ * NB_;
   const size_t nblk = (size_t)c->NB * (c->NB + 1) / 2;
@@ -246,10 +257,7 @@ tw_status tw_reserve_batch(tw_ctx *c, int bmax) {
     free_batch(c);
     return twh::fail(c, TW_ERR_OOM, "batch workspaces");
   }
-  if (c->op_tc) {
-    TW_CUDA(c, launch_optc_build(c->op[TW_MAP_F][TW_PREC_BF16X2], c->op_tc, c->Nf, c->Nd, c->Nm, 0));
-    TW_CUDA(c, cudaDeviceSynchronize());
-  }
+
   c->bmax = bmax;
   TW_CUDA(c, cudaMemset(c->win_dev, 0, B * sizeof(int)));
   return twh::refresh_dd_factor(c, 0);

@@ -246,6 +246,28 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
   }
   TW_CUDA(c, cudaStreamSynchronize(s));
   twh::dfree(c, K);
+  // Phase 2's G* = Gamma_pr F*: G^ = F^ C per frequency, FP64 filter on the
+  // FP64 storage, then converted to the other kept formats
+  if ((c->keep & TW_KEEP_G) && c->op[TW_MAP_F][TW_PREC_FP64]) {
+    const size_t per_w = (size_t)Nd * Nm;
+    // FP64 and complex64 only: bf16 hi+lo storage of G^ rounds at 2^-18 and
+    // that rounding reaches m unsmoothed (1.3e-5 .. 1.6e-5 measured); the
+    // bf16x2 path keeps F^ and the FP32 prior filter
+    for (int fmt = 0; fmt < 2; ++fmt) {
+      if (!c->op[TW_MAP_F][fmt] || c->opG[fmt]) continue;
+      c->opG[fmt] = twh::dalloc(c, (size_t)c->Nf * per_w * (fmt == 0 ? sizeof(cdd) : sizeof(cf)));
+      if (!c->opG[fmt]) return twh::fail(c, TW_ERR_OOM, "G^ storage");
+    }
+    TW_CUDA(c, cudaMemcpyAsync(c->opG[0], c->op[TW_MAP_F][0], (size_t)c->Nf * per_w * sizeof(cdd),
+                               cudaMemcpyDeviceToDevice, s));
+    TW_CUDA(c, launch_prior_cfields_d((cdd *)c->opG[0], (long)c->Nf * Nd, c->Nx, c->Ny, (cd *)c->ws,
+                                      (Nt + 1) / 2, c->lam1d, c->plX, c->plY, c->twXd, c->twYd, s));
+    for (int fmt = 1; fmt < 2; ++fmt)
+      if (c->opG[fmt])
+        TW_CUDA(c, launch_convert_op((const cdd *)c->opG[0], (long)per_w, c->opG[fmt], fmt, (long)per_w,
+                                     (long)per_w, c->Nf, s));
+    TW_CUDA(c, cudaStreamSynchronize(s));
+  }
   return twh::refresh_dd_factor(c, s);
 }
 
@@ -334,8 +356,25 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
         stats->resid_rel = -1.0;
       }
     }
-    // 2) x = F'^T y over the window (y rows >= w are zero), 3) m = Gamma_pr x
-    if (!mixed) {
+    // 2) x = F'^T y over the window (y rows >= w are zero), 3) m = Gamma_pr x;
+    // with G^ kept, m = G'^* y in one adjoint (no prior filter)
+    const void *AG = c->opG[prec];
+    if (AG && !mixed) {
+      { twh::Phase p(c, TW_PH_RFFT_DATA, s);
+        TW_CUDA(c, launch_rfft_time_dd(ysrc, ykind, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
+      { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
+        TW_CUDA(c, launch_gemv_adj_dd(AG, FMT_DD, c->wr, c->wf, Nf, Nd, Nm, s)); }
+      { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+        TW_CUDA(c, launch_irfft_time_dd(c->wf, Nm, mr, 0, Nm, Nm, w, c->plT, c->twT, c->twL, s)); }
+    } else if (AG) {
+      cf *wr = (cf *)c->wr, *wf = (cf *)c->wf;
+      { twh::Phase p(c, TW_PH_RFFT_DATA, s);
+        TW_CUDA(c, launch_rfft_time_f(ysrc, ykind, Nd, w, wr, Nd, Nd, c->plT, c->twTf, c->twLf, s)); }
+      { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
+        TW_CUDA(c, launch_gemv_adj_f(AG, (int)prec, wr, wf, Nf, Nd, Nm, s)); }
+      { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+        TW_CUDA(c, launch_irfft_time_f(wf, Nm, mr, 0, Nm, Nm, w, c->plT, c->twTf, c->twLf, s)); }
+    } else if (!mixed) {
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
         TW_CUDA(c, launch_rfft_time_dd(ysrc, ykind, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);

@@ -24,7 +24,7 @@ PHASES = ["trsv_fwd", "trsv_bwd", "residual", "rfft_data", "gemv_adj", "irfft_pa
 MAP_F, MAP_FQ = 0, 1
 # tw_prec
 PREC_FP64, PREC_C64, PREC_BF16X2 = 0, 1, 2
-KEEP_FP64, KEEP_C64, KEEP_BF16X2 = 1, 2, 4
+KEEP_FP64, KEEP_C64, KEEP_BF16X2, KEEP_G = 1, 2, 4, 8
 # tw_solver
 SOLVE_FACTOR64, SOLVE_FP32_IR = 0, 1
 
