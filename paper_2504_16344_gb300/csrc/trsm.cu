@@ -270,8 +270,7 @@ k_trsm(const T *__restrict__ Lp, const T *__restrict__ Linv, const T *__restrict
     }
     if (has0) o0[gi] = gi < nrows[0] ? res[0] : S::zv();
     if (has1) o1[gi] = gi < nrows[1] ? res[1] : S::zv();
-    __threadfence();
-    __syncthreads();
+    __syncthreads();   // every store before thread 0's (cumulative) release
     if (tid == 0) st_rel(progress, u + 1);
   }
 }

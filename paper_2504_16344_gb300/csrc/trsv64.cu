@@ -119,6 +119,7 @@ __device__ void chain_role(const double *__restrict__ band1, const double *__res
     __syncthreads();
     if (bail) { asm volatile("cp.async.wait_all;" ::: "memory"); return; }
     const long gi = (long)I * NB_ + c;
+    const double w = (q == 0) ? __ldcg(wbuf + gi) : 0.0;   // in flight during the product
     double a = 0.0;
 #pragma unroll
     for (int j = 1; j <= 2; ++j) {
@@ -129,7 +130,6 @@ __device__ void chain_role(const double *__restrict__ band1, const double *__res
       for (int k = q * 16; k < q * 16 + 16; ++k) a = fma(A[k * NB_ + c], zp[k], a);
     }
     red[q][c] = a;
-    const double w = (q == 0) ? __ldcg(wbuf + gi) : 0.0;
     __syncthreads();           // partials in; row u's slots and z_{u-2} consumed
     stage_row(u + 2);          // into row u's slots
     if (q == 0) {
@@ -137,8 +137,9 @@ __device__ void chain_role(const double *__restrict__ band1, const double *__res
       z = gi < nrows ? z : 0.0;
       out[gi] = z;
       zh[u & 1][c] = z;        // overwrites z_{u-2}
-      __threadfence();
     }
+    // the barrier orders every thread's stores before thread 0's release,
+    // which is cumulative: one release publishes the row
     __syncthreads();
     if (tid == 0) rel(progress, u + 1);
   }
@@ -291,12 +292,12 @@ __device__ void worker_role(const double *__restrict__ Lx, const double *__restr
     }
     const int nk = row_tasks(u);
     double *pu = part + ((size_t)u * maxk) * NB_;
-    if (owner) {
-      pu[(size_t)k * NB_ + rrow] = res;
-      __threadfence();
-    }
+    if (owner) pu[(size_t)k * NB_ + rrow] = res;
     __syncthreads();
     if (tid == 0) {
+      // release the partial (fence after the barrier, then the count), and
+      // acquire the other tasks' partials if this one completes the row
+      __threadfence();
       const int done = atomicAdd(cnt + u, 1);
       slast = (done == nk - 1);
       __threadfence();
@@ -308,10 +309,9 @@ __device__ void worker_role(const double *__restrict__ Lx, const double *__restr
       double w = __ldcg(pu + rrow);
       for (int kk = 1; kk < nk; ++kk) w += __ldcg(pu + (size_t)kk * NB_ + rrow);
       wbuf[gi] = gi < nrows ? w : 0.0;
-      __threadfence();
     }
     __syncthreads();
-    if (tid == 0) rel(wflag + I, 1);
+    if (tid == 0) rel(wflag + I, 1);   // cumulative release of the CTA's stores
   }
 }
 
