@@ -96,7 +96,7 @@ __device__ __forceinline__ void add_out<PolD>(void *base, int kind, long off, do
 
 // --------------------------------------------------------- time axis
 template <class P>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, P::occ)
 k_rfft_time(const void *__restrict__ in, int in_kind, long in_ld, int n_in,
             typename P::cx *__restrict__ out, long out_ld, int N, FftPlan pl,
             const typename P::cx *__restrict__ twM, const typename P::cx *__restrict__ twL,
@@ -141,7 +141,7 @@ k_rfft_time(const void *__restrict__ in, int in_kind, long in_ld, int n_in,
 }
 
 template <class P>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, P::occ)
 k_irfft_time(const typename P::cx *__restrict__ in, long in_ld, void *__restrict__ out,
              int out_kind, long out_ld, int N, int n_keep, FftPlan pl,
              const typename P::cx *__restrict__ twM, const typename P::cx *__restrict__ twL,
@@ -198,7 +198,7 @@ struct FieldMap {
 
 // rows pass: pair tp holds z = x_{2tp} + i x_{2tp+1}; FFT along b (length Ny)
 template <class P, bool INV>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, P::occ)
 k_prior_rows(const void *__restrict__ x, int in_kind, void *__restrict__ y, int out_kind,
              typename P::cx *__restrict__ work, int nt, int Nx, int Ny, FftPlan ply,
              const typename P::cx *__restrict__ twy, int BR, FieldMap fm, BatchArg ba, int accum) {
@@ -265,7 +265,7 @@ k_prior_rows(const void *__restrict__ x, int in_kind, void *__restrict__ y, int 
 // columns pass: forward FFT along a (length Nx, stride Ny), scale by lambda,
 // inverse FFT along a, in place in `work`.
 template <class P>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, P::occ)
 k_prior_cols(typename P::cx *__restrict__ work, const typename P::re *__restrict__ lam, int Nx,
              int Ny, FftPlan plx, const typename P::cx *__restrict__ twx, int BC, int nt,
              BatchArg ba) {

@@ -25,7 +25,18 @@ struct FftPlan {
   int M;
   int nst;
   int R[TW_FFT_MAX_STAGES];
+  // division by p (product of the earlier radices) and by S = M / R of each
+  // stage as a multiply-high: q = umulhi(n, mag) then one correction step
+  unsigned pmag[TW_FFT_MAX_STAGES], smag[TW_FFT_MAX_STAGES];
 };
+
+// n / x and n % x for a divisor x >= 1 with mag = floor(2^32 / x) (x = 1: mag unused)
+__device__ __forceinline__ void fdivmod(unsigned n, unsigned x, unsigned mag, unsigned &q, unsigned &r) {
+  if (x == 1) { q = n; r = 0; return; }
+  q = __umulhi(n, mag);
+  r = n - q * x;
+  if (r >= x) { ++q; r -= x; }
+}
 
 template <class P>
 __device__ __forceinline__ typename P::cx ld_cx(const typename P::cx *p);
@@ -126,22 +137,35 @@ struct Bfly {
 template <class P, bool INV, int R>
 __device__ __forceinline__ void fft_pass(const typename P::cx *src, typename P::cx *dst,
                                          const typename P::cx *tab, int M, int p, int B,
-                                         int es, int ss, bool series_fast) {
+                                         int es, int ss, bool series_fast, unsigned pmag,
+                                         unsigned smag) {
   typedef typename P::cx cx;
   const int S = M / R;
   const int tstride = M / (p * R);
   const int total = S * B;
+  const int lgB = __ffs(B) - 1;   // B is a power of two
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     int b, i;
-    if (series_fast) { b = idx % B; i = idx / B; } else { i = idx % S; b = idx / S; }
-    const int k = i % p;
+    if (series_fast) {
+      b = idx & (B - 1);
+      i = idx >> lgB;
+    } else {
+      unsigned q, r;
+      fdivmod((unsigned)idx, (unsigned)S, smag, q, r);
+      i = (int)r;
+      b = (int)q;
+    }
+    unsigned pq, pr;
+    fdivmod((unsigned)i, (unsigned)p, pmag, pq, pr);
+    const int k = (int)pr;
     cx v[R];
     const cx *sb = src + b * ss;
 #pragma unroll
     for (int j = 0; j < R; ++j) v[j] = sb[(i + j * S) * es];
     if (k != 0) {
+      // j k tstride < (R - 1)(p - 1) M / (p R) < M: no reduction needed
 #pragma unroll
-      for (int j = 1; j < R; ++j) v[j] = P::mul(v[j], twid<P, INV>(tab, (j * k * tstride) % M));
+      for (int j = 1; j < R; ++j) v[j] = P::mul(v[j], twid<P, INV>(tab, j * k * tstride));
     }
     Bfly<P, INV, R>::run(v, tab, M);
     const int base = (i - k) * R + k;
@@ -201,12 +225,13 @@ __device__ typename P::cx *fft_run(typename P::cx *buf0, typename P::cx *buf1,
   int p = 1;
   for (int st = 0; st < pl.nst; ++st) {
     const int R = pl.R[st];
+    const unsigned pm = pl.pmag[st], sm = pl.smag[st];
     switch (R) {
-      case 2: fft_pass<P, INV, 2>(src, dst, tab, pl.M, p, B, es, ss, series_fast); break;
-      case 3: fft_pass<P, INV, 3>(src, dst, tab, pl.M, p, B, es, ss, series_fast); break;
-      case 4: fft_pass<P, INV, 4>(src, dst, tab, pl.M, p, B, es, ss, series_fast); break;
-      case 5: fft_pass<P, INV, 5>(src, dst, tab, pl.M, p, B, es, ss, series_fast); break;
-      case 7: fft_pass<P, INV, 7>(src, dst, tab, pl.M, p, B, es, ss, series_fast); break;
+      case 2: fft_pass<P, INV, 2>(src, dst, tab, pl.M, p, B, es, ss, series_fast, pm, sm); break;
+      case 3: fft_pass<P, INV, 3>(src, dst, tab, pl.M, p, B, es, ss, series_fast, pm, sm); break;
+      case 4: fft_pass<P, INV, 4>(src, dst, tab, pl.M, p, B, es, ss, series_fast, pm, sm); break;
+      case 5: fft_pass<P, INV, 5>(src, dst, tab, pl.M, p, B, es, ss, series_fast, pm, sm); break;
+      case 7: fft_pass<P, INV, 7>(src, dst, tab, pl.M, p, B, es, ss, series_fast, pm, sm); break;
       default: fft_pass_generic<P, INV>(src, dst, tab, pl.M, p, R, B, es, ss, series_fast); break;
     }
     __syncthreads();

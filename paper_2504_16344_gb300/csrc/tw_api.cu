@@ -91,6 +91,14 @@ FftPlan make_plan(int M) {
     while (m % q == 0 && n < TW_FFT_MAX_STAGES) { p.R[n++] = q; m /= q; }
   if (m > 1) p.R[n++] = m;  // remaining factor (only for absurd lengths)
   p.nst = n;
+  // magic multipliers for the engine's divisions by p and by S = M / R
+  auto mag = [](unsigned x) -> unsigned { return x <= 1 ? 0u : (unsigned)((1ull << 32) / x); };
+  int prod = 1;
+  for (int st = 0; st < n; ++st) {
+    p.pmag[st] = mag((unsigned)prod);
+    p.smag[st] = mag((unsigned)(M / p.R[st]));
+    prod *= p.R[st];
+  }
   return p;
 }
 
