@@ -166,6 +166,7 @@ struct PolDD {
   typedef cdd cx;
   typedef dd re;
   static constexpr int occ = 2;   // CTAs of 256 threads per SM the FFT kernels aim for
+  static constexpr int smem = 104 * 1024;   // shared-memory budget of one FFT CTA
   static __device__ __forceinline__ cx zero() { return cdd_zero(); }
   static __device__ __forceinline__ cx add(cx a, cx b) { return cdd_add(a, b); }
   static __device__ __forceinline__ cx sub(cx a, cx b) { return cdd_sub(a, b); }
@@ -187,6 +188,7 @@ struct PolF {
   typedef cf cx;
   typedef float re;
   static constexpr int occ = 4;
+  static constexpr int smem = 64 * 1024;
   static __device__ __forceinline__ cx zero() { return cf_zero(); }
   static __device__ __forceinline__ cx add(cx a, cx b) { return cf_add(a, b); }
   static __device__ __forceinline__ cx sub(cx a, cx b) { return cf_sub(a, b); }
@@ -210,6 +212,7 @@ struct PolD {
   typedef cd cx;
   typedef double re;
   static constexpr int occ = 2;
+  static constexpr int smem = 64 * 1024;
   static __device__ __forceinline__ cx make(re r, re i) { cx z; z.re = r; z.im = i; return z; }
   static __device__ __forceinline__ cx zero() { return make(0.0, 0.0); }
   static __device__ __forceinline__ cx add(cx a, cx b) { return make(a.re + b.re, a.im + b.im); }

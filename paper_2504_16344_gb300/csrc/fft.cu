@@ -344,10 +344,10 @@ void ensure_smem(KER k, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-int pick_batch(int len, size_t elem, int cap) {
-  // two ping-pong buffers of len x B elements within ~64 KB
+int pick_batch(int len, size_t elem, int cap, size_t budget) {
+  // two ping-pong buffers of len x B elements within the budget
   int B = 1;
-  while (B * 2 <= cap && (size_t)2 * len * (B * 2) * elem <= 64 * 1024) B *= 2;
+  while (B * 2 <= cap && (size_t)2 * len * (B * 2) * elem <= budget) B *= 2;
   return B;
 }
 
@@ -356,7 +356,7 @@ cudaError_t rfft_time(const void *in, int in_kind, long in_ld, int n_in, typenam
                       long out_ld, int N, const FftPlan &pl, const typename P::cx *twM,
                       const typename P::cx *twL, cudaStream_t s, BatchArg ba = BatchArg{}) {
   if (N <= 0 || ba.count <= 0) return cudaSuccess;
-  const int B = pick_batch(pl.M + 1, sizeof(typename P::cx), 32);
+  const int B = pick_batch(pl.M + 1, sizeof(typename P::cx), 32, P::smem);
   const size_t sm = (size_t)2 * (pl.M + 1) * B * sizeof(typename P::cx);
   ensure_smem(k_rfft_time<P>, sm);
   const dim3 grid((unsigned)((N + B - 1) / B), (unsigned)ba.count);
@@ -372,7 +372,7 @@ cudaError_t irfft_time(const typename P::cx *in, long in_ld, void *out, int out_
                        const typename P::cx *twL, typename P::re invM, cudaStream_t s,
                        BatchArg ba = BatchArg{}) {
   if (N <= 0 || ba.count <= 0) return cudaSuccess;
-  const int B = pick_batch(pl.M + 1, sizeof(typename P::cx), 32);
+  const int B = pick_batch(pl.M + 1, sizeof(typename P::cx), 32, P::smem);
   const size_t sm = (size_t)2 * (pl.M + 1) * B * sizeof(typename P::cx);
   ensure_smem(k_irfft_time<P>, sm);
   const dim3 grid((unsigned)((N + B - 1) / B), (unsigned)ba.count);
@@ -392,9 +392,9 @@ cudaError_t prior(const void *x, int in_kind, void *y, int out_kind, int nt, int
   typedef typename P::cx cx;
   const int np = (nt + 1) / 2;
   int BR = 1;
-  while (BR * 2 <= 16 && (size_t)2 * (BR * 2) * Ny * sizeof(cx) <= 64 * 1024) BR *= 2;
+  while (BR * 2 <= 16 && (size_t)2 * (BR * 2) * Ny * sizeof(cx) <= (size_t)P::smem) BR *= 2;
   int BC = 1;
-  while (BC * 2 <= 16 && (size_t)2 * (BC * 2) * Nx * sizeof(cx) <= 64 * 1024) BC *= 2;
+  while (BC * 2 <= 16 && (size_t)2 * (BC * 2) * Nx * sizeof(cx) <= (size_t)P::smem) BC *= 2;
   const size_t smr = (size_t)2 * BR * Ny * sizeof(cx);
   const size_t smc = (size_t)2 * BC * Nx * sizeof(cx);
   ensure_smem(k_prior_rows<P, false>, smr);
