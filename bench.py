@@ -11,8 +11,12 @@ oracle-made event-0 data of tests/golden/event_c2.npy).  One step is
     q = F_q m                      (tw_forecast: time FFT, GEMV, inverse FFT)
 
 on the FP64-class path (double-float arithmetic, 16-byte operator entries).
-The same step on the mixed path (complex64 operator, FP32 factor + FP64
-refinement) is reported beside it with its error against the FP64 path.
+The same step on the mixed path (complex64 operators, FP32 FFTs; K solved
+with the FP64 factor, or FP32 factor + FP64 refinement) is reported beside it
+with its error against the FP64 path, followed by the batched workload (64
+events with uneven windows + 32 posterior samples, one CUDA graph per
+precision), the serving replay (continuous batching of a Poisson request
+trace) and, with --qoi, the Phase 3 data-to-QoI map and q = Q d.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle
 instead (bounded samples of the same step, extrapolated to a full step).
@@ -149,51 +153,74 @@ def rel(a, b):
 
 
 # --------------------------------------------------------------- CPU oracle
-def oracle_sample(cfg, seed=7):
-    """Time the CPU oracle's online step on bounded samples and extrapolate.
+_ORACLE_INPUTS = {}
 
-    F^T y and F_q m by the direct time-domain sums on a subset of grid
-    points (scaled by Nm / subset), the prior on a subset of time steps
-    (scaled by Nt / subset), and the two triangular solves on an n_s x n_s
-    lower-triangular stand-in factor (scaled by (n / n_s)^2).
-    Returns (extrapolated ms, description, seconds spent).
-    """
+
+def oracle_inputs(cfg, seed=7):
+    """Seeded inputs of the bounded oracle sample (made once per process)."""
     import numpy as np
 
     import synth
+    from oracle import prior as P
+
+    key = (cfg.cid, seed)
+    if key in _ORACLE_INPUTS:
+        return _ORACLE_INPUTS[key]
+    g = synth.rng(seed)
+    ncols = min(cfg.Nm, 8000)
+    cols = np.sort(g.choice(cfg.Nm, size=ncols, replace=False))
+    nts = min(cfg.Nt, 100)
+    ns = min(cfg.n, 12000)
+    inp = dict(
+        ncols=ncols, nts=nts, ns=ns,
+        Fsub=synth.block_column(cfg, "F", cols=cols),
+        Fqsub=synth.block_column(cfg, "Fq", cols=cols),
+        y=g.standard_normal((cfg.Nt, cfg.Nd)),
+        msub=g.standard_normal((cfg.Nt, ncols)),
+        x=g.standard_normal((nts, cfg.Nm)),
+        lam=P.spectrum_for(cfg),
+        Ls=np.tril(g.standard_normal((ns, ns)) * (0.1 / np.sqrt(ns))) + 2.0 * np.eye(ns),
+        b=g.standard_normal(ns))
+    _ORACLE_INPUTS[key] = inp
+    return inp
+
+
+def oracle_sample(cfg, min_seconds=0.0, seed=7):
+    """Time the CPU oracle's online step on a bounded sample and extrapolate.
+
+    One pass: F^T y and F_q m by the direct time-domain sums on a subset of
+    grid points (scaled by Nm / subset), the prior on a subset of time steps
+    (scaled by Nt / subset), and the two triangular solves on an n_s x n_s
+    lower-triangular stand-in factor (scaled by (n / n_s)^2).  Passes repeat
+    until min_seconds of CPU work have been timed (at least one).
+    Returns (median extrapolated ms per step, description, seconds timed).
+    """
     from oracle import posterior as Q
     from oracle import prior as P
     from oracle import toeplitz as T
 
-    g = synth.rng(seed)
-    ncols = min(cfg.Nm, 4000)
-    cols = np.sort(g.choice(cfg.Nm, size=ncols, replace=False))
-    nts = min(cfg.Nt, 40)
-    n = cfg.n
-    ns = min(n, 8000)
-    Fsub = synth.block_column(cfg, "F", cols=cols)
-    Fqsub = synth.block_column(cfg, "Fq", cols=cols)
-    y = g.standard_normal((cfg.Nt, cfg.Nd))
-    msub = g.standard_normal((cfg.Nt, ncols))
-    x = g.standard_normal((nts, cfg.Nm))
-    lam = P.spectrum_for(cfg)
-    Ls = np.tril(g.standard_normal((ns, ns)) * (0.1 / np.sqrt(ns))) + 2.0 * np.eye(ns)
-    b = g.standard_normal(ns)
-    t0 = time.perf_counter()
-    T.p2o_adjoint(Fsub, y)
-    t1 = time.perf_counter()
-    P.prior_apply(x, lam)
-    t2 = time.perf_counter()
-    T.p2o_apply(Fqsub, msub)
-    t3 = time.perf_counter()
-    Q.solve_K(Ls, b)
-    t4 = time.perf_counter()
-    ms = 1e3 * ((t1 - t0) * cfg.Nm / ncols + (t2 - t1) * cfg.Nt / nts
-                + (t3 - t2) * cfg.Nm / ncols + (t4 - t3) * (n / ns) ** 2)
-    desc = (f"oracle direct-sum F^T and F_q on {ncols} of {cfg.Nm} grid points (x{cfg.Nm / ncols:.1f}), "
+    inp = oracle_inputs(cfg, seed)
+    ncols, nts, ns, n = inp["ncols"], inp["nts"], inp["ns"], cfg.n
+    vals, spent, reps = [], 0.0, 0
+    while reps == 0 or spent < min_seconds:
+        t0 = time.perf_counter()
+        T.p2o_adjoint(inp["Fsub"], inp["y"])
+        t1 = time.perf_counter()
+        P.prior_apply(inp["x"], inp["lam"])
+        t2 = time.perf_counter()
+        T.p2o_apply(inp["Fqsub"], inp["msub"])
+        t3 = time.perf_counter()
+        Q.solve_K(inp["Ls"], inp["b"])
+        t4 = time.perf_counter()
+        vals.append(1e3 * ((t1 - t0) * cfg.Nm / ncols + (t2 - t1) * cfg.Nt / nts
+                           + (t3 - t2) * cfg.Nm / ncols + (t4 - t3) * (n / ns) ** 2))
+        spent += t4 - t0
+        reps += 1
+    desc = (f"oracle direct-sum F^T and F_q on {ncols} of {cfg.Nm} grid points (x{cfg.Nm / ncols:.2f}), "
             f"prior on {nts} of {cfg.Nt} steps (x{cfg.Nt / nts:.0f}), two triangular solves of a "
-            f"{ns}x{ns} factor (x{(n / ns) ** 2:.0f}); extrapolated to one full step")
-    return ms, desc, t4 - t0
+            f"{ns}x{ns} factor (x{(n / ns) ** 2:.1f}); extrapolated to one full step; "
+            f"median of {reps} pass(es)")
+    return statistics.median(vals), desc, spent
 
 
 def run_reference(args):
@@ -631,7 +658,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
-        v, desc, spent = oracle_sample(cfg)
+        v, desc, spent = oracle_sample(cfg, min_seconds=10.0)
         cpu = {"value": round(v, 2), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
                "sample": desc, "cpu_seconds": round(spent, 2)}
 
