@@ -228,7 +228,8 @@ def run_reference(args):
     rank, world, _ = rank_info()
     if rank != 0:
         return 0
-    cfg = synth.CONFIGS[2]
+    cfg = synth.small_config(Nd=100, Nx=200, Ny=250, Nt=40, Nq=20, cid=2) if args.small \
+        else synth.CONFIGS[2]
     for _ in range(args.warmup):
         oracle_sample(cfg)
     vals = []
@@ -240,7 +241,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD},
+        "config": {"workload": WORKLOAD if not args.small else WORKLOAD.replace("Nt=400", "Nt=40")},
         "cpu_baseline": {"value": v, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
