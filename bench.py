@@ -619,12 +619,20 @@ def run_ours(args):
         mh = torch.empty(m.shape, dtype=torch.float64).pin_memory()
         qh = torch.empty(q.shape, dtype=torch.float64).pin_memory()
 
+        copy_stream = torch.cuda.Stream(device=dev)
+        m_ready = torch.cuda.Event()
+
         def step_e2e():
             d.copy_(dh, non_blocking=True)
             ctx.infer(tw.PREC_FP64, d, out=m)
+            # m is final here: its copy to the host overlaps the forecast
+            m_ready.record(stream)
+            copy_stream.wait_event(m_ready)
+            with torch.cuda.stream(copy_stream):
+                mh.copy_(m, non_blocking=True)
             ctx.forecast(tw.PREC_FP64, m, out=q)
-            mh.copy_(m, non_blocking=True)
             qh.copy_(q, non_blocking=True)
+            stream.wait_stream(copy_stream)     # the step ends when both results are home
 
         for _ in range(args.warmup):
             step_e2e()
@@ -643,7 +651,8 @@ def run_ours(args):
         e2e = {"value": round(e0.elapsed_time(e1) / args.steps, 4), "unit": "ms",
                "h2d_bytes_per_step": int(dh.numel() * 8),
                "d2h_bytes_per_step": int((mh.numel() + qh.numel()) * 8),
-               "host_wall_ms": round(wall, 4), "path": "tw_infer + tw_forecast through libtw.so"}
+               "host_wall_ms": round(wall, 4),
+               "path": "tw_infer + tw_forecast through libtw.so; m copied to the host during the forecast"}
 
     batch = None
     if not args.no_batch:
