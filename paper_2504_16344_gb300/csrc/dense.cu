@@ -867,21 +867,6 @@ cudaError_t launch_lower_to_float(const double *K, float *K32, long ld, int NB, 
 
 static int trsv_grid(int NBw) { return NBw < 152 * 4 ? NBw : 152 * 4; }
 
-cudaError_t launch_trsv_d(const double *Lp, const double *Linv, const double *Lchain,
-                          const void *rhs, int rhs_kind, double *out, int nrows, int NBw,
-                          int *prog, bool fwd, int *err, int *abort_flag, cudaStream_t s) {
-  if (NBw <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(prog, 0, 2 * sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  if (fwd)
-    k_trsv<double, true><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, out,
-                                                                nrows, NBw, prog, err, abort_flag);
-  else
-    k_trsv<double, false><<<trsv_grid(NBw), 256, 0, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, out,
-                                                                 nrows, NBw, prog, err, abort_flag);
-  count_launches(1);
-  return cudaGetLastError();
-}
 cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const float *Lchain,
                           const void *rhs, int rhs_kind, float *out, int nrows, int NBw, int *prog,
                           bool fwd, int *err, int *abort_flag, cudaStream_t s) {

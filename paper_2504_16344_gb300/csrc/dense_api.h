@@ -23,12 +23,6 @@ cudaError_t launch_double_to_dd(const double *a, dd *b, size_t n, cudaStream_t s
 cudaError_t launch_pack_dd(const dd *K, long ldk, dd *P, int NB, cudaStream_t s);
 cudaError_t launch_pack_f(const float *K, long ldk, float *P, int NB, cudaStream_t s);
 cudaError_t launch_lower_to_float(const double *K, float *K32, long ld, int NB, cudaStream_t s);
-// triangular solves (fwd: L z = b; bwd: L^T x = z), rhs kind 0 double / 1 dd / 2 float
-// prog: two ints (ticket, rows finished), zeroed by the launcher
-// Lchain: M_I = Linv_I L_{I,I-1} (fwd) or C_I = L_{I+1,I} Linv_I (bwd), [NB][64][64]
-cudaError_t launch_trsv_d(const double *Lp, const double *Linv, const double *Lchain,
-                          const void *rhs, int rhs_kind, double *out, int nrows, int NBw,
-                          int *prog, bool fwd, int *err, int *abort_flag, cudaStream_t s);
 
 // FP64 solves of one right-hand side with the block-scaled factor (trsv64.cu)
 struct Trsv64Args {
@@ -52,6 +46,9 @@ void trsv64_task_table(int NB, std::vector<int> &tab, std::vector<int> &prefix);
 cudaError_t launch_trsv64_setup(const double *Lp, const double *Linv, double *Lf, double *Lb,
                                 double *band1, double *band2, int NB, cudaStream_t s);
 cudaError_t launch_trsv64(const Trsv64Args &a, bool fwd, cudaStream_t s);
+// triangular solves (fwd: L z = b; bwd: L^T x = z), rhs kind 0 double / 1 dd / 2 float
+// prog: two ints (ticket, rows finished), zeroed by the launcher
+// Lchain: M_I = Linv_I L_{I,I-1} (fwd) or C_I = L_{I+1,I} Linv_I (bwd), [NB][64][64]
 cudaError_t launch_trsv_f(const float *Lp, const float *Linv, const float *Lchain,
                           const void *rhs, int rhs_kind, float *out, int nrows, int NBw, int *prog,
                           bool fwd, int *err, int *abort_flag, cudaStream_t s);
