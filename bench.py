@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--qoi", action="store_true",
                    help="also time the Phase 3 QoI build (about two minutes) and q = Q d")
+    p.add_argument("--scale", action="store_true",
+                   help="serving at scale instead: 200 sensors, 316x316 grid, 420 steps, 50 "
+                        "forecast points, mixed and FP64 paths in sequence (about 15 minutes)")
     p.add_argument("--requests", type=int, default=1000,
                    help="requests of the serving trace (Poisson 200/s)")
     return p.parse_args()
@@ -145,6 +148,27 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None,
                 "power_w_max": max(power) if power else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def host_available_bytes():
+    """MemAvailable of /proc/meminfo in bytes (None where it cannot be read)."""
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def smi_index(dev):
+    """nvidia-smi's name for a torch device (its UUID; visible-device indices may differ)."""
+    import torch
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        return uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        return dev.index
 
 
 def rel(a, b):
@@ -479,6 +503,173 @@ def run_serve(args, ctx, cfg, sigma, d0, dev):
     return out
 
 
+def run_scale(args):
+    """Serving at scale: the 200-sensor, 316x316-grid (99,856 points), 420-step
+    operator with 50 forecast points and 16 events.  Its FP64-path operators
+    (168 GB) and the complex64 ones (84 GB), with K's set-up (G = Phi C^{1/2},
+    67 GB, and the dense K, 56 GB), do not fit one GPU together, so the two
+    paths run one after the other on the same GPU:
+      1. a complex64 context that forms only the FP64 factor (KEEP_FACTOR64)
+         loads the block columns, forms and factors K (Phase 2) and saves the
+         factor to host memory (the Phase-2 checkpoint);
+      2. an FP64 context loads the block columns and that factor.
+    Each runs the same batch (posterior mean + forecast of every event, with
+    the windows of the trace's first 16 requests, one CUDA graph) and replays
+    the same Poisson request trace with continuous batching.  The event data
+    come from the complex64 apply (inputs only) and serve both paths."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2504_16344_gb300 import build, tw
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    cfg = synth.CONFIGS[5]
+    if args.small:
+        # same sensor and forecast-point counts on a 64 x 79 grid over 84 steps
+        cfg = dataclass_replace(cfg, Nx=64, Ny=79, Nt=84)
+    E, bmax = cfg.events, 16
+    # host memory: the checkpoint (packed factor) and both paths' posterior means
+    NB = -(-cfg.Nd * cfg.Nt // 64)
+    host_need = 8 * 4096 * (NB * (NB + 1) // 2 + NB) + 2 * 8 * E * cfg.Nt * cfg.Nm + (8 << 30)
+    avail = host_available_bytes()
+    if avail is not None and avail < host_need:
+        raise SystemExit(f"serving at scale needs {host_need / 1e9:.0f} GB of host memory, "
+                         f"{avail / 1e9:.0f} GB available")
+    reqs = synth.request_trace(cfg, n=args.requests)
+    arr = np.array([r.t_arrival for r in reqs])
+    ev = np.array([r.event for r in reqs], dtype=np.int32)
+    win = np.array([r.window for r in reqs], dtype=np.int32)
+    win_b = torch.tensor([r.window for r in reqs[:E]], dtype=torch.int32, device=dev)
+    gb = lambda b: round(b / 1e9, 2)
+
+    def load(keep, prior_first):
+        t0 = time.time()
+        ctx = tw.Context(cfg.Nd, cfg.Nq, cfg.Nx, cfg.Ny, cfg.Nt, cfg.Lx, cfg.Ly, keep=keep, device=0)
+        if prior_first:          # G = Phi C^{1/2} is then kept for forming K
+            ctx.set_prior(cfg.nu, cfg.ell, cfg.var)
+        for which, name, rows in ((tw.MAP_F, "F", cfg.Nd), (tw.MAP_FQ, "Fq", cfg.Nq)):
+            for r0 in range(0, rows, 10):
+                col = synth.block_column_torch(cfg, name, dev, r0, min(10, rows - r0))
+                ctx.set_block_column(which, r0, col)
+                del col
+        if not prior_first:
+            ctx.set_prior(cfg.nu, cfg.ell, cfg.var)
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+        return ctx, time.time() - t0
+
+    def run_path(ctx, prec, bank):
+        ctx.reserve_batch(bmax)
+        m = torch.empty((E, cfg.Nt, cfg.Nm), dtype=torch.float64, device=dev)
+        q = torch.empty((E, cfg.Nt, cfg.Nq), dtype=torch.float64, device=dev)
+        stream = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(stream):
+            def body():
+                ctx.infer_batch(prec, bank, win_b, m, q, stream=stream)
+            body()                               # sets kernel attributes before capture
+            stream.synchronize()
+            with ctx.capture(stream) as cap:
+                body()
+            g = cap.graph
+            for _ in range(max(1, args.warmup // 3)):
+                g.launch(stream)
+            stream.synchronize()
+            ctx.check(stream)
+            sampler = ClockSampler(smi_index(dev))
+            sampler.start()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.batch_steps):
+                g.launch(stream)
+            e1.record(stream)
+            stream.synchronize()
+            clocks = sampler.stop()
+            ms = e0.elapsed_time(e1) / args.batch_steps
+            kernels = g.kernel_count()
+            g.close()
+        ctx.check(stream)
+        batch = {"ms_per_batch": round(ms, 2), "ms_per_rhs": round(ms / E, 3),
+                 "graph_kernels": kernels, "clocks": clocks}
+        mh, qh = m.cpu().numpy(), q.cpu().numpy()
+        del m, q
+        torch.cuda.empty_cache()
+        ctx.serve_replay(prec, arr[:8] - arr[0], ev[:8], win[:8], bank, bmax, stream, q_out=False)
+        lat, _, _, st = ctx.serve_replay(prec, arr, ev, win, bank, bmax, stream, q_out=False)
+        _, _, _, sb = ctx.serve_replay(prec, np.zeros_like(arr), ev, win, bank, bmax, stream,
+                                       q_out=False)
+        serve = {"p50_ms": round(float(np.percentile(lat, 50)), 2),
+                 "p99_ms": round(float(np.percentile(lat, 99)), 2),
+                 "max_ms": round(float(lat.max()), 2),
+                 "solves_per_s": round(len(reqs) / st.makespan_s, 1),
+                 "batches": st.batches, "mean_batch": round(st.mean_batch, 2),
+                 "capacity_solves_per_s": round(len(reqs) / sb.makespan_s, 1)}
+        ctx.reserve_batch(0)
+        return batch, serve, mh, qh
+
+    setup = {}
+    # 1) complex64 path; Phase 2 (K formed and factored in FP64) happens here
+    ctx, setup["mixed_load_s"] = load(tw.KEEP_C64 | tw.KEEP_FACTOR64, True)
+    bank = torch.empty((E, cfg.Nt, cfg.Nd), dtype=torch.float64, device=dev)
+    sigma = None
+    for e in range(E):
+        z = torch.from_numpy(synth.event_z(cfg, e)).to(dev)
+        dcl = ctx.p2o_apply(tw.MAP_F, tw.PREC_C64, ctx.prior_apply(z, 0.5))[0]
+        if sigma is None:
+            sigma = cfg.noise_rel * float(torch.sqrt(torch.mean(dcl ** 2)))
+        bank[e] = dcl + sigma * torch.from_numpy(synth.noise_z(cfg, e)).to(dev)
+        del z, dcl
+    t0 = time.time()
+    ctx.factor_K(sigma ** 2)
+    setup["factor_K_s"] = round(time.time() - t0, 1)
+    t0 = time.time()
+    ckpt = ctx.save_factor()
+    setup["save_factor_s"] = round(time.time() - t0, 1)
+    memory = {"checkpoint_gb": gb(ckpt.size), "mixed_context_gb": gb(ctx.device_bytes())}
+    b32, s32, m32, q32 = run_path(ctx, tw.PREC_C64, bank)
+    ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
+    # 2) FP64 path with the saved factor
+    ctx, setup["fp64_load_s"] = load(tw.KEEP_FP64, False)
+    t0 = time.time()
+    ctx.load_factor(ckpt)
+    setup["load_factor_s"] = round(time.time() - t0, 1)
+    del ckpt
+    memory["fp64_context_gb"] = gb(ctx.device_bytes())
+    b64, s64, m64, q64 = run_path(ctx, tw.PREC_FP64, bank)
+    ctx.close()
+    setup = {k: round(v, 1) for k, v in setup.items()}
+    b32["speedup_vs_fp64"] = round(b64["ms_per_batch"] / b32["ms_per_batch"], 3)
+    T = torch.from_numpy
+    b32["m_rel_err_vs_fp64"] = [float(f"{rel(T(m32[e]), T(m64[e])):.3e}") for e in range(E)]
+    b32["q_rel_err_vs_fp64"] = [float(f"{rel(T(q32[e]), T(q64[e])):.3e}") for e in range(E)]
+    s32["capacity_ratio_vs_fp64"] = round(s32["capacity_solves_per_s"] /
+                                          s64["capacity_solves_per_s"], 3)
+    line = {
+        "metric": METRIC, "section": "serving at scale", "value": b32["ms_per_batch"], "unit": "ms",
+        "n_gpus": 1, "steps": args.batch_steps, "warmup": max(1, args.warmup // 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "complex64 operator / FP64-class df64 operator; FP64 factor", "data": "synthetic",
+        "host_memory_available_gb": None if avail is None else round(avail / 1e9, 1),
+        "config": {"workload": (f"Nd={cfg.Nd} sensors, Nm={cfg.Nx}x{cfg.Ny}={cfg.Nm:,} grid points, "
+                                f"Nt={cfg.Nt} steps, Nq={cfg.Nq} forecast points, {E} events; batch: "
+                                f"posterior mean + forecast of every event, windows "
+                                f"{[int(w) for w in win_b.tolist()]}; trace: {len(reqs)} requests, "
+                                f"Poisson at 200/s, windows uniform in [60, {cfg.Nt}]"),
+                   "l2": "inputs larger than L2: the operators (84 / 168 GB) are streamed every batch",
+                   "max_batch": bmax, "sigma": sigma},
+        "setup_s": setup, "memory": memory,
+        "batch": {"mixed_c64": b32, "fp64": b64},
+        "serve": {"mixed_c64": s32, "fp64": s64},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def dataclass_replace(cfg, **kw):
     import dataclasses
     return dataclasses.replace(cfg, **kw)
@@ -563,13 +754,7 @@ def run_ours(args):
         ctx.check()
         return ms, launches, phases
 
-    dev_index = dev.index
-    try:
-        uuid = str(torch.cuda.get_device_properties(dev).uuid)
-        dev_index = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
-    except Exception:
-        pass
-    sampler = ClockSampler(dev_index)
+    sampler = ClockSampler(smi_index(dev))
     sampler.start()
     ms64, launches, phases = timed(tw.PREC_FP64, args.steps, profile=True)
     clocks = sampler.stop()
@@ -706,6 +891,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.scale:
+        return run_scale(args)
     return run_ours(args)
 
 

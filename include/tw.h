@@ -80,6 +80,12 @@ typedef enum { TW_PREC_FP64 = 0, TW_PREC_C64 = 1, TW_PREC_BF16X2 = 2 } tw_prec;
  * the prior filter).  Adds the storage of F's FP64 and complex64 operators;
  * needs TW_KEEP_FP64. */
 #define TW_KEEP_G      8u
+/* TW_KEEP_FACTOR64: tw_factor_K forms only the FP64 factor of K, also in a
+ * context that keeps no FP64 operator (the mixed operator paths then solve
+ * with it, as they do by default when both are present), and skips the FP32
+ * factor.  Lets a complex64 / bf16x2 context run the FP64-factor solves
+ * without the memory of the FP64 operator or of the FP32 factor. */
+#define TW_KEEP_FACTOR64 16u
 
 /*
  * tw_create -- allocate a context for Nd sensors, Nq forecast points, an
@@ -161,10 +167,13 @@ tw_status tw_prior_apply(tw_ctx *ctx, double power, int nrhs, const double *x,
  * time-domain block column as K_(i,j) = noise_var delta_ij I +
  * sum_{s<=min(i,j)} F_{i-s} C F_{j-s}^T (a product G G^T with
  * G = Phi C^{1/2}, then prefix sums along block diagonals), then Cholesky-
- * factored: in native FP64 if TW_KEEP_FP64 was kept (the online solves run
- * in FP64 too), and in FP32 if TW_KEEP_C64 or TW_KEEP_BF16X2 was kept.  K
- * itself is kept as packed double-float blocks (refinement residuals,
- * tw_apply_K).  Needs tw_set_prior and the FP64 operator of F.
+ * factored: in native FP64 if TW_KEEP_FP64 or TW_KEEP_FACTOR64 was kept
+ * (the online solves run in FP64 too), and in FP32 if TW_KEEP_C64 or
+ * TW_KEEP_BF16X2 was kept without TW_KEEP_FACTOR64.  K itself is kept as
+ * packed double-float blocks (refinement residuals, tw_apply_K).  Needs
+ * tw_set_prior, and either the FP64 operator of F or F's block column loaded
+ * after tw_set_prior (TW_ERR_STATE otherwise).  The dense K is released as
+ * soon as it has been factored.
  * Set-up call: allocates, synchronises `stream`, and returns TW_ERR_NOT_SPD
  * (pivot row in tw_last_error) if K is not numerically positive definite.
  * Best accuracy: tw_set_prior, then the block column of F, then this call
@@ -173,10 +182,43 @@ tw_status tw_prior_apply(tw_ctx *ctx, double power, int nrhs, const double *x,
  */
 tw_status tw_factor_K(tw_ctx *ctx, double noise_var, void *stream);
 
+/*
+ * Phase-2 checkpoint.  The offline-online split of the paper (Sec. "Real-time
+ * Bayesian inference and prediction framework": Phases 1-3 run once, Phase 4
+ * reuses their results) lets one context form and factor K and another,
+ * created later or elsewhere with the same sizes, prior and block column,
+ * load the factor instead of forming K again.
+ *
+ * tw_factor_bytes -- size in bytes of the checkpoint of the context's FP64
+ *   factor; 0 when there is none.
+ * tw_save_factor  -- writes the checkpoint to `host` (bytes >= tw_factor_bytes;
+ *   host memory, pageable or pinned, owned by the caller): a 96-byte header
+ *   (magic "TWLFAC01", Nd, Nt, Nx, Ny, block count, block size, noise
+ *   variance, prior parameters, domain size), then the packed lower-triangular
+ *   64x64 blocks of the FP64 Cholesky factor (block (I,J), J <= I, at
+ *   I(I+1)/2 + J, row-major) and the inverses of the diagonal blocks.
+ *   Synchronises `stream`.  TW_ERR_STATE without an FP64 factor, TW_ERR_ARG
+ *   for a short buffer.
+ * tw_load_factor  -- reads such a checkpoint into a context with the same
+ *   Nd, Nt, Nx, Ny, Lx, Ly and prior (tw_set_prior first; TW_ERR_ARG on any
+ *   mismatch, a bad magic or a truncated buffer), then prepares the solves
+ *   exactly as tw_factor_K does after its factorisation (chain blocks,
+ *   single-vector solve tables, G^ when TW_KEEP_G, batch copies).  The
+ *   caller guarantees that the block column of F is the one the factor was
+ *   formed from.  K itself is not part of the checkpoint: afterwards
+ *   tw_apply_K returns TW_ERR_STATE, tw_infer_stats.resid_rel reads -1, and
+ *   the solves use the FP64 factor whatever tw_set_solver selected (no FP32
+ *   factor is held).  Any G held for forming K is released.
+ *   Synchronises the device.
+ */
+size_t tw_factor_bytes(const tw_ctx *ctx);
+tw_status tw_save_factor(tw_ctx *ctx, void *host, size_t bytes, void *stream);
+tw_status tw_load_factor(tw_ctx *ctx, const void *host, size_t bytes, void *stream);
+
 /* Statistics of the last right-hand side of tw_infer (optional output). */
 typedef struct {
   int ir_iters;      /* refinement steps taken (mixed path; 0 for FP64)   */
-  double resid_rel;  /* |d' - K' y| / |d'| with the stored K              */
+  double resid_rel;  /* |d' - K' y| / |d'| with the stored K; -1 without K */
 } tw_infer_stats;
 
 /*

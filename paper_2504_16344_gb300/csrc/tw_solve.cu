@@ -1,6 +1,8 @@
 // tw_solve.cu -- K formation and factorisation, posterior mean, forecast.
 #include <math.h>
+#include <stdint.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 
@@ -66,6 +68,81 @@ tw_status solve32(tw_ctx *c, const void *b, int kind, int nrows, float *y, cudaS
   return TW_OK;
 }
 
+// After the FP64 factor (Lp64, inv64) is in place: the solves' chain blocks,
+// the single-vector solve's block-scaled factor and task table.
+tw_status finish_factor64(tw_ctx *c, cudaStream_t s) {
+  const size_t nblk = (size_t)c->NB * (c->NB + 1) / 2;
+  const size_t blk = (size_t)NB_ * NB_;
+  const size_t np = c->n_pad;
+  if (!c->chF64) c->chF64 = (double *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(double));
+  if (!c->chB64) c->chB64 = (double *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(double));
+  if (!c->chF64 || !c->chB64) return twh::fail(c, TW_ERR_OOM, "chain blocks");
+  TW_CUDA(c, launch_chain_blocks_d(c->Lp64, c->inv64, c->chF64, c->chB64, c->NB, s));
+  std::vector<int> tab;
+  trsv64_task_table(c->NB, tab, c->task_prefix);
+  c->tmaxk = trsv64_max_tasks_per_row(c->NB);
+  auto need = [&](void *&p, size_t bytes) { if (!p) p = twh::dalloc(c, bytes); return p != nullptr; };
+  bool ok = need((void *&)c->Lf64, nblk * blk * sizeof(double)) &&
+            need((void *&)c->Lb64, nblk * blk * sizeof(double)) &&
+            need((void *&)c->band1, (size_t)c->NB * blk * sizeof(double)) &&
+            need((void *&)c->band2, (size_t)c->NB * blk * sizeof(double)) &&
+            need((void *&)c->tasks, tab.size() / 2 * sizeof(int2)) &&
+            need((void *&)c->tpart, (size_t)c->NB * c->tmaxk * NB_ * sizeof(double)) &&
+            need((void *&)c->tcnt, (size_t)c->NB * sizeof(int)) &&
+            need((void *&)c->wbuf64, np * sizeof(double)) &&
+            need((void *&)c->wflag, (size_t)c->NB * sizeof(int));
+  if (!ok) return twh::fail(c, TW_ERR_OOM, "single-vector solve buffers");
+  TW_CUDA(c, cudaMemcpyAsync(c->tasks, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  TW_CUDA(c, launch_trsv64_setup(c->Lp64, c->inv64, c->Lf64, c->Lb64, c->band1, c->band2, c->NB, s));
+  TW_CUDA(c, cudaStreamSynchronize(s));
+  tw_status cs = tw_check(c, s);
+  if (cs != TW_OK) return cs;
+  c->have64 = true;
+  return TW_OK;
+}
+
+// Phase 2's G* = Gamma_pr F*: G^ = F^ C per frequency, FP64 filter on the
+// FP64 storage, then converted to the other kept formats (TW_KEEP_G)
+tw_status form_gstar(tw_ctx *c, cudaStream_t s) {
+  if (!(c->keep & TW_KEEP_G) || !c->op[TW_MAP_F][TW_PREC_FP64]) return TW_OK;
+  const size_t per_w = (size_t)c->Nd * c->Nm;
+  // FP64 and complex64 only: bf16 hi+lo storage of G^ rounds at 2^-18 and
+  // that rounding reaches m unsmoothed (1.3e-5 .. 1.6e-5 measured); the
+  // bf16x2 path keeps F^ and the FP32 prior filter
+  for (int fmt = 0; fmt < 2; ++fmt) {
+    if (!c->op[TW_MAP_F][fmt] || c->opG[fmt]) continue;
+    c->opG[fmt] = twh::dalloc(c, (size_t)c->Nf * per_w * (fmt == 0 ? sizeof(cdd) : sizeof(cf)));
+    if (!c->opG[fmt]) return twh::fail(c, TW_ERR_OOM, "G^ storage");
+  }
+  TW_CUDA(c, cudaMemcpyAsync(c->opG[0], c->op[TW_MAP_F][0], (size_t)c->Nf * per_w * sizeof(cdd),
+                             cudaMemcpyDeviceToDevice, s));
+  TW_CUDA(c, launch_prior_cfields_d((cdd *)c->opG[0], (long)c->Nf * c->Nd, c->Nx, c->Ny, (cd *)c->ws,
+                                    (c->Nt + 1) / 2, c->lam1d, c->plX, c->plY, c->twXd, c->twYd, s));
+  for (int fmt = 1; fmt < 2; ++fmt)
+    if (c->opG[fmt])
+      TW_CUDA(c, launch_convert_op((const cdd *)c->opG[0], (long)per_w, c->opG[fmt], fmt, (long)per_w,
+                                   (long)per_w, c->Nf, s));
+  TW_CUDA(c, cudaStreamSynchronize(s));
+  return TW_OK;
+}
+
+// Phase-2 checkpoint: a fixed header, then the packed FP64 factor blocks and
+// the inverses of its diagonal blocks
+struct FactorHeader {
+  char magic[8];
+  int32_t Nd, Nt, Nx, Ny, NB, blk;
+  uint64_t nblk;
+  double sigma2, nu, ell, var, Lx, Ly;
+  uint64_t reserved;
+};
+static_assert(sizeof(FactorHeader) == 96, "checkpoint header layout");
+const char kFactorMagic[8] = {'T', 'W', 'L', 'F', 'A', 'C', '0', '1'};
+
+size_t factor_payload(int NB) {
+  const size_t nblk = (size_t)NB * (NB + 1) / 2;
+  return (nblk + (size_t)NB) * NB_ * NB_ * sizeof(double);
+}
+
 }  // namespace
 
 extern "C" {
@@ -74,10 +151,13 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
   if (!c) return TW_ERR_ARG;
   if (!(noise_var >= 0.0)) return twh::fail(c, TW_ERR_ARG, "noise variance must be >= 0");
   if (!c->prior_set) return twh::fail(c, TW_ERR_STATE, "tw_set_prior must come before tw_factor_K");
-  if (!c->op[TW_MAP_F][FMT_DD])
-    return twh::fail(c, TW_ERR_STATE, "tw_factor_K needs the FP64 operator (TW_KEEP_FP64)");
   for (char l : c->loaded[TW_MAP_F])
     if (!l) return twh::fail(c, TW_ERR_STATE, "block column of F not fully loaded");
+  bool have_G = c->G != nullptr;
+  for (char g : c->g_rows) have_G = have_G && g;
+  if (!have_G && !c->op[TW_MAP_F][FMT_DD])
+    return twh::fail(c, TW_ERR_STATE,
+                     "without the FP64 operator, tw_set_prior must come before the block column of F");
   cudaStream_t s = (cudaStream_t)stream;
   TW_CUDA(c, cudaSetDevice(c->dev));
   const int Nd = c->Nd, Nt = c->Nt, Nm = c->Nm;
@@ -86,8 +166,10 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
   c->n_pad = c->NB * NB_;
   c->sigma2 = noise_var;
   const long n = c->n, np = c->n_pad;
-  const bool want64 = (c->keep & TW_KEEP_FP64) != 0;
-  const bool want32 = (c->keep & (TW_KEEP_C64 | TW_KEEP_BF16X2)) != 0;
+  const bool want64 = (c->keep & (TW_KEEP_FP64 | TW_KEEP_FACTOR64)) != 0;
+  const bool want32 = (c->keep & (TW_KEEP_C64 | TW_KEEP_BF16X2)) != 0 && !(c->keep & TW_KEEP_FACTOR64);
+  c->have64 = c->have32 = false;
+  c->have_qoi = false;
   tw_status st = ensure_solve_workspace(c);
   if (st != TW_OK) return st;
 
@@ -95,8 +177,6 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
   // column was loaded (tw_set_prior first); otherwise Phi is recovered from
   // the stored operator by the inverse time FFT (K then carries ~1e-14
   // relative error from the double-float operator and filter).
-  bool have_G = c->G != nullptr;
-  for (char g : c->g_rows) have_G = have_G && g;
   dd *G = c->G;
   if (!have_G) {
     if (!G) G = (dd *)twh::dalloc(c, (size_t)n * Nm * sizeof(dd));
@@ -216,58 +296,16 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
     // conditioning (measured 10-30x the FP64 oracle's own error in y).
     TW_CUDA(c, launch_cholesky_d(K, np, c->NB, c->inv64, c->d_err, s));
     TW_CUDA(c, launch_pack_d(K, np, c->Lp64, c->NB, s));
-    if (!c->chF64) c->chF64 = (double *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(double));
-    if (!c->chB64) c->chB64 = (double *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(double));
-    if (!c->chF64 || !c->chB64) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "chain blocks"); }
-    TW_CUDA(c, launch_chain_blocks_d(c->Lp64, c->inv64, c->chF64, c->chB64, c->NB, s));
-    // single-vector solves: block-scaled factor, chain bands, task table
-    {
-      std::vector<int> tab;
-      trsv64_task_table(c->NB, tab, c->task_prefix);
-      c->tmaxk = trsv64_max_tasks_per_row(c->NB);
-      auto need = [&](void *&p, size_t bytes) { if (!p) p = twh::dalloc(c, bytes); return p != nullptr; };
-      bool ok = need((void *&)c->Lf64, nblk * blk * sizeof(double)) &&
-                need((void *&)c->Lb64, nblk * blk * sizeof(double)) &&
-                need((void *&)c->band1, (size_t)c->NB * blk * sizeof(double)) &&
-                need((void *&)c->band2, (size_t)c->NB * blk * sizeof(double)) &&
-                need((void *&)c->tasks, tab.size() / 2 * sizeof(int2)) &&
-                need((void *&)c->tpart, (size_t)c->NB * c->tmaxk * NB_ * sizeof(double)) &&
-                need((void *&)c->tcnt, (size_t)c->NB * sizeof(int)) &&
-                need((void *&)c->wbuf64, (size_t)np * sizeof(double)) &&
-                need((void *&)c->wflag, (size_t)c->NB * sizeof(int));
-      if (!ok) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "single-vector solve buffers"); }
-      TW_CUDA(c, cudaMemcpyAsync(c->tasks, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-      TW_CUDA(c, launch_trsv64_setup(c->Lp64, c->inv64, c->Lf64, c->Lb64, c->band1, c->band2, c->NB, s));
-      TW_CUDA(c, cudaStreamSynchronize(s));
-    }
-    tw_status cs = tw_check(c, stream);
-    if (cs != TW_OK) { twh::dfree(c, K); return cs; }
-    c->have64 = true;
+    TW_CUDA(c, cudaStreamSynchronize(s));
+    twh::dfree(c, K);                   // the dense K is no longer needed
+    K = nullptr;
+    st = finish_factor64(c, s);
+    if (st != TW_OK) return st;
   }
   TW_CUDA(c, cudaStreamSynchronize(s));
   twh::dfree(c, K);
-  // Phase 2's G* = Gamma_pr F*: G^ = F^ C per frequency, FP64 filter on the
-  // FP64 storage, then converted to the other kept formats
-  if ((c->keep & TW_KEEP_G) && c->op[TW_MAP_F][TW_PREC_FP64]) {
-    const size_t per_w = (size_t)Nd * Nm;
-    // FP64 and complex64 only: bf16 hi+lo storage of G^ rounds at 2^-18 and
-    // that rounding reaches m unsmoothed (1.3e-5 .. 1.6e-5 measured); the
-    // bf16x2 path keeps F^ and the FP32 prior filter
-    for (int fmt = 0; fmt < 2; ++fmt) {
-      if (!c->op[TW_MAP_F][fmt] || c->opG[fmt]) continue;
-      c->opG[fmt] = twh::dalloc(c, (size_t)c->Nf * per_w * (fmt == 0 ? sizeof(cdd) : sizeof(cf)));
-      if (!c->opG[fmt]) return twh::fail(c, TW_ERR_OOM, "G^ storage");
-    }
-    TW_CUDA(c, cudaMemcpyAsync(c->opG[0], c->op[TW_MAP_F][0], (size_t)c->Nf * per_w * sizeof(cdd),
-                               cudaMemcpyDeviceToDevice, s));
-    TW_CUDA(c, launch_prior_cfields_d((cdd *)c->opG[0], (long)c->Nf * Nd, c->Nx, c->Ny, (cd *)c->ws,
-                                      (Nt + 1) / 2, c->lam1d, c->plX, c->plY, c->twXd, c->twYd, s));
-    for (int fmt = 1; fmt < 2; ++fmt)
-      if (c->opG[fmt])
-        TW_CUDA(c, launch_convert_op((const cdd *)c->opG[0], (long)per_w, c->opG[fmt], fmt, (long)per_w,
-                                     (long)per_w, c->Nf, s));
-    TW_CUDA(c, cudaStreamSynchronize(s));
-  }
+  st = form_gstar(c, s);
+  if (st != TW_OK) return st;
   return twh::refresh_dd_factor(c, s);
 }
 
@@ -303,6 +341,10 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
                                  cudaMemcpyDeviceToDevice, s));
     else
       TW_CUDA(c, launch_double_to_dd_vec(c->by + (size_t)last * c->n_pad, c->vy, nrows, s));
+    if (!c->Kp64) {   // factor loaded from a checkpoint: K itself is not held
+      stats->resid_rel = -1.0;
+      return TW_OK;
+    }
     TW_CUDA(c, launch_residual(c->Kp64, c->vy, dr, c->vr, nrows, NBw, s));
     TW_CUDA(c, launch_sumsq(c->vr, 1, nrows, c->d_norm, s));
     TW_CUDA(c, launch_sumsq(dr, 0, nrows, c->d_norm + 1, s));
@@ -538,6 +580,84 @@ tw_status tw_set_solver(tw_ctx *c, tw_solver solver) {
     return twh::fail(c, TW_ERR_ARG, "unknown solver");
   c->solver = solver;
   return TW_OK;
+}
+
+size_t tw_factor_bytes(const tw_ctx *c) {
+  if (!c || !c->have64) return 0;
+  return sizeof(FactorHeader) + factor_payload(c->NB);
+}
+
+tw_status tw_save_factor(tw_ctx *c, void *host, size_t bytes, void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (!c->have64) return twh::fail(c, TW_ERR_STATE, "no FP64 factor to save (tw_factor_K first)");
+  const size_t need = tw_factor_bytes(c);
+  if (!host || bytes < need) return twh::fail(c, TW_ERR_ARG, "checkpoint buffer too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  FactorHeader h{};
+  memcpy(h.magic, kFactorMagic, sizeof(h.magic));
+  h.Nd = c->Nd; h.Nt = c->Nt; h.Nx = c->Nx; h.Ny = c->Ny; h.NB = c->NB; h.blk = NB_;
+  h.nblk = (uint64_t)c->NB * (c->NB + 1) / 2;
+  h.sigma2 = c->sigma2; h.nu = c->nu; h.ell = c->ell; h.var = c->var; h.Lx = c->Lx; h.Ly = c->Ly;
+  uint8_t *dst = (uint8_t *)host;
+  memcpy(dst, &h, sizeof(h));
+  const size_t lp = (size_t)h.nblk * NB_ * NB_ * sizeof(double);
+  TW_CUDA(c, cudaMemcpyAsync(dst + sizeof(h), c->Lp64, lp, cudaMemcpyDeviceToHost, s));
+  TW_CUDA(c, cudaMemcpyAsync(dst + sizeof(h) + lp, c->inv64, (size_t)c->NB * NB_ * NB_ * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
+  TW_CUDA(c, cudaStreamSynchronize(s));
+  return TW_OK;
+}
+
+tw_status tw_load_factor(tw_ctx *c, const void *host, size_t bytes, void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (!host || bytes < sizeof(FactorHeader)) return twh::fail(c, TW_ERR_ARG, "checkpoint too short");
+  if (!c->prior_set) return twh::fail(c, TW_ERR_STATE, "tw_set_prior must come before tw_load_factor");
+  FactorHeader h;
+  memcpy(&h, host, sizeof(h));
+  if (memcmp(h.magic, kFactorMagic, sizeof(h.magic)) != 0)
+    return twh::fail(c, TW_ERR_ARG, "not a factor checkpoint");
+  const int NB = (c->Nd * c->Nt + NB_ - 1) / NB_;
+  if (h.Nd != c->Nd || h.Nt != c->Nt || h.Nx != c->Nx || h.Ny != c->Ny || h.blk != NB_ || h.NB != NB ||
+      h.nblk != (uint64_t)NB * (NB + 1) / 2)
+    return twh::fail(c, TW_ERR_ARG, "checkpoint was made for other sizes");
+  if (h.nu != c->nu || h.ell != c->ell || h.var != c->var || h.Lx != c->Lx || h.Ly != c->Ly)
+    return twh::fail(c, TW_ERR_ARG, "checkpoint was made with another prior or domain");
+  if (!(h.sigma2 >= 0.0)) return twh::fail(c, TW_ERR_ARG, "checkpoint noise variance invalid");
+  if (bytes < sizeof(FactorHeader) + factor_payload(NB))
+    return twh::fail(c, TW_ERR_ARG, "checkpoint truncated");
+  cudaStream_t s = (cudaStream_t)stream;
+  TW_CUDA(c, cudaSetDevice(c->dev));
+  TW_CUDA(c, cudaDeviceSynchronize());
+  c->have64 = c->have32 = false;
+  c->have_qoi = false;
+  // K itself is not part of the checkpoint: a K held from an earlier
+  // factorisation would not match the loaded factor
+  twh::dfree(c, c->Kp64);
+  c->Kp64 = nullptr;
+  twh::dfree(c, c->G);      // G is only needed to form K
+  c->G = nullptr;
+  std::fill(c->g_rows.begin(), c->g_rows.end(), 0);
+  c->n = c->Nd * c->Nt;
+  c->NB = NB;
+  c->n_pad = NB * NB_;
+  c->sigma2 = h.sigma2;
+  tw_status st = ensure_solve_workspace(c);
+  if (st != TW_OK) return st;
+  const size_t blk = (size_t)NB_ * NB_;
+  const size_t lp = (size_t)h.nblk * blk * sizeof(double);
+  if (!c->Lp64) c->Lp64 = (double *)twh::dalloc(c, lp);
+  if (!c->inv64) c->inv64 = (double *)twh::dalloc(c, (size_t)NB * blk * sizeof(double));
+  if (!c->Lp64 || !c->inv64) return twh::fail(c, TW_ERR_OOM, "factor buffers");
+  const uint8_t *src = (const uint8_t *)host + sizeof(FactorHeader);
+  TW_CUDA(c, cudaMemcpyAsync(c->Lp64, src, lp, cudaMemcpyHostToDevice, s));
+  TW_CUDA(c, cudaMemcpyAsync(c->inv64, src + lp, (size_t)NB * blk * sizeof(double),
+                             cudaMemcpyHostToDevice, s));
+  st = finish_factor64(c, s);
+  if (st != TW_OK) return st;
+  st = form_gstar(c, s);
+  if (st != TW_OK) return st;
+  return twh::refresh_dd_factor(c, s);
 }
 
 }  // extern "C"

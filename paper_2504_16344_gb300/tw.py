@@ -24,7 +24,7 @@ PHASES = ["trsv_fwd", "trsv_bwd", "residual", "rfft_data", "gemv_adj", "irfft_pa
 MAP_F, MAP_FQ = 0, 1
 # tw_prec
 PREC_FP64, PREC_C64, PREC_BF16X2 = 0, 1, 2
-KEEP_FP64, KEEP_C64, KEEP_BF16X2, KEEP_G = 1, 2, 4, 8
+KEEP_FP64, KEEP_C64, KEEP_BF16X2, KEEP_G, KEEP_FACTOR64 = 1, 2, 4, 8, 16
 # tw_solver
 SOLVE_FACTOR64, SOLVE_FP32_IR = 0, 1
 
@@ -45,6 +45,9 @@ SIGNATURES = {
     "tw_p2o_adjoint": (_S, [_P, _I, _I, _I, _P, _P, _P]),
     "tw_prior_apply": (_S, [_P, _D, _I, _P, _P, _P]),
     "tw_factor_K": (_S, [_P, _D, _P]),
+    "tw_factor_bytes": (ctypes.c_size_t, [_P]),
+    "tw_save_factor": (_S, [_P, _P, ctypes.c_size_t, _P]),
+    "tw_load_factor": (_S, [_P, _P, ctypes.c_size_t, _P]),
     "tw_infer": (_S, [_P, _I, _I, _P, _P, _P, _P, _P]),
     "tw_forecast": (_S, [_P, _I, _I, _P, _P, _P]),
     "tw_solve_K": (_S, [_P, _I, _I, _P, _P, _P, _P]),
@@ -239,6 +242,29 @@ class Context:
     # ------------------------------------------------------------ solve
     def factor_K(self, noise_var, stream=None):
         self._check(self.lib.tw_factor_K(self.h, float(noise_var), _stream_ptr(stream)))
+
+    def factor_bytes(self) -> int:
+        return int(self.lib.tw_factor_bytes(self.h))
+
+    def save_factor(self, path=None, stream=None):
+        """Phase-2 checkpoint of the FP64 factor: a numpy uint8 array (also
+        written to `path` when given)."""
+        import numpy as np
+        n = self.factor_bytes()
+        if n == 0:
+            raise TwError(4, "no FP64 factor to save (factor_K first)")
+        buf = np.empty(n, dtype=np.uint8)
+        self._check(self.lib.tw_save_factor(self.h, buf.ctypes.data, n, _stream_ptr(stream)))
+        if path is not None:
+            buf.tofile(path)
+        return buf
+
+    def load_factor(self, src, stream=None):
+        """Load a checkpoint written by save_factor (array or file path)."""
+        import numpy as np
+        buf = np.fromfile(src, dtype=np.uint8) if isinstance(src, (str, os.PathLike)) else src
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(self.lib.tw_load_factor(self.h, buf.ctypes.data, buf.size, _stream_ptr(stream)))
 
     def set_refinement(self, steps):
         self._check(self.lib.tw_set_refinement(self.h, int(steps)))

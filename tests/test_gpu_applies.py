@@ -22,6 +22,8 @@ CASES = {
     "ragged": synth.small_config(Nd=13, Nx=45, Ny=50, Nt=21, Nq=3, cid=81),
     "mid": synth.small_config(Nd=37, Nx=40, Ny=60, Nt=50, Nq=6, cid=82),
     "long": synth.small_config(Nd=5, Nx=20, Ny=25, Nt=400, Nq=2, cid=83),
+    # the 316 x 316 grid of the serving workload: 316 = 4 * 79, a prime radix-79 pass
+    "grid316": synth.small_config(Nd=4, Nx=316, Ny=316, Nt=6, Nq=2, cid=87),
 }
 
 

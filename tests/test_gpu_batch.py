@@ -30,6 +30,10 @@ CASES = {
     "c1": synth.CONFIGS[1],
     "mid": synth.small_config(Nd=20, Nx=40, Ny=50, Nt=40, Nq=5, cid=84),
     "wide": synth.small_config(Nd=26, Nx=60, Ny=75, Nt=77, Nq=3, cid=85),
+    # 200 sensors and 50 forecast points as in the serving workload (100 KB of
+    # shared memory per adjoint-product CTA, two row passes in the forward
+    # product), a prime grid dimension
+    "s200": synth.small_config(Nd=200, Nx=16, Ny=79, Nt=9, Nq=50, cid=88),
 }
 NEV = 11        # events per case: one full slice of 8 columns plus a ragged one
 BMAX = 12

@@ -31,6 +31,8 @@ CASES = {
     "mid": synth.small_config(Nd=20, Nx=40, Ny=50, Nt=40, Nq=5, cid=84),
     # n = 2002 (odd Nt, Nd not a divisor of 64)
     "wide": synth.small_config(Nd=26, Nx=60, Ny=75, Nt=77, Nq=3, cid=85),
+    # the 316 x 316 grid of the serving workload (prior filter with radix-79 passes)
+    "grid316": synth.small_config(Nd=4, Nx=316, Ny=316, Nt=6, Nq=2, cid=87),
 }
 
 
