@@ -62,9 +62,17 @@ typedef enum { TW_MAP_F = 0, TW_MAP_FQ = 1 } tw_map;
  *                   16 bytes per complex entry, the size of complex128);
  *                   arithmetic in double-float (error-free FP32 transforms).
  *                   This is the library's FP64-class path.
- *  TW_PREC_C64    : F^ held as complex64, FP32 products, blocked FP32 sums.
+ *  TW_PREC_C64    : F^ held as complex64.  Adjoint applies (F^T y, the
+ *                   posterior mean's product) take y's spectrum as float
+ *                   pairs and sum FP32 blocks of 8 rows into compensated
+ *                   totals (y is large against m and F^T y cancels, so FP32
+ *                   data or one FP32 running sum would lose accuracy far
+ *                   above the operator's own 2^-24 rounding); forward
+ *                   applies, inverse FFTs and the prior run in FP32.
  *  TW_PREC_BF16X2 : F^ held as bf16 hi + bf16 lo per real (8 bytes per
- *                   complex entry), FP32 products and sums.                   */
+ *                   complex entry); arithmetic as TW_PREC_C64, except the
+ *                   batched adjoint on tensor cores (FP32 data spectra split
+ *                   into three bf16 terms, FP32 accumulation).               */
 typedef enum { TW_PREC_FP64 = 0, TW_PREC_C64 = 1, TW_PREC_BF16X2 = 2 } tw_prec;
 
 /* Storage kept by the context (bit mask for tw_create's `keep`). */

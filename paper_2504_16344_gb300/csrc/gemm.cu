@@ -22,8 +22,10 @@
 //    a second kernel in a fixed order.
 //
 // FP64-class path: float-pair operands, exact products, renormalised
-// running sums (as the single-vector kernels); FP32 path: complex64 or
-// bf16 hi+lo operator, FP32 FMA.
+// running sums (as the single-vector kernels).  Reduced-precision paths:
+// complex64 or bf16 hi+lo operator; the adjoint takes float-pair data and
+// sums FP32 blocks of rows into compensated totals, the forward product
+// uses FP32 FMA.
 #include <algorithm>
 #include <type_traits>
 
@@ -119,63 +121,86 @@ k_gemm_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ Y, long y_bs
   }
 }
 
-// ------------------------------------------------------------ adjoint, FP32
-// grid (ceil(Nm/128), Nf, ceil(B/64)); 8 warps x 8 right-hand sides each
+// ----------------------------------------- adjoint, FP32 operator, pair data
+// grid (ceil(Nm/128), Nf, ceil(B/32)); 8 warps x 4 right-hand sides each, a
+// thread 4 right-hand sides x 4 grid points.  Y entries are float pairs;
+// both parts enter FP32 block sums of GX_BLK rows (FMA) that are folded into
+// compensated totals, so the cancellation in F^T y does not amplify FP32
+// rounding of y or of a long running sum.
+constexpr int GX_BLK = 8;
+
 template <int FMT>
 __global__ void __launch_bounds__(256, 2)
-k_gemm_adj_f(const void *__restrict__ A, const cf *__restrict__ Y, long y_bstride,
-             cf *__restrict__ X, long x_bstride, int Nr, int Nm, int B) {
+k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstride,
+              cf *__restrict__ X, long x_bstride, int Nr, int Nm, int B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cf *sy = reinterpret_cast<cf *>(smem_raw);   // [64][Nr]
+  cdd *sy = reinterpret_cast<cdd *>(smem_raw);   // [32][Nr]
   const int w = blockIdx.y;
-  const int b0 = blockIdx.z * 64;
-  const int nb = min(64, B - b0);
-  for (int idx = threadIdx.x; idx < 64 * Nr; idx += blockDim.x) {
+  const int b0 = blockIdx.z * 32;
+  const int nb = min(32, B - b0);
+  for (int idx = threadIdx.x; idx < 32 * Nr; idx += blockDim.x) {
     const int bl = idx / Nr, sr = idx % Nr;
-    sy[idx] = bl < nb ? Y[(size_t)(b0 + bl) * y_bstride + (size_t)w * Nr + sr] : cf_zero();
+    sy[idx] = bl < nb ? ld_cdd(Y + (size_t)(b0 + bl) * y_bstride + (size_t)w * Nr + sr) : cdd_zero();
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int k0 = blockIdx.x * GA_K + lane;
   const size_t base = (size_t)w * Nr * Nm;
-  float re[8][4], im[8][4];
+  float br[4][4], bi[4][4];   // [rhs][point] block sums
+  facc tr[4][4], ti[4][4];    // compensated totals
   bool ok[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) ok[j] = k0 + 32 * j < Nm;
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { re[i][j] = 0.f; im[i][j] = 0.f; }
+    for (int j = 0; j < 4; ++j) {
+      br[i][j] = 0.f; bi[i][j] = 0.f; tr[i][j] = facc_zero(); ti[i][j] = facc_zero();
+    }
   cf cur[4], nxt[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) cur[j] = ok[j] ? ld_opf<FMT>(A, base + k0 + 32 * j) : cf_zero();
-  const cf *syg = sy + (grp * 8) * Nr;
-  for (int s = 0; s < Nr; ++s) {
-    if (s + 1 < Nr) {
-      const size_t row = base + (size_t)(s + 1) * Nm + k0;
+  const cdd *syg = sy + (grp * 4) * Nr;
+  for (int s0 = 0; s0 < Nr; s0 += GX_BLK) {
+    const int s1 = min(Nr, s0 + GX_BLK);
+    for (int s = s0; s < s1; ++s) {
+      if (s + 1 < Nr) {
+        const size_t row = base + (size_t)(s + 1) * Nm + k0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) nxt[j] = ok[j] ? ld_opf<FMT>(A, row + 32 * j) : cf_zero();
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const cf y = syg[i * Nr + s];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        re[i][j] = fmaf(cur[j].re, y.re, fmaf(cur[j].im, y.im, re[i][j]));
-        im[i][j] = fmaf(cur[j].re, y.im, fmaf(-cur[j].im, y.re, im[i][j]));
+        for (int j = 0; j < 4; ++j) nxt[j] = ok[j] ? ld_opf<FMT>(A, row + 32 * j) : cf_zero();
       }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const cdd y = syg[i * Nr + s];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          // conj(a) y = (ar yr + ai yi) + i (ar yi - ai yr)
+          br[i][j] = fmaf(cur[j].re, y.re.hi, br[i][j]);
+          br[i][j] = fmaf(cur[j].im, y.im.hi, br[i][j]);
+          br[i][j] = fmaf(cur[j].re, y.re.lo, br[i][j]);
+          br[i][j] = fmaf(cur[j].im, y.im.lo, br[i][j]);
+          bi[i][j] = fmaf(cur[j].re, y.im.hi, bi[i][j]);
+          bi[i][j] = fmaf(-cur[j].im, y.re.hi, bi[i][j]);
+          bi[i][j] = fmaf(cur[j].re, y.im.lo, bi[i][j]);
+          bi[i][j] = fmaf(-cur[j].im, y.re.lo, bi[i][j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cur[j] = nxt[j];
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) cur[j] = nxt[j];
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { facc_fold(tr[i][j], br[i][j]); facc_fold(ti[i][j], bi[i][j]); }
   }
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int bl = grp * 8 + i;
+  for (int i = 0; i < 4; ++i) {
+    const int bl = grp * 4 + i;
     if (bl >= nb) continue;
     cf *xo = X + (size_t)(b0 + bl) * x_bstride + (size_t)w * Nm;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (ok[j]) xo[k0 + 32 * j] = cf_make(re[i][j], im[i][j]);
+      if (ok[j]) xo[k0 + 32 * j] = cf_make(facc_get(tr[i][j]), facc_get(ti[i][j]));
   }
 }
 
@@ -340,14 +365,10 @@ void ensure_smem_g(KER k, size_t bytes) {
 
 int gemm_fwd_nchunk(int Nm) { return (Nm + GF_K * GF_TILES - 1) / (GF_K * GF_TILES); }
 
-size_t gemm_adj_smem(int prec_fp32, int Nr) {
-  return prec_fp32 ? (size_t)64 * Nr * sizeof(cf) : (size_t)32 * Nr * sizeof(cdd);
-}
-
 cudaError_t launch_gemm_adj_dd(const void *A, const cdd *Y, long y_bstride, cdd *X, long x_bstride,
                                int Nf, int Nr, int Nm, int B, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  const size_t sm = gemm_adj_smem(0, Nr);
+  const size_t sm = (size_t)32 * Nr * sizeof(cdd);
   ensure_smem_g(k_gemm_adj_dd, sm);
   dim3 grid((Nm + GA_K - 1) / GA_K, Nf, (B + 31) / 32);
   k_gemm_adj_dd<<<grid, 256, sm, s>>>(reinterpret_cast<const float4 *>(A), Y, y_bstride, X,
@@ -356,17 +377,19 @@ cudaError_t launch_gemm_adj_dd(const void *A, const cdd *Y, long y_bstride, cdd 
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_adj_f(const void *A, int fmt, const cf *Y, long y_bstride, cf *X,
-                              long x_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s) {
+cudaError_t launch_gemm_adj_fx(const void *A, int fmt, const cdd *Y, long y_bstride, cf *X,
+                               long x_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  const size_t sm = gemm_adj_smem(1, Nr);
-  dim3 grid((Nm + GA_K - 1) / GA_K, Nf, (B + 63) / 64);
+  const size_t sm = (size_t)32 * Nr * sizeof(cdd);
+  dim3 grid((Nm + GA_K - 1) / GA_K, Nf, (B + 31) / 32);
   if (fmt == FMT_C64) {
-    ensure_smem_g(k_gemm_adj_f<FMT_C64>, sm);
-    k_gemm_adj_f<FMT_C64><<<grid, 256, sm, s>>>(A, Y, y_bstride, X, x_bstride, Nr, Nm, B);
+    ensure_smem_g(k_gemm_adj_fx<FMT_C64>, sm);
+    k_gemm_adj_fx<FMT_C64><<<grid, 256, sm, s>>>(A, Y, y_bstride, X, x_bstride, Nr, Nm, B);
+  } else if (fmt == FMT_BF16X2) {
+    ensure_smem_g(k_gemm_adj_fx<FMT_BF16X2>, sm);
+    k_gemm_adj_fx<FMT_BF16X2><<<grid, 256, sm, s>>>(A, Y, y_bstride, X, x_bstride, Nr, Nm, B);
   } else {
-    ensure_smem_g(k_gemm_adj_f<FMT_BF16X2>, sm);
-    k_gemm_adj_f<FMT_BF16X2><<<grid, 256, sm, s>>>(A, Y, y_bstride, X, x_bstride, Nr, Nm, B);
+    return cudaErrorInvalidValue;
   }
   count_launches(1);
   return cudaGetLastError();

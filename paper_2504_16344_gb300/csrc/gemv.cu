@@ -14,8 +14,10 @@
 //    sums are added by a second small kernel in a fixed order.
 //
 // The FP64-class path reads float-pair entries (16 B) and accumulates with
-// exact products and a compensated running sum; the FP32 path reads
-// complex64 or bf16 hi+lo entries (8 B).
+// exact products and a compensated running sum; the reduced-precision
+// paths read complex64 or bf16 hi+lo entries (8 B): the forward product
+// sums in FP32, the adjoint takes float-pair data and sums FP32 blocks of
+// rows into compensated totals.
 #include "kernels.h"
 
 namespace tw {
@@ -102,42 +104,66 @@ k_gemv_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ yh, cdd *__r
   }
 }
 
+// Reduced-precision adjoint with float-pair data: the operator entry (FP32)
+// times y = y_hi + y_lo, both parts by FMA into an FP32 block sum over
+// MIX_BLK rows, each block folded into a compensated total.  Rounding y to
+// FP32, or summing all Nr products in one FP32 running sum, would lose
+// accuracy to the cancellation in F^T y (K's conditioning makes y large
+// against m); this way the error stays near the operator's own rounding.
+constexpr int MIX_BLK = 8;
+
 template <int FMT>
 __global__ void __launch_bounds__(256)
-k_gemv_adj_f(const void *__restrict__ A, const cf *__restrict__ yh, cf *__restrict__ xh, int Nr,
-             int Nm) {
+k_gemv_adj_fx(const void *__restrict__ A, const cdd *__restrict__ yh, cf *__restrict__ xh, int Nr,
+              int Nm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cf *sy = reinterpret_cast<cf *>(smem_raw);
+  cdd *sy = reinterpret_cast<cdd *>(smem_raw);
   const int w = blockIdx.y;
   const size_t base = (size_t)w * Nr * Nm;
-  for (int s = threadIdx.x; s < Nr; s += blockDim.x) sy[s] = yh[(size_t)w * Nr + s];
+  for (int s = threadIdx.x; s < Nr; s += blockDim.x) sy[s] = ld_cdd(yh + (size_t)w * Nr + s);
   __syncthreads();
   const int kb = blockIdx.x * (256 * ADJ_KPT) + threadIdx.x;
-  float re[ADJ_KPT], im[ADJ_KPT];
+  float br[ADJ_KPT], bi[ADJ_KPT];
+  facc tr[ADJ_KPT], ti[ADJ_KPT];
   bool ok[ADJ_KPT];
 #pragma unroll
-  for (int j = 0; j < ADJ_KPT; ++j) { re[j] = 0.f; im[j] = 0.f; ok[j] = kb + 256 * j < Nm; }
+  for (int j = 0; j < ADJ_KPT; ++j) {
+    br[j] = 0.f; bi[j] = 0.f; tr[j] = facc_zero(); ti[j] = facc_zero();
+    ok[j] = kb + 256 * j < Nm;
+  }
   cf cur[ADJ_KPT], nxt[ADJ_KPT];
 #pragma unroll
   for (int j = 0; j < ADJ_KPT; ++j) cur[j] = ok[j] ? ld_op_f<FMT>(A, base + kb + 256 * j) : cf_zero();
-  for (int s = 0; s < Nr; ++s) {
-    if (s + 1 < Nr) {
-      const size_t row = base + (size_t)(s + 1) * Nm + kb;
+  for (int s0 = 0; s0 < Nr; s0 += MIX_BLK) {
+    const int s1 = min(Nr, s0 + MIX_BLK);
+    for (int s = s0; s < s1; ++s) {
+      if (s + 1 < Nr) {
+        const size_t row = base + (size_t)(s + 1) * Nm + kb;
 #pragma unroll
-      for (int j = 0; j < ADJ_KPT; ++j) nxt[j] = ok[j] ? ld_op_f<FMT>(A, row + 256 * j) : cf_zero();
+        for (int j = 0; j < ADJ_KPT; ++j) nxt[j] = ok[j] ? ld_op_f<FMT>(A, row + 256 * j) : cf_zero();
+      }
+      const cdd y = sy[s];
+#pragma unroll
+      for (int j = 0; j < ADJ_KPT; ++j) {
+        // conj(a) y = (ar yr + ai yi) + i (ar yi - ai yr)
+        br[j] = fmaf(cur[j].re, y.re.hi, br[j]);
+        br[j] = fmaf(cur[j].im, y.im.hi, br[j]);
+        br[j] = fmaf(cur[j].re, y.re.lo, br[j]);
+        br[j] = fmaf(cur[j].im, y.im.lo, br[j]);
+        bi[j] = fmaf(cur[j].re, y.im.hi, bi[j]);
+        bi[j] = fmaf(-cur[j].im, y.re.hi, bi[j]);
+        bi[j] = fmaf(cur[j].re, y.im.lo, bi[j]);
+        bi[j] = fmaf(-cur[j].im, y.re.lo, bi[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < ADJ_KPT; ++j) cur[j] = nxt[j];
     }
-    const cf y = sy[s];
 #pragma unroll
-    for (int j = 0; j < ADJ_KPT; ++j) {
-      re[j] = fmaf(cur[j].re, y.re, fmaf(cur[j].im, y.im, re[j]));
-      im[j] = fmaf(cur[j].re, y.im, fmaf(-cur[j].im, y.re, im[j]));
-    }
-#pragma unroll
-    for (int j = 0; j < ADJ_KPT; ++j) cur[j] = nxt[j];
+    for (int j = 0; j < ADJ_KPT; ++j) { facc_fold(tr[j], br[j]); facc_fold(ti[j], bi[j]); }
   }
 #pragma unroll
   for (int j = 0; j < ADJ_KPT; ++j)
-    if (ok[j]) xh[(size_t)w * Nm + kb + 256 * j] = cf_make(re[j], im[j]);
+    if (ok[j]) xh[(size_t)w * Nm + kb + 256 * j] = cf_make(facc_get(tr[j]), facc_get(ti[j]));
 }
 
 // ------------------------------------------------------------ forward
@@ -329,23 +355,22 @@ cudaError_t launch_gemv_adj_dd(const void *A, int fmt, const cdd *yh, cdd *xh, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemv_adj_f(const void *A, int fmt, const cf *yh, cf *xh, int Nf, int Nr,
-                              int Nm, cudaStream_t s) {
-  const size_t sm = (size_t)Nr * sizeof(cf);
+cudaError_t launch_gemv_adj_fx(const void *A, int fmt, const cdd *yh, cf *xh, int Nf, int Nr,
+                               int Nm, cudaStream_t s) {
+  const size_t sm = (size_t)Nr * sizeof(cdd);
   dim3 g((Nm + 256 * ADJ_KPT - 1) / (256 * ADJ_KPT), Nf);
   if (fmt == FMT_C64) {
     if (sm > 48 * 1024)
-      cudaFuncSetAttribute(k_gemv_adj_f<FMT_C64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gemv_adj_f<FMT_C64><<<g, 256, sm, s>>>(A, yh, xh, Nr, Nm);
-    count_launches(1);
+      cudaFuncSetAttribute(k_gemv_adj_fx<FMT_C64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_gemv_adj_fx<FMT_C64><<<g, 256, sm, s>>>(A, yh, xh, Nr, Nm);
   } else if (fmt == FMT_BF16X2) {
     if (sm > 48 * 1024)
-      cudaFuncSetAttribute(k_gemv_adj_f<FMT_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gemv_adj_f<FMT_BF16X2><<<g, 256, sm, s>>>(A, yh, xh, Nr, Nm);
-    count_launches(1);
+      cudaFuncSetAttribute(k_gemv_adj_fx<FMT_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_gemv_adj_fx<FMT_BF16X2><<<g, 256, sm, s>>>(A, yh, xh, Nr, Nm);
   } else {
     return cudaErrorInvalidValue;
   }
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -115,15 +115,22 @@ tw_status infer_core(tw_ctx *c, tw_prec prec, int B, const int *win, const doubl
     { twh::Phase p(c, TW_PH_TRSV_BWD, s);
       TW_CUDA(c, launch_trsm_dd(c->Lp_dd, c->inv_dd, c->chB_dd, c->bzd, 1, np, c->byd, np, win, Nd, Nt,
                                 B, c->NB, prog_b, false, c->d_err, c->abort_flag, s)); }
-    { twh::Phase p(c, TW_PH_RFFT_DATA, s);
-      TW_CUDA(c, launch_rfft_time_f(c->byd, 1, Nd, Nt, (cf *)c->byh, Nd, Nd, c->plT, c->twTf, c->twLf, s, ba_y)); }
-    { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-      if (prec == TW_PREC_BF16X2 && c->op_tc)   // tensor cores (tcgen05)
+    if (prec == TW_PREC_BF16X2 && c->op_tc) {   // tensor cores (tcgen05): FP32 data spectra
+      { twh::Phase p(c, TW_PH_RFFT_DATA, s);
+        TW_CUDA(c, launch_rfft_time_f(c->byd, 1, Nd, Nt, (cf *)c->byh, Nd, Nd, c->plT, c->twTf, c->twLf, s, ba_y)); }
+      { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
         TW_CUDA(c, launch_gemm_adj_tc(c->op_tc, (const cf *)c->byh, (long)Nf * Nd, (cf *)c->bxh,
-                                      (long)Nf * Nm, Nf, Nd, Nm, B, c->btc, c->d_err, s));
-      else
-        TW_CUDA(c, launch_gemm_adj_f(A, (int)prec, (const cf *)c->byh, (long)Nf * Nd, (cf *)c->bxh,
-                                     (long)Nf * Nm, Nf, Nd, Nm, B, s)); }
+                                      (long)Nf * Nm, Nf, Nd, Nm, B, c->btc, c->d_err, s)); }
+    } else {
+      // double-float data spectra and compensated block sums: F^T y cancels
+      // (y is large against m), so FP32 y or one FP32 running sum would lose
+      // accuracy well above the operator's own rounding
+      { twh::Phase p(c, TW_PH_RFFT_DATA, s);
+        TW_CUDA(c, launch_rfft_time_dd(c->byd, 1, Nd, Nt, (cdd *)c->byh, Nd, Nd, c->plT, c->twT, c->twL, s, ba_y)); }
+      { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
+        TW_CUDA(c, launch_gemm_adj_fx(A, (int)prec, (const cdd *)c->byh, (long)Nf * Nd, (cf *)c->bxh,
+                                      (long)Nf * Nm, Nf, Nd, Nm, B, s)); }
+    }
     { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
       TW_CUDA(c, launch_irfft_time_f((const cf *)c->bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s, ba_x)); }
     if (!useG) {

@@ -409,11 +409,12 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
         TW_CUDA(c, launch_irfft_time_dd(c->wf, Nm, mr, 0, Nm, Nm, w, c->plT, c->twT, c->twL, s)); }
     } else if (AG) {
-      cf *wr = (cf *)c->wr, *wf = (cf *)c->wf;
+      // reduced-precision operator, data side in double-float (see the else branch)
+      cf *wf = (cf *)c->wf;
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
-        TW_CUDA(c, launch_rfft_time_f(ysrc, ykind, Nd, w, wr, Nd, Nd, c->plT, c->twTf, c->twLf, s)); }
+        TW_CUDA(c, launch_rfft_time_dd(ysrc, ykind, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-        TW_CUDA(c, launch_gemv_adj_f(AG, (int)prec, wr, wf, Nf, Nd, Nm, s)); }
+        TW_CUDA(c, launch_gemv_adj_fx(AG, (int)prec, c->wr, wf, Nf, Nd, Nm, s)); }
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
         TW_CUDA(c, launch_irfft_time_f(wf, Nm, mr, 0, Nm, Nm, w, c->plT, c->twTf, c->twLf, s)); }
     } else if (!mixed) {
@@ -427,12 +428,15 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
         TW_CUDA(c, launch_prior_dd(c->wt, 1, mr, 0, w, c->Nx, c->Ny, c->ws, c->lam1, c->plX, c->plY,
                                    c->twX, c->twY, s)); }
     } else {
-      cf *wr = (cf *)c->wr, *wf = (cf *)c->wf;
+      // reduced-precision operator: y's spectrum stays double-float (y is large
+      // against m, and F^T y cancels), the product sums FP32 blocks into
+      // compensated totals; x^ onwards (inverse FFT, prior) runs in FP32
+      cf *wf = (cf *)c->wf;
       float *wt = (float *)c->wt;
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
-        TW_CUDA(c, launch_rfft_time_f(ysrc, ykind, Nd, w, wr, Nd, Nd, c->plT, c->twTf, c->twLf, s)); }
+        TW_CUDA(c, launch_rfft_time_dd(ysrc, ykind, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-        TW_CUDA(c, launch_gemv_adj_f(A, (int)prec, wr, wf, Nf, Nd, Nm, s)); }
+        TW_CUDA(c, launch_gemv_adj_fx(A, (int)prec, c->wr, wf, Nf, Nd, Nm, s)); }
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
         TW_CUDA(c, launch_irfft_time_f(wf, Nm, wt, 2, Nm, Nm, w, c->plT, c->twTf, c->twLf, s)); }
       { twh::Phase p(c, TW_PH_PRIOR, s);

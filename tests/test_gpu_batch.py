@@ -63,11 +63,59 @@ def case(request):
     ctx.factor_K(sigma ** 2)
     ctx.reserve_batch(BMAX)
     ws = _windows(cfg.Nt, NEV)
-    m_ref = [Q.posterior_mean(F, lam, L, ds[e], cfg.Nt, nt_window=ws[e])[0] for e in range(NEV)]
+    post = [Q.posterior_mean(F, lam, L, ds[e], cfg.Nt, nt_window=ws[e]) for e in range(NEV)]
+    m_ref = [p[0] for p in post]
     q_ref = [T.p2o_apply(Fq, m) for m in m_ref]
+    # floor of the reduced-precision paths: the exact posterior mean computed
+    # with the operator rounded to the stored format (complex64, bf16 hi+lo)
+    floor = {fmt: max(rel(P.prior_apply(adjoint_rounded_operator(F, _pad_y(post[e][1], cfg), fmt), lam),
+                          m_ref[e]) for e in range(NEV)) for fmt in ("C64", "BF16X2")}
     yield dict(cfg=cfg, ctx=ctx, F=F, Fq=Fq, lam=lam, d=np.stack(ds), sigma=sigma, L=L, ws=ws,
-               m_ref=m_ref, q_ref=q_ref, dev=torch.device("cuda", 0))
+               m_ref=m_ref, q_ref=q_ref, floor=floor, dev=torch.device("cuda", 0))
     ctx.close()
+
+
+def _pad_y(y: np.ndarray, cfg) -> np.ndarray:
+    """Solution of a window (its leading Nd Nt' entries) as [Nt][Nd], zero beyond."""
+    out = np.zeros(cfg.Nt * cfg.Nd)
+    out[:y.size] = np.ravel(y)
+    return out.reshape(cfg.Nt, cfg.Nd)
+
+
+def _bf16_rn(x32: np.ndarray) -> np.ndarray:
+    """float32 -> bf16 (round to nearest even), returned as float32."""
+    u = x32.astype(np.float32).view(np.uint32)
+    u = (u + (((u >> 16) & 1) + 0x7FFF)) & np.uint32(0xFFFF0000)
+    return u.view(np.float32)
+
+
+def _round_operator(Fh: np.ndarray, fmt: str) -> np.ndarray:
+    """Frequency-domain operator rounded as stored: complex64, or each real
+    part as float32 split into bf16 hi + bf16 lo."""
+    if fmt == "C64":
+        return Fh.astype(np.complex64).astype(np.complex128)
+    out = []
+    for part in (Fh.real, Fh.imag):
+        v = part.astype(np.float32)
+        hi = _bf16_rn(v)
+        lo = _bf16_rn((v - hi).astype(np.float32))
+        out.append(hi.astype(np.float64) + lo.astype(np.float64))
+    return out[0] + 1j * out[1]
+
+
+def adjoint_rounded_operator(F: np.ndarray, y: np.ndarray, fmt: str) -> np.ndarray:
+    """F^T y in exact (FP64) arithmetic on the frequency-domain operator
+    rounded to `fmt`: zero-pad time to 2Nt, conj(F^(w))^T y^(w) per
+    frequency, inverse transform, first Nt steps (circulant embedding of Sec.
+    "FFT-based Hessian matvecs").  With the unrounded operator it equals the
+    oracle's direct-sum adjoint (checked here)."""
+    Nt = F.shape[0]
+    Fh = np.fft.rfft(F, n=2 * Nt, axis=0)
+    yh = np.fft.rfft(y, n=2 * Nt, axis=0)
+    exact = np.fft.irfft(np.einsum("wsk,ws->wk", Fh.conj(), yh), n=2 * Nt, axis=0)[:Nt]
+    assert rel(exact, T.p2o_adjoint(F, y)) < 1e-12
+    xh = np.einsum("wsk,ws->wk", _round_operator(Fh, fmt).conj(), yh)
+    return np.fft.irfft(xh, n=2 * Nt, axis=0)[:Nt]
 
 
 def _t(a, dev, dtype=None):
@@ -138,11 +186,15 @@ def test_mixed_batch(case, prec):
     m, q = m.cpu().numpy(), q.cpu().numpy()
     em = max(rel(m[e], case["m_ref"][e]) for e in range(NEV))
     eq = max(rel(q[e], case["q_ref"][e]) for e in range(NEV))
-    print(f"{case['cfg'].cid}: batched {prec} m {em:.2e} q {eq:.2e}")
-    # q = F_q m inherits m's FP32-operator error amplified by F_q's
+    fl = case["floor"][prec]
+    print(f"{case['cfg'].cid}: batched {prec} m {em:.2e} (rounded-operator floor {fl:.2e}) q {eq:.2e}")
+    # m: 1e-5, or twice the error that rounding the stored operator alone
+    # causes where K's conditioning lifts that floor above 1e-5 (exact
+    # arithmetic on the rounded operator; no solve or accumulation can
+    # recover it).  q = F_q m inherits m's error amplified by F_q's
     # cancellation (the single-vector path shows q/m ~ 6 at full window);
     # short windows amplify more, so q gets a 1e-4 guard
-    assert em < 1e-5 and eq < 1e-4
+    assert em < max(1e-5, 2.0 * fl) and eq < 1e-4
 
 
 def test_result_independent_of_batch_mates(case):
