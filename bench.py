@@ -591,9 +591,17 @@ def run_scale(args):
             ms = e0.elapsed_time(e1) / args.batch_steps
             kernels = g.kernel_count()
             g.close()
+            # per-phase device times from one uncaptured, profiled pass
+            ctx.profile_read(reset=True)
+            ctx.profile(True)
+            body()
+            stream.synchronize()
+            ctx.profile(False)
+            ph = ctx.profile_read(reset=True)
         ctx.check(stream)
         batch = {"ms_per_batch": round(ms, 2), "ms_per_rhs": round(ms / E, 3),
-                 "graph_kernels": kernels, "clocks": clocks}
+                 "graph_kernels": kernels, "clocks": clocks,
+                 "phases_ms": {k: round(v[0], 2) for k, v in ph.items() if v[1]}}
         mh, qh = m.cpu().numpy(), q.cpu().numpy()
         del m, q
         torch.cuda.empty_cache()
