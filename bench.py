@@ -792,7 +792,9 @@ def run_ours(args):
     mixed = None
     if not args.no_mixed:
         ms32, _, ph32 = timed(tw.PREC_C64, args.steps, profile=True)
-        mixed = {"prec": "complex64 operator and FP32 FFTs/prior; K solved with the double-float factor",
+        mixed = {"prec": ("complex64 operator (G^ when kept); adjoint with double-float data spectra and "
+                          "compensated FP32 sums; FP32 parameter-side FFTs and forecast; K solved with "
+                          "the FP64 factor"),
                  "ms_per_step": round(ms32, 4), "speedup_vs_fp64": round(ms64 / ms32, 3),
                  "m_rel_err_vs_fp64": rel(m, m64), "q_rel_err_vs_fp64": rel(q, q64),
                  "phases_ms": {k: round(v[0] / max(1, args.steps), 4) for k, v in ph32.items() if v[1]}}

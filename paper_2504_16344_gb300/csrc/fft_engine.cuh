@@ -175,43 +175,67 @@ __device__ __forceinline__ void fft_pass(const typename P::cx *src, typename P::
   }
 }
 
-// Pass with a runtime odd radix R (large prime factors): inputs are twiddled
-// in place in src (each butterfly owns its inputs), then every output is a
-// direct R-term sum.  O(R) work per output.
+// Pass with a runtime odd radix R (prime factors above 7).  Step 1, one
+// thread per butterfly (each owns its R inputs): twiddle the inputs, replace
+// v_j, v_{R-j} (j = 1..h, h = (R-1)/2) in place by a_j = v_j + v_{R-j} and
+// b_j = v_j - v_{R-j}, and write u_0 = v_0 + sum a_j.  Step 2, one thread per
+// output pair (q, R-q), q = 1..h (the symmetric form of the odd-radix
+// butterfly above):  c = v_0 + sum_j a_j cos(2 pi j q/R),
+// s = -sum_j b_j sin(2 pi j q/R), u_q = c + i s and u_{R-q} = c - i s
+// (forward; swapped for the inverse).  The twiddle index j q mod R advances
+// by q per term.  O(R) work per output pair.
 template <class P, bool INV>
 __device__ void fft_pass_generic(typename P::cx *src, typename P::cx *dst,
                                  const typename P::cx *tab, int M, int p, int R, int B,
                                  int es, int ss, bool series_fast) {
   typedef typename P::cx cx;
+  typedef typename P::re re;
   const int S = M / R;
   const int tstride = M / (p * R);
+  const int h = (R - 1) / 2;
   const int total = S * B;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     int b, i;
     if (series_fast) { b = idx % B; i = idx / B; } else { i = idx % S; b = idx / S; }
     const int k = i % p;
-    if (k != 0) {
-      cx *sb = src + b * ss;
-      for (int j = 1; j < R; ++j) {
-        cx w = twid<P, INV>(tab, (j * k * tstride) % M);
-        sb[(i + j * S) * es] = P::mul(sb[(i + j * S) * es], w);
+    cx *sb = src + b * ss;
+    cx u0 = sb[i * es];
+    for (int j = 1; j <= h; ++j) {
+      cx vj = sb[(i + j * S) * es], vr = sb[(i + (R - j) * S) * es];
+      if (k != 0) {
+        // j k tstride < (R - 1)(p - 1) M / (p R) < M: no reduction needed
+        vj = P::mul(vj, twid<P, INV>(tab, j * k * tstride));
+        vr = P::mul(vr, twid<P, INV>(tab, (R - j) * k * tstride));
       }
+      const cx a = P::add(vj, vr);
+      sb[(i + j * S) * es] = a;
+      sb[(i + (R - j) * S) * es] = P::sub(vj, vr);
+      u0 = P::add(u0, a);
     }
+    dst[b * ss + ((i - k) * R + k) * es] = u0;
   }
   __syncthreads();
-  const int totq = S * R * B;
+  const int totq = S * h * B;
   for (int idx = threadIdx.x; idx < totq; idx += blockDim.x) {
     int b, i, q;
-    if (series_fast) { b = idx % B; int r = idx / B; i = r % S; q = r / S; }
-    else { i = idx % S; int r = idx / S; b = r % B; q = r / B; }
+    if (series_fast) { b = idx % B; const int r = idx / B; i = r % S; q = r / S + 1; }
+    else { i = idx % S; const int r = idx / S; b = r % B; q = r / B + 1; }
     const int k = i % p;
     const cx *sb = src + b * ss;
-    cx acc = sb[i * es];
-    for (int j = 1; j < R; ++j) {
-      cx w = twid<P, INV>(tab, ((j * q) % R) * S);
-      acc = P::add(acc, P::mul(sb[(i + j * S) * es], w));
+    cx c = sb[i * es];
+    cx sn = P::zero();
+    int t = 0;
+    for (int j = 1; j <= h; ++j) {
+      t += q;
+      if (t >= R) t -= R;
+      const cx w = ld_cx<P>(tab + t * S);              // forward table: cos - i sin
+      c = P::add(c, P::scale_re(sb[(i + j * S) * es], P::real(w)));
+      sn = P::add(sn, P::scale_re(sb[(i + (R - j) * S) * es], P::imag(w)));
     }
-    dst[b * ss + ((i - k) * R + k + q * p) * es] = acc;
+    const cx is = P::mul_i(sn);
+    cx *db = dst + b * ss + ((i - k) * R + k) * es;
+    db[q * p * es] = INV ? P::sub(c, is) : P::add(c, is);
+    db[(R - q) * p * es] = INV ? P::add(c, is) : P::sub(c, is);
   }
 }
 

@@ -131,16 +131,21 @@ k_gemv_adj_fx(const void *__restrict__ A, const cdd *__restrict__ yh, cf *__rest
     br[j] = 0.f; bi[j] = 0.f; tr[j] = facc_zero(); ti[j] = facc_zero();
     ok[j] = kb + 256 * j < Nm;
   }
-  cf cur[ADJ_KPT], nxt[ADJ_KPT];
+  // rows s+1 and s+2 in flight while row s is used (8-byte entries: two rows
+  // ahead keep as many bytes in flight as the 16-byte kernel's one)
+  cf cur[ADJ_KPT], nx1[ADJ_KPT], nx2[ADJ_KPT];
 #pragma unroll
-  for (int j = 0; j < ADJ_KPT; ++j) cur[j] = ok[j] ? ld_op_f<FMT>(A, base + kb + 256 * j) : cf_zero();
+  for (int j = 0; j < ADJ_KPT; ++j) {
+    cur[j] = ok[j] ? ld_op_f<FMT>(A, base + kb + 256 * j) : cf_zero();
+    nx1[j] = (ok[j] && Nr > 1) ? ld_op_f<FMT>(A, base + (size_t)Nm + kb + 256 * j) : cf_zero();
+  }
   for (int s0 = 0; s0 < Nr; s0 += MIX_BLK) {
     const int s1 = min(Nr, s0 + MIX_BLK);
     for (int s = s0; s < s1; ++s) {
-      if (s + 1 < Nr) {
-        const size_t row = base + (size_t)(s + 1) * Nm + kb;
+      if (s + 2 < Nr) {
+        const size_t row = base + (size_t)(s + 2) * Nm + kb;
 #pragma unroll
-        for (int j = 0; j < ADJ_KPT; ++j) nxt[j] = ok[j] ? ld_op_f<FMT>(A, row + 256 * j) : cf_zero();
+        for (int j = 0; j < ADJ_KPT; ++j) nx2[j] = ok[j] ? ld_op_f<FMT>(A, row + 256 * j) : cf_zero();
       }
       const cdd y = sy[s];
 #pragma unroll
@@ -156,7 +161,7 @@ k_gemv_adj_fx(const void *__restrict__ A, const cdd *__restrict__ yh, cf *__rest
         bi[j] = fmaf(-cur[j].im, y.re.lo, bi[j]);
       }
 #pragma unroll
-      for (int j = 0; j < ADJ_KPT; ++j) cur[j] = nxt[j];
+      for (int j = 0; j < ADJ_KPT; ++j) { cur[j] = nx1[j]; nx1[j] = nx2[j]; }
     }
 #pragma unroll
     for (int j = 0; j < ADJ_KPT; ++j) { facc_fold(tr[j], br[j]); facc_fold(ti[j], bi[j]); }
