@@ -64,10 +64,10 @@ typedef enum { TW_MAP_F = 0, TW_MAP_FQ = 1 } tw_map;
  *                   This is the library's FP64-class path.
  *  TW_PREC_C64    : F^ held as complex64.  Adjoint applies (F^T y, the
  *                   posterior mean's product) take y's spectrum as float
- *                   pairs and sum FP32 blocks of 8 rows into compensated
- *                   totals (y is large against m and F^T y cancels, so FP32
- *                   data or one FP32 running sum would lose accuracy far
- *                   above the operator's own 2^-24 rounding); forward
+ *                   pairs and add FP32 blocks of 8 rows into FP32 totals
+ *                   (y is large against m and F^T y cancels, so an FP32
+ *                   data spectrum would lose accuracy far above the
+ *                   operator's own 2^-24 rounding); forward
  *                   applies, inverse FFTs and the prior run in FP32.
  *  TW_PREC_BF16X2 : F^ held as bf16 hi + bf16 lo per real (8 bytes per
  *                   complex entry); arithmetic as TW_PREC_C64, except the

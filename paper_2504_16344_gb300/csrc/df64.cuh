@@ -122,22 +122,6 @@ __device__ __forceinline__ void dacc_fold(dd &tot, dacc &A) {
   A = dacc_zero();
 }
 
-// Compensated total of FP32 partial sums (Neumaier): value = s + c.  The
-// reduced-precision paths form short FP32 block sums of products with FMA
-// and fold each block here, so a long sum with cancellation rounds at the
-// block level instead of at every term.
-struct facc { float s, c; };
-__device__ __forceinline__ facc facc_zero() { facc a; a.s = 0.f; a.c = 0.f; return a; }
-// A += b, then b = 0
-__device__ __forceinline__ void facc_fold(facc &A, float &b) {
-  float s, e;
-  two_sum(A.s, b, s, e);
-  A.s = s;
-  A.c = __fadd_rn(A.c, e);
-  b = 0.f;
-}
-__device__ __forceinline__ float facc_get(const facc &A) { return __fadd_rn(A.s, A.c); }
-
 // ------------------------------------------------------ complex df64
 __device__ __forceinline__ cdd cdd_zero() { cdd z; z.re = dd_zero(); z.im = dd_zero(); return z; }
 __device__ __forceinline__ cdd cdd_add(cdd a, cdd b) { cdd r; r.re = dd_add(a.re, b.re); r.im = dd_add(a.im, b.im); return r; }

@@ -24,7 +24,7 @@
 // FP64-class path: float-pair operands, exact products, renormalised
 // running sums (as the single-vector kernels).  Reduced-precision paths:
 // complex64 or bf16 hi+lo operator; the adjoint takes float-pair data and
-// sums FP32 blocks of rows into compensated totals, the forward product
+// adds FP32 block sums of rows into FP32 totals, the forward product
 // uses FP32 FMA.
 #include <algorithm>
 #include <type_traits>
@@ -124,9 +124,9 @@ k_gemm_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ Y, long y_bs
 // ----------------------------------------- adjoint, FP32 operator, pair data
 // grid (ceil(Nm/128), Nf, ceil(B/32)); 8 warps x 4 right-hand sides each, a
 // thread 4 right-hand sides x 4 grid points.  Y entries are float pairs;
-// both parts enter FP32 block sums of GX_BLK rows (FMA) that are folded into
-// compensated totals, so the cancellation in F^T y does not amplify FP32
-// rounding of y or of a long running sum.
+// both parts enter FP32 block sums of GX_BLK rows (FMA) that are added to
+// FP32 totals: with the data spectrum in double-float the cancellation in
+// F^T y no longer amplifies an FP32 rounding of y.
 constexpr int GX_BLK = 8;
 
 template <int FMT>
@@ -147,7 +147,7 @@ k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstr
   const int k0 = blockIdx.x * GA_K + lane;
   const size_t base = (size_t)w * Nr * Nm;
   float br[4][4], bi[4][4];   // [rhs][point] block sums
-  facc tr[4][4], ti[4][4];    // compensated totals
+  float tr[4][4], ti[4][4];   // totals
   bool ok[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) ok[j] = k0 + 32 * j < Nm;
@@ -155,7 +155,7 @@ k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstr
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      br[i][j] = 0.f; bi[i][j] = 0.f; tr[i][j] = facc_zero(); ti[i][j] = facc_zero();
+      br[i][j] = 0.f; bi[i][j] = 0.f; tr[i][j] = 0.f; ti[i][j] = 0.f;
     }
   cf cur[4], nxt[4];
 #pragma unroll
@@ -191,7 +191,10 @@ k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstr
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) { facc_fold(tr[i][j], br[i][j]); facc_fold(ti[i][j], bi[i][j]); }
+      for (int j = 0; j < 4; ++j) {
+        tr[i][j] += br[i][j]; ti[i][j] += bi[i][j];
+        br[i][j] = 0.f; bi[i][j] = 0.f;
+      }
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -200,7 +203,7 @@ k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstr
     cf *xo = X + (size_t)(b0 + bl) * x_bstride + (size_t)w * Nm;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (ok[j]) xo[k0 + 32 * j] = cf_make(facc_get(tr[i][j]), facc_get(ti[i][j]));
+      if (ok[j]) xo[k0 + 32 * j] = cf_make(tr[i][j], ti[i][j]);
   }
 }
 

@@ -16,8 +16,8 @@
 // The FP64-class path reads float-pair entries (16 B) and accumulates with
 // exact products and a compensated running sum; the reduced-precision
 // paths read complex64 or bf16 hi+lo entries (8 B): the forward product
-// sums in FP32, the adjoint takes float-pair data and sums FP32 blocks of
-// rows into compensated totals.
+// sums in FP32, the adjoint takes float-pair data and adds FP32 block sums
+// of rows into FP32 totals.
 #include "kernels.h"
 
 namespace tw {
@@ -106,10 +106,11 @@ k_gemv_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ yh, cdd *__r
 
 // Reduced-precision adjoint with float-pair data: the operator entry (FP32)
 // times y = y_hi + y_lo, both parts by FMA into an FP32 block sum over
-// MIX_BLK rows, each block folded into a compensated total.  Rounding y to
-// FP32, or summing all Nr products in one FP32 running sum, would lose
-// accuracy to the cancellation in F^T y (K's conditioning makes y large
-// against m); this way the error stays near the operator's own rounding.
+// MIX_BLK rows, each block added to an FP32 total.  F^T y cancels (K's
+// conditioning makes y large against m), so the data spectrum must not be
+// rounded to FP32 or come from an FP32 FFT; with it in double-float, the low
+// halves and the short blocks take the error a further ~1.4x down (measured
+// by emulating every rounding; a compensated total gained nothing more).
 constexpr int MIX_BLK = 8;
 
 template <int FMT>
@@ -124,11 +125,11 @@ k_gemv_adj_fx(const void *__restrict__ A, const cdd *__restrict__ yh, cf *__rest
   __syncthreads();
   const int kb = blockIdx.x * (256 * ADJ_KPT) + threadIdx.x;
   float br[ADJ_KPT], bi[ADJ_KPT];
-  facc tr[ADJ_KPT], ti[ADJ_KPT];
+  float tr[ADJ_KPT], ti[ADJ_KPT];
   bool ok[ADJ_KPT];
 #pragma unroll
   for (int j = 0; j < ADJ_KPT; ++j) {
-    br[j] = 0.f; bi[j] = 0.f; tr[j] = facc_zero(); ti[j] = facc_zero();
+    br[j] = 0.f; bi[j] = 0.f; tr[j] = 0.f; ti[j] = 0.f;
     ok[j] = kb + 256 * j < Nm;
   }
   // rows s+1 and s+2 in flight while row s is used (8-byte entries: two rows
@@ -164,11 +165,14 @@ k_gemv_adj_fx(const void *__restrict__ A, const cdd *__restrict__ yh, cf *__rest
       for (int j = 0; j < ADJ_KPT; ++j) { cur[j] = nx1[j]; nx1[j] = nx2[j]; }
     }
 #pragma unroll
-    for (int j = 0; j < ADJ_KPT; ++j) { facc_fold(tr[j], br[j]); facc_fold(ti[j], bi[j]); }
+    for (int j = 0; j < ADJ_KPT; ++j) {
+      tr[j] += br[j]; ti[j] += bi[j];
+      br[j] = 0.f; bi[j] = 0.f;
+    }
   }
 #pragma unroll
   for (int j = 0; j < ADJ_KPT; ++j)
-    if (ok[j]) xh[(size_t)w * Nm + kb + 256 * j] = cf_make(facc_get(tr[j]), facc_get(ti[j]));
+    if (ok[j]) xh[(size_t)w * Nm + kb + 256 * j] = cf_make(tr[j], ti[j]);
 }
 
 // ------------------------------------------------------------ forward

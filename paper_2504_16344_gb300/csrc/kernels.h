@@ -85,7 +85,7 @@ cudaError_t launch_gemv_fwd_f(const void *A, int fmt, const cf *xh, cf *part, cf
 cudaError_t launch_gemv_adj_dd(const void *A, int fmt, const cdd *yh, cdd *xh, int Nf, int Nr,
                                int Nm, cudaStream_t s);
 // adjoint with an FP32 operator and float-pair data: FP32 block sums of 8
-// rows folded into compensated totals (the reduced-precision paths' F^T y)
+// rows added into FP32 totals (the reduced-precision paths' F^T y)
 cudaError_t launch_gemv_adj_fx(const void *A, int fmt, const cdd *yh, cf *xh, int Nf, int Nr,
                                int Nm, cudaStream_t s);
 
@@ -96,7 +96,7 @@ int gemm_fwd_nchunk(int Nm);
 cudaError_t launch_gemm_adj_dd(const void *A, const cdd *Y, long y_bstride, cdd *X, long x_bstride,
                                int Nf, int Nr, int Nm, int B, cudaStream_t s);
 // adjoint with an FP32 operator (fmt C64 / BF16X2) and float-pair data Y:
-// FP32 block sums of 8 rows folded into compensated totals, X in FP32
+// FP32 block sums of 8 rows added into FP32 totals, X in FP32
 cudaError_t launch_gemm_adj_fx(const void *A, int fmt, const cdd *Y, long y_bstride, cf *X,
                                long x_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s);
 cudaError_t launch_gemm_fwd_dd(const void *A, const cdd *X, long x_bstride, cdd *part, cdd *Yo,

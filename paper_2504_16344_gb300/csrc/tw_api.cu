@@ -415,8 +415,8 @@ tw_status tw_p2o_adjoint(tw_ctx *c, tw_map which, tw_prec prec, int nrhs, const 
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
         TW_CUDA(c, launch_irfft_time_dd(c->wf, Nm, xr, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s)); }
     } else {
-      // FP32 operator; the data-side spectrum in double-float and compensated
-      // block sums in the product (as the posterior mean's adjoint)
+      // FP32 operator; the data-side spectrum in double-float and FP32 block
+      // sums in the product (as the posterior mean's adjoint)
       cf *wf = (cf *)c->wf;
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
         TW_CUDA(c, launch_rfft_time_dd(yr, 0, R, Nt, c->wr, R, R, c->plT, c->twT, c->twL, s)); }

@@ -122,9 +122,9 @@ tw_status infer_core(tw_ctx *c, tw_prec prec, int B, const int *win, const doubl
         TW_CUDA(c, launch_gemm_adj_tc(c->op_tc, (const cf *)c->byh, (long)Nf * Nd, (cf *)c->bxh,
                                       (long)Nf * Nm, Nf, Nd, Nm, B, c->btc, c->d_err, s)); }
     } else {
-      // double-float data spectra and compensated block sums: F^T y cancels
-      // (y is large against m), so FP32 y or one FP32 running sum would lose
-      // accuracy well above the operator's own rounding
+      // double-float data spectra and FP32 block sums: F^T y cancels
+      // (y is large against m), so an FP32 data spectrum would lose accuracy
+      // well above the operator's own rounding
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
         TW_CUDA(c, launch_rfft_time_dd(c->byd, 1, Nd, Nt, (cdd *)c->byh, Nd, Nd, c->plT, c->twT, c->twL, s, ba_y)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);

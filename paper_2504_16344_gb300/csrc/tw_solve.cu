@@ -430,7 +430,7 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
     } else {
       // reduced-precision operator: y's spectrum stays double-float (y is large
       // against m, and F^T y cancels), the product sums FP32 blocks into
-      // compensated totals; x^ onwards (inverse FFT, prior) runs in FP32
+      // FP32 totals; x^ onwards (inverse FFT, prior) runs in FP32
       cf *wf = (cf *)c->wf;
       float *wt = (float *)c->wt;
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
