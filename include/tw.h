@@ -318,6 +318,11 @@ typedef enum {
   TW_PH_RFFT_PARAM,     /* time FFT of a parameter vector                      */
   TW_PH_GEMV_FWD,       /* y^(w) = F^(w) x^(w) incl. the chunk reduction       */
   TW_PH_IRFFT_DATA,     /* inverse time FFT of a data-space vector             */
+  TW_PH_FORM_K,         /* set-up: K = sigma^2 I + prefix sums of G G^T        */
+  TW_PH_CHOLESKY,       /* set-up: FP64 Cholesky of K and packing              */
+  TW_PH_CHOLESKY32,     /* set-up: FP32 factor and its refinement probe        */
+  TW_PH_SOLVE_SETUP,    /* set-up: chain blocks, block-scaled factor, tables   */
+  TW_PH_FORM_GSTAR,     /* set-up: G^ = F^ C per frequency (TW_KEEP_G)         */
   TW_PH_COUNT
 } tw_phase;
 

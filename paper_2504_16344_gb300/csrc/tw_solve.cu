@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
 
 #include "ctx.h"
 #include "dense_api.h"
@@ -71,6 +72,7 @@ tw_status solve32(tw_ctx *c, const void *b, int kind, int nrows, float *y, cudaS
 // After the FP64 factor (Lp64, inv64) is in place: the solves' chain blocks,
 // the single-vector solve's block-scaled factor and task table.
 tw_status finish_factor64(tw_ctx *c, cudaStream_t s) {
+  twh::Phase ph(c, TW_PH_SOLVE_SETUP, s);
   const size_t nblk = (size_t)c->NB * (c->NB + 1) / 2;
   const size_t blk = (size_t)NB_ * NB_;
   const size_t np = c->n_pad;
@@ -105,6 +107,7 @@ tw_status finish_factor64(tw_ctx *c, cudaStream_t s) {
 // FP64 storage, then converted to the other kept formats (TW_KEEP_G)
 tw_status form_gstar(tw_ctx *c, cudaStream_t s) {
   if (!(c->keep & TW_KEEP_G) || !c->op[TW_MAP_F][TW_PREC_FP64]) return TW_OK;
+  twh::Phase ph(c, TW_PH_FORM_GSTAR, s);
   const size_t per_w = (size_t)c->Nd * c->Nm;
   // FP64 and complex64 only: bf16 hi+lo storage of G^ rounds at 2^-18 and
   // that rounding reaches m unsmoothed (1.3e-5 .. 1.6e-5 measured); the
@@ -177,6 +180,8 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
   // column was loaded (tw_set_prior first); otherwise Phi is recovered from
   // the stored operator by the inverse time FFT (K then carries ~1e-14
   // relative error from the double-float operator and filter).
+  // K's formation is timed as one phase (a scope would not end at the packing)
+  std::unique_ptr<twh::Phase> ph(new twh::Phase(c, TW_PH_FORM_K, s));
   dd *G = c->G;
   if (!have_G) {
     if (!G) G = (dd *)twh::dalloc(c, (size_t)n * Nm * sizeof(dd));
@@ -210,8 +215,10 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
   if (!c->Kp64) c->Kp64 = (dd *)twh::dalloc(c, nblk * blk * sizeof(dd));
   if (!c->Kp64) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "packed K"); }
   TW_CUDA(c, launch_pack_d2dd(K, np, c->Kp64, c->NB, s));
+  ph.reset();
   // mixed path: FP32 factor
   if (want32) {
+    twh::Phase p32(c, TW_PH_CHOLESKY32, s);
     if (!c->Lp32) c->Lp32 = (float *)twh::dalloc(c, nblk * blk * sizeof(float));
     if (!c->inv32) c->inv32 = (float *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(float));
     float *K32 = (float *)twh::dalloc(c, (size_t)np * np * sizeof(float));
@@ -294,8 +301,11 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
     // The factorisation and the triangular solves run in native FP64: in
     // double-float the solves' cancellations amplify 2^-48 rounding by K's
     // conditioning (measured 10-30x the FP64 oracle's own error in y).
-    TW_CUDA(c, launch_cholesky_d(K, np, c->NB, c->inv64, c->d_err, s));
-    TW_CUDA(c, launch_pack_d(K, np, c->Lp64, c->NB, s));
+    {
+      twh::Phase pc(c, TW_PH_CHOLESKY, s);
+      TW_CUDA(c, launch_cholesky_d(K, np, c->NB, c->inv64, c->d_err, s));
+      TW_CUDA(c, launch_pack_d(K, np, c->Lp64, c->NB, s));
+    }
     TW_CUDA(c, cudaStreamSynchronize(s));
     twh::dfree(c, K);                   // the dense K is no longer needed
     K = nullptr;

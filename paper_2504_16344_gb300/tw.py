@@ -19,7 +19,8 @@ STATUS_NAMES = ["TW_OK", "TW_ERR_ARG", "TW_ERR_OOM", "TW_ERR_CUDA", "TW_ERR_STAT
                 "TW_ERR_NOT_SPD", "TW_ERR_NOT_CONVERGED", "TW_ERR_TIMEOUT"]
 # tw_phase
 PHASES = ["trsv_fwd", "trsv_bwd", "residual", "rfft_data", "gemv_adj", "irfft_param", "prior",
-          "rfft_param", "gemv_fwd", "irfft_data"]
+          "rfft_param", "gemv_fwd", "irfft_data", "form_K", "cholesky", "cholesky32", "solve_setup",
+          "form_gstar"]
 # tw_map
 MAP_F, MAP_FQ = 0, 1
 # tw_prec
