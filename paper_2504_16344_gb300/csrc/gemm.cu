@@ -53,16 +53,19 @@ template <> __device__ __forceinline__ cf ld_opf<FMT_BF16X2>(const void *A, size
 }
 
 // ------------------------------------------------------------ adjoint, df64
-// grid (ceil(Nm/128), Nf, ceil(B/32)); 8 warps x 4 right-hand sides each
+// grid (ceil(Nm/128), Nf, ceil(B/(8 RW))); 8 warps x RW right-hand sides each
+// (RW = 4, 2 or 1 after the batch size, so small batches leave no warp idle)
+template <int RW>
 __global__ void __launch_bounds__(256, 2)
 k_gemm_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ Y, long y_bstride,
               cdd *__restrict__ X, long x_bstride, int Nr, int Nm, int B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cdd *sy = reinterpret_cast<cdd *>(smem_raw);   // [32][Nr]
+  constexpr int CB = 8 * RW;                      // right-hand sides per CTA
+  cdd *sy = reinterpret_cast<cdd *>(smem_raw);   // [CB][Nr]
   const int w = blockIdx.y;
-  const int b0 = blockIdx.z * 32;
-  const int nb = min(32, B - b0);
-  for (int idx = threadIdx.x; idx < 32 * Nr; idx += blockDim.x) {
+  const int b0 = blockIdx.z * CB;
+  const int nb = min(CB, B - b0);
+  for (int idx = threadIdx.x; idx < CB * Nr; idx += blockDim.x) {
     const int bl = idx / Nr, sr = idx % Nr;
     sy[idx] = bl < nb ? ld_cdd(Y + (size_t)(b0 + bl) * y_bstride + (size_t)w * Nr + sr) : cdd_zero();
   }
@@ -70,18 +73,18 @@ k_gemm_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ Y, long y_bs
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int k0 = blockIdx.x * GA_K + lane;
   const float4 *Aw = A + (size_t)w * Nr * Nm;
-  dacc re[4][4], im[4][4];   // [rhs][point]
+  dacc re[RW][4], im[RW][4];   // [rhs][point]
   bool ok[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) ok[j] = k0 + 32 * j < Nm;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RW; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) { re[i][j] = dacc_zero(); im[i][j] = dacc_zero(); }
   float4 cur[4], nxt[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) cur[j] = ok[j] ? __ldg(Aw + k0 + 32 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
-  const cdd *syg = sy + (grp * 4) * Nr;
+  const cdd *syg = sy + (grp * RW) * Nr;
   for (int s = 0; s < Nr; ++s) {
     if (s + 1 < Nr) {
       const float4 *row = Aw + (size_t)(s + 1) * Nm + k0;
@@ -89,7 +92,7 @@ k_gemm_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ Y, long y_bs
       for (int j = 0; j < 4; ++j) nxt[j] = ok[j] ? __ldg(row + 32 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < RW; ++i) {
       const cdd y = syg[i * Nr + s];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -106,8 +109,8 @@ k_gemm_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ Y, long y_bs
     for (int j = 0; j < 4; ++j) cur[j] = nxt[j];
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int bl = grp * 4 + i;
+  for (int i = 0; i < RW; ++i) {
+    const int bl = grp * RW + i;
     if (bl >= nb) continue;
     cdd *xo = X + (size_t)(b0 + bl) * x_bstride + (size_t)w * Nm;
 #pragma unroll
@@ -122,23 +125,25 @@ k_gemm_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ Y, long y_bs
 }
 
 // ----------------------------------------- adjoint, FP32 operator, pair data
-// grid (ceil(Nm/128), Nf, ceil(B/32)); 8 warps x 4 right-hand sides each, a
-// thread 4 right-hand sides x 4 grid points.  Y entries are float pairs;
+// grid (ceil(Nm/128), Nf, ceil(B/(8 RW))); 8 warps x RW right-hand sides
+// each (RW = 4, 2 or 1 after the batch size), a thread RW right-hand sides x
+// 4 grid points.  Y entries are float pairs;
 // both parts enter FP32 block sums of GX_BLK rows (FMA) that are added to
 // FP32 totals: with the data spectrum in double-float the cancellation in
 // F^T y no longer amplifies an FP32 rounding of y.
 constexpr int GX_BLK = 8;
 
-template <int FMT>
+template <int FMT, int RW>
 __global__ void __launch_bounds__(256, 2)
 k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstride,
               cf *__restrict__ X, long x_bstride, int Nr, int Nm, int B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cdd *sy = reinterpret_cast<cdd *>(smem_raw);   // [32][Nr]
+  constexpr int CB = 8 * RW;                      // right-hand sides per CTA
+  cdd *sy = reinterpret_cast<cdd *>(smem_raw);   // [CB][Nr]
   const int w = blockIdx.y;
-  const int b0 = blockIdx.z * 32;
-  const int nb = min(32, B - b0);
-  for (int idx = threadIdx.x; idx < 32 * Nr; idx += blockDim.x) {
+  const int b0 = blockIdx.z * CB;
+  const int nb = min(CB, B - b0);
+  for (int idx = threadIdx.x; idx < CB * Nr; idx += blockDim.x) {
     const int bl = idx / Nr, sr = idx % Nr;
     sy[idx] = bl < nb ? ld_cdd(Y + (size_t)(b0 + bl) * y_bstride + (size_t)w * Nr + sr) : cdd_zero();
   }
@@ -146,13 +151,13 @@ k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstr
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int k0 = blockIdx.x * GA_K + lane;
   const size_t base = (size_t)w * Nr * Nm;
-  float br[4][4], bi[4][4];   // [rhs][point] block sums
-  float tr[4][4], ti[4][4];   // totals
+  float br[RW][4], bi[RW][4];   // [rhs][point] block sums
+  float tr[RW][4], ti[RW][4];   // totals
   bool ok[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) ok[j] = k0 + 32 * j < Nm;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RW; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       br[i][j] = 0.f; bi[i][j] = 0.f; tr[i][j] = 0.f; ti[i][j] = 0.f;
@@ -160,7 +165,7 @@ k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstr
   cf cur[4], nxt[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) cur[j] = ok[j] ? ld_opf<FMT>(A, base + k0 + 32 * j) : cf_zero();
-  const cdd *syg = sy + (grp * 4) * Nr;
+  const cdd *syg = sy + (grp * RW) * Nr;
   for (int s0 = 0; s0 < Nr; s0 += GX_BLK) {
     const int s1 = min(Nr, s0 + GX_BLK);
     for (int s = s0; s < s1; ++s) {
@@ -170,7 +175,7 @@ k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstr
         for (int j = 0; j < 4; ++j) nxt[j] = ok[j] ? ld_opf<FMT>(A, row + 32 * j) : cf_zero();
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < RW; ++i) {
         const cdd y = syg[i * Nr + s];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -189,7 +194,7 @@ k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstr
       for (int j = 0; j < 4; ++j) cur[j] = nxt[j];
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RW; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         tr[i][j] += br[i][j]; ti[i][j] += bi[i][j];
@@ -197,8 +202,8 @@ k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstr
       }
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int bl = grp * 4 + i;
+  for (int i = 0; i < RW; ++i) {
+    const int bl = grp * RW + i;
     if (bl >= nb) continue;
     cf *xo = X + (size_t)(b0 + bl) * x_bstride + (size_t)w * Nm;
 #pragma unroll
@@ -230,6 +235,13 @@ template <> struct FwdT<cdd> {
     cdd r; r.re = dacc_get(re); r.im = dacc_get(im); return r;
   }
   static __device__ __forceinline__ cdd zx() { return cdd_zero(); }
+  // add the partner lane's partial sum (lane ^ m)
+  static __device__ __forceinline__ void combine(acc &a, int m) {
+    dd o;
+    o.hi = __shfl_xor_sync(0xffffffffu, a.s, m);
+    o.lo = __shfl_xor_sync(0xffffffffu, a.t, m);
+    dacc_add(a, o);
+  }
 };
 template <> struct FwdT<cf> {
   typedef float acc;
@@ -240,6 +252,9 @@ template <> struct FwdT<cf> {
   }
   static __device__ __forceinline__ cf get(const acc &re, const acc &im) { return cf_make(re, im); }
   static __device__ __forceinline__ cf zx() { return cf_zero(); }
+  static __device__ __forceinline__ void combine(acc &a, int m) {
+    a += __shfl_xor_sync(0xffffffffu, a, m);
+  }
 };
 
 // operator entry (complex) from the stored formats
@@ -249,18 +264,25 @@ __device__ __forceinline__ cdd ld_op(const cdd *, const void *A, size_t i) {
 template <int FMT>
 __device__ __forceinline__ cf ld_op_fmt(const void *A, size_t i) { return ld_opf<FMT>(A, i); }
 
-template <class CX, int RPW, int GK, int FMT>
+// LPB lanes per right-hand side: 1 (32 right-hand sides per CTA) or 2 (16;
+// the two lanes of a right-hand side take alternate k and add their sums
+// at the end), so batches of up to 16 leave no lane idle.  The caller fixes
+// LPB per context (from the reserved batch), so a right-hand side's sum
+// order never depends on what shares its batch.
+template <class CX, int RPW, int GK, int FMT, int LPB>
 __global__ void __launch_bounds__(256, 2)
 k_gemm_fwd(const void *__restrict__ A, const CX *__restrict__ X, long x_bstride,
            CX *__restrict__ part, int nchunk, int Nr, int Nm, int B) {
   typedef FwdT<CX> T;
+  constexpr int CB = 32 / LPB;                        // right-hand sides per CTA
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CX *sx = reinterpret_cast<CX *>(smem_raw);          // [32][GK + 1]
-  CX *sa = sx + 32 * (GK + 1);                        // [Nr][GK]
+  CX *sx = reinterpret_cast<CX *>(smem_raw);          // [CB][GK + 1]
+  CX *sa = sx + CB * (GK + 1);                        // [Nr][GK]
   const int w = blockIdx.y, chunk = blockIdx.x;
-  const int b0 = blockIdx.z * 32;
-  const int nb = min(32, B - b0);
+  const int b0 = blockIdx.z * CB;
+  const int nb = min(CB, B - b0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int bl_l = lane % CB, half = lane / CB;       // right-hand side, k phase
   const int kbeg = chunk * GF_K * GF_TILES;
   const int kend = min(Nm, kbeg + GF_K * GF_TILES);
   const size_t base = (size_t)w * Nr * Nm;
@@ -274,7 +296,7 @@ k_gemm_fwd(const void *__restrict__ A, const CX *__restrict__ X, long x_bstride,
     for (int kt = kbeg; kt < kend; kt += GK) {
       const int nk = min(GK, kend - kt);
       __syncthreads();   // previous tile consumed
-      for (int idx = threadIdx.x; idx < 32 * GK; idx += blockDim.x) {
+      for (int idx = threadIdx.x; idx < CB * GK; idx += blockDim.x) {
         const int bl = idx / GK, kk = idx % GK;
         sx[bl * (GK + 1) + kk] = (bl < nb && kk < nk)
             ? X[(size_t)(b0 + bl) * x_bstride + (size_t)w * Nm + kt + kk] : T::zx();
@@ -290,7 +312,7 @@ k_gemm_fwd(const void *__restrict__ A, const CX *__restrict__ X, long x_bstride,
         sa[rl * GK + kk] = v;
       }
       __syncthreads();
-      const CX *xs = sx + lane * (GK + 1);
+      const CX *xs = sx + bl_l * (GK + 1);
       if constexpr (std::is_same<CX, cf>::value) {
         // FP32: a fresh sum per tile, added to the running total, so rounding
         // grows with GK + the tile count rather than the chunk length
@@ -298,7 +320,7 @@ k_gemm_fwd(const void *__restrict__ A, const CX *__restrict__ X, long x_bstride,
 #pragma unroll
         for (int i = 0; i < RPW; ++i) { tre[i] = 0.f; tim[i] = 0.f; }
 #pragma unroll 4
-        for (int kk = 0; kk < nk; ++kk) {
+        for (int kk = half; kk < nk; kk += LPB) {
           const CX x = xs[kk];
 #pragma unroll
           for (int i = 0; i < RPW; ++i) {
@@ -310,7 +332,7 @@ k_gemm_fwd(const void *__restrict__ A, const CX *__restrict__ X, long x_bstride,
         for (int i = 0; i < RPW; ++i) { re[i] += tre[i]; im[i] += tim[i]; }
       } else {
 #pragma unroll 4
-        for (int kk = 0; kk < nk; ++kk) {
+        for (int kk = half; kk < nk; kk += LPB) {
           const CX x = xs[kk];
 #pragma unroll
           for (int i = 0; i < RPW; ++i) {
@@ -320,12 +342,16 @@ k_gemm_fwd(const void *__restrict__ A, const CX *__restrict__ X, long x_bstride,
         }
       }
     }
-    if (lane < nb) {
+    if (LPB == 2) {
+#pragma unroll
+      for (int i = 0; i < RPW; ++i) { T::combine(re[i], 16); T::combine(im[i], 16); }
+    }
+    if (half == 0 && bl_l < nb) {
 #pragma unroll
       for (int i = 0; i < RPW; ++i) {
         const int rl = warp * RPW + i;
         if (rl >= nrp) continue;
-        part[(((size_t)(b0 + lane) * gridDim.y + w) * nchunk + chunk) * Nr + r0 + rl] = T::get(re[i], im[i]);
+        part[(((size_t)(b0 + bl_l) * gridDim.y + w) * nchunk + chunk) * Nr + r0 + rl] = T::get(re[i], im[i]);
       }
     }
   }
@@ -368,55 +394,93 @@ void ensure_smem_g(KER k, size_t bytes) {
 
 int gemm_fwd_nchunk(int Nm) { return (Nm + GF_K * GF_TILES - 1) / (GF_K * GF_TILES); }
 
+// right-hand sides per warp of the adjoint products: 4 (32 per CTA) for
+// large batches, fewer for small ones so that no warp computes empty columns
+static int adj_rw(int B) { return B > 16 ? 4 : (B > 8 ? 2 : 1); }
+
+template <int RW>
+static void adj_dd_run(const void *A, const cdd *Y, long y_bstride, cdd *X, long x_bstride, int Nf,
+                       int Nr, int Nm, int B, cudaStream_t s) {
+  const size_t sm = (size_t)8 * RW * Nr * sizeof(cdd);
+  ensure_smem_g(k_gemm_adj_dd<RW>, sm);
+  dim3 grid((Nm + GA_K - 1) / GA_K, Nf, (B + 8 * RW - 1) / (8 * RW));
+  k_gemm_adj_dd<RW><<<grid, 256, sm, s>>>(reinterpret_cast<const float4 *>(A), Y, y_bstride, X,
+                                          x_bstride, Nr, Nm, B);
+}
+
 cudaError_t launch_gemm_adj_dd(const void *A, const cdd *Y, long y_bstride, cdd *X, long x_bstride,
                                int Nf, int Nr, int Nm, int B, cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  const size_t sm = (size_t)32 * Nr * sizeof(cdd);
-  ensure_smem_g(k_gemm_adj_dd, sm);
-  dim3 grid((Nm + GA_K - 1) / GA_K, Nf, (B + 31) / 32);
-  k_gemm_adj_dd<<<grid, 256, sm, s>>>(reinterpret_cast<const float4 *>(A), Y, y_bstride, X,
-                                      x_bstride, Nr, Nm, B);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gemm_adj_fx(const void *A, int fmt, const cdd *Y, long y_bstride, cf *X,
-                               long x_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s) {
-  if (B <= 0) return cudaSuccess;
-  const size_t sm = (size_t)32 * Nr * sizeof(cdd);
-  dim3 grid((Nm + GA_K - 1) / GA_K, Nf, (B + 31) / 32);
-  if (fmt == FMT_C64) {
-    ensure_smem_g(k_gemm_adj_fx<FMT_C64>, sm);
-    k_gemm_adj_fx<FMT_C64><<<grid, 256, sm, s>>>(A, Y, y_bstride, X, x_bstride, Nr, Nm, B);
-  } else if (fmt == FMT_BF16X2) {
-    ensure_smem_g(k_gemm_adj_fx<FMT_BF16X2>, sm);
-    k_gemm_adj_fx<FMT_BF16X2><<<grid, 256, sm, s>>>(A, Y, y_bstride, X, x_bstride, Nr, Nm, B);
-  } else {
-    return cudaErrorInvalidValue;
+  switch (adj_rw(B)) {
+    case 4: adj_dd_run<4>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;
+    case 2: adj_dd_run<2>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;
+    default: adj_dd_run<1>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;
   }
   count_launches(1);
   return cudaGetLastError();
 }
 
-// rows per warp: one pass covers up to 8*RPW rows
-template <class CX, int RPW, int GK, int FMT>
-static cudaError_t gemm_fwd_run(const void *A, const CX *X, long x_bstride, CX *part, int Nf, int Nr,
-                                int Nm, int B, cudaStream_t s) {
-  const int nchunk = gemm_fwd_nchunk(Nm);
-  const int rows = std::min(Nr, 8 * RPW);
-  const size_t sm = (size_t)(32 * (GK + 1) + rows * GK) * sizeof(CX);
-  ensure_smem_g(k_gemm_fwd<CX, RPW, GK, FMT>, sm);
-  dim3 grid(nchunk, Nf, (B + 31) / 32);
-  k_gemm_fwd<CX, RPW, GK, FMT><<<grid, 256, sm, s>>>(A, X, x_bstride, part, nchunk, Nr, Nm, B);
+template <int FMT, int RW>
+static void adj_fx_run(const void *A, const cdd *Y, long y_bstride, cf *X, long x_bstride, int Nf,
+                       int Nr, int Nm, int B, cudaStream_t s) {
+  const size_t sm = (size_t)8 * RW * Nr * sizeof(cdd);
+  ensure_smem_g(k_gemm_adj_fx<FMT, RW>, sm);
+  dim3 grid((Nm + GA_K - 1) / GA_K, Nf, (B + 8 * RW - 1) / (8 * RW));
+  k_gemm_adj_fx<FMT, RW><<<grid, 256, sm, s>>>(A, Y, y_bstride, X, x_bstride, Nr, Nm, B);
+}
+
+template <int FMT>
+static void adj_fx_pick(const void *A, const cdd *Y, long y_bstride, cf *X, long x_bstride, int Nf,
+                        int Nr, int Nm, int B, cudaStream_t s) {
+  switch (adj_rw(B)) {
+    case 4: adj_fx_run<FMT, 4>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;
+    case 2: adj_fx_run<FMT, 2>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;
+    default: adj_fx_run<FMT, 1>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;
+  }
+}
+
+cudaError_t launch_gemm_adj_fx(const void *A, int fmt, const cdd *Y, long y_bstride, cf *X,
+                               long x_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  if (fmt == FMT_C64)
+    adj_fx_pick<FMT_C64>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s);
+  else if (fmt == FMT_BF16X2)
+    adj_fx_pick<FMT_BF16X2>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s);
+  else
+    return cudaErrorInvalidValue;
   count_launches(1);
   return cudaGetLastError();
 }
 
+// rows per warp: one pass covers up to 8*RPW rows
+template <class CX, int RPW, int GK, int FMT, int LPB>
+static cudaError_t gemm_fwd_run(const void *A, const CX *X, long x_bstride, CX *part, int Nf, int Nr,
+                                int Nm, int B, cudaStream_t s) {
+  const int nchunk = gemm_fwd_nchunk(Nm);
+  const int rows = std::min(Nr, 8 * RPW);
+  const size_t sm = (size_t)((32 / LPB) * (GK + 1) + rows * GK) * sizeof(CX);
+  ensure_smem_g(k_gemm_fwd<CX, RPW, GK, FMT, LPB>, sm);
+  dim3 grid(nchunk, Nf, (B + 32 / LPB - 1) / (32 / LPB));
+  k_gemm_fwd<CX, RPW, GK, FMT, LPB><<<grid, 256, sm, s>>>(A, X, x_bstride, part, nchunk, Nr, Nm, B);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <class CX, int GK, int FMT>
+static cudaError_t gemm_fwd_pick(const void *A, const CX *X, long x_bstride, CX *part, int Nf, int Nr,
+                                 int Nm, int B, int lpb, cudaStream_t s) {
+  if (lpb == 2)
+    return Nr <= 24 ? gemm_fwd_run<CX, 3, GK, FMT, 2>(A, X, x_bstride, part, Nf, Nr, Nm, B, s)
+                    : gemm_fwd_run<CX, 13, GK, FMT, 2>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+  return Nr <= 24 ? gemm_fwd_run<CX, 3, GK, FMT, 1>(A, X, x_bstride, part, Nf, Nr, Nm, B, s)
+                  : gemm_fwd_run<CX, 13, GK, FMT, 1>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+}
+
 cudaError_t launch_gemm_fwd_dd(const void *A, const cdd *X, long x_bstride, cdd *part, cdd *Yo,
-                               long y_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s) {
+                               long y_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s,
+                               int lpb) {
   if (B <= 0) return cudaSuccess;
-  cudaError_t e = Nr <= 24 ? gemm_fwd_run<cdd, 3, 32, FMT_DD>(A, X, x_bstride, part, Nf, Nr, Nm, B, s)
-                           : gemm_fwd_run<cdd, 13, 32, FMT_DD>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+  cudaError_t e = gemm_fwd_pick<cdd, 32, FMT_DD>(A, X, x_bstride, part, Nf, Nr, Nm, B, lpb, s);
   if (e != cudaSuccess) return e;
   const int nchunk = gemm_fwd_nchunk(Nm);
   const long total = (long)B * Nf * Nr;
@@ -428,15 +492,13 @@ cudaError_t launch_gemm_fwd_dd(const void *A, const cdd *X, long x_bstride, cdd 
 
 cudaError_t launch_gemm_fwd_f(const void *A, int fmt, const cf *X, long x_bstride, cf *part,
                               cf *Yo, long y_bstride, int Nf, int Nr, int Nm, int B,
-                              cudaStream_t s) {
+                              cudaStream_t s, int lpb) {
   if (B <= 0) return cudaSuccess;
   cudaError_t e;
   if (fmt == FMT_C64)
-    e = Nr <= 24 ? gemm_fwd_run<cf, 3, 64, FMT_C64>(A, X, x_bstride, part, Nf, Nr, Nm, B, s)
-                 : gemm_fwd_run<cf, 13, 64, FMT_C64>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+    e = gemm_fwd_pick<cf, 64, FMT_C64>(A, X, x_bstride, part, Nf, Nr, Nm, B, lpb, s);
   else
-    e = Nr <= 24 ? gemm_fwd_run<cf, 3, 64, FMT_BF16X2>(A, X, x_bstride, part, Nf, Nr, Nm, B, s)
-                 : gemm_fwd_run<cf, 13, 64, FMT_BF16X2>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+    e = gemm_fwd_pick<cf, 64, FMT_BF16X2>(A, X, x_bstride, part, Nf, Nr, Nm, B, lpb, s);
   if (e != cudaSuccess) return e;
   const int nchunk = gemm_fwd_nchunk(Nm);
   const long total = (long)B * Nf * Nr;

@@ -99,11 +99,13 @@ cudaError_t launch_gemm_adj_dd(const void *A, const cdd *Y, long y_bstride, cdd 
 // FP32 block sums of 8 rows added into FP32 totals, X in FP32
 cudaError_t launch_gemm_adj_fx(const void *A, int fmt, const cdd *Y, long y_bstride, cf *X,
                                long x_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s);
+// lpb: lanes per right-hand side in the forward product (1 or 2, fixed per
+// context so that a right-hand side's sum order does not depend on its batch)
 cudaError_t launch_gemm_fwd_dd(const void *A, const cdd *X, long x_bstride, cdd *part, cdd *Yo,
-                               long y_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s);
+                               long y_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s, int lpb = 1);
 cudaError_t launch_gemm_fwd_f(const void *A, int fmt, const cf *X, long x_bstride, cf *part,
                               cf *Yo, long y_bstride, int Nf, int Nr, int Nm, int B,
-                              cudaStream_t s);
+                              cudaStream_t s, int lpb = 1);
 
 // ---- tensor-core adjoint product (gemm_tc.cu), bf16 hi/lo operator --------
 int gemm_tc_nka(int Nr);

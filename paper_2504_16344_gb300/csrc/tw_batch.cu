@@ -38,6 +38,10 @@ tw_status upload_windows(tw_ctx *c, const int *nt_window, int nrhs, cudaStream_t
   return TW_OK;
 }
 
+// lanes per right-hand side of the batched forward product: 2 when at most 16
+// right-hand sides are reserved (no idle lanes), else 1; fixed per reservation
+int fwd_lpb(const tw_ctx *c) { return c->bmax <= 16 ? 2 : 1; }
+
 tw_status check_batch(tw_ctx *c, tw_prec prec, int nrhs, const int *win) {
   if (prec < 0 || prec > 2 || !c->op[TW_MAP_F][prec])
     return twh::fail(c, TW_ERR_ARG, "requested precision was not kept at tw_create");
@@ -61,7 +65,7 @@ tw_status forecast_core(tw_ctx *c, tw_prec prec, int B, const int *win, const do
       TW_CUDA(c, launch_rfft_time_dd(m, 0, Nm, Nt, (cdd *)c->bxh, Nm, Nm, c->plT, c->twT, c->twL, s, ba_m)); }
     { twh::Phase p(c, TW_PH_GEMV_FWD, s);
       TW_CUDA(c, launch_gemm_fwd_dd(Aq, (const cdd *)c->bxh, (long)Nf * Nm, (cdd *)c->bpart,
-                                    (cdd *)c->byh, (long)Nf * Nq, Nf, Nq, Nm, B, s)); }
+                                    (cdd *)c->byh, (long)Nf * Nq, Nf, Nq, Nm, B, s, fwd_lpb(c))); }
     { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
       TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->byh, Nq, q, 0, Nq, Nq, Nt, c->plT, c->twT, c->twL, s, ba_q)); }
   } else {
@@ -69,7 +73,7 @@ tw_status forecast_core(tw_ctx *c, tw_prec prec, int B, const int *win, const do
       TW_CUDA(c, launch_rfft_time_f(m, 0, Nm, Nt, (cf *)c->bxh, Nm, Nm, c->plT, c->twTf, c->twLf, s, ba_m)); }
     { twh::Phase p(c, TW_PH_GEMV_FWD, s);
       TW_CUDA(c, launch_gemm_fwd_f(Aq, (int)prec, (const cf *)c->bxh, (long)Nf * Nm, (cf *)c->bpart,
-                                   (cf *)c->byh, (long)Nf * Nq, Nf, Nq, Nm, B, s)); }
+                                   (cf *)c->byh, (long)Nf * Nq, Nf, Nq, Nm, B, s, fwd_lpb(c))); }
     { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
       TW_CUDA(c, launch_irfft_time_f((const cf *)c->byh, Nq, q, 0, Nq, Nq, Nt, c->plT, c->twTf, c->twLf, s, ba_q)); }
   }
@@ -165,7 +169,7 @@ tw_status sample_core(tw_ctx *c, tw_prec prec, int B, const int *win, const doub
       TW_CUDA(c, launch_rfft_time_dd(samples, 0, Nm, Nt, (cdd *)c->bxh, Nm, Nm, c->plT, c->twT, c->twL, s, ba_m)); }
     { twh::Phase p(c, TW_PH_GEMV_FWD, s);
       TW_CUDA(c, launch_gemm_fwd_dd(A, (const cdd *)c->bxh, (long)Nf * Nm, (cdd *)c->bpart, (cdd *)c->byh,
-                                    (long)Nf * Nd, Nf, Nd, Nm, B, s)); }
+                                    (long)Nf * Nd, Nf, Nd, Nm, B, s, fwd_lpb(c))); }
     { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
       TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->byh, Nd, c->brd, 0, Nd, Nd, Nt, c->plT, c->twT, c->twL, s, ba_d)); }
   } else {
@@ -173,7 +177,7 @@ tw_status sample_core(tw_ctx *c, tw_prec prec, int B, const int *win, const doub
       TW_CUDA(c, launch_rfft_time_f(samples, 0, Nm, Nt, (cf *)c->bxh, Nm, Nm, c->plT, c->twTf, c->twLf, s, ba_m)); }
     { twh::Phase p(c, TW_PH_GEMV_FWD, s);
       TW_CUDA(c, launch_gemm_fwd_f(A, (int)prec, (const cf *)c->bxh, (long)Nf * Nm, (cf *)c->bpart,
-                                   (cf *)c->byh, (long)Nf * Nd, Nf, Nd, Nm, B, s)); }
+                                   (cf *)c->byh, (long)Nf * Nd, Nf, Nd, Nm, B, s, fwd_lpb(c))); }
     { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
       TW_CUDA(c, launch_irfft_time_f((const cf *)c->byh, Nd, c->brd, 0, Nd, Nd, Nt, c->plT, c->twTf, c->twLf, s, ba_d)); }
   }

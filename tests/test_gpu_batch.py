@@ -302,3 +302,31 @@ def test_captured_graph_replays_with_new_data(case):
     assert torch.equal(m_g, m_u) and torch.equal(q_g, q_u)
     for i, e in enumerate(sel):
         assert rel(m_g[i].cpu().numpy(), case["m_ref"][e]) < 1e-11
+
+
+def test_large_reservation(case):
+    """40 right-hand sides reserved: the adjoint products take 32 per CTA (two
+    slices, one ragged) and the forward product one lane per right-hand side;
+    every column must still match the oracle."""
+    import torch
+    from paper_2504_16344_gb300 import tw
+    ctx, cfg, ws = case["ctx"], case["cfg"], case["ws"]
+    n = 40
+    idx = [r % NEV for r in range(n)]
+    ctx.reserve_batch(n)
+    try:
+        d = _t(case["d"][idx], case["dev"])
+        win = torch.tensor([ws[e] for e in idx], dtype=torch.int32, device=case["dev"])
+        for prec in ("FP64", "C64"):
+            m, q = ctx.infer_batch(getattr(tw, "PREC_" + prec), d, win)
+            ctx.check()
+            m, q = m.cpu().numpy(), q.cpu().numpy()
+            em = max(rel(m[r], case["m_ref"][e]) for r, e in enumerate(idx))
+            eq = max(rel(q[r], case["q_ref"][e]) for r, e in enumerate(idx))
+            print(f"{cfg.cid}: 40 reserved, {prec} m {em:.2e} q {eq:.2e}")
+            if prec == "FP64":
+                assert em < 1e-11 and eq < 1e-11
+            else:
+                assert em < max(1e-5, 2.0 * case["floor"]["C64"]) and eq < 1e-4
+    finally:
+        ctx.reserve_batch(BMAX)
