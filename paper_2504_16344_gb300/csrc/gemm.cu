@@ -469,11 +469,16 @@ static cudaError_t gemm_fwd_run(const void *A, const CX *X, long x_bstride, CX *
 template <class CX, int GK, int FMT>
 static cudaError_t gemm_fwd_pick(const void *A, const CX *X, long x_bstride, CX *part, int Nf, int Nr,
                                  int Nm, int B, int lpb, cudaStream_t s) {
-  if (lpb == 2)
-    return Nr <= 24 ? gemm_fwd_run<CX, 3, GK, FMT, 2>(A, X, x_bstride, part, Nf, Nr, Nm, B, s)
-                    : gemm_fwd_run<CX, 13, GK, FMT, 2>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
-  return Nr <= 24 ? gemm_fwd_run<CX, 3, GK, FMT, 1>(A, X, x_bstride, part, Nf, Nr, Nm, B, s)
-                  : gemm_fwd_run<CX, 13, GK, FMT, 1>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+  // rows per warp: the smallest of 3, 7, 13 that spreads Nr rows over the 8
+  // warps in one pass (13 and several passes beyond 104 rows)
+  if (lpb == 2) {
+    if (Nr <= 24) return gemm_fwd_run<CX, 3, GK, FMT, 2>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+    if (Nr <= 56) return gemm_fwd_run<CX, 7, GK, FMT, 2>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+    return gemm_fwd_run<CX, 13, GK, FMT, 2>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+  }
+  if (Nr <= 24) return gemm_fwd_run<CX, 3, GK, FMT, 1>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+  if (Nr <= 56) return gemm_fwd_run<CX, 7, GK, FMT, 1>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
+  return gemm_fwd_run<CX, 13, GK, FMT, 1>(A, X, x_bstride, part, Nf, Nr, Nm, B, s);
 }
 
 cudaError_t launch_gemm_fwd_dd(const void *A, const cdd *X, long x_bstride, cdd *part, cdd *Yo,
