@@ -162,21 +162,17 @@ k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstr
     for (int j = 0; j < 4; ++j) {
       br[i][j] = 0.f; bi[i][j] = 0.f; tr[i][j] = 0.f; ti[i][j] = 0.f;
     }
-  // operator rows s+1 and s+2 in flight while row s is used
-  cf cur[4], nx1[4], nx2[4];
+  cf cur[4], nxt[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    cur[j] = ok[j] ? ld_opf<FMT>(A, base + k0 + 32 * j) : cf_zero();
-    nx1[j] = (ok[j] && Nr > 1) ? ld_opf<FMT>(A, base + (size_t)Nm + k0 + 32 * j) : cf_zero();
-  }
+  for (int j = 0; j < 4; ++j) cur[j] = ok[j] ? ld_opf<FMT>(A, base + k0 + 32 * j) : cf_zero();
   const cdd *syg = sy + (grp * RW) * Nr;
   for (int s0 = 0; s0 < Nr; s0 += GX_BLK) {
     const int s1 = min(Nr, s0 + GX_BLK);
     for (int s = s0; s < s1; ++s) {
-      if (s + 2 < Nr) {
-        const size_t row = base + (size_t)(s + 2) * Nm + k0;
+      if (s + 1 < Nr) {
+        const size_t row = base + (size_t)(s + 1) * Nm + k0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) nx2[j] = ok[j] ? ld_opf<FMT>(A, row + 32 * j) : cf_zero();
+        for (int j = 0; j < 4; ++j) nxt[j] = ok[j] ? ld_opf<FMT>(A, row + 32 * j) : cf_zero();
       }
 #pragma unroll
       for (int i = 0; i < RW; ++i) {
@@ -195,7 +191,7 @@ k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstr
         }
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) { cur[j] = nx1[j]; nx1[j] = nx2[j]; }
+      for (int j = 0; j < 4; ++j) cur[j] = nxt[j];
     }
 #pragma unroll
     for (int i = 0; i < RW; ++i)
