@@ -6,7 +6,7 @@ tests and the benchmark use oracle-made data without a full CPU apply.
 
 Calls only `oracle/` (and the seeded input generator `synth`).  The paper adds
 1% relative noise to its synthetic observations (Sec. "Application to the
-Cascadia subduction zone"); this build reads it as one global level,
+Cascadia subduction zone"), read here as one global level,
 sigma = 0.01 * rms(F m_true) over all Nd*Nt entries of event 0 with
 m_true = Gamma_pr^{1/2} z.  Both the GPU tests and the benchmark take sigma
 from these files, so K = sigma^2 I + F Gamma_pr F^T is the same on both sides.
