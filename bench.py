@@ -16,7 +16,9 @@ with the FP64 factor, or FP32 factor + FP64 refinement) is reported beside it
 with its error against the FP64 path, followed by the batched workload (64
 events with uneven windows + 32 posterior samples, one CUDA graph per
 precision), the serving replay (continuous batching of a Poisson request
-trace) and, with --qoi, the Phase 3 data-to-QoI map and q = Q d.
+trace) and, with --qoi, the Phase 3 data-to-QoI map and q = Q d.  --scale runs the
+serving-at-scale workload instead (200 sensors, 316x316 grid, 420 steps, 50 forecast points:
+complex64 and FP64 contexts in sequence, the second loading the first one's factor).
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle
 instead (bounded samples of the same step, extrapolated to a full step).
