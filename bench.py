@@ -61,7 +61,8 @@ def parse():
                    help="also time the Phase 3 QoI build (about two minutes) and q = Q d")
     p.add_argument("--scale", action="store_true",
                    help="serving at scale instead: 200 sensors, 316x316 grid, 420 steps, 50 "
-                        "forecast points, mixed and FP64 paths in sequence (about 15 minutes)")
+                        "forecast points, mixed and FP64 paths in sequence (about 10 minutes, most "
+                        "of it forming K)")
     p.add_argument("--requests", type=int, default=1000,
                    help="requests of the serving trace (Poisson 200/s)")
     return p.parse_args()
