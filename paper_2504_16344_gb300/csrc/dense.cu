@@ -751,11 +751,6 @@ __global__ void k_axpy_dd_f(dd *__restrict__ x, const float *__restrict__ delta,
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) { dd d; d.hi = delta[i]; d.lo = 0.f; x[i] = dd_add(x[i], d); }
 }
-// dd -> float copy
-__global__ void k_dd_to_f(const dd *__restrict__ a, float *__restrict__ b, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = __fadd_rn(a[i].hi, a[i].lo);
-}
 // float -> dd copy
 __global__ void k_f_to_dd(const float *__restrict__ a, dd *__restrict__ b, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -849,11 +844,6 @@ cudaError_t launch_double_to_dd(const double *a, dd *b, size_t n, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_dd(const dd *K, long ldk, dd *P, int NB, cudaStream_t s) {
-  k_pack<dd><<<152 * 8, 256, 0, s>>>(K, ldk, P, NB);
-  count_launches(1);
-  return cudaGetLastError();
-}
 cudaError_t launch_pack_f(const float *K, long ldk, float *P, int NB, cudaStream_t s) {
   k_pack<float><<<152 * 8, 256, 0, s>>>(K, ldk, P, NB);
   count_launches(1);
@@ -931,11 +921,6 @@ cudaError_t launch_add_dd(double *sv, const dd *x, long n, cudaStream_t s) {
 }
 cudaError_t launch_axpy_dd_f(dd *x, const float *delta, int n, cudaStream_t s) {
   k_axpy_dd_f<<<(n + 255) / 256, 256, 0, s>>>(x, delta, n);
-  count_launches(1);
-  return cudaGetLastError();
-}
-cudaError_t launch_dd_to_f(const dd *a, float *b, int n, cudaStream_t s) {
-  k_dd_to_f<<<(n + 255) / 256, 256, 0, s>>>(a, b, n);
   count_launches(1);
   return cudaGetLastError();
 }

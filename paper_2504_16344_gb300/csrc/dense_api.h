@@ -20,7 +20,6 @@ cudaError_t launch_cholesky_d(double *K, long ldk, int NB, double *inv, int *err
 cudaError_t launch_pack_d(const double *K, long ldk, double *P, int NB, cudaStream_t s);
 cudaError_t launch_pack_d2dd(const double *K, long ldk, dd *P, int NB, cudaStream_t s);
 cudaError_t launch_double_to_dd(const double *a, dd *b, size_t n, cudaStream_t s);
-cudaError_t launch_pack_dd(const dd *K, long ldk, dd *P, int NB, cudaStream_t s);
 cudaError_t launch_pack_f(const float *K, long ldk, float *P, int NB, cudaStream_t s);
 cudaError_t launch_lower_to_float(const double *K, float *K32, long ld, int NB, cudaStream_t s);
 
@@ -77,7 +76,6 @@ cudaError_t launch_sample_rhs(const double *d, const double *a, const double *z,
                               double *r, int n, cudaStream_t s);
 cudaError_t launch_add_dd(double *sv, const dd *x, long n, cudaStream_t s);
 cudaError_t launch_axpy_dd_f(dd *x, const float *delta, int n, cudaStream_t s);
-cudaError_t launch_dd_to_f(const dd *a, float *b, int n, cudaStream_t s);
 cudaError_t launch_f_to_dd(const float *a, dd *b, int n, cudaStream_t s);
 cudaError_t launch_sumsq(const void *v, int kind, int n, double *out, cudaStream_t s);
 
