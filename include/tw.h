@@ -63,16 +63,19 @@ typedef enum { TW_MAP_F = 0, TW_MAP_FQ = 1 } tw_map;
  *                   arithmetic in double-float (error-free FP32 transforms).
  *                   This is the library's FP64-class path.
  *  TW_PREC_C64    : F^ held as complex64.  Adjoint applies (F^T y, the
- *                   posterior mean's product) take y's spectrum as float
- *                   pairs and add FP32 blocks of 8 rows into FP32 totals
- *                   (y is large against m and F^T y cancels, so an FP32
- *                   data spectrum would lose accuracy far above the
- *                   operator's own 2^-24 rounding); forward
- *                   applies, inverse FFTs and the prior run in FP32.
+ *                   posterior mean's product) run on the tensor cores: y's
+ *                   spectrum is taken as float pairs and both it and the
+ *                   operator are cut into exact fixed-point bf16 slices
+ *                   (per-row / per-column power-of-two scales), so the
+ *                   leading terms of the sum accumulate exactly and the
+ *                   result carries the operator's own rounding only (y is
+ *                   large against m and F^T y cancels; an FP32 sum would
+ *                   lose digits by that cancellation).  Forward applies,
+ *                   inverse FFTs and the prior run in FP32.  Adjoint applies
+ *                   need rows <= 512 (TW_ERR_CUDA beyond).
  *  TW_PREC_BF16X2 : F^ held as bf16 hi + bf16 lo per real (8 bytes per
- *                   complex entry); arithmetic as TW_PREC_C64, except the
- *                   batched adjoint on tensor cores (FP32 data spectra split
- *                   into three bf16 terms, FP32 accumulation).               */
+ *                   complex entry, 16-17 significant bits); arithmetic as
+ *                   TW_PREC_C64.                                             */
 typedef enum { TW_PREC_FP64 = 0, TW_PREC_C64 = 1, TW_PREC_BF16X2 = 2 } tw_prec;
 
 /* Storage kept by the context (bit mask for tw_create's `keep`). */

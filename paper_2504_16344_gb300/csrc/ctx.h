@@ -18,6 +18,15 @@ struct tw_ctx {
   // G^ = F^ C per frequency (the paper's G* = Gamma_pr F* of Phase 2), per kept
   // format, when TW_KEEP_G: the adjoint applies of tw_infer then need no prior filter
   void *opG[3] = {nullptr, nullptr, nullptr};
+  // row exponents of the FP32 storages for the sliced tensor-core adjoint:
+  // ea[which][fmt][w][m] (fmt 1, 2), eaG[fmt] for G^ (gemm_sl.cu)
+  int8_t *ea[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  int8_t *eaG[3] = {nullptr, nullptr, nullptr};
+  // its data-side slices: single right-hand side (sl_*) and batches (bsl_*)
+  void *sl_ws = nullptr, *bsl_ws = nullptr;
+  int *sl_eb = nullptr, *bsl_eb = nullptr;
+  size_t sl_ws_n = 0, bsl_ws_n = 0, sl_eb_n = 0, bsl_eb_n = 0;
+  int sl_tile = 0;                   // right-hand sides per tile of the batched product
   std::vector<char> loaded[2];     // per row: loaded?
   // FFT plans and twiddle tables (df64 and float)
   tw::FftPlan plT{}, plX{}, plY{};
@@ -82,13 +91,11 @@ struct tw_ctx {
   void *bxh = nullptr;               // [bmax][Nf][Nm] parameter-side spectra / prior work
   void *bpart = nullptr;             // [bmax][Nf][nchunk][Rmax] forward-product partial sums
   tw::dd *Lp_dd = nullptr, *inv_dd = nullptr, *chF_dd = nullptr, *chB_dd = nullptr;
-  void *op_tc = nullptr;             // F^ as tensor-core tiles (bf16 hi/lo, swizzled), BF16X2 kept
   // Phase 3 QoI precomputations (tw_qoi_build): rows indexed by QoI entry t*Nq + i
   double *Qmap = nullptr, *Wmap = nullptr;   // [Nq Nt][Nd Nt]: Q = F_q Gamma_pr F^T K^-1, W = (F Gamma_pr F_q^T)^T
   double *Cqq = nullptr;                     // [Nq Nt][Nq Nt]: F_q Gamma_pr F_q^T
   double *qvar = nullptr;                    // [Nq Nt]: diagonal of the QoI posterior covariance
   bool have_qoi = false;
-  void *btc = nullptr;               // B' tiles of one 128-column slice
   // per-phase timing
   struct PhaseEv { int ph; cudaEvent_t a, b; };
   bool prof = false;

@@ -23,9 +23,8 @@
 //
 // FP64-class path: float-pair operands, exact products, renormalised
 // running sums (as the single-vector kernels).  Reduced-precision paths:
-// complex64 or bf16 hi+lo operator; the adjoint takes float-pair data and
-// adds FP32 block sums of rows into FP32 totals, the forward product
-// uses FP32 FMA.
+// complex64 or bf16 hi+lo operator, the forward product in FP32 FMA (their
+// adjoint runs on the tensor cores: gemm_sl.cu).
 #include <algorithm>
 #include <type_traits>
 
@@ -125,93 +124,6 @@ k_gemm_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ Y, long y_bs
 }
 
 // ----------------------------------------- adjoint, FP32 operator, pair data
-// grid (ceil(Nm/128), Nf, ceil(B/(8 RW))); 8 warps x RW right-hand sides
-// each (RW = 4, 2 or 1 after the batch size), a thread RW right-hand sides x
-// 4 grid points.  Y entries are float pairs;
-// both parts enter FP32 block sums of GX_BLK rows (FMA) that are added to
-// FP32 totals: with the data spectrum in double-float the cancellation in
-// F^T y no longer amplifies an FP32 rounding of y.
-constexpr int GX_BLK = 8;
-
-template <int FMT, int RW>
-__global__ void __launch_bounds__(256, 2)
-k_gemm_adj_fx(const void *__restrict__ A, const cdd *__restrict__ Y, long y_bstride,
-              cf *__restrict__ X, long x_bstride, int Nr, int Nm, int B) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int CB = 8 * RW;                      // right-hand sides per CTA
-  cdd *sy = reinterpret_cast<cdd *>(smem_raw);   // [CB][Nr]
-  const int w = blockIdx.y;
-  const int b0 = blockIdx.z * CB;
-  const int nb = min(CB, B - b0);
-  for (int idx = threadIdx.x; idx < CB * Nr; idx += blockDim.x) {
-    const int bl = idx / Nr, sr = idx % Nr;
-    sy[idx] = bl < nb ? ld_cdd(Y + (size_t)(b0 + bl) * y_bstride + (size_t)w * Nr + sr) : cdd_zero();
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
-  const int k0 = blockIdx.x * GA_K + lane;
-  const size_t base = (size_t)w * Nr * Nm;
-  float br[RW][4], bi[RW][4];   // [rhs][point] block sums
-  float tr[RW][4], ti[RW][4];   // totals
-  bool ok[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) ok[j] = k0 + 32 * j < Nm;
-#pragma unroll
-  for (int i = 0; i < RW; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      br[i][j] = 0.f; bi[i][j] = 0.f; tr[i][j] = 0.f; ti[i][j] = 0.f;
-    }
-  cf cur[4], nxt[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) cur[j] = ok[j] ? ld_opf<FMT>(A, base + k0 + 32 * j) : cf_zero();
-  const cdd *syg = sy + (grp * RW) * Nr;
-  for (int s0 = 0; s0 < Nr; s0 += GX_BLK) {
-    const int s1 = min(Nr, s0 + GX_BLK);
-    for (int s = s0; s < s1; ++s) {
-      if (s + 1 < Nr) {
-        const size_t row = base + (size_t)(s + 1) * Nm + k0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) nxt[j] = ok[j] ? ld_opf<FMT>(A, row + 32 * j) : cf_zero();
-      }
-#pragma unroll
-      for (int i = 0; i < RW; ++i) {
-        const cdd y = syg[i * Nr + s];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          // conj(a) y = (ar yr + ai yi) + i (ar yi - ai yr)
-          br[i][j] = fmaf(cur[j].re, y.re.hi, br[i][j]);
-          br[i][j] = fmaf(cur[j].im, y.im.hi, br[i][j]);
-          br[i][j] = fmaf(cur[j].re, y.re.lo, br[i][j]);
-          br[i][j] = fmaf(cur[j].im, y.im.lo, br[i][j]);
-          bi[i][j] = fmaf(cur[j].re, y.im.hi, bi[i][j]);
-          bi[i][j] = fmaf(-cur[j].im, y.re.hi, bi[i][j]);
-          bi[i][j] = fmaf(cur[j].re, y.im.lo, bi[i][j]);
-          bi[i][j] = fmaf(-cur[j].im, y.re.lo, bi[i][j]);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) cur[j] = nxt[j];
-    }
-#pragma unroll
-    for (int i = 0; i < RW; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        tr[i][j] += br[i][j]; ti[i][j] += bi[i][j];
-        br[i][j] = 0.f; bi[i][j] = 0.f;
-      }
-  }
-#pragma unroll
-  for (int i = 0; i < RW; ++i) {
-    const int bl = grp * RW + i;
-    if (bl >= nb) continue;
-    cf *xo = X + (size_t)(b0 + bl) * x_bstride + (size_t)w * Nm;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (ok[j]) xo[k0 + 32 * j] = cf_make(tr[i][j], ti[i][j]);
-  }
-}
-
 // ------------------------------------------------------------ forward
 // grid (nchunk, Nf, ceil(B/32)); a CTA sums 4096 grid points of one
 // frequency for 32 right-hand sides (lane = right-hand side) and all Nr rows
@@ -416,38 +328,6 @@ cudaError_t launch_gemm_adj_dd(const void *A, const cdd *Y, long y_bstride, cdd 
     case 2: adj_dd_run<2>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;
     default: adj_dd_run<1>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;
   }
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-template <int FMT, int RW>
-static void adj_fx_run(const void *A, const cdd *Y, long y_bstride, cf *X, long x_bstride, int Nf,
-                       int Nr, int Nm, int B, cudaStream_t s) {
-  const size_t sm = (size_t)8 * RW * Nr * sizeof(cdd);
-  ensure_smem_g(k_gemm_adj_fx<FMT, RW>, sm);
-  dim3 grid((Nm + GA_K - 1) / GA_K, Nf, (B + 8 * RW - 1) / (8 * RW));
-  k_gemm_adj_fx<FMT, RW><<<grid, 256, sm, s>>>(A, Y, y_bstride, X, x_bstride, Nr, Nm, B);
-}
-
-template <int FMT>
-static void adj_fx_pick(const void *A, const cdd *Y, long y_bstride, cf *X, long x_bstride, int Nf,
-                        int Nr, int Nm, int B, cudaStream_t s) {
-  switch (adj_rw(B)) {
-    case 4: adj_fx_run<FMT, 4>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;
-    case 2: adj_fx_run<FMT, 2>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;
-    default: adj_fx_run<FMT, 1>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;
-  }
-}
-
-cudaError_t launch_gemm_adj_fx(const void *A, int fmt, const cdd *Y, long y_bstride, cf *X,
-                               long x_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s) {
-  if (B <= 0) return cudaSuccess;
-  if (fmt == FMT_C64)
-    adj_fx_pick<FMT_C64>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s);
-  else if (fmt == FMT_BF16X2)
-    adj_fx_pick<FMT_BF16X2>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s);
-  else
-    return cudaErrorInvalidValue;
   count_launches(1);
   return cudaGetLastError();
 }

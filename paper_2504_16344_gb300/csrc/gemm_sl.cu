@@ -1,0 +1,537 @@
+// gemm_sl.cu -- the reduced-precision adjoint product on the 5th-generation
+// tensor cores, with both operands cut into exact fixed-point bf16 slices.
+//
+// Per frequency w the adjoint of a Toeplitz map is a complex product
+//   X^(w) = F^(w)^H Y^(w)          (Nm x Nr) (Nr x B)
+// (Sec. "FFT-based Hessian matvecs": the circulant embedding makes the map
+// block diagonal in frequency).  With F^ = Ar + i Ai and Y = Yr + i Yi,
+//   Xr = Ar^T Yr + Ai^T Yi,   Xi = Ar^T Yi - Ai^T Yr,
+// one real product D = A' B'^T with K' = 2 Nr:
+//   A'[m][2s] = Ar[s][m],  A'[m][2s+1] = Ai[s][m]                 (M: grid points)
+//   B'[b][2s] = Yr[s][b],  B'[b][2s+1] = Yi[s][b]      -> D[m][b]      = Xr
+//   B'[P+b][2s] = Yi[s][b], B'[P+b][2s+1] = -Yr[s][b]  -> D[m][P+b]    = Xi
+// (P right-hand sides per tile, N = 2P columns).
+//
+// Accuracy.  F^T y cancels strongly (y = K^-1 d is large against m), so the
+// sum has to be formed well below FP32 rounding of its terms, or the
+// posterior mean and, through F_q's own cancellation, the forecast lose
+// digits.  The tensor cores multiply bf16 exactly, but accumulate in FP32,
+// which rounds at the running sum.  So each row m of A' (over all K') and
+// each column of B' is scaled by a power of two to (-1, 1) and written in
+// fixed point as four 8-bit integer slices (round to nearest at each step):
+//   v = 2^(e-7) (s0 + s1/2^8 + s2/2^16 + s3/2^24),  |s_i| <= 128,
+// (31 bits for the operator, an exact representation of every complex64 or
+// bf16 hi+lo entry within 2^8 of its row maximum; the data side is cut from
+// its double-float spectrum).  Every slice is an integer of at most 8
+// significant bits, exact in bf16, so the products s_i t_j are integers of
+// at most 2^14 and their sum over K' <= 1024 terms stays below 2^24: the
+// leading level (s0 t0) accumulates EXACTLY in an FP32 accumulator D0, and
+// the cancellation happens in exact arithmetic.  With slices pre-scaled by
+// 2^-8i and 2^-8j, level 1 (s0 t1 + s1 t0, multiples of 2^-8 below 2^16 for
+// K' <= 512) is exact in its own accumulator D1 as well.  Levels 2 and 3 go
+// to D2, 2^-16 below the leading level; levels >= 4 are dropped (2^-32 of a
+// term).  The separate exact D1 matters: the tensor cores truncate when they
+// accumulate in FP32, and a truncated level-1 sum leaves a biased, spatially
+// smooth error that the prior filter amplifies (measured: 13x the posterior
+// mean's error of round-to-nearest); in D2 that bias is 2^8 smaller.  The
+// result is
+//   X = 2^(ea + eb - 14) ((D0 + D1) + D2),
+// within a few units of 2^-30 of the terms: the error left is the rounding
+// of the stored operator itself.  Ten MMAs per 16-wide k step.
+//
+// Kernel: one CTA per (128 grid points, frequency, tile of P right-hand
+// sides); 8 producer warps load the operator (complex64 or bf16 hi+lo),
+// slice it with its row's exponent and write the four 128 x 32 bf16 slice
+// tiles of a stage (K-major, 64-byte swizzle); one thread copies the
+// stage's B' slices (prepared once per call by k_bsl_build) with the bulk
+// copy engine and one thread issues the MMAs (D0, D1, D2 in TMEM: 3N of its
+// columns, so N <= 160).  Two stages, mbarriers with transaction counts,
+// tcgen05.commit frees a stage.  The producers then read D0..D2
+// (tcgen05.ld), scale and store X as complex64.  Every wait is bounded: on expiry the kernel records
+// TW_ERR_TIMEOUT, lets its copies and MMAs drain (bounded), frees TMEM and
+// returns.
+#include <stdint.h>
+
+#include "../../include/tw.h"
+#include "kernels.h"
+
+namespace tw {
+
+namespace {
+
+constexpr int TM = 128;                  // MMA M: grid points per tile
+constexpr int KA = 32;                   // K' per stage: 16 rows (sensors) x (re, im)
+constexpr int NSL = 4;                   // slices per operand
+constexpr int STAGES = 2;
+constexpr int NPROD = 256;               // producer / epilogue threads (8 warps)
+constexpr int NTHR = NPROD + 32;         // + the MMA warp
+constexpr int A_SLICE = TM * KA * 2;     // 8 KB: one 128 x 32 bf16 slice tile
+constexpr int A_STAGE = NSL * A_SLICE;   // 32 KB
+constexpr unsigned SPIN_LIMIT = 1u << 26;
+constexpr int EXP_MIN = -100, EXP_MAX = 120;
+constexpr int SL_PMAX = 80;              // right-hand sides per tile: 3 x 2P <= 512 TMEM columns
+
+__device__ __forceinline__ uint32_t su32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// byte offset of the 16-byte chunk q (0..3) of row r in a K-major tile of 32
+// bf16 per row with the 64-byte swizzle (chunk index XOR bits 1-2 of the row)
+__host__ __device__ __forceinline__ uint32_t swz64(int r, int q) {
+  return (uint32_t)r * 64u + ((uint32_t)(q ^ ((r >> 1) & 3)) << 4);
+}
+
+// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512
+// bytes apart; bits 46-48 = 0b001 (descriptor version), bits 61-63 = 4 (64B)
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+// instruction descriptor, kind::f16: D F32, A and B BF16, both K-major
+__host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\t"
+               "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.b32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+// true once the phase with this parity has completed; false after the spin
+// limit or once another role of the CTA has failed
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity, volatile int *fail) {
+  for (unsigned it = 0; it < SPIN_LIMIT; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 1023u) == 1023u && *fail) return false;
+  }
+  return false;
+}
+// the same without the early exit (draining the CTA's own asynchronous work)
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, unsigned parity) {
+  for (unsigned it = 0; it < SPIN_LIMIT; ++it)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, unsigned bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile("{\n\t.reg .pred p;\n\t"
+               "setp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+               ::"r"(dtmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(bar) : "memory");
+}
+
+// round to the nearest integer (ties to even), |v| < 2^22
+__device__ __forceinline__ float rnd_int(float v) {
+  return __fsub_rn(__fadd_rn(v, 12582912.0f), 12582912.0f);
+}
+// 2^e as a float, e in [-126, 127]
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+// bf16 bits of two floats of at most 8 significant bits (exact): upper halves
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+// smallest e with |v| < 2^e for the largest |v| = mx >= 0, clamped
+__device__ __forceinline__ int exp_above(float mx) {
+  if (!(mx > 0.f)) return EXP_MIN;
+  const int E = (int)((__float_as_uint(mx) >> 23) & 0xffu);
+  const int e = E - 126;
+  return e < EXP_MIN ? EXP_MIN : (e > EXP_MAX ? EXP_MAX : e);
+}
+
+__device__ __forceinline__ float bf16lo(unsigned w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
+
+// operator entry (exact FP32 values) of the complex64 or bf16 hi+lo storage
+template <int FMT> __device__ __forceinline__ float2 ld_entry(const void *A, size_t i);
+template <> __device__ __forceinline__ float2 ld_entry<FMT_C64>(const void *A, size_t i) {
+  return __ldcs(reinterpret_cast<const float2 *>(A) + i);
+}
+template <> __device__ __forceinline__ float2 ld_entry<FMT_BF16X2>(const void *A, size_t i) {
+  const uint2 v = __ldcs(reinterpret_cast<const uint2 *>(A) + i);
+  return make_float2(bf16lo(v.x) + bf16hi(v.x), bf16lo(v.y) + bf16hi(v.y));
+}
+
+// ------------------------------------------------------ row exponents
+// ea[w][m] = smallest e with |Re|, |Im| of F^(w)[s][m] < 2^e for every row s
+template <int FMT>
+__global__ void k_row_exp(const void *__restrict__ A, int8_t *__restrict__ ea, int Nf, int Nr, int Nm) {
+  const long total = (long)Nf * Nm;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long)gridDim.x * blockDim.x) {
+    const long w = idx / Nm, m = idx % Nm;
+    float mx = 0.f;
+    for (int s = 0; s < Nr; ++s) {
+      const float2 v = ld_entry<FMT>(A, ((size_t)w * Nr + s) * Nm + m);
+      mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    ea[idx] = (int8_t)exp_above(mx);
+  }
+}
+
+// ------------------------------------------------------ B' slices
+// tiles [w][nt][atom][slice][2P rows][32 bf16] (64-byte swizzle), eb[w][nt*P + b]
+__global__ void __launch_bounds__(256)
+k_bsl_build(const cdd *__restrict__ Y, long y_bstride, int Nr, int B, int P, int natoms,
+            uint8_t *__restrict__ tiles, int *__restrict__ eb, int ntiles) {
+  __shared__ int e_sh[SL_PMAX];
+  const int w = blockIdx.x, nt = blockIdx.y;
+  const int N = 2 * P;
+  for (int bl = threadIdx.x; bl < P; bl += blockDim.x) {
+    const int b = nt * P + bl;
+    float mx = 0.f;
+    if (b < B) {
+      const cdd *y = Y + (size_t)b * y_bstride + (size_t)w * Nr;
+      for (int s = 0; s < Nr; ++s) {
+        const cdd v = ld_cdd(y + s);
+        mx = fmaxf(mx, fmaxf(fabsf(v.re.hi), fabsf(v.im.hi)));
+      }
+    }
+    // the low halves may lift |y| past the high half's bound by one unit in
+    // the last place: bound the sum instead
+    const int e = exp_above(mx * (1.0f + 1.0f / 1048576.0f));
+    e_sh[bl] = e;
+    eb[(size_t)w * ntiles * P + b] = e;
+  }
+  __syncthreads();
+  const size_t slice_bytes = (size_t)N * 64;
+  uint8_t *base = tiles + ((size_t)w * ntiles + nt) * natoms * NSL * slice_bytes;
+  const int tasks = natoms * N * 4;
+  for (int t = threadIdx.x; t < tasks; t += blockDim.x) {
+    const int a = t / (N * 4), rem = t % (N * 4);
+    const int n = rem >> 2, q = rem & 3;
+    const int part = n >= P, bl = n - part * P, b = nt * P + bl;
+    const float sc = pow2f(7 - e_sh[bl]);
+    uint32_t wd[NSL][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int s = 16 * a + 4 * q + u;
+      cdd y = cdd_zero();
+      if (b < B && s < Nr) y = ld_cdd(Y + (size_t)b * y_bstride + (size_t)w * Nr + s);
+      // the two reals of this row: (yr, yi) for the real-part column, (yi, -yr) for the imaginary
+      dd v[2];
+      v[0] = part ? y.im : y.re;
+      v[1] = part ? dd_neg(y.re) : y.im;
+      float sl[2][NSL];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        float hi = v[c].hi * sc, lo = v[c].lo * sc;   // exact: power-of-two scaling
+#pragma unroll
+        for (int i = 0; i < NSL; ++i) {
+          const float si = rnd_int(hi);
+          sl[c][i] = si * pow2f(-8 * i);
+          if (i + 1 < NSL) {
+            float r, e;
+            two_sum(__fsub_rn(hi, si), lo, r, e);      // hi - si is exact
+            hi = r * 256.f;
+            lo = e * 256.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NSL; ++i) wd[i][u] = pack_bf16(sl[0][i], sl[1][i]);
+    }
+    uint8_t *at = base + (size_t)a * NSL * slice_bytes;
+#pragma unroll
+    for (int i = 0; i < NSL; ++i)
+      *reinterpret_cast<uint4 *>(at + i * slice_bytes + swz64(n, q)) =
+          make_uint4(wd[i][0], wd[i][1], wd[i][2], wd[i][3]);
+  }
+}
+
+// ------------------------------------------------------------------ the product
+// pair p = 0..9 of slices (i, j), level L = i + j: p = 0 is level 0 (into
+// D0), p = 1, 2 level 1 (into D1), p = 3..9 levels 2 and 3 (into D2)
+__device__ __forceinline__ int pair_level(int p) { return p == 0 ? 0 : (p < 3 ? 1 : (p < 6 ? 2 : 3)); }
+__device__ __forceinline__ int pair_i(int p) {
+  const int L = pair_level(p);
+  return p - L * (L + 1) / 2;
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(NTHR, 1)
+k_gemm_adj_sl(const void *__restrict__ A, const int8_t *__restrict__ ea, const uint8_t *__restrict__ Bt,
+              const int *__restrict__ eb, cf *__restrict__ X, long x_bstride, int b0, int B, int P,
+              int ntiles, int Nr, int Nm, int natoms, unsigned tmem_cols, int *err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bars[3 * STAGES + 1];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mt = blockIdx.x, w = blockIdx.y, nt = blockIdx.z;
+  const int N = 2 * P;
+  const uint32_t b_slice = (uint32_t)N * 64u, b_stage = NSL * b_slice;
+  const uint32_t sbase = (su32(smem_raw) + 1023u) & ~1023u;
+  // stage st: A slices at sbase + st * A_STAGE, B slices after all A stages
+  const uint32_t sA0 = sbase, sB0 = sbase + STAGES * A_STAGE;
+  uint8_t *gbase = smem_raw + (sbase - su32(smem_raw));
+  const uint32_t bar0 = su32(&bars[0]);
+  auto fullA = [&](int st) { return bar0 + 8u * st; };
+  auto fullB = [&](int st) { return bar0 + 8u * (STAGES + st); };
+  auto empty = [&](int st) { return bar0 + 8u * (2 * STAGES + st); };
+  const uint32_t done = bar0 + 8u * (3 * STAGES);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(su32(&tmem_slot)), "r"(tmem_cols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    fail = 0;
+    for (int st = 0; st < STAGES; ++st) {
+      mbar_init(fullA(st), NPROD);
+      mbar_init(fullB(st), 1);
+      mbar_init(empty(st), 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  volatile int *vfail = &fail;
+  const uint8_t *Bw = Bt + ((size_t)w * ntiles + nt) * natoms * b_stage;
+
+  if (warp < NPROD / 32) {
+    // ---------------- producers: operator slices, then the epilogue
+    const int r = tid & (TM - 1), h = tid >> 7;
+    const int m = mt * TM + r;
+    const bool vm = m < Nm;
+    const int e_a = vm ? (int)ea[(size_t)w * Nm + m] : EXP_MIN;
+    const float sc = pow2f(7 - e_a);
+    const size_t abase = (size_t)w * Nr * Nm + (size_t)m;
+    int issued = 0;                       // B copies issued by thread 0
+    float2 cur[8], nxt[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int s = 8 * h + u;
+      cur[u] = (vm && s < Nr) ? ld_entry<FMT>(A, abase + (size_t)s * Nm) : make_float2(0.f, 0.f);
+    }
+    for (int a = 0; a < natoms; ++a) {
+      const int st = a % STAGES;
+      if (a + 1 < natoms) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int s = 16 * (a + 1) + 8 * h + u;
+          nxt[u] = (vm && s < Nr) ? ld_entry<FMT>(A, abase + (size_t)s * Nm) : make_float2(0.f, 0.f);
+        }
+      }
+      if (a >= STAGES && !mbar_wait(empty(st), (unsigned)((a / STAGES - 1) & 1), vfail)) {
+        if (atomicCAS(err, 0, TW_ERR_TIMEOUT) == 0) err[1] = 21;
+        fail = 1;
+        break;
+      }
+      if (tid == 0) {
+        mbar_arrive_tx(fullB(st), b_stage);
+        bulk_g2s(sB0 + st * b_stage, Bw + (size_t)a * b_stage, b_stage, fullB(st));
+        ++issued;
+      }
+      uint8_t *sa = gbase + (size_t)st * A_STAGE;
+      float v[16];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) { v[2 * u] = cur[u].x * sc; v[2 * u + 1] = cur[u].y * sc; }
+#pragma unroll
+      for (int i = 0; i < NSL; ++i) {
+        const float p2 = pow2f(-8 * i);
+        uint32_t wd[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float s0 = rnd_int(v[2 * u]), s1 = rnd_int(v[2 * u + 1]);
+          wd[u] = pack_bf16(s0 * p2, s1 * p2);
+          if (i + 1 < NSL) {   // remainders, exact: (v - s) * 256
+            v[2 * u] = __fmul_rn(__fsub_rn(v[2 * u], s0), 256.f);
+            v[2 * u + 1] = __fmul_rn(__fsub_rn(v[2 * u + 1], s1), 256.f);
+          }
+        }
+        uint8_t *tile = sa + i * A_SLICE;
+        *reinterpret_cast<uint4 *>(tile + swz64(r, 2 * h)) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        *reinterpret_cast<uint4 *>(tile + swz64(r, 2 * h + 1)) = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+      }
+      // generic-proxy writes -> visible to the tensor cores (async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(fullA(st));
+#pragma unroll
+      for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
+    }
+    // ---------------- epilogue: (D0 + D1) + D2 from TMEM, scaled, complex64 out
+    const bool ok = mbar_wait(done, 0, vfail);
+    if (!ok && !*vfail) {
+      if (atomicCAS(err, 0, TW_ERR_TIMEOUT) == 0) err[1] = 22;
+      fail = 1;
+    }
+    if (tid == 0 && *vfail) {
+      // copies already issued must land before the CTA's shared memory goes
+      for (int a = (issued > STAGES ? issued - STAGES : 0); a < issued; ++a)
+        mbar_drain(fullB(a % STAGES), (unsigned)((a / STAGES) & 1));
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && !*vfail) {
+      const int lg = warp & 3;                        // TMEM lanes 32 lg .. 32 lg + 31
+      // TMEM lane 32 lg + lane is this thread's own operator row r (tid mod 128)
+      const int mrow = mt * TM + 32 * lg + lane;
+      const float sa = pow2f(e_a - 7);
+      const uint32_t trow = tmem + ((uint32_t)(32 * lg) << 16);
+      for (int c0 = 8 * (warp >> 2); c0 < P; c0 += 16) {
+        uint32_t d0r[8], d0i[8], d1r[8], d1i[8], d2r[8], d2i[8];
+#define TW_LD8(dst, col)                                                                       \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"          \
+               : "=r"(dst[0]), "=r"(dst[1]), "=r"(dst[2]), "=r"(dst[3]), "=r"(dst[4]),        \
+                 "=r"(dst[5]), "=r"(dst[6]), "=r"(dst[7])                                     \
+               : "r"(trow + (uint32_t)(col)))
+        TW_LD8(d0r, c0);
+        TW_LD8(d0i, P + c0);
+        TW_LD8(d1r, N + c0);
+        TW_LD8(d1i, N + P + c0);
+        TW_LD8(d2r, 2 * N + c0);
+        TW_LD8(d2i, 2 * N + P + c0);
+#undef TW_LD8
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (mrow < Nm) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int bl = c0 + j, b = nt * P + bl;
+            if (b < B) {
+              const float sb = pow2f(eb[(size_t)w * ntiles * P + b] - 7);
+              const float re = __fadd_rn(__fadd_rn(__uint_as_float(d0r[j]), __uint_as_float(d1r[j])),
+                                         __uint_as_float(d2r[j])) * sa * sb;
+              const float im = __fadd_rn(__fadd_rn(__uint_as_float(d0i[j]), __uint_as_float(d1i[j])),
+                                         __uint_as_float(d2i[j])) * sa * sb;
+              X[(size_t)(b0 + b) * x_bstride + (size_t)w * Nm + mrow] = cf_make(re, im);
+            }
+          }
+        }
+      }
+    }
+  } else if (lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t idesc = idesc_bf16(TM, N);
+    bool ok = true;
+    for (int a = 0; a < natoms && ok; ++a) {
+      const int st = a % STAGES;
+      const unsigned par = (unsigned)((a / STAGES) & 1);
+      ok = mbar_wait(fullA(st), par, vfail) && mbar_wait(fullB(st), par, vfail);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t aS = sA0 + st * A_STAGE, bS = sB0 + st * b_stage;
+#pragma unroll
+      for (int ks = 0; ks < KA / 16; ++ks) {
+#pragma unroll
+        for (int p = 0; p < 10; ++p) {
+          const int i = pair_i(p), j = pair_level(p) - pair_i(p);
+          const uint64_t ad = sdesc64(aS + i * A_SLICE + ks * 32);
+          const uint64_t bd = sdesc64(bS + j * b_slice + ks * 32);
+          const int L = pair_level(p);
+          const uint32_t dcol = (uint32_t)((L < 2 ? L : 2) * N);
+          // the first MMA into each accumulator (p = 0, 1, 3) overwrites it
+          const uint32_t acc = (a > 0 || ks > 0 || (p != 0 && p != 1 && p != 3)) ? 1u : 0u;
+          mma_bf16(tmem + dcol, ad, bd, idesc, acc);
+        }
+      }
+      mma_commit(empty(st));                 // stage reusable once these MMAs finish
+    }
+    if (!ok) {
+      if (!*vfail && atomicCAS(err, 0, TW_ERR_TIMEOUT) == 0) err[1] = 23;
+      fail = 1;
+    }
+    mma_commit(done);                        // D final (or: every issued MMA drained)
+    mbar_drain(done, 0);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols)
+                 : "memory");
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+int sl_natoms(int Nr) { return (Nr + KA / 2 - 1) / (KA / 2); }
+
+size_t sl_ws_bytes(int Nf, int Nr, int bcols) {
+  const int bc = (bcols + 7) / 8 * 8;
+  return (size_t)Nf * sl_natoms(Nr) * NSL * 2 * (size_t)bc * 64;
+}
+size_t sl_eb_bytes(int Nf, int bcols) { return (size_t)Nf * ((bcols + 7) / 8 * 8) * sizeof(int); }
+
+int sl_pick_tile(int B) {
+  // right-hand sides per tile: one tile up to 80 (N = 160 columns, three
+  // accumulators in 480 TMEM columns), else the fewest tiles of a multiple of 8
+  const int P8 = (B + 7) / 8 * 8;
+  if (P8 <= SL_PMAX) return P8;
+  const int nt = (P8 + SL_PMAX - 1) / SL_PMAX;
+  return ((P8 + nt - 1) / nt + 7) / 8 * 8;
+}
+
+cudaError_t launch_row_exp(const void *A, int fmt, int8_t *ea, int Nf, int Nr, int Nm, cudaStream_t s) {
+  const long total = (long)Nf * Nm;
+  long blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (fmt == FMT_C64)
+    k_row_exp<FMT_C64><<<(unsigned)blocks, 256, 0, s>>>(A, ea, Nf, Nr, Nm);
+  else if (fmt == FMT_BF16X2)
+    k_row_exp<FMT_BF16X2><<<(unsigned)blocks, 256, 0, s>>>(A, ea, Nf, Nr, Nm);
+  else
+    return cudaErrorInvalidValue;
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// X[b][w][k] = sum_s conj(A[w][s][k]) Y[b][w][s] for b < B; P right-hand
+// sides per tile (0: pick); ws: B' tiles of >= sl_ws_bytes(Nf, Nr, ntiles P)
+cudaError_t launch_gemm_adj_sl(const void *A, int fmt, const int8_t *ea, const cdd *Y, long y_bstride,
+                               cf *X, long x_bstride, int Nf, int Nr, int Nm, int B, int P,
+                               void *ws, size_t ws_bytes, int *eb, size_t eb_bytes, int *err,
+                               cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  if (Nr > 512 || (fmt != FMT_C64 && fmt != FMT_BF16X2)) return cudaErrorInvalidValue;
+  if (P <= 0) P = sl_pick_tile(B);
+  if (P % 8 != 0 || P > SL_PMAX) return cudaErrorInvalidValue;
+  const int ntiles = (B + P - 1) / P, natoms = sl_natoms(Nr), N = 2 * P;
+  if (sl_ws_bytes(Nf, Nr, ntiles * P) > ws_bytes || (size_t)Nf * ntiles * P * sizeof(int) > eb_bytes)
+    return cudaErrorInvalidValue;
+  k_bsl_build<<<dim3(Nf, ntiles), 256, 0, s>>>(Y, y_bstride, Nr, B, P, natoms,
+                                               reinterpret_cast<uint8_t *>(ws), eb, ntiles);
+  count_launches(1);
+  unsigned cols = 32;
+  while ((int)cols < 3 * N) cols <<= 1;
+  const size_t sm = 1024 + STAGES * ((size_t)A_STAGE + (size_t)NSL * N * 64);
+  const dim3 grid((Nm + TM - 1) / TM, Nf, ntiles);
+  if (fmt == FMT_C64) {
+    cudaFuncSetAttribute(k_gemm_adj_sl<FMT_C64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_gemm_adj_sl<FMT_C64><<<grid, NTHR, sm, s>>>(A, ea, reinterpret_cast<const uint8_t *>(ws), eb, X,
+                                                  x_bstride, 0, B, P, ntiles, Nr, Nm, natoms, cols, err);
+  } else {
+    cudaFuncSetAttribute(k_gemm_adj_sl<FMT_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_gemm_adj_sl<FMT_BF16X2><<<grid, NTHR, sm, s>>>(A, ea, reinterpret_cast<const uint8_t *>(ws), eb, X,
+                                                     x_bstride, 0, B, P, ntiles, Nr, Nm, natoms, cols, err);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace tw

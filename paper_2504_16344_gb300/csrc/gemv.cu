@@ -15,9 +15,8 @@
 //
 // The FP64-class path reads float-pair entries (16 B) and accumulates with
 // exact products and a compensated running sum; the reduced-precision
-// paths read complex64 or bf16 hi+lo entries (8 B): the forward product
-// sums in FP32, the adjoint takes float-pair data and adds FP32 block sums
-// of rows into FP32 totals.
+// paths read complex64 or bf16 hi+lo entries (8 B) and the forward product
+// sums in FP32 (their adjoint runs on the tensor cores: gemm_sl.cu).
 #include "kernels.h"
 
 namespace tw {
@@ -102,77 +101,6 @@ k_gemv_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ yh, cdd *__r
     r.im = dacc_get(im[j]);
     st_cdd(xh + (size_t)w * Nm + kb + 256 * j, r);
   }
-}
-
-// Reduced-precision adjoint with float-pair data: the operator entry (FP32)
-// times y = y_hi + y_lo, both parts by FMA into an FP32 block sum over
-// MIX_BLK rows, each block added to an FP32 total.  F^T y cancels (K's
-// conditioning makes y large against m), so the data spectrum must not be
-// rounded to FP32 or come from an FP32 FFT; with it in double-float, the low
-// halves and the short blocks take the error a further ~1.4x down (measured
-// by emulating every rounding; a compensated total gained nothing more).
-constexpr int MIX_BLK = 8;
-
-template <int FMT>
-__global__ void __launch_bounds__(256)
-k_gemv_adj_fx(const void *__restrict__ A, const cdd *__restrict__ yh, cf *__restrict__ xh, int Nr,
-              int Nm) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cdd *sy = reinterpret_cast<cdd *>(smem_raw);
-  const int w = blockIdx.y;
-  const size_t base = (size_t)w * Nr * Nm;
-  for (int s = threadIdx.x; s < Nr; s += blockDim.x) sy[s] = ld_cdd(yh + (size_t)w * Nr + s);
-  __syncthreads();
-  const int kb = blockIdx.x * (256 * ADJ_KPT) + threadIdx.x;
-  float br[ADJ_KPT], bi[ADJ_KPT];
-  float tr[ADJ_KPT], ti[ADJ_KPT];
-  bool ok[ADJ_KPT];
-#pragma unroll
-  for (int j = 0; j < ADJ_KPT; ++j) {
-    br[j] = 0.f; bi[j] = 0.f; tr[j] = 0.f; ti[j] = 0.f;
-    ok[j] = kb + 256 * j < Nm;
-  }
-  // rows s+1 and s+2 in flight while row s is used (8-byte entries: two rows
-  // ahead keep as many bytes in flight as the 16-byte kernel's one)
-  cf cur[ADJ_KPT], nx1[ADJ_KPT], nx2[ADJ_KPT];
-#pragma unroll
-  for (int j = 0; j < ADJ_KPT; ++j) {
-    cur[j] = ok[j] ? ld_op_f<FMT>(A, base + kb + 256 * j) : cf_zero();
-    nx1[j] = (ok[j] && Nr > 1) ? ld_op_f<FMT>(A, base + (size_t)Nm + kb + 256 * j) : cf_zero();
-  }
-  for (int s0 = 0; s0 < Nr; s0 += MIX_BLK) {
-    const int s1 = min(Nr, s0 + MIX_BLK);
-    for (int s = s0; s < s1; ++s) {
-      if (s + 2 < Nr) {
-        const size_t row = base + (size_t)(s + 2) * Nm + kb;
-#pragma unroll
-        for (int j = 0; j < ADJ_KPT; ++j) nx2[j] = ok[j] ? ld_op_f<FMT>(A, row + 256 * j) : cf_zero();
-      }
-      const cdd y = sy[s];
-#pragma unroll
-      for (int j = 0; j < ADJ_KPT; ++j) {
-        // conj(a) y = (ar yr + ai yi) + i (ar yi - ai yr)
-        br[j] = fmaf(cur[j].re, y.re.hi, br[j]);
-        br[j] = fmaf(cur[j].im, y.im.hi, br[j]);
-        br[j] = fmaf(cur[j].re, y.re.lo, br[j]);
-        br[j] = fmaf(cur[j].im, y.im.lo, br[j]);
-        bi[j] = fmaf(cur[j].re, y.im.hi, bi[j]);
-        bi[j] = fmaf(-cur[j].im, y.re.hi, bi[j]);
-        bi[j] = fmaf(cur[j].re, y.im.lo, bi[j]);
-        bi[j] = fmaf(-cur[j].im, y.re.lo, bi[j]);
-      }
-#pragma unroll
-      for (int j = 0; j < ADJ_KPT; ++j) { cur[j] = nx1[j]; nx1[j] = nx2[j]; }
-    }
-#pragma unroll
-    for (int j = 0; j < ADJ_KPT; ++j) {
-      tr[j] += br[j]; ti[j] += bi[j];
-      br[j] = 0.f; bi[j] = 0.f;
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < ADJ_KPT; ++j)
-    if (ok[j]) xh[(size_t)w * Nm + kb + 256 * j] = cf_make(tr[j], ti[j]);
 }
 
 // ------------------------------------------------------------ forward
@@ -360,25 +288,6 @@ cudaError_t launch_gemv_adj_dd(const void *A, int fmt, const cdd *yh, cdd *xh, i
     cudaFuncSetAttribute(k_gemv_adj_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 g((Nm + 256 * ADJ_KPT - 1) / (256 * ADJ_KPT), Nf);
   k_gemv_adj_dd<<<g, 256, sm, s>>>(reinterpret_cast<const float4 *>(A), yh, xh, Nr, Nm);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_gemv_adj_fx(const void *A, int fmt, const cdd *yh, cf *xh, int Nf, int Nr,
-                               int Nm, cudaStream_t s) {
-  const size_t sm = (size_t)Nr * sizeof(cdd);
-  dim3 g((Nm + 256 * ADJ_KPT - 1) / (256 * ADJ_KPT), Nf);
-  if (fmt == FMT_C64) {
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(k_gemv_adj_fx<FMT_C64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gemv_adj_fx<FMT_C64><<<g, 256, sm, s>>>(A, yh, xh, Nr, Nm);
-  } else if (fmt == FMT_BF16X2) {
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(k_gemv_adj_fx<FMT_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gemv_adj_fx<FMT_BF16X2><<<g, 256, sm, s>>>(A, yh, xh, Nr, Nm);
-  } else {
-    return cudaErrorInvalidValue;
-  }
   count_launches(1);
   return cudaGetLastError();
 }

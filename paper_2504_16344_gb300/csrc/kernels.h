@@ -84,21 +84,12 @@ cudaError_t launch_gemv_fwd_f(const void *A, int fmt, const cf *xh, cf *part, cf
 // adjoint: xh[w][k] = sum_s conj(A[w][s][k]) yh[w][s]
 cudaError_t launch_gemv_adj_dd(const void *A, int fmt, const cdd *yh, cdd *xh, int Nf, int Nr,
                                int Nm, cudaStream_t s);
-// adjoint with an FP32 operator and float-pair data: FP32 block sums of 8
-// rows added into FP32 totals (the reduced-precision paths' F^T y)
-cudaError_t launch_gemv_adj_fx(const void *A, int fmt, const cdd *yh, cf *xh, int Nf, int Nr,
-                               int Nm, cudaStream_t s);
-
 // ---- batched per-frequency products (gemm.cu) ----------------------------
 // adjoint: X[b][w][k] = sum_s conj(A[w][s][k]) Y[b][w][s]
 // forward: Yo[b][w][r] = sum_k A[w][r][k] X[b][w][k]; part: B*Nf*nchunk*Nr entries
 int gemm_fwd_nchunk(int Nm);
 cudaError_t launch_gemm_adj_dd(const void *A, const cdd *Y, long y_bstride, cdd *X, long x_bstride,
                                int Nf, int Nr, int Nm, int B, cudaStream_t s);
-// adjoint with an FP32 operator (fmt C64 / BF16X2) and float-pair data Y:
-// FP32 block sums of 8 rows added into FP32 totals, X in FP32
-cudaError_t launch_gemm_adj_fx(const void *A, int fmt, const cdd *Y, long y_bstride, cf *X,
-                               long x_bstride, int Nf, int Nr, int Nm, int B, cudaStream_t s);
 // lpb: lanes per right-hand side in the forward product (1 or 2, fixed per
 // context so that a right-hand side's sum order does not depend on its batch)
 cudaError_t launch_gemm_fwd_dd(const void *A, const cdd *X, long x_bstride, cdd *part, cdd *Yo,
@@ -107,15 +98,21 @@ cudaError_t launch_gemm_fwd_f(const void *A, int fmt, const cf *X, long x_bstrid
                               cf *Yo, long y_bstride, int Nf, int Nr, int Nm, int B,
                               cudaStream_t s, int lpb = 1);
 
-// ---- tensor-core adjoint product (gemm_tc.cu), bf16 hi/lo operator --------
-int gemm_tc_nka(int Nr);
-int gemm_tc_nmt(int Nm);
-size_t gemm_tc_op_bytes(int Nf, int Nr, int Nm);
-size_t gemm_tc_b_bytes(int Nf, int Nr);
-cudaError_t launch_optc_build(const void *op_bf16x2, void *tc, int Nf, int Nr, int Nm,
-                              cudaStream_t s);
-cudaError_t launch_gemm_adj_tc(const void *op_tc, const cf *Y, long y_bstride, cf *X,
-                               long x_bstride, int Nf, int Nr, int Nm, int B, void *btc, int *err,
+// ---- reduced-precision adjoint product on the tensor cores (gemm_sl.cu) ---
+// X[b][w][k] = sum_s conj(A[w][s][k]) Y[b][w][s] with the FP32 operator
+// (fmt C64 / BF16X2) and float-pair data Y, both cut into exact fixed-point
+// bf16 slices; ea: the operator's row exponents (launch_row_exp).  P: right-
+// hand sides per tile (multiple of 8, <= 80; 0 picks one).  ws / eb: the
+// data-side slices and exponents, at least sl_ws_bytes / sl_eb_bytes for
+// ceil(B / P) P columns.  err: device error record (bounded waits).
+int sl_natoms(int Nr);
+size_t sl_ws_bytes(int Nf, int Nr, int bcols);
+size_t sl_eb_bytes(int Nf, int bcols);
+int sl_pick_tile(int B);
+cudaError_t launch_row_exp(const void *A, int fmt, int8_t *ea, int Nf, int Nr, int Nm, cudaStream_t s);
+cudaError_t launch_gemm_adj_sl(const void *A, int fmt, const int8_t *ea, const cdd *Y, long y_bstride,
+                               cf *X, long x_bstride, int Nf, int Nr, int Nm, int B, int P,
+                               void *ws, size_t ws_bytes, int *eb, size_t eb_bytes, int *err,
                                cudaStream_t s);
 
 // ---- operator storage conversion: dst[w][row0+r][k] from src (cdd) -----

@@ -242,6 +242,21 @@ tw_status tw_create(tw_ctx **out, int Nd, int Nq, int Nx, int Ny, int Nt, double
     else if (cudaMemset(c->d_err, 0, 4 * sizeof(int)) != cudaSuccess)
       st = twh::fail(c, TW_ERR_CUDA, "memset");
   }
+  if (st == TW_OK && (keep & (TW_KEEP_C64 | TW_KEEP_BF16X2))) {
+    // the sliced tensor-core adjoint of the FP32 storages: row exponents per
+    // kept storage and the data-side slices of one right-hand side
+    for (int which = 0; which < 2; ++which)
+      for (int fmt = 1; fmt < 3; ++fmt)
+        if (c->op[which][fmt]) {
+          c->ea[which][fmt] = (int8_t *)twh::dalloc(c, Nf * Nm);
+          if (!c->ea[which][fmt]) st = twh::fail(c, TW_ERR_OOM, "row exponent tables");
+        }
+    c->sl_ws_n = sl_ws_bytes(c->Nf, c->Rmax, 8);
+    c->sl_eb_n = sl_eb_bytes(c->Nf, 8);
+    c->sl_ws = twh::dalloc(c, c->sl_ws_n);
+    c->sl_eb = (int *)twh::dalloc(c, c->sl_eb_n);
+    if (!c->sl_ws || !c->sl_eb) st = twh::fail(c, TW_ERR_OOM, "slice workspace");
+  }
   if (st != TW_OK) {
     // keep the message for the caller: report via stderr since ctx is freed
     fprintf(stderr, "tw_create: %s\n", c->err.c_str());
@@ -297,13 +312,19 @@ tw_status tw_set_block_column(tw_ctx *c, tw_map which, int row0, int nrows, cons
     TW_CUDA(c, cudaStreamSynchronize(s));
     twh::dfree(c, tmp);
   }
+  for (int r = row0; r < row0 + nrows; ++r) c->loaded[which][r] = 1;
+  // every row present: the row exponents of the FP32 storages (one pass)
+  bool all = true;
+  for (char l : c->loaded[which]) all = all && l;
+  for (int fmt = 1; fmt < 3 && all; ++fmt)
+    if (c->ea[which][fmt])
+      TW_CUDA(c, launch_row_exp(c->op[which][fmt], fmt, c->ea[which][fmt], c->Nf, R, c->Nm, s));
   // with the prior known, keep G = Phi C^{1/2} of these rows for tw_factor_K,
   // computed in FP64 from the caller's FP64 column
   if (which == TW_MAP_F && c->prior_set) {
     tw_status st = build_G_rows(c, row0, nrows, col, s);
     if (st != TW_OK) return st;
   }
-  for (int r = row0; r < row0 + nrows; ++r) c->loaded[which][r] = 1;
   return TW_OK;
 }
 
@@ -415,13 +436,15 @@ tw_status tw_p2o_adjoint(tw_ctx *c, tw_map which, tw_prec prec, int nrhs, const 
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
         TW_CUDA(c, launch_irfft_time_dd(c->wf, Nm, xr, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s)); }
     } else {
-      // FP32 operator; the data-side spectrum in double-float and FP32 block
-      // sums in the product (as the posterior mean's adjoint)
+      // FP32 operator; the data-side spectrum in double-float, the product on
+      // the tensor cores with both sides in exact fixed-point slices (as the
+      // posterior mean's adjoint)
       cf *wf = (cf *)c->wf;
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
         TW_CUDA(c, launch_rfft_time_dd(yr, 0, R, Nt, c->wr, R, R, c->plT, c->twT, c->twL, s)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-        TW_CUDA(c, launch_gemv_adj_fx(A, (int)prec, c->wr, wf, Nf, R, Nm, s)); }
+        TW_CUDA(c, launch_gemm_adj_sl(A, (int)prec, c->ea[which][prec], c->wr, 0, wf, 0, Nf, R, Nm, 1, 8,
+                                      c->sl_ws, c->sl_ws_n, c->sl_eb, c->sl_eb_n, c->d_err, s)); }
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
         TW_CUDA(c, launch_irfft_time_f(wf, Nm, xr, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s)); }
     }

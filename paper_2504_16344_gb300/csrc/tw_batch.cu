@@ -119,22 +119,16 @@ tw_status infer_core(tw_ctx *c, tw_prec prec, int B, const int *win, const doubl
     { twh::Phase p(c, TW_PH_TRSV_BWD, s);
       TW_CUDA(c, launch_trsm_dd(c->Lp_dd, c->inv_dd, c->chB_dd, c->bzd, 1, np, c->byd, np, win, Nd, Nt,
                                 B, c->NB, prog_b, false, c->d_err, c->abort_flag, s)); }
-    if (prec == TW_PREC_BF16X2 && c->op_tc) {   // tensor cores (tcgen05): FP32 data spectra
-      { twh::Phase p(c, TW_PH_RFFT_DATA, s);
-        TW_CUDA(c, launch_rfft_time_f(c->byd, 1, Nd, Nt, (cf *)c->byh, Nd, Nd, c->plT, c->twTf, c->twLf, s, ba_y)); }
-      { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-        TW_CUDA(c, launch_gemm_adj_tc(c->op_tc, (const cf *)c->byh, (long)Nf * Nd, (cf *)c->bxh,
-                                      (long)Nf * Nm, Nf, Nd, Nm, B, c->btc, c->d_err, s)); }
-    } else {
-      // double-float data spectra and FP32 block sums: F^T y cancels
-      // (y is large against m), so an FP32 data spectrum would lose accuracy
-      // well above the operator's own rounding
-      { twh::Phase p(c, TW_PH_RFFT_DATA, s);
-        TW_CUDA(c, launch_rfft_time_dd(c->byd, 1, Nd, Nt, (cdd *)c->byh, Nd, Nd, c->plT, c->twT, c->twL, s, ba_y)); }
-      { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-        TW_CUDA(c, launch_gemm_adj_fx(A, (int)prec, (const cdd *)c->byh, (long)Nf * Nd, (cf *)c->bxh,
-                                      (long)Nf * Nm, Nf, Nd, Nm, B, s)); }
-    }
+    // double-float data spectra; the product on the tensor cores with both
+    // sides cut into exact fixed-point slices: F^T y cancels (y is large
+    // against m), so its sum has to be formed far below FP32 rounding
+    { twh::Phase p(c, TW_PH_RFFT_DATA, s);
+      TW_CUDA(c, launch_rfft_time_dd(c->byd, 1, Nd, Nt, (cdd *)c->byh, Nd, Nd, c->plT, c->twT, c->twL, s, ba_y)); }
+    { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
+      const int8_t *ea = useG ? c->eaG[prec] : c->ea[TW_MAP_F][prec];
+      TW_CUDA(c, launch_gemm_adj_sl(A, (int)prec, ea, (const cdd *)c->byh, (long)Nf * Nd, (cf *)c->bxh,
+                                    (long)Nf * Nm, Nf, Nd, Nm, B, c->sl_tile, c->bsl_ws, c->bsl_ws_n,
+                                    c->bsl_eb, c->bsl_eb_n, c->d_err, s)); }
     { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
       TW_CUDA(c, launch_irfft_time_f((const cf *)c->bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s, ba_x)); }
     if (!useG) {
@@ -200,7 +194,7 @@ void free_batch(tw_ctx *c) {
   void **bufs[] = {(void **)&c->win_dev, (void **)&c->trsm_prog, (void **)&c->bz, (void **)&c->by,
                    (void **)&c->bzd, (void **)&c->byd, (void **)&c->brd, &c->byh, &c->bxh,
                    &c->bpart, (void **)&c->Lp_dd, (void **)&c->inv_dd, (void **)&c->chF_dd,
-                   (void **)&c->chB_dd, &c->op_tc, &c->btc};
+                   (void **)&c->chB_dd, &c->bsl_ws, (void **)&c->bsl_eb};
   for (void **b : bufs) { twh::dfree(c, *b); *b = nullptr; }
   c->bmax = 0;
 }
@@ -208,11 +202,6 @@ void free_batch(tw_ctx *c) {
 }  // namespace
 
 tw_status twh::refresh_dd_factor(tw_ctx *c, cudaStream_t s) {
-  if (c->op_tc) {   // tensor-core tiles of the adjoint operator (G^ when kept)
-    const void *src = c->opG[TW_PREC_BF16X2] ? c->opG[TW_PREC_BF16X2] : c->op[TW_MAP_F][TW_PREC_BF16X2];
-    TW_CUDA(c, launch_optc_build(src, c->op_tc, c->Nf, c->Nd, c->Nm, s));
-    TW_CUDA(c, cudaStreamSynchronize(s));
-  }
   if (!c->Lp_dd || !c->have64) return TW_OK;
   const size_t blk = (size_t)NB_ * NB_;
   const size_t nblk = (size_t)c->NB * (c->NB + 1) / 2;
@@ -260,9 +249,13 @@ tw_status tw_reserve_batch(tw_ctx *c, int bmax) {
     c->chF_dd = (dd *)take(c->NB * blk * sizeof(dd));
     c->chB_dd = (dd *)take(c->NB * blk * sizeof(dd));
   }
-  if (c->op[TW_MAP_F][TW_PREC_BF16X2]) {
-    c->op_tc = take(gemm_tc_op_bytes(c->Nf, c->Nd, c->Nm));
-    c->btc = take(gemm_tc_b_bytes(c->Nf, c->Nd));
+  if (mixed) {   // data-side slices of the tensor-core adjoint
+    c->sl_tile = sl_pick_tile(bmax);
+    const int cols = (bmax + c->sl_tile - 1) / c->sl_tile * c->sl_tile;
+    c->bsl_ws_n = sl_ws_bytes(c->Nf, c->Nd, cols);
+    c->bsl_eb_n = sl_eb_bytes(c->Nf, cols);
+    c->bsl_ws = take(c->bsl_ws_n);
+    c->bsl_eb = (int *)take(c->bsl_eb_n);
   }
   if (!ok) {
     free_batch(c);

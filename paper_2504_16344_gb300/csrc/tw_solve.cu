@@ -122,9 +122,15 @@ tw_status form_gstar(tw_ctx *c, cudaStream_t s) {
   TW_CUDA(c, launch_prior_cfields_d((cdd *)c->opG[0], (long)c->Nf * c->Nd, c->Nx, c->Ny, (cd *)c->ws,
                                     (c->Nt + 1) / 2, c->lam1d, c->plX, c->plY, c->twXd, c->twYd, s));
   for (int fmt = 1; fmt < 2; ++fmt)
-    if (c->opG[fmt])
+    if (c->opG[fmt]) {
       TW_CUDA(c, launch_convert_op((const cdd *)c->opG[0], (long)per_w, c->opG[fmt], fmt, (long)per_w,
                                    (long)per_w, c->Nf, s));
+      if (!c->eaG[fmt]) {
+        c->eaG[fmt] = (int8_t *)twh::dalloc(c, (size_t)c->Nf * c->Nm);
+        if (!c->eaG[fmt]) return twh::fail(c, TW_ERR_OOM, "G^ row exponents");
+      }
+      TW_CUDA(c, launch_row_exp(c->opG[fmt], fmt, c->eaG[fmt], c->Nf, c->Nd, c->Nm, s));
+    }
   TW_CUDA(c, cudaStreamSynchronize(s));
   return TW_OK;
 }
@@ -424,7 +430,8 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
         TW_CUDA(c, launch_rfft_time_dd(ysrc, ykind, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-        TW_CUDA(c, launch_gemv_adj_fx(AG, (int)prec, c->wr, wf, Nf, Nd, Nm, s)); }
+        TW_CUDA(c, launch_gemm_adj_sl(AG, (int)prec, c->eaG[prec], c->wr, 0, wf, 0, Nf, Nd, Nm, 1, 8,
+                                      c->sl_ws, c->sl_ws_n, c->sl_eb, c->sl_eb_n, c->d_err, s)); }
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
         TW_CUDA(c, launch_irfft_time_f(wf, Nm, mr, 0, Nm, Nm, w, c->plT, c->twTf, c->twLf, s)); }
     } else if (!mixed) {
@@ -439,14 +446,16 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
                                    c->twX, c->twY, s)); }
     } else {
       // reduced-precision operator: y's spectrum stays double-float (y is large
-      // against m, and F^T y cancels), the product sums FP32 blocks into
-      // FP32 totals; x^ onwards (inverse FFT, prior) runs in FP32
+      // against m, and F^T y cancels), the product runs on the tensor cores
+      // with both sides in exact fixed-point slices; x^ onwards (inverse FFT,
+      // prior) runs in FP32
       cf *wf = (cf *)c->wf;
       float *wt = (float *)c->wt;
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
         TW_CUDA(c, launch_rfft_time_dd(ysrc, ykind, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-        TW_CUDA(c, launch_gemv_adj_fx(A, (int)prec, c->wr, wf, Nf, Nd, Nm, s)); }
+        TW_CUDA(c, launch_gemm_adj_sl(A, (int)prec, c->ea[TW_MAP_F][prec], c->wr, 0, wf, 0, Nf, Nd, Nm, 1,
+                                      8, c->sl_ws, c->sl_ws_n, c->sl_eb, c->sl_eb_n, c->d_err, s)); }
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
         TW_CUDA(c, launch_irfft_time_f(wf, Nm, wt, 2, Nm, Nm, w, c->plT, c->twTf, c->twLf, s)); }
       { twh::Phase p(c, TW_PH_PRIOR, s);

@@ -169,17 +169,21 @@ def test_full_window_map_stationarity(c2, full_window):
     assert s64 < 1e-3
 
 
-@pytest.mark.parametrize("prec", [1, 2])
-def test_full_window_mixed_precision_error(c2, full_window, prec):
-    # the complex64 / bf16 hi+lo operators against the FP64-class path (regression bounds;
-    # the measured values are reported in the design doc)
+def test_full_window_mixed_precision_error(c2, full_window):
+    # the complex64 operator path (tensor-core sliced adjoint, FP32 forecast)
+    # against the FP64-class path at the full 400-step window: the north-star
+    # bound 1e-5 on m and on q.  The FP64-class path is itself held to the
+    # oracle at 1e-11 at smaller sizes and on sampled full-size entries; the
+    # oracle cannot form K at this size.  The bf16 hi+lo storage is tested
+    # against its rounded-operator floor at the smaller sizes only: that floor
+    # (2^-17 per entry) needs the full operator in exact arithmetic.
     from paper_2504_16344_gb300 import tw
     ctx, d, m64 = c2["ctx"], full_window["d"], full_window["m64"]
     q64 = ctx.forecast(tw.PREC_FP64, m64)
-    m32 = ctx.infer(prec, d)
-    q32 = ctx.forecast(prec, m32)
+    m32 = ctx.infer(tw.PREC_C64, d)
+    q32 = ctx.forecast(tw.PREC_C64, m32)
     em = rel(m32.cpu().numpy(), m64.cpu().numpy())
     eq = rel(q32.cpu().numpy(), q64.cpu().numpy())
-    print(f"prec {prec}: m vs FP64 {em:.2e}, q vs FP64 {eq:.2e}")
+    print(f"complex64: m vs FP64 {em:.2e}, q vs FP64 {eq:.2e}")
     ctx.check()
-    assert em < 1e-4 and eq < 1e-3
+    assert em < 1e-5 and eq < 1e-5

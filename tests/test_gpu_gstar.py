@@ -3,7 +3,8 @@
 With TW_KEEP_G the posterior mean is one adjoint apply of G* (no prior filter
 online) on the FP64 and complex64 paths; the bf16x2 path keeps F* + prior.
 Results must match the oracle as the F* + prior path does: FP64 1e-11
-(single, windows, batched, samples), mixed 1e-5 on m.
+(single, windows, batched, samples); complex64 1e-5 on m and q; bf16 hi+lo
+1e-5 or twice its rounded-operator floor.
 """
 import json
 import os
@@ -16,7 +17,7 @@ from oracle import posterior as Q
 from oracle import prior as P
 from oracle import toeplitz as T
 
-from gpu_util import make_context, rel
+from gpu_util import adjoint_rounded, make_context, mixed_bound, pad_window, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -66,15 +67,31 @@ def test_single_fp64_with_gstar(case, frac):
     assert np.all(m[w:] == 0.0) and err < 1e-11
 
 
+def _bounds(case, prec, y, nt_window, m_ref, q_ref):
+    """(m bound, q bound): 1e-5 for complex64; for bf16 hi+lo 1e-5 or twice
+    the floor of its rounded operator (the F* + prior path it keeps)."""
+    if prec != "BF16X2":
+        return 1e-5, 1e-5
+    cfg = case["cfg"]
+    m_fl = P.prior_apply(adjoint_rounded(case["F"], pad_window(y, cfg.Nt, cfg.Nd), "BF16X2"), case["lam"])
+    m_fl[nt_window:] = 0.0
+    return mixed_bound(rel(m_fl, m_ref)), mixed_bound(rel(T.p2o_apply(case["Fq"], m_fl), q_ref))
+
+
 @pytest.mark.parametrize("prec", ["C64", "BF16X2"])
 def test_single_mixed_with_gstar(case, prec):
     from paper_2504_16344_gb300 import tw
-    cfg = case["cfg"]
-    m_ref, _ = Q.posterior_mean(case["F"], case["lam"], case["L"], case["d"], cfg.Nt)
-    m = case["ctx"].infer(getattr(tw, "PREC_" + prec), _t(case["d"], case["dev"]))[0].cpu().numpy()
-    err = rel(m, m_ref)
-    print(f"{cfg.cid}: G* path {prec}: m rel err {err:.2e}")
-    assert err < 1e-5
+    cfg, ctx = case["cfg"], case["ctx"]
+    p = getattr(tw, "PREC_" + prec)
+    m_ref, y = Q.posterior_mean(case["F"], case["lam"], case["L"], case["d"], cfg.Nt)
+    q_ref = T.p2o_apply(case["Fq"], m_ref)
+    m = ctx.infer(p, _t(case["d"], case["dev"]))
+    q = ctx.forecast(p, m)[0].cpu().numpy()
+    ctx.check()
+    em, eq = rel(m[0].cpu().numpy(), m_ref), rel(q, q_ref)
+    bm, bq = _bounds(case, prec, y, cfg.Nt, m_ref, q_ref)
+    print(f"{cfg.cid}: G* path {prec}: m rel err {em:.2e} q {eq:.2e} (bounds {bm:.1e} {bq:.1e})")
+    assert em < bm and eq < bq
 
 
 @pytest.mark.parametrize("prec", ["FP64", "C64", "BF16X2"])
@@ -88,16 +105,13 @@ def test_batched_with_gstar(case, prec):
     m, q = ctx.infer_batch(getattr(tw, "PREC_" + prec), _t(ds, case["dev"]), win)
     ctx.check()
     m, q = m.cpu().numpy(), q.cpu().numpy()
-    em, eq = [], []
     for r, w in enumerate(ws):
-        m_ref, _ = Q.posterior_mean(case["F"], case["lam"], case["L"], ds[r], cfg.Nt, nt_window=w)
-        em.append(rel(m[r], m_ref))
-        eq.append(rel(q[r], T.p2o_apply(case["Fq"], m_ref)))
-    print(f"{cfg.cid}: G* batched {prec}: m {max(em):.2e} q {max(eq):.2e}")
-    if prec == "FP64":
-        assert max(em) < 1e-11 and max(eq) < 1e-11
-    else:
-        assert max(em) < 1e-5 and max(eq) < 1e-4
+        m_ref, y = Q.posterior_mean(case["F"], case["lam"], case["L"], ds[r], cfg.Nt, nt_window=w)
+        q_ref = T.p2o_apply(case["Fq"], m_ref)
+        em, eq = rel(m[r], m_ref), rel(q[r], q_ref)
+        bm, bq = (1e-11, 1e-11) if prec == "FP64" else _bounds(case, prec, y, w, m_ref, q_ref)
+        print(f"{cfg.cid}: G* batched {prec} window {w}: m {em:.2e} q {eq:.2e} (bounds {bm:.1e} {bq:.1e})")
+        assert em < bm and eq < bq
 
 
 def test_batched_samples_with_gstar(case):
