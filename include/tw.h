@@ -63,16 +63,17 @@ typedef enum { TW_MAP_F = 0, TW_MAP_FQ = 1 } tw_map;
  *                   arithmetic in double-float (error-free FP32 transforms).
  *                   This is the library's FP64-class path.
  *  TW_PREC_C64    : F^ held as complex64.  Adjoint applies (F^T y, the
- *                   posterior mean's product) run on the tensor cores: y's
- *                   spectrum is taken as float pairs and both it and the
- *                   operator are cut into exact fixed-point bf16 slices
- *                   (per-row / per-column power-of-two scales), so the
- *                   leading terms of the sum accumulate exactly and the
- *                   result carries the operator's own rounding only (y is
- *                   large against m and F^T y cancels; an FP32 sum would
- *                   lose digits by that cancellation).  Forward applies,
- *                   inverse FFTs and the prior run in FP32.  Adjoint applies
- *                   need rows <= 512 (TW_ERR_CUDA beyond).
+ *                   posterior mean's product) take y's spectrum as float
+ *                   pairs and sum without rounding loss, so the result
+ *                   carries the operator's own rounding only (y is large
+ *                   against m and F^T y cancels; an FP32 sum would lose
+ *                   digits by that cancellation): one right-hand side with
+ *                   exact products and double-float running sums, batches
+ *                   on the tensor cores with both sides cut into exact
+ *                   fixed-point bf16 slices (per-row / per-column power-of-
+ *                   two scales, the leading terms accumulated exactly;
+ *                   batched adjoints need rows <= 512, TW_ERR_CUDA beyond).
+ *                   Forward applies, inverse FFTs and the prior run in FP32.
  *  TW_PREC_BF16X2 : F^ held as bf16 hi + bf16 lo per real (8 bytes per
  *                   complex entry, 16-17 significant bits); arithmetic as
  *                   TW_PREC_C64.                                             */
@@ -156,7 +157,10 @@ tw_status tw_p2o_apply(tw_ctx *ctx, tw_map which, tw_prec prec, int nrhs,
 /*
  * tw_p2o_adjoint -- x = F^T y (Euclidean adjoint; y [nrhs][Nt][Nd], x
  * [nrhs][Nt][Nm]) or F_q^T y: x_j = sum_{i>=j} F_{i-j}^T y_i, computed as
- * irfft( F^(w)^H rfft(y)(w) ) truncated to Nt steps.
+ * irfft( F^(w)^H rfft(y)(w) ) truncated to Nt steps.  With a reduced
+ * precision, several right-hand sides and a reserved batch
+ * (tw_reserve_batch), they run as batches of the per-frequency matrix
+ * product on the tensor cores.
  */
 tw_status tw_p2o_adjoint(tw_ctx *ctx, tw_map which, tw_prec prec, int nrhs,
                          const double *y, double *x, void *stream);

@@ -18,14 +18,14 @@ struct tw_ctx {
   // G^ = F^ C per frequency (the paper's G* = Gamma_pr F* of Phase 2), per kept
   // format, when TW_KEEP_G: the adjoint applies of tw_infer then need no prior filter
   void *opG[3] = {nullptr, nullptr, nullptr};
-  // row exponents of the FP32 storages for the sliced tensor-core adjoint:
-  // ea[which][fmt][w][m] (fmt 1, 2), eaG[fmt] for G^ (gemm_sl.cu)
+  // row exponents of the FP32 storages for the batched adjoint on the tensor
+  // cores: ea[which][fmt][w][m] (fmt 1, 2), eaG[fmt] for G^ (gemm_sl.cu)
   int8_t *ea[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
   int8_t *eaG[3] = {nullptr, nullptr, nullptr};
-  // its data-side slices: single right-hand side (sl_*) and batches (bsl_*)
-  void *sl_ws = nullptr, *bsl_ws = nullptr;
-  int *sl_eb = nullptr, *bsl_eb = nullptr;
-  size_t sl_ws_n = 0, bsl_ws_n = 0, sl_eb_n = 0, bsl_eb_n = 0;
+  // its data-side slices and column exponents (tw_reserve_batch)
+  void *bsl_ws = nullptr;
+  int *bsl_eb = nullptr;
+  size_t bsl_ws_n = 0, bsl_eb_n = 0;
   int sl_tile = 0;                   // right-hand sides per tile of the batched product
   std::vector<char> loaded[2];     // per row: loaded?
   // FFT plans and twiddle tables (df64 and float)

@@ -39,15 +39,17 @@
 // within a few units of 2^-30 of the terms: the error left is the rounding
 // of the stored operator itself.  Ten MMAs per 16-wide k step.
 //
-// Kernel: one CTA per (128 grid points, frequency, tile of P right-hand
-// sides); 8 producer warps load the operator (complex64 or bf16 hi+lo),
-// slice it with its row's exponent and write the four 128 x 32 bf16 slice
-// tiles of a stage (K-major, 64-byte swizzle); one thread copies the
-// stage's B' slices (prepared once per call by k_bsl_build) with the bulk
-// copy engine and one thread issues the MMAs (D0, D1, D2 in TMEM: 3N of its
-// columns, so N <= 160).  Two stages, mbarriers with transaction counts,
-// tcgen05.commit frees a stage.  The producers then read D0..D2
-// (tcgen05.ld), scale and store X as complex64.  Every wait is bounded: on expiry the kernel records
+// Kernel: persistent, one CTA per SM looping over (128 grid points,
+// frequency, tile of P right-hand sides); 8 producer warps stream the
+// operator (complex64 or bf16 hi+lo) through a 4-stage cp.async ring (64 KB
+// in flight per SM), slice it with its row's exponent and write the four
+// 128 x 32 bf16 slice tiles of a stage (K-major, 64-byte swizzle); one
+// thread copies the stage's B' slices (prepared once per call by
+// k_bsl_build) with the bulk copy engine and one thread issues the MMAs
+// (D0, D1, D2 in TMEM: 3N of its columns, so N <= 160).  Two slice stages,
+// mbarriers with transaction counts, tcgen05.commit frees a stage.  After a
+// tile's last stage the producers read D0..D2 (tcgen05.ld), scale and store
+// X as complex64, while the ring already holds the next tile's operator.  Every wait is bounded: on expiry the kernel records
 // TW_ERR_TIMEOUT, lets its copies and MMAs drain (bounded), frees TMEM and
 // returns.
 #include <stdint.h>
@@ -62,9 +64,7 @@ namespace {
 constexpr int TM = 128;                  // MMA M: grid points per tile
 constexpr int KA = 32;                   // K' per stage: 16 rows (sensors) x (re, im)
 constexpr int NSL = 4;                   // slices per operand
-constexpr int STAGES = 2;
-constexpr int NPROD = 256;               // producer / epilogue threads (8 warps)
-constexpr int NTHR = NPROD + 32;         // + the MMA warp
+constexpr int NPROD = 256;               // producer threads (8 warps)
 constexpr int A_SLICE = TM * KA * 2;     // 8 KB: one 128 x 32 bf16 slice tile
 constexpr int A_STAGE = NSL * A_SLICE;   // 32 KB
 constexpr unsigned SPIN_LIMIT = 1u << 26;
@@ -272,28 +272,67 @@ __device__ __forceinline__ int pair_i(int p) {
   return p - L * (L + 1) / 2;
 }
 
+// raw-operator ring: RAW_D stages of 16 rows x 128 grid points (8 bytes per
+// entry), each thread's own 8 entries of a stage copied by cp.async
+constexpr int RAW_D = 4;
+constexpr int RAW_STAGE = 16 * TM * 8;   // 16 KB
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src, unsigned bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// the exact FP32 value of an operator entry held as 8 raw bytes
+template <int FMT> __device__ __forceinline__ float2 decode_entry(uint2 v);
+template <> __device__ __forceinline__ float2 decode_entry<FMT_C64>(uint2 v) {
+  return make_float2(__uint_as_float(v.x), __uint_as_float(v.y));
+}
+template <> __device__ __forceinline__ float2 decode_entry<FMT_BF16X2>(uint2 v) {
+  return make_float2(bf16lo(v.x) + bf16hi(v.x), bf16lo(v.y) + bf16hi(v.y));
+}
+
+// Persistent: CTA b takes tiles b, b + gridDim.x, ... of the (grid tile,
+// frequency, right-hand-side tile) space, grid tile fastest (CTAs running at
+// the same time share a frequency, so its B' slices stay in L2).  Atoms
+// (16-row K' stages) are numbered across the CTA's tiles, so the raw ring,
+// the slice stages and their barriers run on without a break between tiles.
+// Warp roles: 0-7 producers, 8 the MMA issuer, 9-12 the epilogue (TMEM lane
+// quarter = warp mod 4).  The accumulators are double-buffered in TMEM when
+// 2 x 3N columns fit (N <= 80): the MMAs of tile i+1 then run while the
+// epilogue drains tile i.
+constexpr int NEPI = 128;                // epilogue threads (4 warps)
+constexpr int NTHR_P = NPROD + 32 + NEPI;
+constexpr int MAXST = 4;                 // slice stages (as many as shared memory allows)
+
 template <int FMT>
-__global__ void __launch_bounds__(NTHR, 1)
+__global__ void __launch_bounds__(NTHR_P, 1)
 k_gemm_adj_sl(const void *__restrict__ A, const int8_t *__restrict__ ea, const uint8_t *__restrict__ Bt,
-              const int *__restrict__ eb, cf *__restrict__ X, long x_bstride, int b0, int B, int P,
-              int ntiles, int Nr, int Nm, int natoms, unsigned tmem_cols, int *err) {
+              const int *__restrict__ eb, cf *__restrict__ X, long x_bstride, int B, int P, int ntiles,
+              int Nr, int Nm, int Nf, int natoms, int S, int nbuf, unsigned tmem_cols, int *err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bars[3 * STAGES + 1];
+  __shared__ __align__(8) uint64_t bars[3 * MAXST + 5];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int mt = blockIdx.x, w = blockIdx.y, nt = blockIdx.z;
   const int N = 2 * P;
+  const int nmt = (Nm + TM - 1) / TM;
+  const int T = nmt * Nf * ntiles;
+  const int my_tiles = (int)blockIdx.x < T ? (T - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const uint32_t b_slice = (uint32_t)N * 64u, b_stage = NSL * b_slice;
   const uint32_t sbase = (su32(smem_raw) + 1023u) & ~1023u;
-  // stage st: A slices at sbase + st * A_STAGE, B slices after all A stages
-  const uint32_t sA0 = sbase, sB0 = sbase + STAGES * A_STAGE;
+  // [raw ring RAW_D x 16 KB][A slices S x 32 KB][B' slices S x b_stage]
+  const uint32_t sRaw = sbase, sA0 = sbase + RAW_D * RAW_STAGE, sB0 = sA0 + S * A_STAGE;
   uint8_t *gbase = smem_raw + (sbase - su32(smem_raw));
   const uint32_t bar0 = su32(&bars[0]);
   auto fullA = [&](int st) { return bar0 + 8u * st; };
-  auto fullB = [&](int st) { return bar0 + 8u * (STAGES + st); };
-  auto empty = [&](int st) { return bar0 + 8u * (2 * STAGES + st); };
-  const uint32_t done = bar0 + 8u * (3 * STAGES);
+  auto fullB = [&](int st) { return bar0 + 8u * (MAXST + st); };
+  auto empty = [&](int st) { return bar0 + 8u * (2 * MAXST + st); };
+  auto tfull = [&](int bf) { return bar0 + 8u * (3 * MAXST + bf); };       // D of a buffer final
+  auto tempty = [&](int bf) { return bar0 + 8u * (3 * MAXST + 2 + bf); };  // D read out
+  const uint32_t drain = bar0 + 8u * (3 * MAXST + 4);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  ::"r"(su32(&tmem_slot)), "r"(tmem_cols) : "memory");
@@ -301,12 +340,16 @@ k_gemm_adj_sl(const void *__restrict__ A, const int8_t *__restrict__ ea, const u
   }
   if (tid == 0) {
     fail = 0;
-    for (int st = 0; st < STAGES; ++st) {
+    for (int st = 0; st < S; ++st) {
       mbar_init(fullA(st), NPROD);
       mbar_init(fullB(st), 1);
       mbar_init(empty(st), 1);
     }
-    mbar_init(done, 1);
+    for (int bf = 0; bf < 2; ++bf) {
+      mbar_init(tfull(bf), 1);
+      mbar_init(tempty(bf), NEPI);
+    }
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -314,88 +357,175 @@ k_gemm_adj_sl(const void *__restrict__ A, const int8_t *__restrict__ ea, const u
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
   volatile int *vfail = &fail;
-  const uint8_t *Bw = Bt + ((size_t)w * ntiles + nt) * natoms * b_stage;
+  auto tile_of = [&](int i, int &mt, int &w, int &nt) {
+    const int t = (int)blockIdx.x + i * (int)gridDim.x;
+    mt = t % nmt;
+    w = (t / nmt) % Nf;
+    nt = t / (nmt * Nf);
+  };
 
   if (warp < NPROD / 32) {
-    // ---------------- producers: operator slices, then the epilogue
+    // ---------------- producers: operator slices
     const int r = tid & (TM - 1), h = tid >> 7;
-    const int m = mt * TM + r;
-    const bool vm = m < Nm;
-    const int e_a = vm ? (int)ea[(size_t)w * Nm + m] : EXP_MIN;
-    const float sc = pow2f(7 - e_a);
-    const size_t abase = (size_t)w * Nr * Nm + (size_t)m;
-    int issued = 0;                       // B copies issued by thread 0
-    float2 cur[8], nxt[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int s = 8 * h + u;
-      cur[u] = (vm && s < Nr) ? ld_entry<FMT>(A, abase + (size_t)s * Nm) : make_float2(0.f, 0.f);
-    }
-    for (int a = 0; a < natoms; ++a) {
-      const int st = a % STAGES;
-      if (a + 1 < natoms) {
+    // the issue pointer runs RAW_D - 1 atoms ahead of the consumer: its tile
+    // (local index, grid row offset) and atom, advanced without divisions
+    int ii = 0, ia = 0;
+    size_t ibase = 0;                                 // entry offset of (w, row 8h, grid point m)
+    bool ivalid = false;
+    auto set_issue_tile = [&](int i) {
+      if (i >= my_tiles) return;
+      int mt, w, nt;
+      tile_of(i, mt, w, nt);
+      const int m = mt * TM + r;
+      ivalid = m < Nm;
+      ibase = ((size_t)w * Nr + 8 * h) * Nm + (size_t)m;
+    };
+    set_issue_tile(0);
+    int islot = 0;
+    auto issue = [&]() {
+      if (ii < my_tiles) {
+        const uint32_t dst = sRaw + (uint32_t)islot * RAW_STAGE + (uint32_t)tid * 8u;
+        const int s0 = 16 * ia + 8 * h;
+        const uint8_t *src0 = reinterpret_cast<const uint8_t *>(A) + (ibase + (size_t)16 * ia * Nm) * 8;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const int s = 16 * (a + 1) + 8 * h + u;
-          nxt[u] = (vm && s < Nr) ? ld_entry<FMT>(A, abase + (size_t)s * Nm) : make_float2(0.f, 0.f);
+          const bool ok = ivalid && s0 + u < Nr;
+          cp_async8(dst + (uint32_t)u * (NPROD * 8u), ok ? src0 + (size_t)u * Nm * 8 : (const uint8_t *)A,
+                    ok ? 8u : 0u);
         }
+        if (++ia == natoms) { ia = 0; set_issue_tile(++ii); }
       }
-      if (a >= STAGES && !mbar_wait(empty(st), (unsigned)((a / STAGES - 1) & 1), vfail)) {
-        if (atomicCAS(err, 0, TW_ERR_TIMEOUT) == 0) err[1] = 21;
+      cp_async_commit();
+      islot = (islot + 1) & (RAW_D - 1);
+    };
+#pragma unroll
+    for (int g = 0; g < RAW_D - 1; ++g) issue();
+    int issued = 0;                                  // B' copies issued by thread 0
+    int st = 0, use = 0, slot = 0;                   // slice stage, its use count, raw slot
+    bool ok = true;
+    for (int i = 0; i < my_tiles && ok; ++i) {
+      int mt, w, nt;
+      tile_of(i, mt, w, nt);
+      const int m = mt * TM + r;
+      const float sc = pow2f(7 - (m < Nm ? (int)ea[(size_t)w * Nm + m] : EXP_MIN));
+      const uint8_t *Bw = Bt + ((size_t)w * ntiles + nt) * natoms * b_stage;
+      for (int a = 0; a < natoms; ++a) {
+        issue();
+        cp_async_wait<RAW_D - 1>();                  // this atom's entries have landed
+        const uint8_t *raw = gbase + (size_t)slot * RAW_STAGE + (size_t)tid * 8;
+        slot = (slot + 1) & (RAW_D - 1);
+        float v[16];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float2 e = decode_entry<FMT>(*reinterpret_cast<const uint2 *>(raw + u * (NPROD * 8)));
+          v[2 * u] = e.x * sc;
+          v[2 * u + 1] = e.y * sc;
+        }
+        if (use > 0 && !mbar_wait(empty(st), (unsigned)((use - 1) & 1), vfail)) {
+          if (!*vfail && atomicCAS(err, 0, TW_ERR_TIMEOUT) == 0) err[1] = 21;
+          fail = 1;
+          ok = false;
+          break;
+        }
+        if (tid == 0) {
+          mbar_arrive_tx(fullB(st), b_stage);
+          bulk_g2s(sB0 + st * b_stage, Bw + (size_t)a * b_stage, b_stage, fullB(st));
+          ++issued;
+        }
+        uint8_t *sa = gbase + RAW_D * RAW_STAGE + (size_t)st * A_STAGE;
+        // slice i = v rounded to the grid 2^-8i (v - slices so far, exact):
+        // (x + 1.5 2^(23-8i)) - 1.5 2^(23-8i) rounds x to a multiple of 2^-8i
+#pragma unroll
+        for (int il = 0; il < NSL; ++il) {
+          const float M = pow2f(23 - 8 * il) * 1.5f;
+          uint32_t wd[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float s0 = __fsub_rn(__fadd_rn(v[2 * u], M), M);
+            const float s1 = __fsub_rn(__fadd_rn(v[2 * u + 1], M), M);
+            wd[u] = pack_bf16(s0, s1);
+            if (il + 1 < NSL) {
+              v[2 * u] = __fsub_rn(v[2 * u], s0);
+              v[2 * u + 1] = __fsub_rn(v[2 * u + 1], s1);
+            }
+          }
+          uint8_t *tile = sa + il * A_SLICE;
+          *reinterpret_cast<uint4 *>(tile + swz64(r, 2 * h)) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+          *reinterpret_cast<uint4 *>(tile + swz64(r, 2 * h + 1)) = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+        }
+        // generic-proxy writes -> visible to the tensor cores (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(fullA(st));
+        if (++st == S) { st = 0; ++use; }
+      }
+    }
+    cp_async_wait<0>();                              // own copies drained before exit
+    if (tid == 0 && *vfail) {
+      // bulk copies already issued must land before the CTA's shared memory goes
+      for (int a = (issued > S ? issued - S : 0); a < issued; ++a)
+        mbar_drain(fullB(a % S), (unsigned)((a / S) & 1));
+    }
+  } else if (warp == NPROD / 32) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      const uint32_t idesc = idesc_bf16(TM, N);
+      bool ok = true;
+      int st = 0, use = 0;
+      for (int i = 0; i < my_tiles && ok; ++i) {
+        const int bf = i % nbuf;
+        // the epilogue has read this buffer's previous tile
+        if (i >= nbuf && !mbar_wait(tempty(bf), (unsigned)((i / nbuf - 1) & 1), vfail)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dbase = tmem + (uint32_t)(bf * 3 * N);
+        for (int a = 0; a < natoms; ++a) {
+          const unsigned par = (unsigned)(use & 1);
+          ok = mbar_wait(fullA(st), par, vfail) && mbar_wait(fullB(st), par, vfail);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t aS = sA0 + st * A_STAGE, bS = sB0 + st * b_stage;
+#pragma unroll
+          for (int ks = 0; ks < KA / 16; ++ks) {
+#pragma unroll
+            for (int p = 0; p < 10; ++p) {
+              const int si = pair_i(p), sj = pair_level(p) - pair_i(p);
+              const uint64_t ad = sdesc64(aS + si * A_SLICE + ks * 32);
+              const uint64_t bd = sdesc64(bS + sj * b_slice + ks * 32);
+              const int L = pair_level(p);
+              const uint32_t dcol = (uint32_t)((L < 2 ? L : 2) * N);
+              // the first MMA of a tile into each accumulator (p = 0, 1, 3) overwrites it
+              const uint32_t acc = (a > 0 || ks > 0 || (p != 0 && p != 1 && p != 3)) ? 1u : 0u;
+              mma_bf16(dbase + dcol, ad, bd, idesc, acc);
+            }
+          }
+          mma_commit(empty(st));             // stage reusable once these MMAs finish
+          if (++st == S) { st = 0; ++use; }
+        }
+        if (ok) mma_commit(tfull(bf));       // this tile's D final
+      }
+      if (!ok && !*vfail && atomicCAS(err, 0, TW_ERR_TIMEOUT) == 0) err[1] = 23;
+      if (!ok) fail = 1;
+      // every issued MMA complete before TMEM is released
+      mma_commit(drain);
+      mbar_drain(drain, 0);
+    }
+  } else {
+    // ---------------- epilogue: (D0 + D1) + D2 from TMEM, scaled, complex64 out
+    const int lg = warp & 3;                          // TMEM lanes 32 lg .. 32 lg + 31
+    const int r = 32 * lg + lane;
+    for (int i = 0; i < my_tiles; ++i) {
+      int mt, w, nt;
+      tile_of(i, mt, w, nt);
+      const int bf = i % nbuf;
+      if (!mbar_wait(tfull(bf), (unsigned)((i / nbuf) & 1), vfail) || *vfail) {
+        if (!*vfail && atomicCAS(err, 0, TW_ERR_TIMEOUT) == 0) err[1] = 22;
         fail = 1;
         break;
       }
-      if (tid == 0) {
-        mbar_arrive_tx(fullB(st), b_stage);
-        bulk_g2s(sB0 + st * b_stage, Bw + (size_t)a * b_stage, b_stage, fullB(st));
-        ++issued;
-      }
-      uint8_t *sa = gbase + (size_t)st * A_STAGE;
-      float v[16];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) { v[2 * u] = cur[u].x * sc; v[2 * u + 1] = cur[u].y * sc; }
-#pragma unroll
-      for (int i = 0; i < NSL; ++i) {
-        const float p2 = pow2f(-8 * i);
-        uint32_t wd[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const float s0 = rnd_int(v[2 * u]), s1 = rnd_int(v[2 * u + 1]);
-          wd[u] = pack_bf16(s0 * p2, s1 * p2);
-          if (i + 1 < NSL) {   // remainders, exact: (v - s) * 256
-            v[2 * u] = __fmul_rn(__fsub_rn(v[2 * u], s0), 256.f);
-            v[2 * u + 1] = __fmul_rn(__fsub_rn(v[2 * u + 1], s1), 256.f);
-          }
-        }
-        uint8_t *tile = sa + i * A_SLICE;
-        *reinterpret_cast<uint4 *>(tile + swz64(r, 2 * h)) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-        *reinterpret_cast<uint4 *>(tile + swz64(r, 2 * h + 1)) = make_uint4(wd[4], wd[5], wd[6], wd[7]);
-      }
-      // generic-proxy writes -> visible to the tensor cores (async proxy)
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(fullA(st));
-#pragma unroll
-      for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
-    }
-    // ---------------- epilogue: (D0 + D1) + D2 from TMEM, scaled, complex64 out
-    const bool ok = mbar_wait(done, 0, vfail);
-    if (!ok && !*vfail) {
-      if (atomicCAS(err, 0, TW_ERR_TIMEOUT) == 0) err[1] = 22;
-      fail = 1;
-    }
-    if (tid == 0 && *vfail) {
-      // copies already issued must land before the CTA's shared memory goes
-      for (int a = (issued > STAGES ? issued - STAGES : 0); a < issued; ++a)
-        mbar_drain(fullB(a % STAGES), (unsigned)((a / STAGES) & 1));
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok && !*vfail) {
-      const int lg = warp & 3;                        // TMEM lanes 32 lg .. 32 lg + 31
-      // TMEM lane 32 lg + lane is this thread's own operator row r (tid mod 128)
-      const int mrow = mt * TM + 32 * lg + lane;
-      const float sa = pow2f(e_a - 7);
-      const uint32_t trow = tmem + ((uint32_t)(32 * lg) << 16);
-      for (int c0 = 8 * (warp >> 2); c0 < P; c0 += 16) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int m = mt * TM + r;
+      const float sa = pow2f((m < Nm ? (int)ea[(size_t)w * Nm + m] : EXP_MIN) - 7);
+      const uint32_t trow = tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(bf * 3 * N);
+      for (int c0 = 0; c0 < P; c0 += 8) {
         uint32_t d0r[8], d0i[8], d1r[8], d1i[8], d2r[8], d2i[8];
 #define TW_LD8(dst, col)                                                                       \
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"          \
@@ -410,55 +540,27 @@ k_gemm_adj_sl(const void *__restrict__ A, const int8_t *__restrict__ ea, const u
         TW_LD8(d2i, 2 * N + P + c0);
 #undef TW_LD8
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (mrow < Nm) {
+        if (c0 + 8 >= P) {
+          // the buffer is read: the MMAs of a later tile may overwrite it
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          mbar_arrive(tempty(bf));
+        }
+        if (m < Nm) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const int bl = c0 + j, b = nt * P + bl;
+            const int b = nt * P + c0 + j;
             if (b < B) {
               const float sb = pow2f(eb[(size_t)w * ntiles * P + b] - 7);
               const float re = __fadd_rn(__fadd_rn(__uint_as_float(d0r[j]), __uint_as_float(d1r[j])),
                                          __uint_as_float(d2r[j])) * sa * sb;
               const float im = __fadd_rn(__fadd_rn(__uint_as_float(d0i[j]), __uint_as_float(d1i[j])),
                                          __uint_as_float(d2i[j])) * sa * sb;
-              X[(size_t)(b0 + b) * x_bstride + (size_t)w * Nm + mrow] = cf_make(re, im);
+              X[(size_t)b * x_bstride + (size_t)w * Nm + m] = cf_make(re, im);
             }
           }
         }
       }
     }
-  } else if (lane == 0) {
-    // ---------------- MMA issuer
-    const uint32_t idesc = idesc_bf16(TM, N);
-    bool ok = true;
-    for (int a = 0; a < natoms && ok; ++a) {
-      const int st = a % STAGES;
-      const unsigned par = (unsigned)((a / STAGES) & 1);
-      ok = mbar_wait(fullA(st), par, vfail) && mbar_wait(fullB(st), par, vfail);
-      if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t aS = sA0 + st * A_STAGE, bS = sB0 + st * b_stage;
-#pragma unroll
-      for (int ks = 0; ks < KA / 16; ++ks) {
-#pragma unroll
-        for (int p = 0; p < 10; ++p) {
-          const int i = pair_i(p), j = pair_level(p) - pair_i(p);
-          const uint64_t ad = sdesc64(aS + i * A_SLICE + ks * 32);
-          const uint64_t bd = sdesc64(bS + j * b_slice + ks * 32);
-          const int L = pair_level(p);
-          const uint32_t dcol = (uint32_t)((L < 2 ? L : 2) * N);
-          // the first MMA into each accumulator (p = 0, 1, 3) overwrites it
-          const uint32_t acc = (a > 0 || ks > 0 || (p != 0 && p != 1 && p != 3)) ? 1u : 0u;
-          mma_bf16(tmem + dcol, ad, bd, idesc, acc);
-        }
-      }
-      mma_commit(empty(st));                 // stage reusable once these MMAs finish
-    }
-    if (!ok) {
-      if (!*vfail && atomicCAS(err, 0, TW_ERR_TIMEOUT) == 0) err[1] = 23;
-      fail = 1;
-    }
-    mma_commit(done);                        // D final (or: every issued MMA drained)
-    mbar_drain(done, 0);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -517,18 +619,31 @@ cudaError_t launch_gemm_adj_sl(const void *A, int fmt, const int8_t *ea, const c
   k_bsl_build<<<dim3(Nf, ntiles), 256, 0, s>>>(Y, y_bstride, Nr, B, P, natoms,
                                                reinterpret_cast<uint8_t *>(ws), eb, ntiles);
   count_launches(1);
+  // TMEM: three accumulators of N columns, twice when 6N columns fit
+  const int nbuf = 6 * N <= 512 ? 2 : 1;
   unsigned cols = 32;
-  while ((int)cols < 3 * N) cols <<= 1;
-  const size_t sm = 1024 + STAGES * ((size_t)A_STAGE + (size_t)NSL * N * 64);
-  const dim3 grid((Nm + TM - 1) / TM, Nf, ntiles);
+  while ((int)cols < nbuf * 3 * N) cols <<= 1;
+  // slice stages: as many (up to 4) as 227 KB of shared memory allows
+  const size_t fixed = 1024 + (size_t)RAW_D * RAW_STAGE, per_stage = (size_t)A_STAGE + (size_t)NSL * N * 64;
+  int S = MAXST;
+  while (S > 2 && fixed + S * per_stage > 227u * 1024u) --S;
+  const size_t sm = fixed + S * per_stage;
+  // persistent: one CTA per SM (the shared memory allows no second one)
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long tiles = (long)((Nm + TM - 1) / TM) * Nf * ntiles;
+  const unsigned grid = (unsigned)(tiles < nsm ? tiles : (nsm > 0 ? nsm : 1));
   if (fmt == FMT_C64) {
     cudaFuncSetAttribute(k_gemm_adj_sl<FMT_C64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gemm_adj_sl<FMT_C64><<<grid, NTHR, sm, s>>>(A, ea, reinterpret_cast<const uint8_t *>(ws), eb, X,
-                                                  x_bstride, 0, B, P, ntiles, Nr, Nm, natoms, cols, err);
+    k_gemm_adj_sl<FMT_C64><<<grid, NTHR_P, sm, s>>>(A, ea, reinterpret_cast<const uint8_t *>(ws), eb, X,
+                                                    x_bstride, B, P, ntiles, Nr, Nm, Nf, natoms, S, nbuf,
+                                                    cols, err);
   } else {
     cudaFuncSetAttribute(k_gemm_adj_sl<FMT_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_gemm_adj_sl<FMT_BF16X2><<<grid, NTHR, sm, s>>>(A, ea, reinterpret_cast<const uint8_t *>(ws), eb, X,
-                                                     x_bstride, 0, B, P, ntiles, Nr, Nm, natoms, cols, err);
+    k_gemm_adj_sl<FMT_BF16X2><<<grid, NTHR_P, sm, s>>>(A, ea, reinterpret_cast<const uint8_t *>(ws), eb,
+                                                       X, x_bstride, B, P, ntiles, Nr, Nm, Nf, natoms, S,
+                                                       nbuf, cols, err);
   }
   count_launches(1);
   return cudaGetLastError();

@@ -15,8 +15,9 @@
 //
 // The FP64-class path reads float-pair entries (16 B) and accumulates with
 // exact products and a compensated running sum; the reduced-precision
-// paths read complex64 or bf16 hi+lo entries (8 B) and the forward product
-// sums in FP32 (their adjoint runs on the tensor cores: gemm_sl.cu).
+// paths read complex64 or bf16 hi+lo entries (8 B): the forward product
+// sums in FP32; the adjoint of one right-hand side forms exact products and
+// a double-float running sum (several right-hand sides: gemm_sl.cu).
 #include "kernels.h"
 
 namespace tw {
@@ -100,6 +101,114 @@ k_gemv_adj_dd(const float4 *__restrict__ A, const cdd *__restrict__ yh, cdd *__r
     r.re = dacc_get(re[j]);
     r.im = dacc_get(im[j]);
     st_cdd(xh + (size_t)w * Nm + kb + 256 * j, r);
+  }
+}
+
+// ----------------------------------------- adjoint, FP32 operator, one RHS
+// Reduced-precision adjoint for ONE right-hand side: the complex64 (or bf16
+// hi+lo) operator times y's double-float spectrum, summed without rounding
+// loss.  F^T y cancels (y = K^-1 d is large against m), so a plain FP32 sum
+// of the terms would lose digits by that cancellation.  Each product of an
+// operator entry a and y_hi is made exact (p + e = a y_hi by FMA), the large
+// parts p are added to a running sum with TwoSum (Knuth) and the rounding
+// errors, e, and the a y_lo terms are gathered in FP32 side sums: the result
+// is the exact product of the rounded operator with y to about 2^-44 of the
+// terms.  The real and imaginary parts of one grid point travel together in
+// packed FP32 pairs (add/mul/fma.rn.f32x2), which halves the instruction
+// count: the kernel streams the 8-byte operator at HBM speed.
+struct f2 { unsigned long long v; };
+__device__ __forceinline__ f2 f2_make(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 f2_split(f2 a) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a.v));
+  return r;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { f2 r; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v)); return r; }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { f2 r; asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v)); return r; }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { f2 r; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v)); return r; }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 r; asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v)); return r;
+}
+
+// y row s as the packed operands of the kernel below: with yr, yi float pairs,
+//   Y1 = (yr, yi)   (x ar -> the ar terms of Re, Im)
+//   Y2 = (yi, -yr)  (x ai -> the ai terms)
+// high parts, their negations (exact products via FMA) and low parts
+struct AdjRow { f2 y1, y1n, y1l, y2, y2n, y2l; };
+
+__device__ __forceinline__ void acc_two_sum(f2 &S, f2 &C, f2 pn) {
+  // S + p with p = -pn: s = S - pn, exact error err = (S - (s - bb)) - (pn + bb)
+  const f2 s = sub2(S, pn);
+  const f2 bb = sub2(s, S);
+  const f2 err = sub2(sub2(S, sub2(s, bb)), add2(pn, bb));
+  S = s;
+  C = add2(C, err);
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(256)
+k_gemv_adj_cx(const void *__restrict__ A, const cdd *__restrict__ yh, cf *__restrict__ xh, int Nr,
+              int Nm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  AdjRow *sy = reinterpret_cast<AdjRow *>(smem_raw);
+  const int w = blockIdx.y;
+  const size_t base = (size_t)w * Nr * Nm;
+  for (int s = threadIdx.x; s < Nr; s += blockDim.x) {
+    const cdd y = ld_cdd(yh + (size_t)w * Nr + s);
+    AdjRow r;
+    r.y1 = f2_make(y.re.hi, y.im.hi);
+    r.y1n = f2_make(-y.re.hi, -y.im.hi);
+    r.y1l = f2_make(y.re.lo, y.im.lo);
+    r.y2 = f2_make(y.im.hi, -y.re.hi);
+    r.y2n = f2_make(-y.im.hi, y.re.hi);
+    r.y2l = f2_make(y.im.lo, -y.re.lo);
+    sy[s] = r;
+  }
+  __syncthreads();
+  const int kb = blockIdx.x * (256 * ADJ_KPT) + threadIdx.x;
+  f2 S[ADJ_KPT], C[ADJ_KPT], L[ADJ_KPT];
+  bool ok[ADJ_KPT];
+#pragma unroll
+  for (int j = 0; j < ADJ_KPT; ++j) {
+    S[j] = f2_make(0.f, 0.f); C[j] = S[j]; L[j] = S[j];
+    ok[j] = kb + 256 * j < Nm;
+  }
+  // rows s+1 and s+2 in flight while row s is used (8-byte entries)
+  cf cur[ADJ_KPT], nx1[ADJ_KPT], nx2[ADJ_KPT];
+#pragma unroll
+  for (int j = 0; j < ADJ_KPT; ++j) {
+    cur[j] = ok[j] ? ld_op_f<FMT>(A, base + kb + 256 * j) : cf_zero();
+    nx1[j] = (ok[j] && Nr > 1) ? ld_op_f<FMT>(A, base + (size_t)Nm + kb + 256 * j) : cf_zero();
+  }
+  for (int s = 0; s < Nr; ++s) {
+    if (s + 2 < Nr) {
+      const size_t row = base + (size_t)(s + 2) * Nm + kb;
+#pragma unroll
+      for (int j = 0; j < ADJ_KPT; ++j) nx2[j] = ok[j] ? ld_op_f<FMT>(A, row + 256 * j) : cf_zero();
+    }
+    const AdjRow y = sy[s];
+#pragma unroll
+    for (int j = 0; j < ADJ_KPT; ++j) {
+      // conj(a) y = ar (yr, yi) + ai (yi, -yr)
+      const f2 a1 = f2_make(cur[j].re, cur[j].re), a2 = f2_make(cur[j].im, cur[j].im);
+      const f2 p1n = mul2(a1, y.y1n), p2n = mul2(a2, y.y2n);      // -(a y_hi), rounded
+      const f2 e1 = fma2(a1, y.y1, p1n), e2 = fma2(a2, y.y2, p2n); // their exact errors
+      acc_two_sum(S[j], C[j], p1n);
+      acc_two_sum(S[j], C[j], p2n);
+      L[j] = add2(fma2(a2, y.y2l, fma2(a1, y.y1l, L[j])), add2(e1, e2));
+    }
+#pragma unroll
+    for (int j = 0; j < ADJ_KPT; ++j) { cur[j] = nx1[j]; nx1[j] = nx2[j]; }
+  }
+#pragma unroll
+  for (int j = 0; j < ADJ_KPT; ++j) {
+    if (!ok[j]) continue;
+    const float2 r = f2_split(add2(S[j], add2(C[j], L[j])));
+    xh[(size_t)w * Nm + kb + 256 * j] = cf_make(r.x, r.y);
   }
 }
 
@@ -288,6 +397,25 @@ cudaError_t launch_gemv_adj_dd(const void *A, int fmt, const cdd *yh, cdd *xh, i
     cudaFuncSetAttribute(k_gemv_adj_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   dim3 g((Nm + 256 * ADJ_KPT - 1) / (256 * ADJ_KPT), Nf);
   k_gemv_adj_dd<<<g, 256, sm, s>>>(reinterpret_cast<const float4 *>(A), yh, xh, Nr, Nm);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_adj_cx(const void *A, int fmt, const cdd *yh, cf *xh, int Nf, int Nr, int Nm,
+                               cudaStream_t s) {
+  const size_t sm = (size_t)Nr * sizeof(AdjRow);
+  dim3 g((Nm + 256 * ADJ_KPT - 1) / (256 * ADJ_KPT), Nf);
+  if (fmt == FMT_C64) {
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_gemv_adj_cx<FMT_C64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_gemv_adj_cx<FMT_C64><<<g, 256, sm, s>>>(A, yh, xh, Nr, Nm);
+  } else if (fmt == FMT_BF16X2) {
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_gemv_adj_cx<FMT_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_gemv_adj_cx<FMT_BF16X2><<<g, 256, sm, s>>>(A, yh, xh, Nr, Nm);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   count_launches(1);
   return cudaGetLastError();
 }

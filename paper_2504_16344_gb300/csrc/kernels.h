@@ -84,6 +84,11 @@ cudaError_t launch_gemv_fwd_f(const void *A, int fmt, const cf *xh, cf *part, cf
 // adjoint: xh[w][k] = sum_s conj(A[w][s][k]) yh[w][s]
 cudaError_t launch_gemv_adj_dd(const void *A, int fmt, const cdd *yh, cdd *xh, int Nf, int Nr,
                                int Nm, cudaStream_t s);
+// adjoint for one right-hand side with an FP32 operator (fmt C64 / BF16X2)
+// and float-pair data: exact products, double-float running sums, x^ in FP32
+cudaError_t launch_gemv_adj_cx(const void *A, int fmt, const cdd *yh, cf *xh, int Nf, int Nr, int Nm,
+                               cudaStream_t s);
+
 // ---- batched per-frequency products (gemm.cu) ----------------------------
 // adjoint: X[b][w][k] = sum_s conj(A[w][s][k]) Y[b][w][s]
 // forward: Yo[b][w][r] = sum_k A[w][r][k] X[b][w][k]; part: B*Nf*nchunk*Nr entries

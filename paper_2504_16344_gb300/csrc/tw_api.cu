@@ -243,19 +243,13 @@ tw_status tw_create(tw_ctx **out, int Nd, int Nq, int Nx, int Ny, int Nt, double
       st = twh::fail(c, TW_ERR_CUDA, "memset");
   }
   if (st == TW_OK && (keep & (TW_KEEP_C64 | TW_KEEP_BF16X2))) {
-    // the sliced tensor-core adjoint of the FP32 storages: row exponents per
-    // kept storage and the data-side slices of one right-hand side
+    // row exponents of the FP32 storages for the batched adjoint on the tensor cores
     for (int which = 0; which < 2; ++which)
       for (int fmt = 1; fmt < 3; ++fmt)
         if (c->op[which][fmt]) {
           c->ea[which][fmt] = (int8_t *)twh::dalloc(c, Nf * Nm);
           if (!c->ea[which][fmt]) st = twh::fail(c, TW_ERR_OOM, "row exponent tables");
         }
-    c->sl_ws_n = sl_ws_bytes(c->Nf, c->Rmax, 8);
-    c->sl_eb_n = sl_eb_bytes(c->Nf, 8);
-    c->sl_ws = twh::dalloc(c, c->sl_ws_n);
-    c->sl_eb = (int *)twh::dalloc(c, c->sl_eb_n);
-    if (!c->sl_ws || !c->sl_eb) st = twh::fail(c, TW_ERR_OOM, "slice workspace");
   }
   if (st != TW_OK) {
     // keep the message for the caller: report via stderr since ctx is freed
@@ -425,6 +419,26 @@ tw_status tw_p2o_adjoint(tw_ctx *c, tw_map which, tw_prec prec, int nrhs, const 
   TW_CUDA(c, cudaSetDevice(c->dev));
   const int R = rows_of(c, which), Nt = c->Nt, Nf = c->Nf, Nm = c->Nm;
   const void *A = c->op[which][prec];
+  if (prec != TW_PREC_FP64 && nrhs > 1 && c->bmax > 0) {
+    // several right-hand sides with a reserved batch: the per-frequency
+    // products as one matrix product on the tensor cores (exact slices)
+    for (int r0 = 0; r0 < nrhs; r0 += c->bmax) {
+      const int nb = std::min(c->bmax, nrhs - r0);
+      const BatchArg ba_y{nb, (long)Nt * R, (long)Nf * R, 0, nullptr};
+      const BatchArg ba_x{nb, (long)Nf * Nm, (long)Nt * Nm, 0, nullptr};
+      { twh::Phase p(c, TW_PH_RFFT_DATA, s);
+        TW_CUDA(c, launch_rfft_time_dd(y + (size_t)r0 * Nt * R, 0, R, Nt, (cdd *)c->byh, R, R, c->plT,
+                                       c->twT, c->twL, s, ba_y)); }
+      { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
+        TW_CUDA(c, launch_gemm_adj_sl(A, (int)prec, c->ea[which][prec], (const cdd *)c->byh, (long)Nf * R,
+                                      (cf *)c->bxh, (long)Nf * Nm, Nf, R, Nm, nb, c->sl_tile, c->bsl_ws,
+                                      c->bsl_ws_n, c->bsl_eb, c->bsl_eb_n, c->d_err, s)); }
+      { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+        TW_CUDA(c, launch_irfft_time_f((const cf *)c->bxh, Nm, x + (size_t)r0 * Nt * Nm, 0, Nm, Nm, Nt,
+                                       c->plT, c->twTf, c->twLf, s, ba_x)); }
+    }
+    return TW_OK;
+  }
   for (int r = 0; r < nrhs; ++r) {
     const double *yr = y + (size_t)r * Nt * R;
     double *xr = x + (size_t)r * Nt * Nm;
@@ -436,15 +450,13 @@ tw_status tw_p2o_adjoint(tw_ctx *c, tw_map which, tw_prec prec, int nrhs, const 
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
         TW_CUDA(c, launch_irfft_time_dd(c->wf, Nm, xr, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s)); }
     } else {
-      // FP32 operator; the data-side spectrum in double-float, the product on
-      // the tensor cores with both sides in exact fixed-point slices (as the
-      // posterior mean's adjoint)
+      // FP32 operator; the data-side spectrum in double-float, exact products
+      // and a double-float running sum (as the posterior mean's adjoint)
       cf *wf = (cf *)c->wf;
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
         TW_CUDA(c, launch_rfft_time_dd(yr, 0, R, Nt, c->wr, R, R, c->plT, c->twT, c->twL, s)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-        TW_CUDA(c, launch_gemm_adj_sl(A, (int)prec, c->ea[which][prec], c->wr, 0, wf, 0, Nf, R, Nm, 1, 8,
-                                      c->sl_ws, c->sl_ws_n, c->sl_eb, c->sl_eb_n, c->d_err, s)); }
+        TW_CUDA(c, launch_gemv_adj_cx(A, (int)prec, c->wr, wf, Nf, R, Nm, s)); }
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
         TW_CUDA(c, launch_irfft_time_f(wf, Nm, xr, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s)); }
     }

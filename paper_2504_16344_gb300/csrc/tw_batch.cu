@@ -252,7 +252,7 @@ tw_status tw_reserve_batch(tw_ctx *c, int bmax) {
   if (mixed) {   // data-side slices of the tensor-core adjoint
     c->sl_tile = sl_pick_tile(bmax);
     const int cols = (bmax + c->sl_tile - 1) / c->sl_tile * c->sl_tile;
-    c->bsl_ws_n = sl_ws_bytes(c->Nf, c->Nd, cols);
+    c->bsl_ws_n = sl_ws_bytes(c->Nf, c->Rmax, cols);
     c->bsl_eb_n = sl_eb_bytes(c->Nf, cols);
     c->bsl_ws = take(c->bsl_ws_n);
     c->bsl_eb = (int *)take(c->bsl_eb_n);

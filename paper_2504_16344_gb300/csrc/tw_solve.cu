@@ -430,8 +430,7 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
         TW_CUDA(c, launch_rfft_time_dd(ysrc, ykind, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-        TW_CUDA(c, launch_gemm_adj_sl(AG, (int)prec, c->eaG[prec], c->wr, 0, wf, 0, Nf, Nd, Nm, 1, 8,
-                                      c->sl_ws, c->sl_ws_n, c->sl_eb, c->sl_eb_n, c->d_err, s)); }
+        TW_CUDA(c, launch_gemv_adj_cx(AG, (int)prec, c->wr, wf, Nf, Nd, Nm, s)); }
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
         TW_CUDA(c, launch_irfft_time_f(wf, Nm, mr, 0, Nm, Nm, w, c->plT, c->twTf, c->twLf, s)); }
     } else if (!mixed) {
@@ -446,16 +445,14 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
                                    c->twX, c->twY, s)); }
     } else {
       // reduced-precision operator: y's spectrum stays double-float (y is large
-      // against m, and F^T y cancels), the product runs on the tensor cores
-      // with both sides in exact fixed-point slices; x^ onwards (inverse FFT,
-      // prior) runs in FP32
+      // against m, and F^T y cancels), the product forms exact products and a
+      // double-float running sum; x^ onwards (inverse FFT, prior) runs in FP32
       cf *wf = (cf *)c->wf;
       float *wt = (float *)c->wt;
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
         TW_CUDA(c, launch_rfft_time_dd(ysrc, ykind, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-        TW_CUDA(c, launch_gemm_adj_sl(A, (int)prec, c->ea[TW_MAP_F][prec], c->wr, 0, wf, 0, Nf, Nd, Nm, 1,
-                                      8, c->sl_ws, c->sl_ws_n, c->sl_eb, c->sl_eb_n, c->d_err, s)); }
+        TW_CUDA(c, launch_gemv_adj_cx(A, (int)prec, c->wr, wf, Nf, Nd, Nm, s)); }
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
         TW_CUDA(c, launch_irfft_time_f(wf, Nm, wt, 2, Nm, Nm, w, c->plT, c->twTf, c->twLf, s)); }
       { twh::Phase p(c, TW_PH_PRIOR, s);

@@ -163,27 +163,33 @@ def test_mixed_batch(case, prec):
 
 
 @pytest.mark.parametrize("prec", ["C64", "BF16X2"])
-def test_sliced_adjoint_at_rounded_operator_floor(case, prec):
+def test_adjoint_at_rounded_operator_floor(case, prec):
     """F^T y with y = K^-1 d (the posterior mean's product, whose sum over
-    sensors cancels strongly) on the tensor cores: against exact arithmetic
-    on the operator rounded as stored, the difference must be the kernel's
-    own rounding (levels below 2^-32 of a term dropped, the FP32 partial
-    accumulator, complex64 x^ and its FP32 inverse FFT: a few 2^-24 of |x|),
-    far below both the 1e-5 target and the storage's own floor on these
-    cases.  An FP32 accumulation of the terms would miss by the cancellation
-    factor (up to 10^3 here)."""
+    sensors cancels strongly), for one right-hand side at a time (exact
+    products, double-float running sums) and for a batch (tensor cores,
+    exact fixed-point slices): against exact arithmetic on the operator
+    rounded as stored, the difference must be the kernels' own rounding
+    (complex64 x^ and its FP32 inverse FFT, and on the tensor cores levels
+    below 2^-32 of a term and the FP32 partial accumulator: a few 2^-24 of
+    |x|), far below both the 1e-5 target and the storage's own floor.  An
+    FP32 accumulation of the terms would miss by the cancellation factor (up
+    to 10^3 here)."""
     from paper_2504_16344_gb300 import tw
     ctx, cfg = case["ctx"], case["cfg"]
-    ys = np.stack([pad_window(case["post"][e][1], cfg.Nt, cfg.Nd) for e in (0, 2)])
-    x = ctx.p2o_adjoint(tw.MAP_F, getattr(tw, "PREC_" + prec), _t(ys, case["dev"])).cpu().numpy()
+    p = getattr(tw, "PREC_" + prec)
+    evs = (0, 2, 5)
+    ys = np.stack([pad_window(case["post"][e][1], cfg.Nt, cfg.Nd) for e in evs])
+    xb = ctx.p2o_adjoint(tw.MAP_F, p, _t(ys, case["dev"])).cpu().numpy()           # batched
+    xs = np.stack([ctx.p2o_adjoint(tw.MAP_F, p, _t(ys[i:i + 1], case["dev"]))[0].cpu().numpy()
+                   for i in range(len(evs))])                                        # one at a time
     ctx.check()
-    for i, e in enumerate((0, 2)):
+    for i, e in enumerate(evs):
         exact = T.p2o_adjoint(case["F"], ys[i])
         x_fl = adjoint_rounded(case["F"], ys[i], prec)
-        err, fl = rel(x[i], x_fl), rel(x_fl, exact)
-        print(f"{cfg.cid}: sliced adjoint {prec} event {e}: vs rounded-operator exact {err:.2e} "
-              f"(that floor vs exact {fl:.2e})")
-        assert err < 2e-6
+        eb, es, fl = rel(xb[i], x_fl), rel(xs[i], x_fl), rel(x_fl, exact)
+        print(f"{cfg.cid}: adjoint {prec} event {e}: vs rounded-operator exact: batched {eb:.2e}, "
+              f"single {es:.2e} (that floor vs exact {fl:.2e})")
+        assert eb < 2e-6 and es < 2e-6
 
 
 def test_result_independent_of_batch_mates(case):
