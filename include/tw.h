@@ -434,45 +434,59 @@ void tw_graph_destroy(tw_graph *graph);
  * ---- Serving (Phase 4 under a stream of requests).
  * A request names an event (a data vector in a device-resident bank) and an
  * observation window Nt'; it is served when its posterior mean and
- * forecast are computed and the forecast is in host memory.  Admission:
- * requests queue in arrival order; whenever the device is idle and requests
- * wait, the oldest min(waiting, max_batch) start as one batch
- * (work-conserving continuous batching; max_batch <= the reserved batch,
- * which tw_reserve_batch sized from device memory).
+ * forecast are computed and the forecast is in host memory.  Continuous
+ * batching over "lanes": a lane is one set of batch workspaces and slot
+ * buffers with its own stream, holding a batch of up to max_batch requests.
+ * Requests queue in arrival order; whenever a lane is free and requests
+ * wait, the oldest min(waiting, max_batch) start in that lane at once, while
+ * the other lanes' batches are still running, so requests that arrive during
+ * a batch start as soon as any lane frees up and their kernels overlap the
+ * running batches' on the device.  Lane 0 is the context's reserved batch
+ * (tw_reserve_batch); the session adds lanes while device memory allows
+ * (cudaMemGetInfo, 2 GB margin), up to the requested count.
  */
 typedef struct {
   int batches;         /* batches launched                                   */
   int max_batch;       /* largest batch                                      */
   double mean_batch;   /* requests per batch                                 */
   double makespan_s;   /* first arrival to last completion                   */
-  double busy_s;       /* summed device time of the batches                  */
+  double busy_s;       /* summed start-to-completion time of the batches
+                          (batches that overlap count in full)               */
+  int lanes;           /* lanes the session used                             */
+  int max_in_flight;   /* most batches in flight at once                     */
 } tw_serve_stats;
 
 /*
  * tw_serve_replay -- replay a trace in real time: request i arrives
  * arrival_s[i] seconds (host, sorted) after the call starts its clock,
  * with event[i] in [0, nevents) and window[i] in [1, Nt] (host arrays).
- * event_data: device [nevents][Nt][Nd].  Outputs (host): latency_ms[i] =
- * completion - arrival; q_out [nreq][Nt][Nq] and m_out [nreq][Nt][Nm]
- * (either may be NULL; copying m_out is outside the timed path but slows
- * the replay).  stats may be NULL.  Needs tw_reserve_batch; allocates its
- * slot buffers (max_batch x (Nt Nm + Nt Nd + Nt Nq) doubles) before the clock
- * starts and frees them on return.  `stream` must be a created stream.
+ * event_data: device [nevents][Nt][Nd].  lanes: batches in flight at most
+ * (1..4; 0 = as many as device memory allows, up to 4).  Outputs (host):
+ * latency_ms[i] = completion - arrival; q_out [nreq][Nt][Nq] and m_out
+ * [nreq][Nt][Nm] (either may be NULL; copying m_out is outside the timed path
+ * but slows the replay).  stats may be NULL.  Needs tw_reserve_batch
+ * (max_batch <= the reserved batch); allocates the extra lanes' workspaces,
+ * each lane's slot buffers (max_batch x (Nt Nm + Nt Nd + Nt Nq) doubles) and
+ * streams before the clock starts, and frees them on return.  `stream` (lane
+ * 0's) must be a created stream.  A result does not depend on the lane or on
+ * the batch it ran in (bitwise).
  */
 tw_status tw_serve_replay(tw_ctx *ctx, tw_prec prec, int nreq, const double *arrival_s,
                           const int *event, const int *window, int nevents,
-                          const double *event_data, int max_batch, double *latency_ms,
+                          const double *event_data, int max_batch, int lanes, double *latency_ms,
                           double *q_out, double *m_out, tw_serve_stats *stats, void *stream);
 
 /*
- * tw_serve_simulate -- the same admission policy on a virtual clock with a
- * modelled batch time of cost_ms + cost_ms_per_req * batch size (host
- * only, no device use): latency_ms[i] and the batch index batch_of[i]
- * (may be NULL) of each request.  Returns TW_ERR_ARG for unsorted arrivals,
- * max_batch < 1 or NULL arrays.
+ * tw_serve_simulate -- the same admission policy on a virtual clock, each
+ * lane a server whose batch takes cost_ms + cost_ms_per_req * batch size
+ * (host only, no device use; the lanes of the model do not slow each other):
+ * latency_ms[i] and the batch index batch_of[i] (may be NULL; batches are
+ * numbered in start order) of each request.  Returns TW_ERR_ARG for
+ * unsorted arrivals, max_batch < 1, lanes < 1 or NULL arrays.
  */
-tw_status tw_serve_simulate(int nreq, const double *arrival_s, int max_batch, double cost_ms,
-                            double cost_ms_per_req, double *latency_ms, int *batch_of);
+tw_status tw_serve_simulate(int nreq, const double *arrival_s, int max_batch, int lanes,
+                            double cost_ms, double cost_ms_per_req, double *latency_ms,
+                            int *batch_of);
 
 /*
  * ---- Phase 3 / Phase 4 for the QoI (Sec. "Real-time Bayesian inference and

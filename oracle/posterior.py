@@ -39,7 +39,11 @@ def block_products(Fcol: np.ndarray, lam: np.ndarray, Nt: int | None = None) -> 
     Nt = Fcol.shape[0] if Nt is None else Nt
     _, Nd, Nm = Fcol.shape
     Phi = Fcol[:Nt].reshape(Nt * Nd, Nm)
-    H = prior_apply(Phi, lam)          # rows F_u C  (C is symmetric)
+    # rows F_u C (C is symmetric), filtered a bounded number of rows at a time
+    # (each row's filter is independent; this only limits host memory)
+    H = np.empty_like(Phi)
+    for r0 in range(0, Phi.shape[0], 512):
+        H[r0:r0 + 512] = prior_apply(Phi[r0:r0 + 512], lam)
     return H @ Phi.T
 
 

@@ -8,6 +8,27 @@
 #include "../../include/tw.h"
 #include "kernels.h"
 
+// One set of batch workspaces ("lane"), RHS-major: a batch of up to bmax
+// right-hand sides runs in it.  The context's reserved batch is one lane;
+// the serving loop adds lanes so that several batches run at the same time.
+struct tw_lane {
+  int bmax = 0;
+  int *win_dev = nullptr;            // [bmax] windows of host-window batched calls
+  int *trsm_prog = nullptr;          // [2][trsm_prog_ints(bmax)] solve counters
+  double *bz = nullptr, *by = nullptr;      // [bmax][n_pad] FP64 solves
+  tw::dd *bzd = nullptr, *byd = nullptr;    // [bmax][n_pad] float-pair solves (mixed)
+  double *brd = nullptr;             // [bmax][Nt][Nd] data-side scratch (samples)
+  void *byh = nullptr;               // [bmax][Nf][Rmax] data-side spectra (16-byte entries)
+  void *bxh = nullptr;               // [bmax][Nf][Nm] parameter-side spectra / prior work
+  void *bpart = nullptr;             // [bmax][Nf][nchunk][Rmax] forward-product partial sums
+  // data-side slices and column exponents of the tensor-core adjoint
+  void *bsl_ws = nullptr;
+  int *bsl_eb = nullptr;
+  size_t bsl_ws_n = 0, bsl_eb_n = 0;
+  int sl_tile = 0;                   // right-hand sides per tile of that product
+  size_t bytes = 0;                  // device bytes of the lane
+};
+
 struct tw_ctx {
   int dev = 0;
   int Nd = 0, Nq = 0, Nx = 0, Ny = 0, Nt = 0, Nm = 0, Nf = 0, Rmax = 0;
@@ -22,11 +43,6 @@ struct tw_ctx {
   // cores: ea[which][fmt][w][m] (fmt 1, 2), eaG[fmt] for G^ (gemm_sl.cu)
   int8_t *ea[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
   int8_t *eaG[3] = {nullptr, nullptr, nullptr};
-  // its data-side slices and column exponents (tw_reserve_batch)
-  void *bsl_ws = nullptr;
-  int *bsl_eb = nullptr;
-  size_t bsl_ws_n = 0, bsl_eb_n = 0;
-  int sl_tile = 0;                   // right-hand sides per tile of the batched product
   std::vector<char> loaded[2];     // per row: loaded?
   // FFT plans and twiddle tables (df64 and float)
   tw::FftPlan plT{}, plX{}, plY{};
@@ -80,16 +96,8 @@ struct tw_ctx {
   int ir_steps = 3;
   int solver = TW_SOLVE_FACTOR64;
   double ir_probe_resid = 0.0;
-  // batched right-hand sides (tw_reserve_batch): RHS-major workspaces
-  int bmax = 0;
-  int *win_dev = nullptr;            // [bmax] windows of host-window batched calls
-  int *trsm_prog = nullptr;          // [2][trsm_prog_ints(bmax)] solve counters
-  double *bz = nullptr, *by = nullptr;      // [bmax][n_pad] FP64 solves
-  tw::dd *bzd = nullptr, *byd = nullptr;    // [bmax][n_pad] float-pair solves (mixed)
-  double *brd = nullptr;             // [bmax][Nt][Nd] data-side scratch (samples)
-  void *byh = nullptr;               // [bmax][Nf][Rmax] data-side spectra (16-byte entries)
-  void *bxh = nullptr;               // [bmax][Nf][Nm] parameter-side spectra / prior work
-  void *bpart = nullptr;             // [bmax][Nf][nchunk][Rmax] forward-product partial sums
+  // batched right-hand sides (tw_reserve_batch): the reserved lane
+  tw_lane lane;
   tw::dd *Lp_dd = nullptr, *inv_dd = nullptr, *chF_dd = nullptr, *chB_dd = nullptr;
   // Phase 3 QoI precomputations (tw_qoi_build): rows indexed by QoI entry t*Nq + i
   double *Qmap = nullptr, *Wmap = nullptr;   // [Nq Nt][Nd Nt]: Q = F_q Gamma_pr F^T K^-1, W = (F Gamma_pr F_q^T)^T
@@ -134,6 +142,13 @@ tw_status refresh_dd_factor(tw_ctx *c, cudaStream_t s);
 
 // host-window calls routed to the batched path (tw_batch.cu)
 namespace twb {
+// allocate / free a lane's workspaces (bmax right-hand sides)
+tw_status alloc_lane(tw_ctx *c, tw_lane &L, int bmax);
+void free_lane(tw_ctx *c, tw_lane &L);
+size_t lane_bytes(const tw_ctx *c, int bmax);
+// the batched posterior mean (+ forecast when q) of B right-hand sides in lane L
+tw_status infer_core(tw_ctx *c, tw_lane &L, tw_prec prec, int B, const int *win, const double *rhs,
+                     long rhs_bstride, double *m, double *q, cudaStream_t s);
 tw_status infer_host_windows(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window,
                              const double *d, double *m, cudaStream_t s);
 tw_status sample_host_windows(tw_ctx *c, int ns, const int *nt_window, const double *d,

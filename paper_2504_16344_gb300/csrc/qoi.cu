@@ -140,7 +140,7 @@ tw_status tw_qoi_build(tw_ctx *c, void *stream) {
   if (!c) return TW_ERR_ARG;
   if (!c->have64 || !c->op[TW_MAP_F][TW_PREC_FP64] || !c->op[TW_MAP_FQ][TW_PREC_FP64])
     return twh::fail(c, TW_ERR_STATE, "tw_qoi_build needs the FP64 operators and factor");
-  if (c->bmax <= 0) return twh::fail(c, TW_ERR_STATE, "tw_reserve_batch must come first");
+  if (c->lane.bmax <= 0) return twh::fail(c, TW_ERR_STATE, "tw_reserve_batch must come first");
   for (char l : c->loaded[TW_MAP_FQ])
     if (!l) return twh::fail(c, TW_ERR_STATE, "block column of F_q not fully loaded");
   cudaStream_t s = (cudaStream_t)stream;
@@ -148,7 +148,7 @@ tw_status tw_qoi_build(tw_ctx *c, void *stream) {
   const int Nd = c->Nd, Nq = c->Nq, Nt = c->Nt, Nm = c->Nm, Nf = c->Nf;
   const int nq = Nq * Nt, n = Nd * Nt;
   const long np = c->n_pad;
-  const int Bq = std::min(c->bmax, 96);
+  const int Bq = std::min(c->lane.bmax, 96);
   auto need = [&](void *&p, size_t bytes) { if (!p) p = twh::dalloc(c, bytes); return p != nullptr; };
   bool ok = need((void *&)c->Qmap, (size_t)nq * n * sizeof(double)) &&
             need((void *&)c->Wmap, (size_t)nq * n * sizeof(double)) &&
@@ -160,8 +160,8 @@ tw_status tw_qoi_build(tw_ctx *c, void *stream) {
   auto cleanup = [&]() { twh::dfree(c, eq); twh::dfree(c, cq); twh::dfree(c, u); };
   if (!ok || !eq || !cq || !u) { cleanup(); return twh::fail(c, TW_ERR_OOM, "QoI map buffers"); }
   const void *AF = c->op[TW_MAP_F][TW_PREC_FP64], *AQ = c->op[TW_MAP_FQ][TW_PREC_FP64];
-  int *prog_f = c->trsm_prog, *prog_b = c->trsm_prog + trsm_prog_ints(c->bmax);
-  k_fill_int<<<(Bq + 255) / 256, 256, 0, s>>>(c->win_dev, Nt, Bq);
+  int *prog_f = c->lane.trsm_prog, *prog_b = c->lane.trsm_prog + trsm_prog_ints(c->lane.bmax);
+  k_fill_int<<<(Bq + 255) / 256, 256, 0, s>>>(c->lane.win_dev, Nt, Bq);
   count_launches(1);
   for (int j0 = 0; j0 < nq; j0 += Bq) {
     const int B = std::min(Bq, nq - j0);
@@ -175,34 +175,34 @@ tw_status tw_qoi_build(tw_ctx *c, void *stream) {
     k_unit_qoi<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(eq, nq, j0, B);
     count_launches(1);
     // u = Gamma_pr F_q^T e
-    TW_CUDA(c, launch_rfft_time_dd(eq, 0, Nq, Nt, (cdd *)c->byh, Nq, Nq, c->plT, c->twT, c->twL, s, ba_e));
-    TW_CUDA(c, launch_gemm_adj_dd(AQ, (const cdd *)c->byh, (long)Nf * Nq, (cdd *)c->bxh, (long)Nf * Nm,
+    TW_CUDA(c, launch_rfft_time_dd(eq, 0, Nq, Nt, (cdd *)c->lane.byh, Nq, Nq, c->plT, c->twT, c->twL, s, ba_e));
+    TW_CUDA(c, launch_gemm_adj_dd(AQ, (const cdd *)c->lane.byh, (long)Nf * Nq, (cdd *)c->lane.bxh, (long)Nf * Nm,
                                   Nf, Nq, Nm, B, s));
-    TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->bxh, Nm, u, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s, ba_u));
-    TW_CUDA(c, launch_prior_dd(u, 0, u, 0, Nt, c->Nx, c->Ny, (cdd *)c->bxh, c->lam1, c->plX, c->plY,
+    TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->lane.bxh, Nm, u, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s, ba_u));
+    TW_CUDA(c, launch_prior_dd(u, 0, u, 0, Nt, c->Nx, c->Ny, (cdd *)c->lane.bxh, c->lam1, c->plX, c->plY,
                                c->twX, c->twY, s, ba_p, 0));
     // spectra of u, then c = F_q u and w = F u
-    TW_CUDA(c, launch_rfft_time_dd(u, 0, Nm, Nt, (cdd *)c->bxh, Nm, Nm, c->plT, c->twT, c->twL, s, ba_r));
-    TW_CUDA(c, launch_gemm_fwd_dd(AQ, (const cdd *)c->bxh, (long)Nf * Nm, (cdd *)c->bpart, (cdd *)c->byh,
+    TW_CUDA(c, launch_rfft_time_dd(u, 0, Nm, Nt, (cdd *)c->lane.bxh, Nm, Nm, c->plT, c->twT, c->twL, s, ba_r));
+    TW_CUDA(c, launch_gemm_fwd_dd(AQ, (const cdd *)c->lane.bxh, (long)Nf * Nm, (cdd *)c->lane.bpart, (cdd *)c->lane.byh,
                                   (long)Nf * Nq, Nf, Nq, Nm, B, s));
-    TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->byh, Nq, cq, 0, Nq, Nq, Nt, c->plT, c->twT, c->twL, s, ba_q));
-    TW_CUDA(c, launch_gemm_fwd_dd(AF, (const cdd *)c->bxh, (long)Nf * Nm, (cdd *)c->bpart, (cdd *)c->byh,
+    TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->lane.byh, Nq, cq, 0, Nq, Nq, Nt, c->plT, c->twT, c->twL, s, ba_q));
+    TW_CUDA(c, launch_gemm_fwd_dd(AF, (const cdd *)c->lane.bxh, (long)Nf * Nm, (cdd *)c->lane.bpart, (cdd *)c->lane.byh,
                                   (long)Nf * Nd, Nf, Nd, Nm, B, s));
-    TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->byh, Nd, c->brd, 0, Nd, Nd, Nt, c->plT, c->twT, c->twL, s, ba_d));
+    TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->lane.byh, Nd, c->lane.brd, 0, Nd, Nd, Nt, c->plT, c->twT, c->twL, s, ba_d));
     // y = K^{-1} w
-    TW_CUDA(c, launch_trsm_d(c->Lp64, c->inv64, c->chF64, c->brd, 0, (long)n, c->bz, np, c->win_dev, Nd,
+    TW_CUDA(c, launch_trsm_d(c->Lp64, c->inv64, c->chF64, c->lane.brd, 0, (long)n, c->lane.bz, np, c->lane.win_dev, Nd,
                              Nt, B, c->NB, prog_f, true, c->d_err, c->abort_flag, s));
-    TW_CUDA(c, launch_trsm_d(c->Lp64, c->inv64, c->chB64, c->bz, 0, np, c->by, np, c->win_dev, Nd, Nt, B,
+    TW_CUDA(c, launch_trsm_d(c->Lp64, c->inv64, c->chB64, c->lane.bz, 0, np, c->lane.by, np, c->lane.win_dev, Nd, Nt, B,
                              c->NB, prog_b, false, c->d_err, c->abort_flag, s));
     // rows of Q, W, C and the variances
-    TW_CUDA(c, cudaMemcpy2DAsync(c->Qmap + (size_t)j0 * n, (size_t)n * sizeof(double), c->by,
+    TW_CUDA(c, cudaMemcpy2DAsync(c->Qmap + (size_t)j0 * n, (size_t)n * sizeof(double), c->lane.by,
                                  (size_t)np * sizeof(double), (size_t)n * sizeof(double), B,
                                  cudaMemcpyDeviceToDevice, s));
-    TW_CUDA(c, cudaMemcpyAsync(c->Wmap + (size_t)j0 * n, c->brd, (size_t)B * n * sizeof(double),
+    TW_CUDA(c, cudaMemcpyAsync(c->Wmap + (size_t)j0 * n, c->lane.brd, (size_t)B * n * sizeof(double),
                                cudaMemcpyDeviceToDevice, s));
     TW_CUDA(c, cudaMemcpyAsync(c->Cqq + (size_t)j0 * nq, cq, (size_t)B * nq * sizeof(double),
                                cudaMemcpyDeviceToDevice, s));
-    k_qoi_var<<<B, 256, 0, s>>>(cq, c->by, np, c->brd, n, nq, j0, c->qvar);
+    k_qoi_var<<<B, 256, 0, s>>>(cq, c->lane.by, np, c->lane.brd, n, nq, j0, c->qvar);
     count_launches(1);
     TW_CUDA(c, cudaGetLastError());
   }

@@ -2,12 +2,16 @@
 // context with continuous batching (policy in serve_policy.h).
 //
 // Each request names an event (its data vector sits in a device-resident
-// bank) and a window Nt'.  A batch gathers its requests' data into slot
-// buffers, runs the batched posterior mean + forecast (tw_infer_batch) and
-// copies the forecasts to pinned host memory; the batch's completion time is
-// its host enqueue time plus the device time between two events recorded
-// around that work, and a request's latency is completion minus arrival.
-// One batch is in flight at a time: the batched kernels fill the GPU.
+// bank) and a window Nt'.  A batch gathers its requests' data into its
+// lane's slot buffers, runs the batched posterior mean + forecast in that
+// lane's workspaces on the lane's own stream and copies the forecasts to
+// pinned host memory.  Several lanes are in flight at once: a request that
+// arrives while batches run starts as soon as any lane is free, and its
+// kernels overlap the running batches' on the device.  Lane 0 is the
+// context's reserved batch; the session adds lanes while device memory
+// allows (up to the requested count).  Completion times come from device
+// events against one reference event recorded when the clock starts; a
+// request's latency is its batch's completion minus its arrival.
 #include <algorithm>
 #include <chrono>
 #include <thread>
@@ -33,44 +37,79 @@ double now_s(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// one lane of a serving session: workspaces, slot buffers, stream, staging
+struct ServeLane {
+  tw_lane *work = nullptr;        // the batch workspaces (lane 0: the context's)
+  bool owned = false;             // workspaces allocated by the session
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  double *d_slot = nullptr, *m_slot = nullptr, *q_slot = nullptr;
+  int *idx_dev = nullptr, *idx_host = nullptr;
+  double *q_host = nullptr;
+  cudaEvent_t done = nullptr;
+  int first = 0, count = 0;       // the batch in flight
+};
+
+constexpr int MAX_LANES = 4;
+
 }  // namespace
 
 extern "C" {
 
-tw_status tw_serve_simulate(int nreq, const double *arrival_s, int max_batch, double cost_ms,
-                            double cost_ms_per_req, double *latency_ms, int *batch_of) {
-  if (nreq < 0 || max_batch < 1 || (nreq > 0 && (!arrival_s || !latency_ms))) return TW_ERR_ARG;
+tw_status tw_serve_simulate(int nreq, const double *arrival_s, int max_batch, int lanes,
+                            double cost_ms, double cost_ms_per_req, double *latency_ms,
+                            int *batch_of) {
+  if (nreq < 0 || max_batch < 1 || lanes < 1 || (nreq > 0 && (!arrival_s || !latency_ms)))
+    return TW_ERR_ARG;
   for (int i = 1; i < nreq; ++i)
     if (arrival_s[i] < arrival_s[i - 1]) return TW_ERR_ARG;
-  twserve::Policy pol(nreq, arrival_s, max_batch);
+  twserve::Policy pol(nreq, arrival_s, max_batch, lanes);
+  std::vector<double> end(lanes, 0.0);
+  std::vector<int> first(lanes, 0), count(lanes, 0);
   double t = nreq ? arrival_s[0] : 0.0;
   int nb_id = 0;
   while (!pol.done()) {
     pol.admit(t);
-    if (!pol.waiting()) { t = pol.next_arrival(); continue; }
-    int first, count;
-    pol.take(&first, &count);
-    const double t_end = t + 1e-3 * (cost_ms + cost_ms_per_req * count);
-    for (int i = first; i < first + count; ++i) {
-      latency_ms[i] = 1e3 * (t_end - arrival_s[i]);
-      if (batch_of) batch_of[i] = nb_id;
+    // every free lane takes a batch while requests wait
+    int l;
+    while (pol.waiting() && (l = pol.free_lane()) >= 0) {
+      pol.take(l, &first[l], &count[l]);
+      end[l] = t + 1e-3 * (cost_ms + cost_ms_per_req * count[l]);
+      for (int i = first[l]; i < first[l] + count[l]; ++i)
+        if (batch_of) batch_of[i] = nb_id;
+      ++nb_id;
     }
-    ++nb_id;
-    t = t_end;
+    // advance to the next event: a batch finishing or a request arriving
+    const double inf = 1e300;
+    const double t_arr = pol.all_taken() || pol.next_arrival() < 0 ? inf : pol.next_arrival();
+    int l_end = -1;
+    for (int k = 0; k < lanes; ++k)
+      if (count[k] > 0 && (l_end < 0 || end[k] < end[l_end])) l_end = k;
+    const double t_end = l_end < 0 ? inf : end[l_end];
+    if (t_end <= t_arr) {
+      t = t_end;
+      for (int i = first[l_end]; i < first[l_end] + count[l_end]; ++i)
+        latency_ms[i] = 1e3 * (t - arrival_s[i]);
+      count[l_end] = 0;
+      pol.release(l_end);
+    } else if (t_arr < inf) {
+      t = std::max(t, t_arr);
+    }
   }
   return TW_OK;
 }
 
 tw_status tw_serve_replay(tw_ctx *c, tw_prec prec, int nreq, const double *arrival_s,
                           const int *event, const int *window, int nevents,
-                          const double *event_data, int max_batch, double *latency_ms,
+                          const double *event_data, int max_batch, int lanes, double *latency_ms,
                           double *q_out, double *m_out, tw_serve_stats *stats, void *stream) {
   if (!c) return TW_ERR_ARG;
   if (nreq < 0 || nevents < 1 || !event_data ||
       (nreq > 0 && (!arrival_s || !event || !window || !latency_ms)))
     return twh::fail(c, TW_ERR_ARG, "bad trace arguments");
-  if (max_batch < 1 || max_batch > c->bmax)
+  if (max_batch < 1 || max_batch > c->lane.bmax)
     return twh::fail(c, TW_ERR_ARG, "max_batch must be in [1, reserved batch]");
+  if (lanes < 0 || lanes > MAX_LANES) return twh::fail(c, TW_ERR_ARG, "lanes must be in [0, 4]");
   if (!stream) return twh::fail(c, TW_ERR_ARG, "serving needs a created stream");
   for (int i = 0; i < nreq; ++i) {
     if (event[i] < 0 || event[i] >= nevents) return twh::fail(c, TW_ERR_ARG, "event out of range");
@@ -78,101 +117,161 @@ tw_status tw_serve_replay(tw_ctx *c, tw_prec prec, int nreq, const double *arriv
     if (i > 0 && arrival_s[i] < arrival_s[i - 1])
       return twh::fail(c, TW_ERR_ARG, "arrivals must be sorted");
   }
-  cudaStream_t s = (cudaStream_t)stream;
   TW_CUDA(c, cudaSetDevice(c->dev));
+  TW_CUDA(c, cudaDeviceSynchronize());
   const int Nt = c->Nt, Nd = c->Nd, Nm = c->Nm, Nq = c->Nq;
   const size_t B = max_batch;
   const long drow = (long)Nt * Nd;
-  // session buffers (set-up, before the clock starts)
-  double *d_slot = (double *)twh::dalloc(c, B * drow * sizeof(double));
-  double *m_slot = (double *)twh::dalloc(c, B * (size_t)Nt * Nm * sizeof(double));
-  double *q_slot = (double *)twh::dalloc(c, B * (size_t)Nt * Nq * sizeof(double));
-  int *idx_dev = (int *)twh::dalloc(c, 2 * B * sizeof(int));
-  int *idx_host = nullptr;
-  double *q_host = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  auto cleanup = [&]() {
-    twh::dfree(c, d_slot); twh::dfree(c, m_slot); twh::dfree(c, q_slot); twh::dfree(c, idx_dev);
-    if (idx_host) cudaFreeHost(idx_host);
-    if (q_host) cudaFreeHost(q_host);
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
-  };
-  if (!d_slot || !m_slot || !q_slot || !idx_dev) { cleanup(); return twh::fail(c, TW_ERR_OOM, "serving slots"); }
-  if (cudaMallocHost(&idx_host, 2 * B * sizeof(int)) != cudaSuccess ||
-      cudaMallocHost(&q_host, B * (size_t)Nt * Nq * sizeof(double)) != cudaSuccess ||
-      cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess) {
-    cleanup();
-    return twh::fail(c, TW_ERR_OOM, "pinned staging / events");
-  }
-  twserve::Policy pol(nreq, arrival_s, max_batch);
-  int batches = 0, maxb = 0;
-  double busy = 0.0, t_last = 0.0;
+  const size_t slot_bytes = B * ((size_t)drow + (size_t)Nt * Nm + (size_t)Nt * Nq) * sizeof(double) +
+                            2 * B * sizeof(int);
+  // lanes: the reserved batch, plus more while device memory allows (up to
+  // `lanes`, 0 = as many as fit, at most four), with a 2 GB margin
+  const int want = lanes == 0 ? MAX_LANES : lanes;
+  std::vector<ServeLane> L(1);
+  L[0].work = &c->lane;
+  L[0].stream = (cudaStream_t)stream;
   tw_status st = TW_OK;
-  const auto t0 = std::chrono::steady_clock::now();
-  while (!pol.done()) {
-    pol.admit(now_s(t0));
-    if (!pol.waiting()) {
-      // idle: sleep until the next arrival (short naps keep the clock honest)
-      const double wait = pol.next_arrival() - now_s(t0);
-      if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait, 2e-4)));
-      continue;
+  cudaEvent_t ev_ref = nullptr;
+  auto cleanup = [&]() {
+    for (ServeLane &l : L) {
+      twh::dfree(c, l.d_slot); twh::dfree(c, l.m_slot); twh::dfree(c, l.q_slot); twh::dfree(c, l.idx_dev);
+      if (l.idx_host) cudaFreeHost(l.idx_host);
+      if (l.q_host) cudaFreeHost(l.q_host);
+      if (l.done) cudaEventDestroy(l.done);
+      if (l.own_stream) cudaStreamDestroy(l.stream);
+      if (l.owned) { twb::free_lane(c, *l.work); delete l.work; }
     }
-    int first, count;
-    pol.take(&first, &count);
-    for (int k = 0; k < count; ++k) {
-      idx_host[k] = event[first + k];
-      idx_host[B + k] = window[first + k];
-    }
-    const double t_enq = now_s(t0);
-    if (cudaEventRecord(ev0, s) != cudaSuccess ||
-        cudaMemcpyAsync(idx_dev, idx_host, 2 * B * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) {
-      st = twh::fail(c, TW_ERR_CUDA, "serving: enqueue");
+    if (ev_ref) cudaEventDestroy(ev_ref);
+  };
+  // extra lanes copy the reserved lane's size: the batched kernels' tiling
+  // follows it, and a result must not depend on the lane it ran in
+  const size_t lane_need = twb::lane_bytes(c, c->lane.bmax) + slot_bytes;
+  while ((int)L.size() < want) {
+    size_t freeb = 0, totalb = 0;
+    if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) break;
+    // this lane's slots and the next lane's workspaces must fit beside a margin
+    if (freeb < slot_bytes * L.size() + lane_need + ((size_t)2 << 30)) break;
+    ServeLane l;
+    l.work = new tw_lane();
+    l.owned = true;
+    if (twb::alloc_lane(c, *l.work, c->lane.bmax) != TW_OK) {
+      delete l.work;
       break;
     }
-    const long tot = drow * count;
-    k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(event_data, idx_dev, d_slot, drow, count);
-    count_launches(1);
-    st = tw_infer_batch(c, prec, count, idx_dev + B, d_slot, m_slot, q_slot, stream);
-    if (st != TW_OK) break;
-    if (cudaMemcpyAsync(q_host, q_slot, (size_t)count * Nt * Nq * sizeof(double),
-                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaEventRecord(ev1, s) != cudaSuccess) {
-      st = twh::fail(c, TW_ERR_CUDA, "serving: result copy");
+    if (cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      twb::free_lane(c, *l.work);
+      delete l.work;
       break;
     }
-    // wait for the batch while admitting arrivals
-    while (cudaEventQuery(ev1) == cudaErrorNotReady) {
-      pol.admit(now_s(t0));
-      std::this_thread::sleep_for(std::chrono::microseconds(50));
-    }
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, ev0, ev1) != cudaSuccess) {
-      st = twh::fail(c, TW_ERR_CUDA, "serving: batch timing");
-      break;
-    }
-    const double t_done = t_enq + 1e-3 * ms;
-    busy += 1e-3 * ms;
-    t_last = std::max(t_last, t_done);
-    for (int k = 0; k < count; ++k) latency_ms[first + k] = 1e3 * (t_done - arrival_s[first + k]);
-    if (q_out)
-      std::copy(q_host, q_host + (size_t)count * Nt * Nq, q_out + (size_t)first * Nt * Nq);
-    if (m_out &&
-        cudaMemcpy(m_out + (size_t)first * Nt * Nm, m_slot, (size_t)count * Nt * Nm * sizeof(double),
-                   cudaMemcpyDeviceToHost) != cudaSuccess) {
-      st = twh::fail(c, TW_ERR_CUDA, "serving: m copy");
-      break;
-    }
-    ++batches;
-    maxb = std::max(maxb, count);
+    l.own_stream = true;
+    L.push_back(l);
   }
-  if (st == TW_OK) st = tw_check(c, stream);
+  cudaGetLastError();
+  for (ServeLane &l : L) {
+    l.d_slot = (double *)twh::dalloc(c, B * drow * sizeof(double));
+    l.m_slot = (double *)twh::dalloc(c, B * (size_t)Nt * Nm * sizeof(double));
+    l.q_slot = (double *)twh::dalloc(c, B * (size_t)Nt * Nq * sizeof(double));
+    l.idx_dev = (int *)twh::dalloc(c, 2 * B * sizeof(int));
+    if (!l.d_slot || !l.m_slot || !l.q_slot || !l.idx_dev ||
+        cudaMallocHost(&l.idx_host, 2 * B * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&l.q_host, B * (size_t)Nt * Nq * sizeof(double)) != cudaSuccess ||
+        cudaEventCreate(&l.done) != cudaSuccess) {
+      cleanup();
+      return twh::fail(c, TW_ERR_OOM, "serving slots / pinned staging / events");
+    }
+  }
+  if (cudaEventCreate(&ev_ref) != cudaSuccess) {
+    cleanup();
+    return twh::fail(c, TW_ERR_CUDA, "serving: reference event");
+  }
+  const int nl = (int)L.size();
+  twserve::Policy pol(nreq, arrival_s, max_batch, nl);
+  int batches = 0, maxb = 0, max_inflight = 0;
+  double busy = 0.0, t_last = 0.0;
+  std::vector<double> t_start(nl, 0.0);
+  TW_CUDA(c, cudaDeviceSynchronize());
+  const auto t0 = std::chrono::steady_clock::now();
+  if (cudaEventRecord(ev_ref, L[0].stream) != cudaSuccess || cudaEventSynchronize(ev_ref) != cudaSuccess) {
+    cleanup();
+    return twh::fail(c, TW_ERR_CUDA, "serving: reference event");
+  }
+  const double t_ref = now_s(t0);     // host time of the device reference point
+  while (!pol.done() && st == TW_OK) {
+    bool progressed = false;
+    // completions
+    for (int k = 0; k < nl && st == TW_OK; ++k) {
+      ServeLane &l = L[k];
+      if (l.count == 0 || cudaEventQuery(l.done) != cudaSuccess) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev_ref, l.done) != cudaSuccess) {
+        st = twh::fail(c, TW_ERR_CUDA, "serving: batch timing");
+        break;
+      }
+      const double t_done = t_ref + 1e-3 * ms;
+      busy += std::max(0.0, t_done - t_start[k]);
+      t_last = std::max(t_last, t_done);
+      for (int i = 0; i < l.count; ++i) latency_ms[l.first + i] = 1e3 * (t_done - arrival_s[l.first + i]);
+      if (q_out)
+        std::copy(l.q_host, l.q_host + (size_t)l.count * Nt * Nq, q_out + (size_t)l.first * Nt * Nq);
+      if (m_out && cudaMemcpy(m_out + (size_t)l.first * Nt * Nm, l.m_slot,
+                              (size_t)l.count * Nt * Nm * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        st = twh::fail(c, TW_ERR_CUDA, "serving: m copy");
+        break;
+      }
+      l.count = 0;
+      pol.release(k);
+      progressed = true;
+    }
+    if (st != TW_OK) break;
+    // launches: every free lane takes the oldest waiting requests
+    pol.admit(now_s(t0));
+    int k;
+    while (st == TW_OK && pol.waiting() && (k = pol.free_lane()) >= 0) {
+      ServeLane &l = L[k];
+      pol.take(k, &l.first, &l.count);
+      for (int i = 0; i < l.count; ++i) {
+        l.idx_host[i] = event[l.first + i];
+        l.idx_host[B + i] = window[l.first + i];
+      }
+      t_start[k] = std::max(now_s(t0), t_ref);
+      if (cudaMemcpyAsync(l.idx_dev, l.idx_host, 2 * B * sizeof(int), cudaMemcpyHostToDevice, l.stream) !=
+          cudaSuccess) {
+        st = twh::fail(c, TW_ERR_CUDA, "serving: enqueue");
+        break;
+      }
+      const long tot = drow * l.count;
+      k_gather_rows<<<(unsigned)((tot + 255) / 256), 256, 0, l.stream>>>(event_data, l.idx_dev, l.d_slot,
+                                                                          drow, l.count);
+      count_launches(1);
+      st = twb::infer_core(c, *l.work, prec, l.count, l.idx_dev + B, l.d_slot, drow, l.m_slot, l.q_slot,
+                           l.stream);
+      if (st != TW_OK) break;
+      if (cudaMemcpyAsync(l.q_host, l.q_slot, (size_t)l.count * Nt * Nq * sizeof(double),
+                          cudaMemcpyDeviceToHost, l.stream) != cudaSuccess ||
+          cudaEventRecord(l.done, l.stream) != cudaSuccess) {
+        st = twh::fail(c, TW_ERR_CUDA, "serving: result copy");
+        break;
+      }
+      ++batches;
+      maxb = std::max(maxb, l.count);
+      max_inflight = std::max(max_inflight, pol.in_flight());
+      progressed = true;
+    }
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  if (st != TW_OK) {
+    for (ServeLane &l : L) cudaStreamSynchronize(l.stream);
+  }
+  for (ServeLane &l : L)
+    if (st == TW_OK) st = tw_check(c, l.stream);
   if (stats) {
     stats->batches = batches;
     stats->max_batch = maxb;
     stats->mean_batch = batches ? (double)nreq / batches : 0.0;
     stats->makespan_s = nreq ? t_last - arrival_s[0] : 0.0;
     stats->busy_s = busy;
+    stats->lanes = nl;
+    stats->max_in_flight = max_inflight;
   }
   cleanup();
   return st;

@@ -419,22 +419,22 @@ tw_status tw_p2o_adjoint(tw_ctx *c, tw_map which, tw_prec prec, int nrhs, const 
   TW_CUDA(c, cudaSetDevice(c->dev));
   const int R = rows_of(c, which), Nt = c->Nt, Nf = c->Nf, Nm = c->Nm;
   const void *A = c->op[which][prec];
-  if (prec != TW_PREC_FP64 && nrhs > 1 && c->bmax > 0) {
+  if (prec != TW_PREC_FP64 && nrhs > 1 && c->lane.bmax > 0) {
     // several right-hand sides with a reserved batch: the per-frequency
     // products as one matrix product on the tensor cores (exact slices)
-    for (int r0 = 0; r0 < nrhs; r0 += c->bmax) {
-      const int nb = std::min(c->bmax, nrhs - r0);
+    for (int r0 = 0; r0 < nrhs; r0 += c->lane.bmax) {
+      const int nb = std::min(c->lane.bmax, nrhs - r0);
       const BatchArg ba_y{nb, (long)Nt * R, (long)Nf * R, 0, nullptr};
       const BatchArg ba_x{nb, (long)Nf * Nm, (long)Nt * Nm, 0, nullptr};
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
-        TW_CUDA(c, launch_rfft_time_dd(y + (size_t)r0 * Nt * R, 0, R, Nt, (cdd *)c->byh, R, R, c->plT,
+        TW_CUDA(c, launch_rfft_time_dd(y + (size_t)r0 * Nt * R, 0, R, Nt, (cdd *)c->lane.byh, R, R, c->plT,
                                        c->twT, c->twL, s, ba_y)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-        TW_CUDA(c, launch_gemm_adj_sl(A, (int)prec, c->ea[which][prec], (const cdd *)c->byh, (long)Nf * R,
-                                      (cf *)c->bxh, (long)Nf * Nm, Nf, R, Nm, nb, c->sl_tile, c->bsl_ws,
-                                      c->bsl_ws_n, c->bsl_eb, c->bsl_eb_n, c->d_err, s)); }
+        TW_CUDA(c, launch_gemm_adj_sl(A, (int)prec, c->ea[which][prec], (const cdd *)c->lane.byh, (long)Nf * R,
+                                      (cf *)c->lane.bxh, (long)Nf * Nm, Nf, R, Nm, nb, c->lane.sl_tile, c->lane.bsl_ws,
+                                      c->lane.bsl_ws_n, c->lane.bsl_eb, c->lane.bsl_eb_n, c->d_err, s)); }
       { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
-        TW_CUDA(c, launch_irfft_time_f((const cf *)c->bxh, Nm, x + (size_t)r0 * Nt * Nm, 0, Nm, Nm, Nt,
+        TW_CUDA(c, launch_irfft_time_f((const cf *)c->lane.bxh, Nm, x + (size_t)r0 * Nt * Nm, 0, Nm, Nm, Nt,
                                        c->plT, c->twTf, c->twLf, s, ba_x)); }
     }
     return TW_OK;

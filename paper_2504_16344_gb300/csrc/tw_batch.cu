@@ -34,27 +34,31 @@ tw_status upload_windows(tw_ctx *c, const int *nt_window, int nrhs, cudaStream_t
     w[r] = nt_window ? nt_window[r] : c->Nt;
     if (w[r] < 1 || w[r] > c->Nt) return twh::fail(c, TW_ERR_ARG, "window must be in [1, Nt]");
   }
-  TW_CUDA(c, cudaMemcpyAsync(c->win_dev, w.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+  TW_CUDA(c, cudaMemcpyAsync(c->lane.win_dev, w.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
   return TW_OK;
 }
 
 // lanes per right-hand side of the batched forward product: 2 when at most 16
 // right-hand sides are reserved (no idle lanes), else 1; fixed per reservation
-int fwd_lpb(const tw_ctx *c) { return c->bmax <= 16 ? 2 : 1; }
+int fwd_lpb(const tw_lane &L) { return L.bmax <= 16 ? 2 : 1; }
 
 tw_status check_batch(tw_ctx *c, tw_prec prec, int nrhs, const int *win) {
   if (prec < 0 || prec > 2 || !c->op[TW_MAP_F][prec])
     return twh::fail(c, TW_ERR_ARG, "requested precision was not kept at tw_create");
-  if (c->bmax <= 0) return twh::fail(c, TW_ERR_STATE, "tw_reserve_batch must come first");
-  if (nrhs > c->bmax) return twh::fail(c, TW_ERR_ARG, "more right-hand sides than reserved");
+  if (c->lane.bmax <= 0) return twh::fail(c, TW_ERR_STATE, "tw_reserve_batch must come first");
+  if (nrhs > c->lane.bmax) return twh::fail(c, TW_ERR_ARG, "more right-hand sides than reserved");
   if (nrhs > 0 && !win) return twh::fail(c, TW_ERR_ARG, "windows (device array) required");
   if (prec == TW_PREC_FP64 ? !c->have64 : !c->Lp_dd)
     return twh::fail(c, TW_ERR_STATE, "batched solves need the FP64 factor (tw_factor_K)");
   return TW_OK;
 }
 
+}  // namespace
+
+namespace twb {
+
 // q = F_q m for B right-hand sides; rows t >= win[b] of m are taken as zero
-tw_status forecast_core(tw_ctx *c, tw_prec prec, int B, const int *win, const double *m,
+tw_status forecast_core(tw_ctx *c, tw_lane &L, tw_prec prec, int B, const int *win, const double *m,
                         double *q, cudaStream_t s) {
   const int Nt = c->Nt, Nm = c->Nm, Nf = c->Nf, Nq = c->Nq;
   const void *Aq = c->op[TW_MAP_FQ][prec];
@@ -62,87 +66,87 @@ tw_status forecast_core(tw_ctx *c, tw_prec prec, int B, const int *win, const do
   const BatchArg ba_q{B, (long)Nf * Nq, (long)Nt * Nq, 0, nullptr};
   if (prec == TW_PREC_FP64) {
     { twh::Phase p(c, TW_PH_RFFT_PARAM, s);
-      TW_CUDA(c, launch_rfft_time_dd(m, 0, Nm, Nt, (cdd *)c->bxh, Nm, Nm, c->plT, c->twT, c->twL, s, ba_m)); }
+      TW_CUDA(c, launch_rfft_time_dd(m, 0, Nm, Nt, (cdd *)L.bxh, Nm, Nm, c->plT, c->twT, c->twL, s, ba_m)); }
     { twh::Phase p(c, TW_PH_GEMV_FWD, s);
-      TW_CUDA(c, launch_gemm_fwd_dd(Aq, (const cdd *)c->bxh, (long)Nf * Nm, (cdd *)c->bpart,
-                                    (cdd *)c->byh, (long)Nf * Nq, Nf, Nq, Nm, B, s, fwd_lpb(c))); }
+      TW_CUDA(c, launch_gemm_fwd_dd(Aq, (const cdd *)L.bxh, (long)Nf * Nm, (cdd *)L.bpart,
+                                    (cdd *)L.byh, (long)Nf * Nq, Nf, Nq, Nm, B, s, fwd_lpb(L))); }
     { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
-      TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->byh, Nq, q, 0, Nq, Nq, Nt, c->plT, c->twT, c->twL, s, ba_q)); }
+      TW_CUDA(c, launch_irfft_time_dd((const cdd *)L.byh, Nq, q, 0, Nq, Nq, Nt, c->plT, c->twT, c->twL, s, ba_q)); }
   } else {
     { twh::Phase p(c, TW_PH_RFFT_PARAM, s);
-      TW_CUDA(c, launch_rfft_time_f(m, 0, Nm, Nt, (cf *)c->bxh, Nm, Nm, c->plT, c->twTf, c->twLf, s, ba_m)); }
+      TW_CUDA(c, launch_rfft_time_f(m, 0, Nm, Nt, (cf *)L.bxh, Nm, Nm, c->plT, c->twTf, c->twLf, s, ba_m)); }
     { twh::Phase p(c, TW_PH_GEMV_FWD, s);
-      TW_CUDA(c, launch_gemm_fwd_f(Aq, (int)prec, (const cf *)c->bxh, (long)Nf * Nm, (cf *)c->bpart,
-                                   (cf *)c->byh, (long)Nf * Nq, Nf, Nq, Nm, B, s, fwd_lpb(c))); }
+      TW_CUDA(c, launch_gemm_fwd_f(Aq, (int)prec, (const cf *)L.bxh, (long)Nf * Nm, (cf *)L.bpart,
+                                   (cf *)L.byh, (long)Nf * Nq, Nf, Nq, Nm, B, s, fwd_lpb(L))); }
     { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
-      TW_CUDA(c, launch_irfft_time_f((const cf *)c->byh, Nq, q, 0, Nq, Nq, Nt, c->plT, c->twTf, c->twLf, s, ba_q)); }
+      TW_CUDA(c, launch_irfft_time_f((const cf *)L.byh, Nq, q, 0, Nq, Nq, Nt, c->plT, c->twTf, c->twLf, s, ba_q)); }
   }
   return TW_OK;
 }
 
 // m = Gamma_pr F'^T K'^{-1} d' per right-hand side (window win[b]); rhs
 // column b at rhs + b * rhs_bstride (FP64, [Nt][Nd]); q = F_q m if q != NULL
-tw_status infer_core(tw_ctx *c, tw_prec prec, int B, const int *win, const double *rhs,
+tw_status infer_core(tw_ctx *c, tw_lane &L, tw_prec prec, int B, const int *win, const double *rhs,
                      long rhs_bstride, double *m, double *q, cudaStream_t s) {
   const int Nd = c->Nd, Nt = c->Nt, Nm = c->Nm, Nf = c->Nf;
   const long np = c->n_pad;
   // with G^ = F^ C kept the adjoint gives m directly (no prior filter)
   const bool useG = c->opG[prec] != nullptr;
   const void *A = useG ? c->opG[prec] : c->op[TW_MAP_F][prec];
-  int *prog_f = c->trsm_prog, *prog_b = c->trsm_prog + trsm_prog_ints(c->bmax);
+  int *prog_f = L.trsm_prog, *prog_b = L.trsm_prog + trsm_prog_ints(L.bmax);
   const BatchArg ba_y{B, np, (long)Nf * Nd, 0, win};
   const BatchArg ba_x{B, (long)Nf * Nm, (long)Nt * Nm, 0, win};
   const BatchArg ba_p{B, (long)Nt * Nm, (long)Nt * Nm, (long)((Nt + 1) / 2) * Nm, win};
   if (prec == TW_PREC_FP64) {
     { twh::Phase p(c, TW_PH_TRSV_FWD, s);
-      TW_CUDA(c, launch_trsm_d(c->Lp64, c->inv64, c->chF64, rhs, 0, rhs_bstride, c->bz, np, win, Nd,
+      TW_CUDA(c, launch_trsm_d(c->Lp64, c->inv64, c->chF64, rhs, 0, rhs_bstride, L.bz, np, win, Nd,
                                Nt, B, c->NB, prog_f, true, c->d_err, c->abort_flag, s)); }
     { twh::Phase p(c, TW_PH_TRSV_BWD, s);
-      TW_CUDA(c, launch_trsm_d(c->Lp64, c->inv64, c->chB64, c->bz, 0, np, c->by, np, win, Nd, Nt, B,
+      TW_CUDA(c, launch_trsm_d(c->Lp64, c->inv64, c->chB64, L.bz, 0, np, L.by, np, win, Nd, Nt, B,
                                c->NB, prog_b, false, c->d_err, c->abort_flag, s)); }
     { twh::Phase p(c, TW_PH_RFFT_DATA, s);
-      TW_CUDA(c, launch_rfft_time_dd(c->by, 0, Nd, Nt, (cdd *)c->byh, Nd, Nd, c->plT, c->twT, c->twL, s, ba_y)); }
+      TW_CUDA(c, launch_rfft_time_dd(L.by, 0, Nd, Nt, (cdd *)L.byh, Nd, Nd, c->plT, c->twT, c->twL, s, ba_y)); }
     { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
-      TW_CUDA(c, launch_gemm_adj_dd(A, (const cdd *)c->byh, (long)Nf * Nd, (cdd *)c->bxh, (long)Nf * Nm,
+      TW_CUDA(c, launch_gemm_adj_dd(A, (const cdd *)L.byh, (long)Nf * Nd, (cdd *)L.bxh, (long)Nf * Nm,
                                     Nf, Nd, Nm, B, s)); }
     { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
-      TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s, ba_x)); }
+      TW_CUDA(c, launch_irfft_time_dd((const cdd *)L.bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s, ba_x)); }
     if (!useG) {
       twh::Phase p(c, TW_PH_PRIOR, s);
-      TW_CUDA(c, launch_prior_dd(m, 0, m, 0, Nt, c->Nx, c->Ny, (cdd *)c->bxh, c->lam1, c->plX, c->plY,
+      TW_CUDA(c, launch_prior_dd(m, 0, m, 0, Nt, c->Nx, c->Ny, (cdd *)L.bxh, c->lam1, c->plX, c->plY,
                                  c->twX, c->twY, s, ba_p, 0));
     }
   } else {
     { twh::Phase p(c, TW_PH_TRSV_FWD, s);
-      TW_CUDA(c, launch_trsm_dd(c->Lp_dd, c->inv_dd, c->chF_dd, rhs, 0, rhs_bstride, c->bzd, np, win,
+      TW_CUDA(c, launch_trsm_dd(c->Lp_dd, c->inv_dd, c->chF_dd, rhs, 0, rhs_bstride, L.bzd, np, win,
                                 Nd, Nt, B, c->NB, prog_f, true, c->d_err, c->abort_flag, s)); }
     { twh::Phase p(c, TW_PH_TRSV_BWD, s);
-      TW_CUDA(c, launch_trsm_dd(c->Lp_dd, c->inv_dd, c->chB_dd, c->bzd, 1, np, c->byd, np, win, Nd, Nt,
+      TW_CUDA(c, launch_trsm_dd(c->Lp_dd, c->inv_dd, c->chB_dd, L.bzd, 1, np, L.byd, np, win, Nd, Nt,
                                 B, c->NB, prog_b, false, c->d_err, c->abort_flag, s)); }
     // double-float data spectra; the product on the tensor cores with both
     // sides cut into exact fixed-point slices: F^T y cancels (y is large
     // against m), so its sum has to be formed far below FP32 rounding
     { twh::Phase p(c, TW_PH_RFFT_DATA, s);
-      TW_CUDA(c, launch_rfft_time_dd(c->byd, 1, Nd, Nt, (cdd *)c->byh, Nd, Nd, c->plT, c->twT, c->twL, s, ba_y)); }
+      TW_CUDA(c, launch_rfft_time_dd(L.byd, 1, Nd, Nt, (cdd *)L.byh, Nd, Nd, c->plT, c->twT, c->twL, s, ba_y)); }
     { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
       const int8_t *ea = useG ? c->eaG[prec] : c->ea[TW_MAP_F][prec];
-      TW_CUDA(c, launch_gemm_adj_sl(A, (int)prec, ea, (const cdd *)c->byh, (long)Nf * Nd, (cf *)c->bxh,
-                                    (long)Nf * Nm, Nf, Nd, Nm, B, c->sl_tile, c->bsl_ws, c->bsl_ws_n,
-                                    c->bsl_eb, c->bsl_eb_n, c->d_err, s)); }
+      TW_CUDA(c, launch_gemm_adj_sl(A, (int)prec, ea, (const cdd *)L.byh, (long)Nf * Nd, (cf *)L.bxh,
+                                    (long)Nf * Nm, Nf, Nd, Nm, B, L.sl_tile, L.bsl_ws, L.bsl_ws_n,
+                                    L.bsl_eb, L.bsl_eb_n, c->d_err, s)); }
     { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
-      TW_CUDA(c, launch_irfft_time_f((const cf *)c->bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s, ba_x)); }
+      TW_CUDA(c, launch_irfft_time_f((const cf *)L.bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s, ba_x)); }
     if (!useG) {
       twh::Phase p(c, TW_PH_PRIOR, s);
-      TW_CUDA(c, launch_prior_f(m, 0, m, 0, Nt, c->Nx, c->Ny, (cf *)c->bxh, c->lam1f, c->plX, c->plY,
+      TW_CUDA(c, launch_prior_f(m, 0, m, 0, Nt, c->Nx, c->Ny, (cf *)L.bxh, c->lam1f, c->plX, c->plY,
                                 c->twXf, c->twYf, s, ba_p, 0));
     }
   }
-  if (q) return forecast_core(c, prec, B, win, m, q, s);
+  if (q) return forecast_core(c, L, prec, B, win, m, q, s);
   return TW_OK;
 }
 
 // s = m_pr + Gamma_pr F'^T K'^{-1} (d' - F' m_pr - sigma z_n), m_pr = Gamma_pr^{1/2} z_m
-tw_status sample_core(tw_ctx *c, tw_prec prec, int B, const int *win, const double *d,
+tw_status sample_core(tw_ctx *c, tw_lane &L, tw_prec prec, int B, const int *win, const double *d,
                       const double *z_m, const double *z_n, double sigma, double *samples,
                       cudaStream_t s) {
   const int Nd = c->Nd, Nt = c->Nt, Nm = c->Nm, Nf = c->Nf;
@@ -153,50 +157,112 @@ tw_status sample_core(tw_ctx *c, tw_prec prec, int B, const int *win, const doub
   const bool f64 = prec == TW_PREC_FP64;
   // m_pr into the output
   { twh::Phase p(c, TW_PH_PRIOR, s);
-    if (f64) TW_CUDA(c, launch_prior_dd(z_m, 0, samples, 0, Nt, c->Nx, c->Ny, (cdd *)c->bxh, c->lamh,
+    if (f64) TW_CUDA(c, launch_prior_dd(z_m, 0, samples, 0, Nt, c->Nx, c->Ny, (cdd *)L.bxh, c->lamh,
                                         c->plX, c->plY, c->twX, c->twY, s, ba_full, 0));
-    else TW_CUDA(c, launch_prior_f(z_m, 0, samples, 0, Nt, c->Nx, c->Ny, (cf *)c->bxh, c->lamhf,
+    else TW_CUDA(c, launch_prior_f(z_m, 0, samples, 0, Nt, c->Nx, c->Ny, (cf *)L.bxh, c->lamhf,
                                    c->plX, c->plY, c->twXf, c->twYf, s, ba_full, 0)); }
   // a = F' m_pr (the leading window blocks depend on m_pr's leading blocks only)
   if (f64) {
     { twh::Phase p(c, TW_PH_RFFT_PARAM, s);
-      TW_CUDA(c, launch_rfft_time_dd(samples, 0, Nm, Nt, (cdd *)c->bxh, Nm, Nm, c->plT, c->twT, c->twL, s, ba_m)); }
+      TW_CUDA(c, launch_rfft_time_dd(samples, 0, Nm, Nt, (cdd *)L.bxh, Nm, Nm, c->plT, c->twT, c->twL, s, ba_m)); }
     { twh::Phase p(c, TW_PH_GEMV_FWD, s);
-      TW_CUDA(c, launch_gemm_fwd_dd(A, (const cdd *)c->bxh, (long)Nf * Nm, (cdd *)c->bpart, (cdd *)c->byh,
-                                    (long)Nf * Nd, Nf, Nd, Nm, B, s, fwd_lpb(c))); }
+      TW_CUDA(c, launch_gemm_fwd_dd(A, (const cdd *)L.bxh, (long)Nf * Nm, (cdd *)L.bpart, (cdd *)L.byh,
+                                    (long)Nf * Nd, Nf, Nd, Nm, B, s, fwd_lpb(L))); }
     { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
-      TW_CUDA(c, launch_irfft_time_dd((const cdd *)c->byh, Nd, c->brd, 0, Nd, Nd, Nt, c->plT, c->twT, c->twL, s, ba_d)); }
+      TW_CUDA(c, launch_irfft_time_dd((const cdd *)L.byh, Nd, L.brd, 0, Nd, Nd, Nt, c->plT, c->twT, c->twL, s, ba_d)); }
   } else {
     { twh::Phase p(c, TW_PH_RFFT_PARAM, s);
-      TW_CUDA(c, launch_rfft_time_f(samples, 0, Nm, Nt, (cf *)c->bxh, Nm, Nm, c->plT, c->twTf, c->twLf, s, ba_m)); }
+      TW_CUDA(c, launch_rfft_time_f(samples, 0, Nm, Nt, (cf *)L.bxh, Nm, Nm, c->plT, c->twTf, c->twLf, s, ba_m)); }
     { twh::Phase p(c, TW_PH_GEMV_FWD, s);
-      TW_CUDA(c, launch_gemm_fwd_f(A, (int)prec, (const cf *)c->bxh, (long)Nf * Nm, (cf *)c->bpart,
-                                   (cf *)c->byh, (long)Nf * Nd, Nf, Nd, Nm, B, s, fwd_lpb(c))); }
+      TW_CUDA(c, launch_gemm_fwd_f(A, (int)prec, (const cf *)L.bxh, (long)Nf * Nm, (cf *)L.bpart,
+                                   (cf *)L.byh, (long)Nf * Nd, Nf, Nd, Nm, B, s, fwd_lpb(L))); }
     { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
-      TW_CUDA(c, launch_irfft_time_f((const cf *)c->byh, Nd, c->brd, 0, Nd, Nd, Nt, c->plT, c->twTf, c->twLf, s, ba_d)); }
+      TW_CUDA(c, launch_irfft_time_f((const cf *)L.byh, Nd, L.brd, 0, Nd, Nd, Nt, c->plT, c->twTf, c->twLf, s, ba_d)); }
   }
   const long nd = (long)B * Nt * Nd;
-  k_sample_rhs_b<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(d, c->brd, z_n, sigma, c->brd, nd);
+  k_sample_rhs_b<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(d, L.brd, z_n, sigma, L.brd, nd);
   count_launches(1);
   TW_CUDA(c, cudaGetLastError());
-  tw_status st = infer_core(c, prec, B, win, c->brd, (long)Nt * Nd, samples, nullptr, s);
+  tw_status st = infer_core(c, L, prec, B, win, L.brd, (long)Nt * Nd, samples, nullptr, s);
   if (st != TW_OK) return st;
   // add m_pr back (recomputed: no second parameter-sized buffer is needed)
   twh::Phase p(c, TW_PH_PRIOR, s);
-  if (f64) TW_CUDA(c, launch_prior_dd(z_m, 0, samples, 0, Nt, c->Nx, c->Ny, (cdd *)c->bxh, c->lamh,
+  if (f64) TW_CUDA(c, launch_prior_dd(z_m, 0, samples, 0, Nt, c->Nx, c->Ny, (cdd *)L.bxh, c->lamh,
                                       c->plX, c->plY, c->twX, c->twY, s, ba_full, 1));
-  else TW_CUDA(c, launch_prior_f(z_m, 0, samples, 0, Nt, c->Nx, c->Ny, (cf *)c->bxh, c->lamhf,
+  else TW_CUDA(c, launch_prior_f(z_m, 0, samples, 0, Nt, c->Nx, c->Ny, (cf *)L.bxh, c->lamhf,
                                  c->plX, c->plY, c->twXf, c->twYf, s, ba_full, 1));
   return TW_OK;
 }
 
-void free_batch(tw_ctx *c) {
-  void **bufs[] = {(void **)&c->win_dev, (void **)&c->trsm_prog, (void **)&c->bz, (void **)&c->by,
-                   (void **)&c->bzd, (void **)&c->byd, (void **)&c->brd, &c->byh, &c->bxh,
-                   &c->bpart, (void **)&c->Lp_dd, (void **)&c->inv_dd, (void **)&c->chF_dd,
-                   (void **)&c->chB_dd, &c->bsl_ws, (void **)&c->bsl_eb};
+size_t lane_bytes(const tw_ctx *c, int bmax) {
+  const size_t B = bmax, np = c->n_pad, Nt = c->Nt, Nf = c->Nf, Nm = c->Nm, R = c->Rmax;
+  const bool mixed = c->op[TW_MAP_F][TW_PREC_C64] || c->op[TW_MAP_F][TW_PREC_BF16X2];
+  size_t b = B * sizeof(int) + 2 * (size_t)trsm_prog_ints(bmax) * sizeof(int) + 2 * B * np * sizeof(double) +
+             B * Nt * c->Nd * sizeof(double) + B * Nf * R * sizeof(cdd) + B * Nf * Nm * sizeof(cdd) +
+             B * Nf * (size_t)gemm_fwd_nchunk(c->Nm) * R * sizeof(cdd);
+  if (mixed) {
+    const int tile = sl_pick_tile(bmax), cols = (bmax + tile - 1) / tile * tile;
+    b += 2 * B * np * sizeof(dd) + sl_ws_bytes(c->Nf, c->Rmax, cols) + sl_eb_bytes(c->Nf, cols);
+  }
+  return b;
+}
+
+void free_lane(tw_ctx *c, tw_lane &L) {
+  void **bufs[] = {(void **)&L.win_dev, (void **)&L.trsm_prog, (void **)&L.bz, (void **)&L.by,
+                   (void **)&L.bzd, (void **)&L.byd, (void **)&L.brd, &L.byh, &L.bxh, &L.bpart,
+                   &L.bsl_ws, (void **)&L.bsl_eb};
   for (void **b : bufs) { twh::dfree(c, *b); *b = nullptr; }
-  c->bmax = 0;
+  L.bmax = 0;
+  L.bytes = 0;
+}
+
+tw_status alloc_lane(tw_ctx *c, tw_lane &L, int bmax) {
+  free_lane(c, L);
+  const size_t B = bmax, np = c->n_pad, Nt = c->Nt, Nf = c->Nf, Nm = c->Nm, R = c->Rmax;
+  const bool mixed = c->op[TW_MAP_F][TW_PREC_C64] || c->op[TW_MAP_F][TW_PREC_BF16X2];
+  bool ok = true;
+  auto take = [&](size_t bytes) -> void * {
+    void *p = twh::dalloc(c, bytes);
+    ok = ok && p;
+    return p;
+  };
+  L.win_dev = (int *)take(B * sizeof(int));
+  L.trsm_prog = (int *)take(2 * (size_t)trsm_prog_ints(bmax) * sizeof(int));
+  L.bz = (double *)take(B * np * sizeof(double));
+  L.by = (double *)take(B * np * sizeof(double));
+  L.brd = (double *)take(B * Nt * c->Nd * sizeof(double));
+  L.byh = take(B * Nf * R * sizeof(cdd));
+  L.bxh = take(B * Nf * Nm * sizeof(cdd));   // >= B * ceil(Nt/2) * Nm: also the prior's work
+  L.bpart = take(B * Nf * (size_t)gemm_fwd_nchunk(c->Nm) * R * sizeof(cdd));
+  if (mixed) {
+    L.bzd = (dd *)take(B * np * sizeof(dd));
+    L.byd = (dd *)take(B * np * sizeof(dd));
+    // data-side slices of the tensor-core adjoint
+    L.sl_tile = sl_pick_tile(bmax);
+    const int cols = (bmax + L.sl_tile - 1) / L.sl_tile * L.sl_tile;
+    L.bsl_ws_n = sl_ws_bytes(c->Nf, c->Rmax, cols);
+    L.bsl_eb_n = sl_eb_bytes(c->Nf, cols);
+    L.bsl_ws = take(L.bsl_ws_n);
+    L.bsl_eb = (int *)take(L.bsl_eb_n);
+  }
+  if (!ok) {
+    free_lane(c, L);
+    return twh::fail(c, TW_ERR_OOM, "batch workspaces");
+  }
+  L.bmax = bmax;
+  L.bytes = lane_bytes(c, bmax);
+  TW_CUDA(c, cudaMemset(L.win_dev, 0, B * sizeof(int)));
+  return TW_OK;
+}
+
+}  // namespace twb
+
+namespace {
+
+void free_batch(tw_ctx *c) {
+  twb::free_lane(c, c->lane);
+  void **bufs[] = {(void **)&c->Lp_dd, (void **)&c->inv_dd, (void **)&c->chF_dd, (void **)&c->chB_dd};
+  for (void **b : bufs) { twh::dfree(c, *b); *b = nullptr; }
 }
 
 }  // namespace
@@ -223,51 +289,27 @@ tw_status tw_reserve_batch(tw_ctx *c, int bmax) {
   TW_CUDA(c, cudaDeviceSynchronize());
   free_batch(c);
   if (bmax == 0) return TW_OK;
-  const size_t B = bmax, np = c->n_pad, Nt = c->Nt, Nf = c->Nf, Nm = c->Nm, R = c->Rmax;
   const bool mixed = c->op[TW_MAP_F][TW_PREC_C64] || c->op[TW_MAP_F][TW_PREC_BF16X2];
-  const size_t blk = (size_t)NB_ * NB_;
-  const size_t nblk = (size_t)c->NB * (c->NB + 1) / 2;
-  bool ok = true;
-  auto take = [&](size_t bytes) -> void * {
-    void *p = twh::dalloc(c, bytes);
-    ok = ok && p;
-    return p;
-  };
-  c->win_dev = (int *)take(B * sizeof(int));
-  c->trsm_prog = (int *)take(2 * (size_t)trsm_prog_ints(bmax) * sizeof(int));
-  c->bz = (double *)take(B * np * sizeof(double));
-  c->by = (double *)take(B * np * sizeof(double));
-  c->brd = (double *)take(B * Nt * c->Nd * sizeof(double));
-  c->byh = take(B * Nf * R * sizeof(cdd));
-  c->bxh = take(B * Nf * Nm * sizeof(cdd));   // >= B * ceil(Nt/2) * Nm: also the prior's work
-  c->bpart = take(B * Nf * (size_t)gemm_fwd_nchunk(c->Nm) * R * sizeof(cdd));
-  if (mixed) {
-    c->bzd = (dd *)take(B * np * sizeof(dd));
-    c->byd = (dd *)take(B * np * sizeof(dd));
-    c->Lp_dd = (dd *)take(nblk * blk * sizeof(dd));
-    c->inv_dd = (dd *)take(c->NB * blk * sizeof(dd));
-    c->chF_dd = (dd *)take(c->NB * blk * sizeof(dd));
-    c->chB_dd = (dd *)take(c->NB * blk * sizeof(dd));
+  if (mixed) {   // float-pair copy of the FP64 factor for the mixed batched solves
+    const size_t blk = (size_t)NB_ * NB_, nblk = (size_t)c->NB * (c->NB + 1) / 2;
+    c->Lp_dd = (dd *)twh::dalloc(c, nblk * blk * sizeof(dd));
+    c->inv_dd = (dd *)twh::dalloc(c, c->NB * blk * sizeof(dd));
+    c->chF_dd = (dd *)twh::dalloc(c, c->NB * blk * sizeof(dd));
+    c->chB_dd = (dd *)twh::dalloc(c, c->NB * blk * sizeof(dd));
+    if (!c->Lp_dd || !c->inv_dd || !c->chF_dd || !c->chB_dd) {
+      free_batch(c);
+      return twh::fail(c, TW_ERR_OOM, "batch workspaces");
+    }
   }
-  if (mixed) {   // data-side slices of the tensor-core adjoint
-    c->sl_tile = sl_pick_tile(bmax);
-    const int cols = (bmax + c->sl_tile - 1) / c->sl_tile * c->sl_tile;
-    c->bsl_ws_n = sl_ws_bytes(c->Nf, c->Rmax, cols);
-    c->bsl_eb_n = sl_eb_bytes(c->Nf, cols);
-    c->bsl_ws = take(c->bsl_ws_n);
-    c->bsl_eb = (int *)take(c->bsl_eb_n);
-  }
-  if (!ok) {
+  tw_status st = twb::alloc_lane(c, c->lane, bmax);
+  if (st != TW_OK) {
     free_batch(c);
-    return twh::fail(c, TW_ERR_OOM, "batch workspaces");
+    return st;
   }
-
-  c->bmax = bmax;
-  TW_CUDA(c, cudaMemset(c->win_dev, 0, B * sizeof(int)));
   return twh::refresh_dd_factor(c, 0);
 }
 
-int tw_batch_capacity(const tw_ctx *c) { return c ? c->bmax : -1; }
+int tw_batch_capacity(const tw_ctx *c) { return c ? c->lane.bmax : -1; }
 
 tw_status tw_infer_batch(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window_dev,
                          const double *d, double *m, double *q, void *stream) {
@@ -276,7 +318,7 @@ tw_status tw_infer_batch(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window
   tw_status st = check_batch(c, prec, nrhs, nt_window_dev);
   if (st != TW_OK || nrhs == 0) return st;
   TW_CUDA(c, cudaSetDevice(c->dev));
-  return infer_core(c, prec, nrhs, nt_window_dev, d, (long)c->Nt * c->Nd, m, q, (cudaStream_t)stream);
+  return twb::infer_core(c, c->lane, prec, nrhs, nt_window_dev, d, (long)c->Nt * c->Nd, m, q, (cudaStream_t)stream);
 }
 
 tw_status tw_sample_posterior_batch(tw_ctx *c, tw_prec prec, int ns, const int *nt_window_dev,
@@ -289,7 +331,7 @@ tw_status tw_sample_posterior_batch(tw_ctx *c, tw_prec prec, int ns, const int *
   tw_status st = check_batch(c, prec, ns, nt_window_dev);
   if (st != TW_OK || ns == 0) return st;
   TW_CUDA(c, cudaSetDevice(c->dev));
-  return sample_core(c, prec, ns, nt_window_dev, d, z_m, z_n, sigma, samples, (cudaStream_t)stream);
+  return twb::sample_core(c, c->lane, prec, ns, nt_window_dev, d, z_m, z_n, sigma, samples, (cudaStream_t)stream);
 }
 
 tw_status tw_forecast_batch(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window_dev,
@@ -298,11 +340,11 @@ tw_status tw_forecast_batch(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_win
   if (nrhs < 0 || (nrhs > 0 && (!m || !q))) return twh::fail(c, TW_ERR_ARG, "bad rhs");
   if (prec < 0 || prec > 2 || !c->op[TW_MAP_FQ][prec])
     return twh::fail(c, TW_ERR_ARG, "requested precision was not kept at tw_create");
-  if (c->bmax <= 0) return twh::fail(c, TW_ERR_STATE, "tw_reserve_batch must come first");
-  if (nrhs > c->bmax) return twh::fail(c, TW_ERR_ARG, "more right-hand sides than reserved");
+  if (c->lane.bmax <= 0) return twh::fail(c, TW_ERR_STATE, "tw_reserve_batch must come first");
+  if (nrhs > c->lane.bmax) return twh::fail(c, TW_ERR_ARG, "more right-hand sides than reserved");
   if (nrhs == 0) return TW_OK;
   TW_CUDA(c, cudaSetDevice(c->dev));
-  return forecast_core(c, prec, nrhs, nt_window_dev, m, q, (cudaStream_t)stream);
+  return twb::forecast_core(c, c->lane, prec, nrhs, nt_window_dev, m, q, (cudaStream_t)stream);
 }
 
 // ---- CUDA graphs of batched calls
@@ -369,11 +411,11 @@ namespace twb {
 
 tw_status infer_host_windows(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window,
                              const double *d, double *m, cudaStream_t s) {
-  for (int r0 = 0; r0 < nrhs; r0 += c->bmax) {
-    const int nb = std::min(c->bmax, nrhs - r0);
+  for (int r0 = 0; r0 < nrhs; r0 += c->lane.bmax) {
+    const int nb = std::min(c->lane.bmax, nrhs - r0);
     tw_status st = upload_windows(c, nt_window ? nt_window + r0 : nullptr, nb, s);
     if (st != TW_OK) return st;
-    st = infer_core(c, prec, nb, c->win_dev, d + (size_t)r0 * c->Nt * c->Nd, (long)c->Nt * c->Nd,
+    st = infer_core(c, c->lane, prec, nb, c->lane.win_dev, d + (size_t)r0 * c->Nt * c->Nd, (long)c->Nt * c->Nd,
                     m + (size_t)r0 * c->Nt * c->Nm, nullptr, s);
     if (st != TW_OK) return st;
   }
@@ -384,11 +426,11 @@ tw_status sample_host_windows(tw_ctx *c, int ns, const int *nt_window, const dou
                               const double *z_m, const double *z_n, double sigma, double *samples,
                               cudaStream_t s) {
   const size_t pm = (size_t)c->Nt * c->Nm, pd = (size_t)c->Nt * c->Nd;
-  for (int k0 = 0; k0 < ns; k0 += c->bmax) {
-    const int nb = std::min(c->bmax, ns - k0);
+  for (int k0 = 0; k0 < ns; k0 += c->lane.bmax) {
+    const int nb = std::min(c->lane.bmax, ns - k0);
     tw_status st = upload_windows(c, nt_window ? nt_window + k0 : nullptr, nb, s);
     if (st != TW_OK) return st;
-    st = sample_core(c, TW_PREC_FP64, nb, c->win_dev, d + k0 * pd, z_m + k0 * pm, z_n + k0 * pd,
+    st = sample_core(c, c->lane, TW_PREC_FP64, nb, c->lane.win_dev, d + k0 * pd, z_m + k0 * pm, z_n + k0 * pd,
                      sigma, samples + k0 * pm, s);
     if (st != TW_OK) return st;
   }
@@ -398,9 +440,9 @@ tw_status sample_host_windows(tw_ctx *c, int ns, const int *nt_window, const dou
 tw_status forecast_full(tw_ctx *c, tw_prec prec, int nrhs, const double *m, double *q,
                         cudaStream_t s) {
   const size_t pm = (size_t)c->Nt * c->Nm, pq = (size_t)c->Nt * c->Nq;
-  for (int r0 = 0; r0 < nrhs; r0 += c->bmax) {
-    const int nb = std::min(c->bmax, nrhs - r0);
-    tw_status st = forecast_core(c, prec, nb, nullptr, m + r0 * pm, q + r0 * pq, s);
+  for (int r0 = 0; r0 < nrhs; r0 += c->lane.bmax) {
+    const int nb = std::min(c->lane.bmax, nrhs - r0);
+    tw_status st = forecast_core(c, c->lane, prec, nb, nullptr, m + r0 * pm, q + r0 * pq, s);
     if (st != TW_OK) return st;
   }
   return TW_OK;

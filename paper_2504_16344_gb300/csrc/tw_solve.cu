@@ -343,20 +343,20 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
   const void *A = c->op[TW_MAP_F][prec];
   if (stats) { stats->ir_iters = 0; stats->resid_rel = 0.0; }
   // several right-hand sides with a reserved batch: batched solves and products
-  if (nrhs > 1 && c->bmax > 0 && (mixed ? (!use32 && c->Lp_dd) : c->have64)) {
+  if (nrhs > 1 && c->lane.bmax > 0 && (mixed ? (!use32 && c->Lp_dd) : c->have64)) {
     tw_status st = twb::infer_host_windows(c, prec, nrhs, nt_window, d, m, s);
     if (st != TW_OK || !stats) return st;
     // residual of the last right-hand side (its solution is the batch's last column)
-    const int last = (nrhs - 1) % c->bmax;
+    const int last = (nrhs - 1) % c->lane.bmax;
     const int w = nt_window ? nt_window[nrhs - 1] : Nt;
     const int nrows = Nd * w;
     const int NBw = (nrows + NB_ - 1) / NB_;
     const double *dr = d + (size_t)(nrhs - 1) * Nt * Nd;
     if (mixed)
-      TW_CUDA(c, cudaMemcpyAsync(c->vy, c->byd + (size_t)last * c->n_pad, (size_t)nrows * sizeof(dd),
+      TW_CUDA(c, cudaMemcpyAsync(c->vy, c->lane.byd + (size_t)last * c->n_pad, (size_t)nrows * sizeof(dd),
                                  cudaMemcpyDeviceToDevice, s));
     else
-      TW_CUDA(c, launch_double_to_dd_vec(c->by + (size_t)last * c->n_pad, c->vy, nrows, s));
+      TW_CUDA(c, launch_double_to_dd_vec(c->lane.by + (size_t)last * c->n_pad, c->vy, nrows, s));
     if (!c->Kp64) {   // factor loaded from a checkpoint: K itself is not held
       stats->resid_rel = -1.0;
       return TW_OK;
@@ -535,7 +535,7 @@ tw_status tw_sample_posterior(tw_ctx *c, int ns, const int *nt_window, const dou
     return twh::fail(c, TW_ERR_STATE, "tw_sample_posterior needs the FP64 factor and operator");
   cudaStream_t s = (cudaStream_t)stream;
   TW_CUDA(c, cudaSetDevice(c->dev));
-  if (ns > 1 && c->bmax > 0)
+  if (ns > 1 && c->lane.bmax > 0)
     return twb::sample_host_windows(c, ns, nt_window, d, z_m, z_n, sigma, samples, s);
   const int Nd = c->Nd, Nt = c->Nt, Nm = c->Nm, Nf = c->Nf;
   const void *A = c->op[TW_MAP_F][FMT_DD];
@@ -576,7 +576,7 @@ tw_status tw_sample_posterior(tw_ctx *c, int ns, const int *nt_window, const dou
 }
 
 tw_status tw_forecast(tw_ctx *c, tw_prec prec, int nrhs, const double *m, double *q, void *stream) {
-  if (c && nrhs > 1 && c->bmax > 0 && prec >= 0 && prec <= 2 && c->op[TW_MAP_FQ][prec] && m && q) {
+  if (c && nrhs > 1 && c->lane.bmax > 0 && prec >= 0 && prec <= 2 && c->op[TW_MAP_FQ][prec] && m && q) {
     for (char l : c->loaded[TW_MAP_FQ])
       if (!l) return twh::fail(c, TW_ERR_STATE, "block column not fully loaded");
     TW_CUDA(c, cudaSetDevice(c->dev));

@@ -73,8 +73,8 @@ SIGNATURES = {
     "tw_graph_launch": (_S, [_P, _P]),
     "tw_graph_kernel_count": (_I, [_P]),
     "tw_graph_destroy": (None, [_P]),
-    "tw_serve_replay": (_S, [_P, _I, _I, _P, _P, _P, _I, _P, _I, _P, _P, _P, _P, _P]),
-    "tw_serve_simulate": (_S, [_I, _P, _I, _D, _D, _P, _P]),
+    "tw_serve_replay": (_S, [_P, _I, _I, _P, _P, _P, _I, _P, _I, _I, _P, _P, _P, _P, _P]),
+    "tw_serve_simulate": (_S, [_I, _P, _I, _I, _D, _D, _P, _P]),
     "tw_qoi_build": (_S, [_P, _P]),
     "tw_qoi_apply": (_S, [_P, _I, _P, _P, _P]),
     "tw_qoi_variance": (_S, [_P, _P, _P]),
@@ -91,7 +91,8 @@ class InferStats(ctypes.Structure):
 class ServeStats(ctypes.Structure):
     _fields_ = [("batches", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("mean_batch", ctypes.c_double), ("makespan_s", ctypes.c_double),
-                ("busy_s", ctypes.c_double)]
+                ("busy_s", ctypes.c_double), ("lanes", ctypes.c_int),
+                ("max_in_flight", ctypes.c_int)]
 
 
 class TwError(RuntimeError):
@@ -401,8 +402,9 @@ class Context:
         return out
 
     def serve_replay(self, prec, arrival_s, event, window, event_data, max_batch, stream,
-                     q_out=True, m_out=False):
-        """Replay a request trace (host arrays) with continuous batching.
+                     q_out=True, m_out=False, lanes=0):
+        """Replay a request trace (host arrays) with continuous batching over
+        up to `lanes` batches in flight (0: as many as device memory allows, <= 4).
 
         Returns (latency_ms [n], q [n][Nt][Nq] or None, m [n][Nt][Nm] or None, ServeStats)."""
         import numpy as np
@@ -419,7 +421,7 @@ class Context:
         st = ServeStats()
         ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
         self._check(self.lib.tw_serve_replay(self.h, prec, n, ptr(arr), ptr(ev), ptr(win), ne, pe,
-                                             int(max_batch), ptr(lat), ptr(q), ptr(m),
+                                             int(max_batch), int(lanes), ptr(lat), ptr(q), ptr(m),
                                              ctypes.byref(st), _stream_ptr(stream)))
         return lat, q, m, st
 
@@ -515,14 +517,15 @@ class _Capture:
         return False
 
 
-def serve_simulate(arrival_s, max_batch, cost_ms, cost_ms_per_req):
-    """The serving policy on a virtual clock: (latency_ms [n], batch index [n]). Host only."""
+def serve_simulate(arrival_s, max_batch, cost_ms, cost_ms_per_req, lanes=1):
+    """The serving policy on a virtual clock with `lanes` batch lanes:
+    (latency_ms [n], batch index [n] in start order).  Host only."""
     import numpy as np
     arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
     n = len(arr)
     lat = np.zeros(n, dtype=np.float64)
     bid = np.zeros(n, dtype=np.int32)
-    st = load().tw_serve_simulate(n, arr.ctypes.data_as(ctypes.c_void_p), int(max_batch),
+    st = load().tw_serve_simulate(n, arr.ctypes.data_as(ctypes.c_void_p), int(max_batch), int(lanes),
                                   float(cost_ms), float(cost_ms_per_req),
                                   lat.ctypes.data_as(ctypes.c_void_p),
                                   bid.ctypes.data_as(ctypes.c_void_p))
