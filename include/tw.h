@@ -401,6 +401,40 @@ int tw_batch_capacity(const tw_ctx *ctx);
 tw_status tw_infer_batch(tw_ctx *ctx, tw_prec prec, int nrhs, const int *nt_window_dev,
                          const double *d, double *m, double *q, void *stream);
 
+/*
+ * Tiles of the batched per-frequency products.  tw_reserve_batch times the
+ * legal candidates on the context's operator and workspaces (CUDA events,
+ * one warm-up launch, the mean of two) and keeps the fastest; the choice is
+ * cached for the process by shape (Nd, Nq, Nx, Ny, Nt, bmax, keep), so a
+ * later context of the same shape takes it without measuring.  The
+ * environment variable TW_AUTOTUNE=0 keeps the built-in rules instead.
+ *   adj_tile  : right-hand sides per tensor-core tile of the reduced-
+ *               precision adjoint (multiple of 8, <= 80; more tiles re-read
+ *               the operator, fewer leave the MMA narrow)
+ *   adj_rw    : right-hand sides per warp of the FP64-class adjoint (1, 2, 4;
+ *               0 = by batch size)
+ *   fwd_lanes : lanes per right-hand side of the forward products (1, 2)
+ * A column's result never depends on its batch mates for any choice; it
+ * can differ in the last bits between choices (fwd_lanes changes the order
+ * of its sums), so every lane of a context uses the same tiles.
+ */
+typedef struct {
+  int adj_tile, adj_rw, fwd_lanes;
+  double adj_tile_ms, adj_rw_ms, fwd_lanes_ms;  /* time of each choice; -1 if not measured */
+  int tuned;            /* 1 measured (now or by an earlier context), 0 built-in
+                           rules, 2 set by tw_set_batch_tiles                  */
+} tw_tiles;
+
+/* The tiles the reserved batch uses (TW_ERR_STATE without tw_reserve_batch). */
+tw_status tw_batch_tiles(const tw_ctx *ctx, tw_tiles *out);
+/* Use these tiles instead (validated; the *_ms fields are ignored). */
+tw_status tw_set_batch_tiles(tw_ctx *ctx, const tw_tiles *tiles);
+/* The selection rule: index of the smallest positive time among n (-1 if
+ * none; ties keep the earlier candidate).  Host only. */
+int tw_autotune_pick(int n, const double *ms);
+/* Forget the process-wide cache of measured tiles. */
+void tw_autotune_clear_cache(void);
+
 /* tw_sample_posterior for ns <= bmax samples with windows in DEVICE memory
  * (values in [0, Nt]); prec as tw_infer_batch.  No allocation, no
  * synchronisation (capturable). */

@@ -21,11 +21,18 @@ struct tw_lane {
   void *byh = nullptr;               // [bmax][Nf][Rmax] data-side spectra (16-byte entries)
   void *bxh = nullptr;               // [bmax][Nf][Nm] parameter-side spectra / prior work
   void *bpart = nullptr;             // [bmax][Nf][nchunk][Rmax] forward-product partial sums
-  // data-side slices and column exponents of the tensor-core adjoint
+  // data-side slices and column exponents of the tensor-core adjoint (sized
+  // for any tile of up to 80 right-hand sides)
   void *bsl_ws = nullptr;
   int *bsl_eb = nullptr;
   size_t bsl_ws_n = 0, bsl_eb_n = 0;
-  int sl_tile = 0;                   // right-hand sides per tile of that product
+  // tiles of the batched products (tw_batch_tiles): right-hand sides per
+  // tensor-core tile (mixed adjoint) and per warp (FP64-class adjoint), lanes
+  // per right-hand side (forward products); chosen by measurement at
+  // tw_reserve_batch, the same for every lane of a context
+  int sl_tile = 0;
+  int adj_rw = 0;
+  int fwd_lpb = 1;
   size_t bytes = 0;                  // device bytes of the lane
 };
 
@@ -96,8 +103,10 @@ struct tw_ctx {
   int ir_steps = 3;
   int solver = TW_SOLVE_FACTOR64;
   double ir_probe_resid = 0.0;
-  // batched right-hand sides (tw_reserve_batch): the reserved lane
+  // batched right-hand sides (tw_reserve_batch): the reserved lane and the
+  // tiles chosen for its products
   tw_lane lane;
+  tw_tiles tiles{};
   tw::dd *Lp_dd = nullptr, *inv_dd = nullptr, *chF_dd = nullptr, *chB_dd = nullptr;
   // Phase 3 QoI precomputations (tw_qoi_build): rows indexed by QoI entry t*Nq + i
   double *Qmap = nullptr, *Wmap = nullptr;   // [Nq Nt][Nd Nt]: Q = F_q Gamma_pr F^T K^-1, W = (F Gamma_pr F_q^T)^T
@@ -149,6 +158,10 @@ size_t lane_bytes(const tw_ctx *c, int bmax);
 // the batched posterior mean (+ forecast when q) of B right-hand sides in lane L
 tw_status infer_core(tw_ctx *c, tw_lane &L, tw_prec prec, int B, const int *win, const double *rhs,
                      long rhs_bstride, double *m, double *q, cudaStream_t s);
+// measure the tile candidates of the batched products on lane L (or take
+// them from the process-wide cache of earlier contexts with the same shapes)
+tw_status autotune_lane(tw_ctx *c, tw_lane &L);
+void copy_tiles(tw_lane &dst, const tw_lane &src);
 tw_status infer_host_windows(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window,
                              const double *d, double *m, cudaStream_t s);
 tw_status sample_host_windows(tw_ctx *c, int ns, const int *nt_window, const double *d,

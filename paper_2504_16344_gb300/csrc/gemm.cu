@@ -321,9 +321,10 @@ static void adj_dd_run(const void *A, const cdd *Y, long y_bstride, cdd *X, long
 }
 
 cudaError_t launch_gemm_adj_dd(const void *A, const cdd *Y, long y_bstride, cdd *X, long x_bstride,
-                               int Nf, int Nr, int Nm, int B, cudaStream_t s) {
+                               int Nf, int Nr, int Nm, int B, cudaStream_t s, int rw) {
   if (B <= 0) return cudaSuccess;
-  switch (adj_rw(B)) {
+  if (rw != 0 && rw != 1 && rw != 2 && rw != 4) return cudaErrorInvalidValue;
+  switch (rw ? rw : adj_rw(B)) {
     case 4: adj_dd_run<4>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;
     case 2: adj_dd_run<2>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;
     default: adj_dd_run<1>(A, Y, y_bstride, X, x_bstride, Nf, Nr, Nm, B, s); break;

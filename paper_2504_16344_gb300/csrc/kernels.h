@@ -93,8 +93,10 @@ cudaError_t launch_gemv_adj_cx(const void *A, int fmt, const cdd *yh, cf *xh, in
 // adjoint: X[b][w][k] = sum_s conj(A[w][s][k]) Y[b][w][s]
 // forward: Yo[b][w][r] = sum_k A[w][r][k] X[b][w][k]; part: B*Nf*nchunk*Nr entries
 int gemm_fwd_nchunk(int Nm);
+// rw: right-hand sides per warp (1, 2 or 4; 0 picks after B).  Each column's
+// sum runs over the rows in the same order whatever rw is.
 cudaError_t launch_gemm_adj_dd(const void *A, const cdd *Y, long y_bstride, cdd *X, long x_bstride,
-                               int Nf, int Nr, int Nm, int B, cudaStream_t s);
+                               int Nf, int Nr, int Nm, int B, cudaStream_t s, int rw = 0);
 // lpb: lanes per right-hand side in the forward product (1 or 2, fixed per
 // context so that a right-hand side's sum order does not depend on its batch)
 cudaError_t launch_gemm_fwd_dd(const void *A, const cdd *X, long x_bstride, cdd *part, cdd *Yo,

@@ -158,6 +158,7 @@ tw_status tw_serve_replay(tw_ctx *c, tw_prec prec, int nreq, const double *arriv
       delete l.work;
       break;
     }
+    twb::copy_tiles(*l.work, c->lane);
     if (cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) != cudaSuccess) {
       twb::free_lane(c, *l.work);
       delete l.work;

@@ -38,9 +38,9 @@ tw_status upload_windows(tw_ctx *c, const int *nt_window, int nrhs, cudaStream_t
   return TW_OK;
 }
 
-// lanes per right-hand side of the batched forward product: 2 when at most 16
-// right-hand sides are reserved (no idle lanes), else 1; fixed per reservation
-int fwd_lpb(const tw_lane &L) { return L.bmax <= 16 ? 2 : 1; }
+// lanes per right-hand side of the batched forward product, fixed per
+// reservation (a column's sum order must not depend on its batch)
+int fwd_lpb(const tw_lane &L) { return L.fwd_lpb; }
 
 tw_status check_batch(tw_ctx *c, tw_prec prec, int nrhs, const int *win) {
   if (prec < 0 || prec > 2 || !c->op[TW_MAP_F][prec])
@@ -108,7 +108,7 @@ tw_status infer_core(tw_ctx *c, tw_lane &L, tw_prec prec, int B, const int *win,
       TW_CUDA(c, launch_rfft_time_dd(L.by, 0, Nd, Nt, (cdd *)L.byh, Nd, Nd, c->plT, c->twT, c->twL, s, ba_y)); }
     { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
       TW_CUDA(c, launch_gemm_adj_dd(A, (const cdd *)L.byh, (long)Nf * Nd, (cdd *)L.bxh, (long)Nf * Nm,
-                                    Nf, Nd, Nm, B, s)); }
+                                    Nf, Nd, Nm, B, s, L.adj_rw)); }
     { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
       TW_CUDA(c, launch_irfft_time_dd((const cdd *)L.bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s, ba_x)); }
     if (!useG) {
@@ -201,7 +201,7 @@ size_t lane_bytes(const tw_ctx *c, int bmax) {
              B * Nt * c->Nd * sizeof(double) + B * Nf * R * sizeof(cdd) + B * Nf * Nm * sizeof(cdd) +
              B * Nf * (size_t)gemm_fwd_nchunk(c->Nm) * R * sizeof(cdd);
   if (mixed) {
-    const int tile = sl_pick_tile(bmax), cols = (bmax + tile - 1) / tile * tile;
+    const int cols = (bmax + 7) / 8 * 8 + 80;
     b += 2 * B * np * sizeof(dd) + sl_ws_bytes(c->Nf, c->Rmax, cols) + sl_eb_bytes(c->Nf, cols);
   }
   return b;
@@ -237,9 +237,10 @@ tw_status alloc_lane(tw_ctx *c, tw_lane &L, int bmax) {
   if (mixed) {
     L.bzd = (dd *)take(B * np * sizeof(dd));
     L.byd = (dd *)take(B * np * sizeof(dd));
-    // data-side slices of the tensor-core adjoint
+    // data-side slices of the tensor-core adjoint, for any tile P <= 80:
+    // ceil(bmax / P) P < bmax + 80 columns
     L.sl_tile = sl_pick_tile(bmax);
-    const int cols = (bmax + L.sl_tile - 1) / L.sl_tile * L.sl_tile;
+    const int cols = (bmax + 7) / 8 * 8 + 80;
     L.bsl_ws_n = sl_ws_bytes(c->Nf, c->Rmax, cols);
     L.bsl_eb_n = sl_eb_bytes(c->Nf, cols);
     L.bsl_ws = take(L.bsl_ws_n);
@@ -250,6 +251,8 @@ tw_status alloc_lane(tw_ctx *c, tw_lane &L, int bmax) {
     return twh::fail(c, TW_ERR_OOM, "batch workspaces");
   }
   L.bmax = bmax;
+  L.adj_rw = 0;
+  L.fwd_lpb = bmax <= 16 ? 2 : 1;      // defaults until measured
   L.bytes = lane_bytes(c, bmax);
   TW_CUDA(c, cudaMemset(L.win_dev, 0, B * sizeof(int)));
   return TW_OK;
@@ -306,7 +309,9 @@ tw_status tw_reserve_batch(tw_ctx *c, int bmax) {
     free_batch(c);
     return st;
   }
-  return twh::refresh_dd_factor(c, 0);
+  st = twh::refresh_dd_factor(c, 0);
+  if (st != TW_OK) return st;
+  return twb::autotune_lane(c, c->lane);
 }
 
 int tw_batch_capacity(const tw_ctx *c) { return c ? c->lane.bmax : -1; }

@@ -64,6 +64,10 @@ SIGNATURES = {
     "tw_check": (_S, [_P, _P]),
     "tw_device_bytes": (ctypes.c_size_t, [_P]),
     "tw_reserve_batch": (_S, [_P, _I]),
+    "tw_batch_tiles": (_S, [_P, _P]),
+    "tw_set_batch_tiles": (_S, [_P, _P]),
+    "tw_autotune_pick": (_I, [_I, _P]),
+    "tw_autotune_clear_cache": (None, []),
     "tw_batch_capacity": (_I, [_P]),
     "tw_infer_batch": (_S, [_P, _I, _I, _P, _P, _P, _P, _P]),
     "tw_sample_posterior_batch": (_S, [_P, _I, _I, _P, _P, _P, _P, _D, _P, _P]),
@@ -93,6 +97,16 @@ class ServeStats(ctypes.Structure):
                 ("mean_batch", ctypes.c_double), ("makespan_s", ctypes.c_double),
                 ("busy_s", ctypes.c_double), ("lanes", ctypes.c_int),
                 ("max_in_flight", ctypes.c_int)]
+
+
+class Tiles(ctypes.Structure):
+    """Tiles of the batched products (tw_tiles)."""
+    _fields_ = [("adj_tile", ctypes.c_int), ("adj_rw", ctypes.c_int), ("fwd_lanes", ctypes.c_int),
+                ("adj_tile_ms", ctypes.c_double), ("adj_rw_ms", ctypes.c_double),
+                ("fwd_lanes_ms", ctypes.c_double), ("tuned", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class TwError(RuntimeError):
@@ -360,6 +374,16 @@ class Context:
     def batch_capacity(self) -> int:
         return int(self.lib.tw_batch_capacity(self.h))
 
+    def batch_tiles(self) -> Tiles:
+        """The tiles of the batched products (measured at reserve_batch)."""
+        t = Tiles()
+        self._check(self.lib.tw_batch_tiles(self.h, ctypes.byref(t)))
+        return t
+
+    def set_batch_tiles(self, adj_tile: int, adj_rw: int, fwd_lanes: int):
+        t = Tiles(int(adj_tile), int(adj_rw), int(fwd_lanes), -1.0, -1.0, -1.0, 0)
+        self._check(self.lib.tw_set_batch_tiles(self.h, ctypes.byref(t)))
+
     def infer_batch(self, prec, d, windows_dev, m=None, q=None, forecast=True, stream=None):
         """Posterior means (and forecasts) of d [B][Nt][Nd]; windows_dev: int32 CUDA tensor [B]."""
         import torch
@@ -532,6 +556,17 @@ def serve_simulate(arrival_s, max_batch, cost_ms, cost_ms_per_req, lanes=1):
     if st != OK:
         raise TwError(st, "tw_serve_simulate failed")
     return lat, bid
+
+
+def autotune_pick(ms) -> int:
+    """The tile tuner's selection rule on a list of times (host only)."""
+    import numpy as np
+    a = np.ascontiguousarray(ms, dtype=np.float64)
+    return int(load().tw_autotune_pick(len(a), a.ctypes.data_as(ctypes.c_void_p)))
+
+
+def autotune_clear_cache():
+    load().tw_autotune_clear_cache()
 
 
 def kernel_launches() -> int:

@@ -221,6 +221,13 @@ def request_trace(cfg: Config, n: int = 10_000, rate: float = 200.0, lo: int = 6
     return [Request(float(t[i]), int(ev[i]), int(win[i])) for i in range(n)]
 
 
+def sample_entries(n_total: int, count: int, seed: int) -> np.ndarray:
+    """Sorted distinct flat indices in [0, n_total) drawn with a seeded
+    generator: the entries at which a stored reference vector is compared."""
+    g = np.random.default_rng(seed)
+    return np.sort(g.choice(n_total, size=min(count, n_total), replace=False))
+
+
 def nbytes_gb(x) -> float:
     return float(x) / 1e9
 

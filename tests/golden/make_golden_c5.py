@@ -39,8 +39,7 @@ SAMPLE_SEED = 5_020
 
 def sample_index(cfg, window):
     """Flat indices into m [Nt][Nm] of the stored entries (inside the window)."""
-    g = np.random.default_rng(SAMPLE_SEED + window)
-    return np.sort(g.choice(window * cfg.Nm, size=NSAMPLE, replace=False))
+    return synth.sample_entries(window * cfg.Nm, NSAMPLE, SAMPLE_SEED + window)
 
 
 def main():
@@ -54,7 +53,7 @@ def main():
         m_true = P.prior_apply(synth.event_z(cfg, e)[:w], lam, 0.5)
         d = T.p2o_apply(Fw, m_true) + sigma * synth.noise_z(cfg, e)[:w]
         L = Q.cholesky(Q.form_K(Fw, lam, sigma ** 2))
-        m, _ = Q.posterior_mean(Fw, lam, L, d, cfg.Nt)
+        m, _ = Q.posterior_mean(Fw, lam, L, d, cfg.Nt, nt_window=w)
         del Fw, L
 
         def fq(lag):

@@ -54,3 +54,26 @@ def test_create_rejects_bad_sizes_without_touching_a_gpu(lib):
     assert l.tw_create(ctypes.byref(h), 0, 1, 4, 4, 4, 1.0, 1.0, 1, 0) == tw.ERR_ARG
     assert l.tw_create(ctypes.byref(h), 4, 1, 4, 4, 4, 1.0, 1.0, 0, 0) == tw.ERR_ARG
     assert l.tw_create(ctypes.byref(h), 4, 1, 4, 4, 4, -1.0, 1.0, 1, 0) == tw.ERR_ARG
+
+
+def test_autotune_selection_rule(lib):
+    """The tile tuner keeps the smallest positive time; failed or missing
+    measurements (<= 0, NaN) never win; ties keep the earlier candidate."""
+    from paper_2504_16344_gb300 import tw
+    assert tw.autotune_pick([3.0, 1.5, 2.0]) == 1
+    assert tw.autotune_pick([-1.0, 4.0, 0.0, 5.0]) == 1
+    assert tw.autotune_pick([2.0, 2.0, 3.0]) == 0
+    assert tw.autotune_pick([float("nan"), 7.0]) == 1
+    assert tw.autotune_pick([-1.0, 0.0]) == -1
+    assert tw.autotune_pick([]) == -1
+    tw.autotune_clear_cache()
+
+
+def test_tile_struct_matches_header():
+    """The binding's tw_tiles layout is the header's: three ints, three doubles, one int."""
+    from paper_2504_16344_gb300 import tw
+    names = [f for f, _ in tw.Tiles._fields_]
+    text = open(os.path.join(ROOT, "include", "tw.h")).read()
+    body = text[text.index("typedef struct {\n  int adj_tile"):text.index("} tw_tiles;")]
+    order = re.findall(r"\b(adj_tile|adj_rw|fwd_lanes|adj_tile_ms|adj_rw_ms|fwd_lanes_ms|tuned)\b", body)
+    assert names == order

@@ -316,3 +316,37 @@ def test_large_reservation(case):
                 assert em < mixed_bound(case["floor"]["C64"]) and eq < mixed_bound(case["floor_q"]["C64"])
     finally:
         ctx.reserve_batch(BMAX)
+
+
+def test_every_tile_candidate_matches_oracle(case):
+    """The tuner measured its candidates at reserve_batch; every legal tile of
+    the batched products gives the oracle's result (and the bound of the
+    path), so the choice is a matter of speed only."""
+    import torch
+    from paper_2504_16344_gb300 import tw
+    ctx, ws = case["ctx"], case["ws"]
+    t0 = ctx.batch_tiles()
+    print(f"{case['cfg'].cid}: tuned tiles {t0.as_dict()}")
+    assert t0.tuned == 1 and t0.adj_tile_ms > 0 and t0.adj_rw_ms > 0 and t0.fwd_lanes_ms > 0
+    win = torch.tensor(ws, dtype=torch.int32, device=case["dev"])
+    d = _t(case["d"], case["dev"])
+
+    def errs(prec):
+        m, q = ctx.infer_batch(prec, d, win)
+        ctx.check()
+        m, q = m.cpu().numpy(), q.cpu().numpy()
+        return (max(rel(m[e], case["m_ref"][e]) for e in range(NEV)),
+                max(rel(q[e], case["q_ref"][e]) for e in range(NEV)))
+
+    try:
+        for P in range(8, (BMAX + 7) // 8 * 8 + 1, 8):
+            ctx.set_batch_tiles(P, t0.adj_rw, t0.fwd_lanes)
+            em, eq = errs(tw.PREC_C64)
+            assert em < mixed_bound(case["floor"]["C64"]) and eq < mixed_bound(case["floor_q"]["C64"]), P
+        for rw in (1, 2, 4):
+            for lanes in (1, 2):
+                ctx.set_batch_tiles(t0.adj_tile, rw, lanes)
+                em, eq = errs(tw.PREC_FP64)
+                assert em < 1e-11 and eq < 1e-11, (rw, lanes)
+    finally:
+        ctx.set_batch_tiles(t0.adj_tile, t0.adj_rw, t0.fwd_lanes)
