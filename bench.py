@@ -254,6 +254,15 @@ def oracle_sample(cfg, min_seconds=0.0, seed=7):
     return statistics.median(vals), desc, spent
 
 
+def oracle_threads():
+    """Threads the oracle's BLAS uses: the thread-count variables if set, else every core."""
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(var, "")
+        if v.isdigit() and int(v) > 0:
+            return int(v)
+    return os.cpu_count()
+
+
 def run_reference(args):
     import synth
     rank, world, _ = rank_info()
@@ -273,7 +282,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if not args.small else WORKLOAD.replace("Nt=400", "Nt=40")},
-        "cpu_baseline": {"value": v, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": oracle_threads(), "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -986,7 +995,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
         v, desc, spent = oracle_sample(cfg, min_seconds=10.0)
-        cpu = {"value": round(v, 2), "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": round(v, 2), "unit": "ms", "cores": oracle_threads(), "kind": "oracle",
                "sample": desc, "cpu_seconds": round(spent, 2)}
 
     # replicas: every rank runs the same step; the time of a step is the max over ranks

@@ -51,6 +51,7 @@ struct tw_ctx {
   int8_t *ea[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
   int8_t *eaG[3] = {nullptr, nullptr, nullptr};
   std::vector<char> loaded[2];     // per row: loaded?
+  std::vector<unsigned long long> col_hash;   // per row of F: fingerprint of its block column
   // FFT plans and twiddle tables (df64 and float)
   tw::FftPlan plT{}, plX{}, plY{};
   tw::cdd *twT = nullptr, *twL = nullptr, *twX = nullptr, *twY = nullptr;
@@ -143,6 +144,8 @@ tw_status cuda_fail(tw_ctx *c, cudaError_t e, const char *where);
 void *dalloc(tw_ctx *c, size_t bytes);   // tracked cudaMalloc; nullptr on failure
 void dfree(tw_ctx *c, void *p);
 tw::FftPlan make_plan(int M);
+// fingerprint of F's whole block column (from the per-row ones)
+unsigned long long column_fingerprint(const tw_ctx *c);
 // batch copies after a factorisation: the float-pair factor for mixed batched
 // solves and the tensor-core operator tiles (no-op unless reserved)
 tw_status refresh_dd_factor(tw_ctx *c, cudaStream_t s);

@@ -16,6 +16,14 @@ void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed);
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace tw
 
+// splitmix64 finaliser (Steele, Lea and Flood 2014): a well-mixed 64-bit hash
+__host__ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
 namespace twh {
 
 static cudaEvent_t get_event(tw_ctx *c) {
@@ -102,6 +110,12 @@ FftPlan make_plan(int M) {
   return p;
 }
 
+unsigned long long column_fingerprint(const tw_ctx *c) {
+  unsigned long long h = 0x5457u;
+  for (size_t r = 0; r < c->col_hash.size(); ++r) h = mix64(h ^ mix64(c->col_hash[r] + r));
+  return h;
+}
+
 }  // namespace twh
 
 namespace {
@@ -176,6 +190,26 @@ tw_status build_G_rows(tw_ctx *c, int row0, int nrows, const double *col, cudaSt
   return TW_OK;
 }
 
+// per-row fingerprint of a block-column chunk [Nt][nrows][Nm]: the sum over
+// its entries of mix64(bits ^ mix64(position in the row)), so that a
+// checkpoint can tell whether it was formed from the same operator
+__global__ void k_col_hash(const double *__restrict__ col, int nrows, int Nm,
+                           unsigned long long *__restrict__ row_hash) {
+  __shared__ unsigned long long red[256];
+  const int l = blockIdx.x / nrows, r = blockIdx.x % nrows;
+  const double *p = col + ((size_t)l * nrows + r) * Nm;
+  unsigned long long h = 0;
+  for (int k = threadIdx.x; k < Nm; k += blockDim.x)
+    h += mix64((unsigned long long)__double_as_longlong(p[k]) ^ mix64((unsigned long long)l * Nm + k));
+  red[threadIdx.x] = h;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(row_hash + r, red[0]);
+}
+
 size_t op_elem_bytes(int fmt) { return fmt == FMT_DD ? sizeof(cdd) : 8; }
 
 int rows_of(const tw_ctx *c, int which) { return which == TW_MAP_F ? c->Nd : c->Nq; }
@@ -208,6 +242,7 @@ tw_status tw_create(tw_ctx **out, int Nd, int Nq, int Nx, int Ny, int Nt, double
   c->Lx = Lx; c->Ly = Ly; c->keep = keep;
   c->loaded[0].assign(Nd, 0);
   c->loaded[1].assign(Nq, 0);
+  c->col_hash.assign(Nd, 0ull);
   tw_status st = TW_OK;
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) { st = twh::cuda_fail(c, e, "cudaSetDevice"); delete c; return st; }
@@ -307,6 +342,19 @@ tw_status tw_set_block_column(tw_ctx *c, tw_map which, int row0, int nrows, cons
     twh::dfree(c, tmp);
   }
   for (int r = row0; r < row0 + nrows; ++r) c->loaded[which][r] = 1;
+  if (which == TW_MAP_F) {
+    // fingerprints of these rows of F (checked by tw_load_factor)
+    unsigned long long *dh = (unsigned long long *)twh::dalloc(c, (size_t)nrows * sizeof(unsigned long long));
+    if (!dh) return twh::fail(c, TW_ERR_OOM, "block-column fingerprint");
+    TW_CUDA(c, cudaMemsetAsync(dh, 0, (size_t)nrows * sizeof(unsigned long long), s));
+    k_col_hash<<<(unsigned)c->Nt * nrows, 256, 0, s>>>(col, nrows, c->Nm, dh);
+    count_launches(1);
+    TW_CUDA(c, cudaGetLastError());
+    TW_CUDA(c, cudaMemcpyAsync(c->col_hash.data() + row0, dh, (size_t)nrows * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, s));
+    TW_CUDA(c, cudaStreamSynchronize(s));
+    twh::dfree(c, dh);
+  }
   // every row present: the row exponents of the FP32 storages (one pass)
   bool all = true;
   for (char l : c->loaded[which]) all = all && l;

@@ -142,10 +142,10 @@ struct FactorHeader {
   int32_t Nd, Nt, Nx, Ny, NB, blk;
   uint64_t nblk;
   double sigma2, nu, ell, var, Lx, Ly;
-  uint64_t reserved;
+  uint64_t col_hash;      // fingerprint of the block column of F that K was formed from
 };
 static_assert(sizeof(FactorHeader) == 96, "checkpoint header layout");
-const char kFactorMagic[8] = {'T', 'W', 'L', 'F', 'A', 'C', '0', '1'};
+const char kFactorMagic[8] = {'T', 'W', 'L', 'F', 'A', 'C', '0', '2'};
 
 size_t factor_payload(int NB) {
   const size_t nblk = (size_t)NB * (NB + 1) / 2;
@@ -619,6 +619,7 @@ tw_status tw_save_factor(tw_ctx *c, void *host, size_t bytes, void *stream) {
   h.Nd = c->Nd; h.Nt = c->Nt; h.Nx = c->Nx; h.Ny = c->Ny; h.NB = c->NB; h.blk = NB_;
   h.nblk = (uint64_t)c->NB * (c->NB + 1) / 2;
   h.sigma2 = c->sigma2; h.nu = c->nu; h.ell = c->ell; h.var = c->var; h.Lx = c->Lx; h.Ly = c->Ly;
+  h.col_hash = twh::column_fingerprint(c);
   uint8_t *dst = (uint8_t *)host;
   memcpy(dst, &h, sizeof(h));
   const size_t lp = (size_t)h.nblk * NB_ * NB_ * sizeof(double);
@@ -644,6 +645,10 @@ tw_status tw_load_factor(tw_ctx *c, const void *host, size_t bytes, void *stream
   if (h.nu != c->nu || h.ell != c->ell || h.var != c->var || h.Lx != c->Lx || h.Ly != c->Ly)
     return twh::fail(c, TW_ERR_ARG, "checkpoint was made with another prior or domain");
   if (!(h.sigma2 >= 0.0)) return twh::fail(c, TW_ERR_ARG, "checkpoint noise variance invalid");
+  for (char l : c->loaded[TW_MAP_F])
+    if (!l) return twh::fail(c, TW_ERR_STATE, "load the block column of F before the factor");
+  if (h.col_hash != twh::column_fingerprint(c))
+    return twh::fail(c, TW_ERR_ARG, "checkpoint was formed from another block column of F");
   if (bytes < sizeof(FactorHeader) + factor_payload(NB))
     return twh::fail(c, TW_ERR_ARG, "checkpoint truncated");
   cudaStream_t s = (cudaStream_t)stream;

@@ -70,7 +70,7 @@ def test_checkpoint_size_and_header(case):
     nblk = NB * (NB + 1) // 2
     buf = case["buf"]
     assert buf.size == case["ref"].factor_bytes() == 96 + 8 * 64 * 64 * (nblk + NB)
-    assert bytes(buf[:8]) == b"TWLFAC01"
+    assert bytes(buf[:8]) == b"TWLFAC02"
     hdr = np.frombuffer(buf[8:32].tobytes(), dtype=np.int32)
     assert list(hdr) == [cfg.Nd, cfg.Nt, cfg.Nx, cfg.Ny, NB, 64]
     assert np.frombuffer(buf[40:48].tobytes(), dtype=np.float64)[0] == case["sigma"] ** 2
@@ -184,6 +184,23 @@ def test_checkpoint_mismatch_refused(case):
         assert status_of(lambda: ctx.load_factor(buf[:50])) == 1
         ctx.load_factor(buf)       # the intact checkpoint still loads
         ctx.check()
+    finally:
+        ctx.close()
+
+
+def test_factor_of_another_block_column_refused(case):
+    """Same sizes, prior and domain, but another synthetic operator (other
+    sensor positions): the checkpoint's block-column fingerprint differs and
+    the factor is refused instead of giving wrong posterior means."""
+    from paper_2504_16344_gb300 import tw
+    cfg = case["cfg"]
+    other = synth.small_config(Nd=cfg.Nd, Nx=cfg.Nx, Ny=cfg.Ny, Nt=cfg.Nt, Nq=cfg.Nq, cid=cfg.cid + 50)
+    ctx = make_context(other, keep=tw.KEEP_FP64, prior=False)
+    try:
+        ctx.set_prior(cfg.nu, cfg.ell, cfg.var)
+        with pytest.raises(tw.TwError) as ei:
+            ctx.load_factor(case["buf"])
+        assert ei.value.status == 1 and "block column" in str(ei.value)
     finally:
         ctx.close()
 
