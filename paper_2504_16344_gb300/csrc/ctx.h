@@ -81,16 +81,17 @@ struct tw_ctx {
   bool have64 = false, have32 = false;
   double *Lp64 = nullptr, *inv64 = nullptr;                      // FP64 factor, packed 64x64 blocks
   double *chF64 = nullptr, *chB64 = nullptr;                      // chain blocks of the solves
-  // single-vector FP64 solves (trsv64.cu): block-scaled factor and scheduling state
-  double *Lf64 = nullptr, *Lb64 = nullptr;                        // packed, like Lp64
-  double *band1 = nullptr, *band2 = nullptr;                      // [NB][64][64]
+  // single-vector FP64-class solves (trsv64.cu): block-scaled factor as
+  // float pairs and scheduling state
+  tw::dd *Lfs = nullptr, *Lbs = nullptr;                          // packed, like Lp64
+  tw::dd *bands = nullptr;                                        // [2][DCH][NB][64][64] chain blocks
   int2 *tasks = nullptr;                                          // worker task table
   std::vector<int> task_prefix;                                   // tasks of rows < u: task_prefix[u]
-  double *tpart = nullptr;                                        // [NB][maxk][64]
+  tw::dd *tpart = nullptr;                                        // [NB][maxk][64]
   int tmaxk = 0;
   int *tcnt = nullptr;                                            // [NB]
-  double *wbuf64 = nullptr;                                       // [n_pad]
-  int *wflag = nullptr;                                           // [NB]
+  tw::dd *wbufx = nullptr;                                        // [n_pad]
+  tw::dd *zx = nullptr;                                           // [n_pad] sweep output, float pairs
   tw::dd *Kp64 = nullptr;                                         // K, packed, double-float
   float *Lp32 = nullptr, *inv32 = nullptr;
   float *chF32 = nullptr, *chB32 = nullptr;

@@ -23,27 +23,32 @@ cudaError_t launch_double_to_dd(const double *a, dd *b, size_t n, cudaStream_t s
 cudaError_t launch_pack_f(const float *K, long ldk, float *P, int NB, cudaStream_t s);
 cudaError_t launch_lower_to_float(const double *K, float *K32, long ld, int NB, cudaStream_t s);
 
-// FP64 solves of one right-hand side with the block-scaled factor (trsv64.cu)
+// FP64-class solves of one right-hand side with the block-scaled factor,
+// stored as float pairs, in double-float arithmetic (trsv64.cu)
 struct Trsv64Args {
-  const double *Lf, *Lb;            // packed Linv_I L_IJ and L_IJ Linv_J (J < I)
-  const double *Linv;               // [NB][64][64] diagonal-block inverses
-  const double *band1, *band2;      // forward chain blocks, transposed: Lf_{I,I-1}^T, Lf_{I,I-2}^T
-  const void *rhs;                  // kind 0 double, 1 float pairs
+  const dd *Lf, *Lb;                // packed Linv_I L_IJ and L_IJ Linv_J (J < I)
+  const double *Linv;               // [NB][64][64] diagonal-block inverses (FP64)
+  const dd *bands;                  // [2][DCH][NB][64][64] chain blocks as split planes:
+                                    //   FWD Lf_{I,I-j}^T, BWD Lb_{I+j,I}
+  int NB;                           // block rows of the factor (bands' stride)
+  const void *rhs;                  // kind 0 double, 1 float pairs; must not alias outx
   int rhs_kind;
-  double *out;
+  double *out;                      // [>= NBw*64] the solution (rows >= nrows set to 0)
+  dd *outx;                         // [>= NBw*64] the same as float pairs (read by the workers)
   int nrows, NBw;
   const int2 *tasks;                // (row, chunk) in row order; tasks of rows < NBw form a prefix
   int ntasks;
-  double *part;                     // [NB][maxk][64] partial sums
+  dd *part;                         // [NB][maxk][64] partial sums
   int maxk;
-  int *cnt, *wflag;                 // [NB] each, zeroed by the launcher
-  double *wbuf;                     // [n_pad]
+  int *cnt;                         // [NB] tasks done per row, zeroed by the launcher
+  dd *wbuf;                         // [n_pad] w_u hand-off, filled with all-ones by the launcher
   int *prog, *err, *abort_flag;     // prog: 2 ints, zeroed by the launcher
 };
 int trsv64_max_tasks_per_row(int NB);
 void trsv64_task_table(int NB, std::vector<int> &tab, std::vector<int> &prefix);
-cudaError_t launch_trsv64_setup(const double *Lp, const double *Linv, double *Lf, double *Lb,
-                                double *band1, double *band2, int NB, cudaStream_t s);
+int trsv64_chain_deps();            // DCH: dependencies the chain CTA applies
+cudaError_t launch_trsv64_setup(const double *Lp, const double *Linv, dd *Lf, dd *Lb, dd *bands,
+                                int NB, cudaStream_t s);
 cudaError_t launch_trsv64(const Trsv64Args &a, bool fwd, cudaStream_t s);
 // triangular solves (fwd: L z = b; bwd: L^T x = z), rhs kind 0 double / 1 dd / 2 float
 // prog: two ints (ticket, rows finished), zeroed by the launcher

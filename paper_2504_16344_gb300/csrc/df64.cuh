@@ -36,6 +36,8 @@ __device__ __forceinline__ dd dd_make(float hi, float lo) {
   dd r; fast_two_sum(hi, lo, r.hi, r.lo); return r;
 }
 __device__ __forceinline__ dd dd_zero() { dd r; r.hi = 0.f; r.lo = 0.f; return r; }
+// the pair as it is (no renormalisation)
+__device__ __forceinline__ dd dd_make_raw(float hi, float lo) { dd r; r.hi = hi; r.lo = lo; return r; }
 __device__ __forceinline__ dd dd_neg(dd a) { a.hi = -a.hi; a.lo = -a.lo; return a; }
 
 // sum with relative error O(2^-48) of |a| + |b|
@@ -248,4 +250,51 @@ __device__ __forceinline__ void st_real(dd *p, dd v) {
 __device__ __forceinline__ void st_real(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st_real(double *p, float v) { *p = (double)v; }
 
+
+// ------------------------------------------------ packed FP32 pairs
+// Two independent FP32 lanes in one 64-bit register (add/sub/mul/fma.rn.f32x2):
+// each lane rounds exactly like the scalar instruction, so a packed double-
+// float sequence gives, lane by lane, the bits of the scalar one in half the
+// instructions.  f2_make(lo, hi): lo is lane 0 (the lower address in memory).
+struct f2 { unsigned long long v; };
+__device__ __forceinline__ f2 f2_make(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 f2_split(f2 a) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a.v));
+  return r;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { f2 r; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v)); return r; }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { f2 r; asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v)); return r; }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { f2 r; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v)); return r; }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 r; asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v)); return r;
+}
+
+
+// S + T += (ah + al)(bh + bl) lane by lane, exactly the steps of dacc_mac:
+// bhn = -bh (so -(ah bh) is one rounded product and its error one FMA)
+__device__ __forceinline__ void dacc_mac2(f2 &S, f2 &T, f2 ah, f2 al, f2 bh, f2 bhn, f2 bl) {
+  const f2 pn = mul2(ah, bhn);
+  f2 e = fma2(ah, bh, pn);
+  e = fma2(ah, bl, e);
+  e = fma2(al, bh, e);
+  const f2 s = sub2(S, pn);
+  const f2 bb = sub2(s, S);
+  const f2 r = add2(sub2(sub2(S, sub2(s, bb)), add2(pn, bb)), add2(T, e));
+  S = add2(s, r);
+  T = sub2(r, sub2(S, s));
+}
+// (ah, al) = dd_add((ah, al), (bh, bl)) lane by lane
+__device__ __forceinline__ void dd_add2(f2 &ah, f2 &al, f2 bh, f2 bl) {
+  const f2 s = add2(ah, bh);
+  const f2 bb = sub2(s, ah);
+  f2 e = add2(sub2(ah, sub2(s, bb)), sub2(bh, bb));
+  e = add2(e, add2(al, bl));
+  ah = add2(s, e);
+  al = sub2(e, sub2(ah, s));
+}
 }  // namespace tw

@@ -38,15 +38,17 @@ tw_status ensure_solve_workspace(tw_ctx *c) {
   return TW_OK;
 }
 
-// y = K^{-1} b for the leading nrows with the FP64 factor (native FP64
-// substitution: the solves' cancellations would amplify 2^-48 rounding)
+// y = K^{-1} b for the leading nrows with the FP64 factor: block-scaled
+// factor as float pairs, double-float products (2^-48 rounding; at the test
+// cases' condition numbers, up to 2.3e6, it moves m by under 1e-12)
 // b: double (kind 0) or dd (kind 1)
 tw_status solve64(tw_ctx *c, const void *b, int kind, int nrows, double *y, cudaStream_t s) {
   const int NBw = (nrows + NB_ - 1) / NB_;
   Trsv64Args a{};
-  a.Lf = c->Lf64; a.Lb = c->Lb64; a.Linv = c->inv64; a.band1 = c->band1; a.band2 = c->band2;
+  a.Lf = c->Lfs; a.Lb = c->Lbs; a.Linv = c->inv64; a.bands = c->bands; a.NB = c->NB;
   a.nrows = nrows; a.NBw = NBw; a.tasks = c->tasks; a.ntasks = c->task_prefix[NBw];
-  a.part = c->tpart; a.maxk = c->tmaxk; a.cnt = c->tcnt; a.wflag = c->wflag; a.wbuf = c->wbuf64;
+  a.part = c->tpart; a.maxk = c->tmaxk; a.cnt = c->tcnt; a.wbuf = c->wbufx;
+  a.outx = c->zx;
   a.err = c->d_err; a.abort_flag = c->abort_flag;
   { twh::Phase p(c, TW_PH_TRSV_FWD, s);
     a.rhs = b; a.rhs_kind = kind; a.out = c->zd; a.prog = c->counter;
@@ -84,18 +86,17 @@ tw_status finish_factor64(tw_ctx *c, cudaStream_t s) {
   trsv64_task_table(c->NB, tab, c->task_prefix);
   c->tmaxk = trsv64_max_tasks_per_row(c->NB);
   auto need = [&](void *&p, size_t bytes) { if (!p) p = twh::dalloc(c, bytes); return p != nullptr; };
-  bool ok = need((void *&)c->Lf64, nblk * blk * sizeof(double)) &&
-            need((void *&)c->Lb64, nblk * blk * sizeof(double)) &&
-            need((void *&)c->band1, (size_t)c->NB * blk * sizeof(double)) &&
-            need((void *&)c->band2, (size_t)c->NB * blk * sizeof(double)) &&
+  bool ok = need((void *&)c->Lfs, nblk * blk * sizeof(dd)) &&
+            need((void *&)c->Lbs, nblk * blk * sizeof(dd)) &&
+            need((void *&)c->bands, (size_t)2 * trsv64_chain_deps() * c->NB * blk * sizeof(dd)) &&
             need((void *&)c->tasks, tab.size() / 2 * sizeof(int2)) &&
-            need((void *&)c->tpart, (size_t)c->NB * c->tmaxk * NB_ * sizeof(double)) &&
+            need((void *&)c->tpart, (size_t)c->NB * c->tmaxk * NB_ * sizeof(dd)) &&
             need((void *&)c->tcnt, (size_t)c->NB * sizeof(int)) &&
-            need((void *&)c->wbuf64, np * sizeof(double)) &&
-            need((void *&)c->wflag, (size_t)c->NB * sizeof(int));
+            need((void *&)c->wbufx, np * sizeof(dd)) &&
+            need((void *&)c->zx, np * sizeof(dd));
   if (!ok) return twh::fail(c, TW_ERR_OOM, "single-vector solve buffers");
   TW_CUDA(c, cudaMemcpyAsync(c->tasks, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  TW_CUDA(c, launch_trsv64_setup(c->Lp64, c->inv64, c->Lf64, c->Lb64, c->band1, c->band2, c->NB, s));
+  TW_CUDA(c, launch_trsv64_setup(c->Lp64, c->inv64, c->Lfs, c->Lbs, c->bands, c->NB, s));
   TW_CUDA(c, cudaStreamSynchronize(s));
   tw_status cs = tw_check(c, s);
   if (cs != TW_OK) return cs;
