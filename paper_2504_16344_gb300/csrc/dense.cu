@@ -7,8 +7,9 @@
 // column without unit-vector applies: with Phi the (Nd Nt) x Nm matrix whose
 // row block u is F_u and G = Phi C^{1/2},
 //   P = G G^T,  K_(i,j) = sigma^2 delta_ij I + sum_{s<=min(i,j)} P_(i-s, j-s),
-// i.e. a symmetric rank-Nm product followed by prefix sums along the Nd x Nd
-// block diagonals (time-major ordering, as in the paper's data vectors).
+// i.e. a symmetric rank-Nm product (on the tensor cores, gemm_syrk.cu)
+// followed by prefix sums along the Nd x Nd block diagonals (time-major
+// ordering, as in the paper's data vectors).
 //
 // All matrices use 64 x 64 tiles.  K is held in full (lower triangle used)
 // with leading dimension n_pad = 64 * ceil(n/64); the padding has an
@@ -65,18 +66,10 @@ template <> __device__ __forceinline__ double ld_cg<double>(const double *p) { r
 // C[tile (I,J)] = (subtract ? C - S : S),  S = sum_k A[i][k] B[j][k]
 // A rows >= arows and B rows >= brows are zero.  lower: skip J > I.
 // Products accumulate in T over runs of 32 and the run sums are added into
-// totals of type TC: for K's formation T = dd (double-float products, FP32
-// pipe) and TC = double, so the long sum over Nm rounds at FP64's 2^-53
-// rather than at double-float's 2^-48 of the running total.
+// totals of type TC (the Cholesky's trailing updates: TC = T).
 template <class T, class TC> struct Fold;
 template <class T> struct Fold<T, T> {
   static __device__ __forceinline__ void run(T &tot, typename DS<T>::acc &a) { DS<T>::fold(tot, a); }
-};
-template <> struct Fold<dd, double> {
-  static __device__ __forceinline__ void run(double &tot, dacc &a) {
-    tot += (double)a.s + (double)a.t;
-    a = dacc_zero();
-  }
 };
 
 template <class T, class TC = T>
@@ -776,13 +769,6 @@ template <class KER> void smem_attr(KER k, size_t bytes) {
 }  // namespace
 
 // ======================================================================= host
-cudaError_t launch_form_P(const dd *G, long ldg, int n, int kdim, double *K, long ldk, int NB,
-                          cudaStream_t s) {
-  k_gemm_nt<dd, double><<<dim3(NB, NB), 256, 0, s>>>(G, ldg, n, G, ldg, n, kdim, K, ldk, 1, 0);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_K_from_P(double *K, long ldk, int Nd, int Nt, int n, int n_pad, double sigma2,
                             cudaStream_t s) {
   const long total = (long)Nt * Nd * Nd;

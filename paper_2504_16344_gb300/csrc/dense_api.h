@@ -1,6 +1,7 @@
 // dense_api.h -- host launchers of dense.cu (internal).
 #pragma once
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include <vector>
 
@@ -8,9 +9,16 @@
 
 namespace tw {
 
-// P = G G^T (lower 64x64 tiles) into K (FP64); G: [n][kdim] dd, row stride ldg
-cudaError_t launch_form_P(const dd *G, long ldg, int n, int kdim, double *K, long ldk, int NB,
-                          cudaStream_t s);
+// P = G G^T (lower 64x64 tiles) into K (FP64); G: [n][kdim] dd, row stride ldg.
+// Tensor cores with exact bf16 slices of G (gemm_syrk.cu): tl = the tile list
+// of syrk_tile_list(n_pad) in device memory, eg syrk_exp_rows(n_pad) ints, ws
+// a multiple of syrk_ws_bytes_per_atom(n_pad) bytes (at least 4 of them)
+void syrk_tile_list(int n_pad, std::vector<int2> &tl);
+size_t syrk_ws_bytes_per_atom(int n_pad);
+int syrk_exp_rows(int n_pad);
+cudaError_t launch_form_P_tc(const dd *G, long ldg, int n, int kdim, double *K, long ldk, int n_pad,
+                             uint8_t *ws, size_t ws_bytes, int *eg, const int2 *tl, int ntl, int *err,
+                             cudaStream_t s);
 // K = sigma2 I + block-diagonal prefix sums of P (in place, FP64), identity padding
 cudaError_t launch_K_from_P(double *K, long ldk, int Nd, int Nt, int n, int n_pad, double sigma2,
                             cudaStream_t s);

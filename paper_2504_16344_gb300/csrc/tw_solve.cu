@@ -210,8 +210,34 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
   double *K = (double *)twh::dalloc(c, (size_t)np * np * sizeof(double));
   if (!K) { twh::dfree(c, G); return twh::fail(c, TW_ERR_OOM, "K buffer"); }
   TW_CUDA(c, cudaMemsetAsync(K, 0, (size_t)np * np * sizeof(double), s));
-  TW_CUDA(c, launch_form_P(G, Nm, (int)n, Nm, K, np, c->NB, s));
-  TW_CUDA(c, cudaStreamSynchronize(s));
+  {
+    // P on the tensor cores from exact slices of G, one panel of up to 8192
+    // grid points of slices at a time (as large as free memory allows)
+    std::vector<int2> tl;
+    syrk_tile_list((int)np, tl);
+    const size_t per_atom = syrk_ws_bytes_per_atom((int)np);
+    size_t free_b = 0, total_b = 0;
+    TW_CUDA(c, cudaMemGetInfo(&free_b, &total_b));
+    const size_t margin = (size_t)2 << 30;
+    const size_t avail = free_b > margin ? free_b - margin : 0;
+    const size_t wsb = std::min(per_atom * 256, avail / per_atom * per_atom);
+    int2 *dtl = (int2 *)twh::dalloc(c, tl.size() * sizeof(int2));
+    int *eg = (int *)twh::dalloc(c, (size_t)syrk_exp_rows((int)np) * sizeof(int));
+    uint8_t *ws = wsb >= per_atom * 4 ? (uint8_t *)twh::dalloc(c, wsb) : nullptr;
+    if (!dtl || !eg || !ws) {
+      twh::dfree(c, ws); twh::dfree(c, eg); twh::dfree(c, dtl); twh::dfree(c, K); twh::dfree(c, G);
+      return twh::fail(c, TW_ERR_OOM, "slices of G for K's formation");
+    }
+    TW_CUDA(c, cudaMemcpyAsync(dtl, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    TW_CUDA(c, launch_form_P_tc(G, Nm, (int)n, Nm, K, np, (int)np, ws, wsb, eg, dtl, (int)tl.size(),
+                                c->d_err, s));
+    TW_CUDA(c, cudaStreamSynchronize(s));
+    twh::dfree(c, ws);
+    twh::dfree(c, eg);
+    twh::dfree(c, dtl);
+    tw_status cs = tw_check(c, s);
+    if (cs != TW_OK) { twh::dfree(c, K); twh::dfree(c, G); return cs; }
+  }
   twh::dfree(c, G);
   TW_CUDA(c, launch_K_from_P(K, np, Nd, Nt, (int)n, (int)np, noise_var, s));
 
