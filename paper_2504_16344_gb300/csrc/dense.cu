@@ -781,8 +781,12 @@ cudaError_t launch_K_from_P(double *K, long ldk, int Nd, int Nt, int n, int n_pa
   return cudaGetLastError();
 }
 
+// Right-looking blocked Cholesky, 64-wide panels.  With slice workspaces
+// (FP64 only) the rank-64 trailing updates run as exact products on the
+// tensor cores (gemm_syrk.cu), else as SIMT products.
 template <class T>
-cudaError_t cholesky_t(T *K, long ldk, int NB, T *inv, int *err, cudaStream_t s) {
+cudaError_t cholesky_t(T *K, long ldk, int NB, T *inv, int *err, cudaStream_t s, uint8_t *ws = nullptr,
+                       size_t ws_bytes = 0, int *eg = nullptr) {
   const size_t sm_potrf = 2 * NB_ * (NB_ + 1) * sizeof(T);
   const size_t sm_trsm = 2 * NB_ * (NB_ + 1) * sizeof(T);
   smem_attr(k_potrf_diag<T>, sm_potrf);
@@ -797,6 +801,13 @@ cudaError_t cholesky_t(T *K, long ldk, int NB, T *inv, int *err, cudaStream_t s)
       count_launches(1);
       const T *panel = diag + (long)NB_ * ldk;               // rows (J+1)*64.., cols J*64..
       T *trail = diag + (long)NB_ * ldk + NB_;
+      if constexpr (sizeof(T) == sizeof(double)) {
+        if (ws) {
+          cudaError_t e = launch_syrk_update_d(panel, ldk, trail, ldk, nt * NB_, ws, ws_bytes, eg, err, s);
+          if (e != cudaSuccess) return e;
+          continue;
+        }
+      }
       k_gemm_nt<T><<<dim3(nt, nt), 256, 0, s>>>(panel, ldk, nt * NB_, panel, ldk, nt * NB_, NB_,
                                                 trail, ldk, 1, 1);
       count_launches(1);
@@ -811,8 +822,9 @@ cudaError_t launch_cholesky_f(float *K, long ldk, int NB, float *inv, int *err, 
   return cholesky_t<float>(K, ldk, NB, inv, err, s);
 }
 
-cudaError_t launch_cholesky_d(double *K, long ldk, int NB, double *inv, int *err, cudaStream_t s) {
-  return cholesky_t<double>(K, ldk, NB, inv, err, s);
+cudaError_t launch_cholesky_d(double *K, long ldk, int NB, double *inv, int *err, uint8_t *ws,
+                              size_t ws_bytes, int *eg, cudaStream_t s) {
+  return cholesky_t<double>(K, ldk, NB, inv, err, s, ws, ws_bytes, eg);
 }
 cudaError_t launch_pack_d(const double *K, long ldk, double *P, int NB, cudaStream_t s) {
   k_pack<double><<<152 * 8, 256, 0, s>>>(K, ldk, P, NB);

@@ -230,6 +230,65 @@ k_syrk_slice(const dd *__restrict__ G, long ldg, int n, int kdim, int k0, const 
   }
 }
 
+// ------------------------------------------ FP64 panels (the Cholesky's updates)
+// eg[i] = smallest e with |A_ik| < 2^e over the kdim columns of row i
+__global__ void __launch_bounds__(256)
+k_syrk_row_exp_d(const double *__restrict__ A, long ld, int n, int kdim, int *__restrict__ eg, int nrows) {
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (warp >= nrows) return;
+  double mx = 0.0;
+  if (warp < n)
+    for (int k = lane; k < kdim; k += 32) mx = fmax(mx, fabs(A[(size_t)warp * ld + k]));
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, m));
+  if (lane == 0) {
+    int e = SK_EXP_MIN;
+    if (warp < n && mx > 0.0) {
+      frexp(mx, &e);                    // mx = f 2^e, f in [1/2, 1): mx < 2^e
+      e = e < SK_EXP_MIN ? SK_EXP_MIN : (e > SK_EXP_MAX ? SK_EXP_MAX : e);
+    }
+    eg[warp] = e;
+  }
+}
+
+// slices of an FP64 panel in the layout of k_syrk_slice: seven 8-bit slices
+// hold the 53-bit significand of every entry within 2^2 of its row maximum
+// exactly (steps in FP64: scaling by a power of two, rint, and (x - s) 256
+// are exact)
+__global__ void __launch_bounds__(256)
+k_syrk_slice_d(const double *__restrict__ A, long ld, int n, int kdim, const int *__restrict__ eg,
+               uint8_t *__restrict__ tiles, int natoms) {
+  const int a = blockIdx.x, T = blockIdx.y;
+  const int r = threadIdx.x & (SK_TM - 1), h = threadIdx.x >> 7;
+  const int i = T * SK_TM + r;
+  const int kb = SK_KA * a + 16 * h;
+  const int e = eg[i];
+  double x[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u)
+    x[u] = (i < n && kb + u < kdim) ? ldexp(A[(size_t)i * ld + kb + u], 7 - e) : 0.0;
+  uint8_t *base = tiles + ((size_t)T * natoms + a) * SK_NSL * SK_A_SLICE;
+#pragma unroll
+  for (int s = 0; s < SK_NSL; ++s) {
+    uint32_t wd[8];
+#pragma unroll
+    for (int u2 = 0; u2 < 8; ++u2) {
+      float sl[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int u = 2 * u2 + c;
+        const double si = rint(x[u]);
+        sl[c] = (float)si * pow2f(-8 * s);
+        x[u] = (x[u] - si) * 256.0;
+      }
+      wd[u2] = pack_bf16(sl[0], sl[1]);
+    }
+    uint8_t *tile = base + (size_t)s * SK_A_SLICE;
+    *reinterpret_cast<uint4 *>(tile + swz64(r, 2 * h)) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    *reinterpret_cast<uint4 *>(tile + swz64(r, 2 * h + 1)) = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+  }
+}
+
 // pair number p = 0..27 -> (slice of A, slice of B), by level L = 0..6
 __device__ __forceinline__ void syrk_pair(int p, int &si, int &sj, int &L) {
   int l = 0, first = 0;
@@ -240,14 +299,28 @@ __device__ __forceinline__ void syrk_pair(int p, int &si, int &sj, int &L) {
 }
 
 // ------------------------------------------------------------------ the product
-// K[i][j] (+)= P_ij over this panel for the tiles tl[] (row tile I of 128, column
-// tile J of 32), entries of the lower 64-block triangle and below n_pad only.
+// tile number t: from the list tl, or (tl == nullptr) in row-major order over
+// the lower triangle of 128-row tiles, row tile I holding column tiles
+// 0 .. 4I+3.  A column tile at or past nc is empty (the last row tile of a
+// size that is not a multiple of 128); every role skips it alike.
+__device__ __forceinline__ bool tile_at(const int2 *__restrict__ tl, int t, int nc, int2 &out) {
+  if (tl) { out = tl[t]; return true; }
+  int I = (int)((sqrt(1.0 + 2.0 * (double)t) - 1.0) * 0.5);
+  while (2 * (I + 1) * (I + 2) <= t) ++I;
+  while (I > 0 && 2 * I * (I + 1) > t) --I;
+  out = make_int2(I, t - 2 * I * (I + 1));
+  return out.y < nc;
+}
+
+// K[i][j] = / += / -= P_ij (mode 0 / 1 / 2) over this panel for the tiles (row
+// tile I of 128, column tile J of 32), entries of the lower 64-block triangle
+// below n_pad only (n_pad a multiple of 64).
 // Warp roles: 0 the bulk-copy issuer, 1 the MMA issuer, 2-5 the epilogue (TMEM
 // lane quarter = warp mod 4).  Chunks (SK_CHUNK atoms) alternate between two
 // TMEM buffers of SK_NACC x 32 columns.
 __global__ void __launch_bounds__(SK_NTHR, 1)
 k_syrk_sl(const uint8_t *__restrict__ Sl, const int *__restrict__ eg, const int2 *__restrict__ tl,
-          int ntl, int natoms, double *__restrict__ K, long ldk, int n_pad, int first,
+          int ntl, int natoms, double *__restrict__ K, long ldk, int n_pad, int mode,
           unsigned tmem_cols, int *err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2 * SK_S + 5];
@@ -256,6 +329,7 @@ k_syrk_sl(const uint8_t *__restrict__ Sl, const int *__restrict__ eg, const int2
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int my_tiles = (int)blockIdx.x < ntl ? (ntl - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int nchunk = (natoms + SK_CHUNK - 1) / SK_CHUNK;
+  const int nc = (n_pad + SK_TN - 1) / SK_TN;
   const uint32_t sbase = (su32(smem_raw) + 1023u) & ~1023u;
   const uint32_t bar0 = su32(&bars[0]);
   auto full = [&](int st) { return bar0 + 8u * st; };
@@ -293,7 +367,8 @@ k_syrk_sl(const uint8_t *__restrict__ Sl, const int *__restrict__ eg, const int2
       int st = 0, use = 0, issued = 0;
       bool ok = true;
       for (int i = 0; i < my_tiles && ok; ++i) {
-        const int2 t = tl[(int)blockIdx.x + i * (int)gridDim.x];
+        int2 t;
+        if (!tile_at(tl, (int)blockIdx.x + i * (int)gridDim.x, nc, t)) continue;
         const uint8_t *Abase = Sl + (size_t)t.x * natoms * SK_A_STAGE;
         const uint8_t *Bbase = Sl + (size_t)(t.y >> 2) * natoms * SK_A_STAGE + (size_t)(t.y & 3) * SK_B_SLICE;
         for (int a = 0; a < natoms; ++a) {
@@ -325,6 +400,8 @@ k_syrk_sl(const uint8_t *__restrict__ Sl, const int *__restrict__ eg, const int2
       bool ok = true;
       int st = 0, use = 0, g = 0;                     // stage, its use count, chunk count
       for (int i = 0; i < my_tiles && ok; ++i) {
+        int2 t;
+        if (!tile_at(tl, (int)blockIdx.x + i * (int)gridDim.x, nc, t)) continue;
         for (int c = 0; c < nchunk && ok; ++c, ++g) {
           const int bf = g & 1;
           // the epilogue has read this buffer's previous chunk
@@ -369,7 +446,8 @@ k_syrk_sl(const uint8_t *__restrict__ Sl, const int *__restrict__ eg, const int2
     int g = 0;
     bool ok = true;
     for (int i = 0; i < my_tiles && ok; ++i) {
-      const int2 t = tl[(int)blockIdx.x + i * (int)gridDim.x];
+      int2 t;
+      if (!tile_at(tl, (int)blockIdx.x + i * (int)gridDim.x, nc, t)) continue;
       long long T[SK_TN];
       float F[SK_TN];
 #pragma unroll
@@ -409,17 +487,30 @@ k_syrk_sl(const uint8_t *__restrict__ Sl, const int *__restrict__ eg, const int2
         mbar_arrive(tempty(bf));
       }
       if (!ok) break;
-      const long row = (long)t.x * SK_TM + r;
-      if (row < n_pad) {
+      // a 32-column tile lies inside one 64-block: one mask for the row
+      const long row = (long)t.x * SK_TM + r, col0 = (long)t.y * SK_TN;
+      if (row < n_pad && col0 < n_pad && (col0 >> 6) <= (row >> 6)) {
         const int ei = eg[row];
-        double *Krow = K + row * ldk;
+        double2 *Kp = reinterpret_cast<double2 *>(K + row * ldk + col0);
+        double old[SK_TN];
+        if (mode != 0) {
 #pragma unroll
-        for (int j = 0; j < SK_TN; ++j) {
-          const long col = (long)t.y * SK_TN + j;
-          if (col < n_pad && (col >> 6) <= (row >> 6)) {
-            const double v = ldexp((double)T[j] * 0x1p-32 + (double)F[j], ei + eg[col] - 14);
-            Krow[col] = first ? v : Krow[col] + v;
+          for (int q = 0; q < SK_TN / 2; ++q) {
+            const double2 o = Kp[q];
+            old[2 * q] = o.x;
+            old[2 * q + 1] = o.y;
           }
+        }
+#pragma unroll
+        for (int q = 0; q < SK_TN / 2; ++q) {
+          double v[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j = 2 * q + h;
+            const double p = ldexp((double)T[j] * 0x1p-32 + (double)F[j], ei + eg[col0 + j] - 14);
+            v[h] = mode == 0 ? p : (mode == 1 ? old[j] + p : old[j] - p);
+          }
+          Kp[q] = make_double2(v[0], v[1]);
         }
       }
     }
@@ -477,12 +568,37 @@ cudaError_t launch_form_P_tc(const dd *G, long ldg, int n, int kdim, double *K, 
     const int na = std::min(per_panel, atoms_total - a0);
     k_syrk_slice<<<dim3((unsigned)na, (unsigned)nt), 256, 0, s>>>(G, ldg, n, kdim, a0 * SK_KA, eg, ws, na);
     count_launches(1);
-    k_syrk_sl<<<grid, SK_NTHR, sm, s>>>(ws, eg, tl, ntl, na, K, ldk, n_pad, a0 == 0 ? 1 : 0, 512u, err);
+    k_syrk_sl<<<grid, SK_NTHR, sm, s>>>(ws, eg, tl, ntl, na, K, ldk, n_pad, a0 == 0 ? 0 : 1, 512u, err);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// C -= A A^T for the lower 64-block triangle of the m x m array C (row
+// stride ldc; m a multiple of 64), A the m x 64 FP64 panel (row stride lda):
+// the blocked Cholesky's trailing update, exact products on the tensor cores.
+// ws >= syrk_ws_bytes_per_atom(m) * 2 bytes, eg >= syrk_exp_rows(m) ints.
+cudaError_t launch_syrk_update_d(const double *A, long lda, double *C, long ldc, int m, uint8_t *ws,
+                                 size_t ws_bytes, int *eg, int *err, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  if (m % 64 != 0 || ws_bytes < syrk_ws_bytes_per_atom(m) * 2) return cudaErrorInvalidValue;
+  const int nt = (m + SK_TM - 1) / SK_TM, nrows = nt * SK_TM, natoms = 64 / SK_KA;
+  k_syrk_row_exp_d<<<(unsigned)(((long)nrows * 32 + 255) / 256), 256, 0, s>>>(A, lda, m, 64, eg, nrows);
+  count_launches(1);
+  k_syrk_slice_d<<<dim3((unsigned)natoms, (unsigned)nt), 256, 0, s>>>(A, lda, m, 64, eg, ws, natoms);
+  count_launches(1);
+  const size_t sm = (size_t)SK_S * SK_STAGE + 1024;
+  cudaFuncSetAttribute(k_syrk_sl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int ntl = 2 * nt * (nt + 1);                 // closed-form row-major order
+  const unsigned grid = (unsigned)std::max(1, std::min(ntl, nsm));
+  k_syrk_sl<<<grid, SK_NTHR, sm, s>>>(ws, eg, nullptr, ntl, natoms, C, ldc, m, 2, 512u, err);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 }  // namespace tw

@@ -331,13 +331,22 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
     if (!c->Lp64) c->Lp64 = (double *)twh::dalloc(c, nblk * blk * sizeof(double));
     if (!c->inv64) c->inv64 = (double *)twh::dalloc(c, (size_t)c->NB * blk * sizeof(double));
     if (!c->Lp64 || !c->inv64) { twh::dfree(c, K); return twh::fail(c, TW_ERR_OOM, "factor buffers"); }
-    // The factorisation and the triangular solves run in native FP64: in
-    // double-float the solves' cancellations amplify 2^-48 rounding by K's
-    // conditioning (measured 10-30x the FP64 oracle's own error in y).
+    // The factorisation runs in FP64: the panels on the FP64 pipe, the
+    // rank-64 trailing updates as exact products on the tensor cores
     {
       twh::Phase pc(c, TW_PH_CHOLESKY, s);
-      TW_CUDA(c, launch_cholesky_d(K, np, c->NB, c->inv64, c->d_err, s));
+      const size_t wsb = syrk_ws_bytes_per_atom((int)np) * 2;
+      uint8_t *ws = (uint8_t *)twh::dalloc(c, wsb);
+      int *eg = (int *)twh::dalloc(c, (size_t)syrk_exp_rows((int)np) * sizeof(int));
+      if (!ws || !eg) {
+        twh::dfree(c, ws); twh::dfree(c, eg); twh::dfree(c, K);
+        return twh::fail(c, TW_ERR_OOM, "Cholesky update slices");
+      }
+      TW_CUDA(c, launch_cholesky_d(K, np, c->NB, c->inv64, c->d_err, ws, wsb, eg, s));
       TW_CUDA(c, launch_pack_d(K, np, c->Lp64, c->NB, s));
+      TW_CUDA(c, cudaStreamSynchronize(s));
+      twh::dfree(c, ws);
+      twh::dfree(c, eg);
     }
     TW_CUDA(c, cudaStreamSynchronize(s));
     twh::dfree(c, K);                   // the dense K is no longer needed
