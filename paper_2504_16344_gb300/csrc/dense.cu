@@ -781,12 +781,10 @@ cudaError_t launch_K_from_P(double *K, long ldk, int Nd, int Nt, int n, int n_pa
   return cudaGetLastError();
 }
 
-// Right-looking blocked Cholesky, 64-wide panels.  With slice workspaces
-// (FP64 only) the rank-64 trailing updates run as exact products on the
-// tensor cores (gemm_syrk.cu), else as SIMT products.
+// Right-looking blocked Cholesky, 64-wide panels, rank-64 trailing updates
+// as SIMT products.
 template <class T>
-cudaError_t cholesky_t(T *K, long ldk, int NB, T *inv, int *err, cudaStream_t s, uint8_t *ws = nullptr,
-                       size_t ws_bytes = 0, int *eg = nullptr) {
+cudaError_t cholesky_t(T *K, long ldk, int NB, T *inv, int *err, cudaStream_t s) {
   const size_t sm_potrf = 2 * NB_ * (NB_ + 1) * sizeof(T);
   const size_t sm_trsm = 2 * NB_ * (NB_ + 1) * sizeof(T);
   smem_attr(k_potrf_diag<T>, sm_potrf);
@@ -801,13 +799,6 @@ cudaError_t cholesky_t(T *K, long ldk, int NB, T *inv, int *err, cudaStream_t s,
       count_launches(1);
       const T *panel = diag + (long)NB_ * ldk;               // rows (J+1)*64.., cols J*64..
       T *trail = diag + (long)NB_ * ldk + NB_;
-      if constexpr (sizeof(T) == sizeof(double)) {
-        if (ws) {
-          cudaError_t e = launch_syrk_update_d(panel, ldk, trail, ldk, nt * NB_, ws, ws_bytes, eg, err, s);
-          if (e != cudaSuccess) return e;
-          continue;
-        }
-      }
       k_gemm_nt<T><<<dim3(nt, nt), 256, 0, s>>>(panel, ldk, nt * NB_, panel, ldk, nt * NB_, NB_,
                                                 trail, ldk, 1, 1);
       count_launches(1);
@@ -822,9 +813,52 @@ cudaError_t launch_cholesky_f(float *K, long ldk, int NB, float *inv, int *err, 
   return cholesky_t<float>(K, ldk, NB, inv, err, s);
 }
 
+// FP64 with the trailing updates on the tensor cores: super-steps of SW
+// block columns.  Within a super-step each column first takes the deferred
+// updates of the super-step's earlier columns (FP64 SIMT, k <= 64 (SW-1)),
+// then its diagonal block and panel; the trailing matrix then takes one
+// rank-64 SW update (exact products, gemm_syrk.cu), so the update's FP64
+// read-modify-write of K is paid once per SW columns.
+constexpr int CHOL_SW = 4;
+int cholesky_tc_width() { return CHOL_SW; }
+
 cudaError_t launch_cholesky_d(double *K, long ldk, int NB, double *inv, int *err, uint8_t *ws,
                               size_t ws_bytes, int *eg, cudaStream_t s) {
-  return cholesky_t<double>(K, ldk, NB, inv, err, s, ws, ws_bytes, eg);
+  if (!ws) return cholesky_t<double>(K, ldk, NB, inv, err, s);
+  const size_t sm_potrf = 2 * NB_ * (NB_ + 1) * sizeof(double);
+  const size_t sm_trsm = 2 * NB_ * (NB_ + 1) * sizeof(double);
+  smem_attr(k_potrf_diag<double>, sm_potrf);
+  smem_attr(k_trsm_panel<double>, sm_trsm);
+  for (int J0 = 0; J0 < NB; J0 += CHOL_SW) {
+    const int w = std::min(CHOL_SW, NB - J0);
+    for (int jj = 0; jj < w; ++jj) {
+      const int J = J0 + jj, nrow = NB - J;
+      double *colJ = K + (long)J * NB_ * ldk + (long)J * NB_;
+      if (jj > 0) {
+        // block column J, rows J..: minus L(rows, J0..J-1) L(J, J0..J-1)^T
+        const double *A = K + (long)J * NB_ * ldk + (long)J0 * NB_;
+        k_gemm_nt<double><<<dim3(1, nrow), 256, 0, s>>>(A, ldk, nrow * NB_, A, ldk, NB_, jj * NB_, colJ,
+                                                        ldk, 0, 1);
+        count_launches(1);
+      }
+      k_potrf_diag<double><<<1, 256, sm_potrf, s>>>(K, ldk, J, inv + (size_t)J * NB_ * NB_, err);
+      count_launches(1);
+      if (nrow > 1) {
+        k_trsm_panel<double><<<nrow - 1, 64, sm_trsm, s>>>(K, ldk, J);
+        count_launches(1);
+      }
+    }
+    const int m = (NB - J0 - w) * NB_;
+    if (m > 0) {
+      const double *A = K + (long)(J0 + w) * NB_ * ldk + (long)J0 * NB_;
+      double *C = K + (long)(J0 + w) * NB_ * ldk + (long)(J0 + w) * NB_;
+      cudaError_t e = launch_syrk_update_d(A, ldk, w * NB_, C, ldk, m, ws, ws_bytes, eg, err, s);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 cudaError_t launch_pack_d(const double *K, long ldk, double *P, int NB, cudaStream_t s) {
   k_pack<double><<<152 * 8, 256, 0, s>>>(K, ldk, P, NB);

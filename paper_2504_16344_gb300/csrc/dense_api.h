@@ -16,8 +16,9 @@ namespace tw {
 void syrk_tile_list(int n_pad, std::vector<int2> &tl);
 size_t syrk_ws_bytes_per_atom(int n_pad);
 int syrk_exp_rows(int n_pad);
-cudaError_t launch_syrk_update_d(const double *A, long lda, double *C, long ldc, int m, uint8_t *ws,
-                                 size_t ws_bytes, int *eg, int *err, cudaStream_t s);
+cudaError_t launch_syrk_update_d(const double *A, long lda, int kdim, double *C, long ldc, int m,
+                                 uint8_t *ws, size_t ws_bytes, int *eg, int *err, cudaStream_t s);
+int cholesky_tc_width();   // block columns per tensor-core trailing update
 cudaError_t launch_form_P_tc(const dd *G, long ldg, int n, int kdim, double *K, long ldk, int n_pad,
                              uint8_t *ws, size_t ws_bytes, int *eg, const int2 *tl, int ntl, int *err,
                              cudaStream_t s);
@@ -27,8 +28,8 @@ cudaError_t launch_K_from_P(double *K, long ldk, int Nd, int Nt, int n, int n_pa
 // blocked Cholesky in place (lower), inverses of the diagonal blocks to inv
 cudaError_t launch_cholesky_f(float *K, long ldk, int NB, float *inv, int *err, cudaStream_t s);
 // FP64: the trailing updates on the tensor cores with slice workspaces ws
-// (>= syrk_ws_bytes_per_atom(64 NB) * 2 bytes) and eg (>= syrk_exp_rows(64 NB)
-// ints); ws = nullptr keeps them on the FP64 pipe
+// (>= syrk_ws_bytes_per_atom(64 NB) * 2 * cholesky_tc_width() bytes) and eg
+// (>= syrk_exp_rows(64 NB) ints); ws = nullptr keeps them on the FP64 pipe
 cudaError_t launch_cholesky_d(double *K, long ldk, int NB, double *inv, int *err, uint8_t *ws,
                               size_t ws_bytes, int *eg, cudaStream_t s);
 cudaError_t launch_pack_d(const double *K, long ldk, double *P, int NB, cudaStream_t s);

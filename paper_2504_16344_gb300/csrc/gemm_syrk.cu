@@ -577,17 +577,20 @@ cudaError_t launch_form_P_tc(const dd *G, long ldg, int n, int kdim, double *K, 
 }
 
 // C -= A A^T for the lower 64-block triangle of the m x m array C (row
-// stride ldc; m a multiple of 64), A the m x 64 FP64 panel (row stride lda):
-// the blocked Cholesky's trailing update, exact products on the tensor cores.
-// ws >= syrk_ws_bytes_per_atom(m) * 2 bytes, eg >= syrk_exp_rows(m) ints.
-cudaError_t launch_syrk_update_d(const double *A, long lda, double *C, long ldc, int m, uint8_t *ws,
-                                 size_t ws_bytes, int *eg, int *err, cudaStream_t s) {
+// stride ldc; m a multiple of 64), A the m x kdim FP64 panel (row stride lda,
+// kdim a multiple of 32): the blocked Cholesky's trailing update, exact
+// products on the tensor cores.  ws >= syrk_ws_bytes_per_atom(m) * kdim / 32
+// bytes, eg >= syrk_exp_rows(m) ints.
+cudaError_t launch_syrk_update_d(const double *A, long lda, int kdim, double *C, long ldc, int m,
+                                 uint8_t *ws, size_t ws_bytes, int *eg, int *err, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  if (m % 64 != 0 || ws_bytes < syrk_ws_bytes_per_atom(m) * 2) return cudaErrorInvalidValue;
-  const int nt = (m + SK_TM - 1) / SK_TM, nrows = nt * SK_TM, natoms = 64 / SK_KA;
-  k_syrk_row_exp_d<<<(unsigned)(((long)nrows * 32 + 255) / 256), 256, 0, s>>>(A, lda, m, 64, eg, nrows);
+  const int natoms = kdim / SK_KA;
+  if (m % 64 != 0 || kdim % SK_KA != 0 || natoms < 1 || ws_bytes < syrk_ws_bytes_per_atom(m) * natoms)
+    return cudaErrorInvalidValue;
+  const int nt = (m + SK_TM - 1) / SK_TM, nrows = nt * SK_TM;
+  k_syrk_row_exp_d<<<(unsigned)(((long)nrows * 32 + 255) / 256), 256, 0, s>>>(A, lda, m, kdim, eg, nrows);
   count_launches(1);
-  k_syrk_slice_d<<<dim3((unsigned)natoms, (unsigned)nt), 256, 0, s>>>(A, lda, m, 64, eg, ws, natoms);
+  k_syrk_slice_d<<<dim3((unsigned)natoms, (unsigned)nt), 256, 0, s>>>(A, lda, m, kdim, eg, ws, natoms);
   count_launches(1);
   const size_t sm = (size_t)SK_S * SK_STAGE + 1024;
   cudaFuncSetAttribute(k_syrk_sl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -335,7 +335,7 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
     // rank-64 trailing updates as exact products on the tensor cores
     {
       twh::Phase pc(c, TW_PH_CHOLESKY, s);
-      const size_t wsb = syrk_ws_bytes_per_atom((int)np) * 2;
+      const size_t wsb = syrk_ws_bytes_per_atom((int)np) * 2 * cholesky_tc_width();
       uint8_t *ws = (uint8_t *)twh::dalloc(c, wsb);
       int *eg = (int *)twh::dalloc(c, (size_t)syrk_exp_rows((int)np) * sizeof(int));
       if (!ws || !eg) {
