@@ -861,8 +861,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     def step(prec):
-        ctx.infer(prec, d, out=m)
-        ctx.forecast(prec, m, out=q)
+        # posterior mean and forecast in one call: with G^ kept the forecast's
+        # time FFT of m is taken in the kernel that produces m
+        ctx.infer_forecast(prec, d, m=m, q=q)
 
     def barrier():
         if world > 1:

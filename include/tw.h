@@ -296,6 +296,21 @@ tw_status tw_sample_posterior(tw_ctx *ctx, int ns, const int *nt_window, const d
 tw_status tw_forecast(tw_ctx *ctx, tw_prec prec, int nrhs, const double *m, double *q,
                       void *stream);
 
+/*
+ * tw_infer_forecast -- tw_infer followed by tw_forecast of its result in one
+ * call (Phase 4: m_map, then q_map = F_q m_map): m [nrhs][Nt][Nm] and
+ * q [nrhs][Nt][Nq] as those two calls give them; arguments and errors as
+ * theirs.  With G^ kept (TW_KEEP_G) and one right-hand side at a time (no
+ * reserved batch or nrhs = 1), the inverse time FFT that produces m also
+ * takes m's forward time FFT for the forecast in the same kernel, from shared
+ * memory: the forecast then does not read m back.  The FP64 path's q may
+ * differ from tw_forecast's in the last bits (m's spectrum is taken from the
+ * double-float m before its rounding to FP64); the reduced-precision paths
+ * give the same bits.
+ */
+tw_status tw_infer_forecast(tw_ctx *ctx, tw_prec prec, int nrhs, const int *nt_window, const double *d,
+                            double *m, double *q, tw_infer_stats *stats, void *stream);
+
 /* Number of iterative-refinement steps of the mixed-precision tw_infer
  * (range 0..50).  tw_factor_K picks it by refining a probe right-hand side
  * until the FP64 residual stops falling; this call overrides that choice. */

@@ -187,6 +187,74 @@ k_irfft_time(const typename P::cx *__restrict__ in, long in_ld, void *__restrict
   }
 }
 
+// Inverse transform of a parameter spectrum (x^ -> m, truncated to the
+// window, written to `out`) followed in shared memory by the forward
+// transform of m (-> m^ into `spec`, which may be `in`: a CTA reads all of its
+// columns before it writes them).  The forecast's time FFT of m then needs no
+// second pass over m in HBM and no conversion of m back from its stored type.
+template <class P>
+__global__ void __launch_bounds__(256, P::occ)
+k_irfft_rfft_time(const typename P::cx *in, long in_ld, void *__restrict__ out, int out_kind,
+                  long out_ld, typename P::cx *spec, long spec_ld, int N, int n_keep, FftPlan pl,
+                  const typename P::cx *__restrict__ twM, const typename P::cx *__restrict__ twL,
+                  typename P::re invM, int B) {
+  typedef typename P::cx cx;
+  typedef typename P::re re;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M = pl.M;
+  cx *buf0 = reinterpret_cast<cx *>(smem_raw);
+  cx *buf1 = buf0 + (M + 1) * B;
+  const long n0 = (long)blockIdx.x * B;
+  for (int idx = threadIdx.x; idx < (M + 1) * B; idx += blockDim.x) {
+    const int b = idx % B, k = idx / B;
+    const long n = n0 + b;
+    buf0[k * B + b] = (n < N) ? in[(long)k * in_ld + n] : P::zero();
+  }
+  __syncthreads();
+  // inverse: Z_k = E_k + i O_k (as in k_irfft_time)
+  for (int idx = threadIdx.x; idx < M * B; idx += blockDim.x) {
+    const int b = idx % B, k = idx / B;
+    cx xk = buf0[k * B + b];
+    cx xc = P::conj(buf0[(M - k) * B + b]);
+    cx E = P::scale2(P::add(xk, xc), 0.5f);
+    cx O = P::scale2(P::mul(P::sub(xk, xc), P::conj(ld_cx<P>(twL + k))), 0.5f);
+    buf1[k * B + b] = P::add(E, P::mul_i(O));
+  }
+  __syncthreads();
+  cx *z = fft_run<P, true>(buf1, buf0, twM, pl, B, B, 1, true);
+  cx *w = z == buf0 ? buf1 : buf0;
+  // m_t = invM (Re, Im) z_{t/2} for t < n_keep, else 0: written out, and
+  // packed again as the forward transform's input m_{2j} + i m_{2j+1}
+  for (int idx = threadIdx.x; idx < M * B; idx += blockDim.x) {
+    const int b = idx % B, j = idx / B;
+    const long n = n0 + b;
+    const cx zz = z[j * B + b];
+    const int t0 = 2 * j, t1 = 2 * j + 1;
+    re r0 = P::re_zero(), r1 = P::re_zero();
+    if (t0 < n_keep) r0 = P::re_mul(P::real(zz), invM);
+    if (t1 < n_keep) r1 = P::re_mul(P::imag(zz), invM);
+    // the padded transform of length 2M holds m_t for t < M only
+    if (n < N) {
+      if (t0 < M) st_out<P>(out, out_kind, (long)t0 * out_ld + n, r0);
+      if (t1 < M) st_out<P>(out, out_kind, (long)t1 * out_ld + n, r1);
+    }
+    w[j * B + b] = P::make(t0 < M ? r0 : P::re_zero(), t1 < M ? r1 : P::re_zero());
+  }
+  __syncthreads();
+  cx *Z = fft_run<P, false>(w, z, twM, pl, B, B, 1, true);
+  // X_k = (Z_k + conj Z_{M-k})/2 + W_L^k (Z_k - conj Z_{M-k})/(2i)  (as in k_rfft_time)
+  for (int idx = threadIdx.x; idx < (M + 1) * B; idx += blockDim.x) {
+    const int b = idx % B, k = idx / B;
+    const long n = n0 + b;
+    if (n >= N) continue;
+    cx zk = Z[(k % M) * B + b];
+    cx zc = P::conj(Z[((M - k) % M) * B + b]);
+    cx E = P::scale2(P::add(zk, zc), 0.5f);
+    cx O = P::scale2(P::mul_mi(P::sub(zk, zc)), 0.5f);
+    spec[(long)k * spec_ld + n] = P::add(E, P::mul(ld_cx<P>(twL + k), O));
+  }
+}
+
 // ------------------------------------------------------- Matern filter
 // output field of input field t: (t / per) * stride + off + t % per
 struct FieldMap {
@@ -423,6 +491,37 @@ cudaError_t launch_rfft_time_f(const void *in, int in_kind, long in_ld, int n_in
                                long out_ld, int N, const FftPlan &pl, const cf *twM,
                                const cf *twL, cudaStream_t s, const BatchArg &ba) {
   return rfft_time<PolF>(in, in_kind, in_ld, n_in, out, out_ld, N, pl, twM, twL, s, ba);
+}
+template <class P>
+cudaError_t irfft_rfft_time(const typename P::cx *in, long in_ld, void *out, int out_kind, long out_ld,
+                            typename P::cx *spec, long spec_ld, int N, int n_keep, const FftPlan &pl,
+                            const typename P::cx *twM, const typename P::cx *twL, typename P::re invM,
+                            cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  const int B = pick_batch(pl.M + 1, sizeof(typename P::cx), 32, P::smem);
+  const size_t sm = (size_t)2 * (pl.M + 1) * B * sizeof(typename P::cx);
+  ensure_smem(k_irfft_rfft_time<P>, sm);
+  k_irfft_rfft_time<P><<<(unsigned)((N + B - 1) / B), 256, sm, s>>>(in, in_ld, out, out_kind, out_ld, spec,
+                                                                    spec_ld, N, n_keep, pl, twM, twL, invM, B);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_irfft_rfft_time_dd(const cdd *in, long in_ld, void *out, int out_kind, long out_ld,
+                                      cdd *spec, long spec_ld, int N, int n_keep, const FftPlan &pl,
+                                      const cdd *twM, const cdd *twL, cudaStream_t s) {
+  const double inv = 1.0 / pl.M;
+  dd invM;
+  invM.hi = (float)inv;
+  invM.lo = (float)(inv - (double)invM.hi);
+  return irfft_rfft_time<PolDD>(in, in_ld, out, out_kind, out_ld, spec, spec_ld, N, n_keep, pl, twM, twL,
+                                invM, s);
+}
+cudaError_t launch_irfft_rfft_time_f(const cf *in, long in_ld, void *out, int out_kind, long out_ld,
+                                     cf *spec, long spec_ld, int N, int n_keep, const FftPlan &pl,
+                                     const cf *twM, const cf *twL, cudaStream_t s) {
+  return irfft_rfft_time<PolF>(in, in_ld, out, out_kind, out_ld, spec, spec_ld, N, n_keep, pl, twM, twL,
+                               (float)(1.0 / pl.M), s);
 }
 cudaError_t launch_irfft_time_dd(const cdd *in, long in_ld, void *out, int out_kind, long out_ld,
                                  int N, int n_keep, const FftPlan &pl, const cdd *twM,

@@ -361,8 +361,12 @@ tw_status tw_factor_K(tw_ctx *c, double noise_var, void *stream) {
   return twh::refresh_dd_factor(c, s);
 }
 
-tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, const double *d,
-                   double *m, tw_infer_stats *stats, void *stream) {
+namespace {
+
+// tw_infer; with q (and G^ kept) also the forecast q = F_q m of each right-hand
+// side, its time FFT of m taken in the same kernel as m's inverse FFT
+tw_status infer_impl(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, const double *d,
+                     double *m, double *q, tw_infer_stats *stats, void *stream) {
   if (!c) return TW_ERR_ARG;
   if (nrhs < 0 || (nrhs > 0 && (!d || !m))) return twh::fail(c, TW_ERR_ARG, "bad rhs");
   const bool mixed = prec != TW_PREC_FP64;
@@ -453,13 +457,26 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
     // 2) x = F'^T y over the window (y rows >= w are zero), 3) m = Gamma_pr x;
     // with G^ kept, m = G'^* y in one adjoint (no prior filter)
     const void *AG = c->opG[prec];
+    const int Nq = c->Nq;
+    double *qr = q ? q + (size_t)r * Nt * Nq : nullptr;
     if (AG && !mixed) {
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
         TW_CUDA(c, launch_rfft_time_dd(ysrc, ykind, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
         TW_CUDA(c, launch_gemv_adj_dd(AG, FMT_DD, c->wr, c->wf, Nf, Nd, Nm, s)); }
-      { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
-        TW_CUDA(c, launch_irfft_time_dd(c->wf, Nm, mr, 0, Nm, Nm, w, c->plT, c->twT, c->twL, s)); }
+      if (qr) {
+        // m, and m^ (in place of x^) for the forecast
+        { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+          TW_CUDA(c, launch_irfft_rfft_time_dd(c->wf, Nm, mr, 0, Nm, c->wf, Nm, Nm, w, c->plT, c->twT,
+                                               c->twL, s)); }
+        { twh::Phase p(c, TW_PH_GEMV_FWD, s);
+          TW_CUDA(c, launch_gemv_fwd_dd(c->op[TW_MAP_FQ][0], FMT_DD, c->wf, c->part, c->wr, Nf, Nq, Nm, s)); }
+        { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
+          TW_CUDA(c, launch_irfft_time_dd(c->wr, Nq, qr, 0, Nq, Nq, Nt, c->plT, c->twT, c->twL, s)); }
+      } else {
+        twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+        TW_CUDA(c, launch_irfft_time_dd(c->wf, Nm, mr, 0, Nm, Nm, w, c->plT, c->twT, c->twL, s));
+      }
     } else if (AG) {
       // reduced-precision operator, data side in double-float (see the else branch)
       cf *wf = (cf *)c->wf;
@@ -467,8 +484,18 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
         TW_CUDA(c, launch_rfft_time_dd(ysrc, ykind, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
       { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
         TW_CUDA(c, launch_gemv_adj_cx(AG, (int)prec, c->wr, wf, Nf, Nd, Nm, s)); }
-      { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
-        TW_CUDA(c, launch_irfft_time_f(wf, Nm, mr, 0, Nm, Nm, w, c->plT, c->twTf, c->twLf, s)); }
+      if (qr) {
+        cf *wr = (cf *)c->wr, *part = (cf *)c->part;
+        { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+          TW_CUDA(c, launch_irfft_rfft_time_f(wf, Nm, mr, 0, Nm, wf, Nm, Nm, w, c->plT, c->twTf, c->twLf, s)); }
+        { twh::Phase p(c, TW_PH_GEMV_FWD, s);
+          TW_CUDA(c, launch_gemv_fwd_f(c->op[TW_MAP_FQ][prec], (int)prec, wf, part, wr, Nf, Nq, Nm, s)); }
+        { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
+          TW_CUDA(c, launch_irfft_time_f(wr, Nq, qr, 0, Nq, Nq, Nt, c->plT, c->twTf, c->twLf, s)); }
+      } else {
+        twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
+        TW_CUDA(c, launch_irfft_time_f(wf, Nm, mr, 0, Nm, Nm, w, c->plT, c->twTf, c->twLf, s));
+      }
     } else if (!mixed) {
       { twh::Phase p(c, TW_PH_RFFT_DATA, s);
         TW_CUDA(c, launch_rfft_time_dd(ysrc, ykind, Nd, w, c->wr, Nd, Nd, c->plT, c->twT, c->twL, s)); }
@@ -495,10 +522,37 @@ tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, cons
         TW_CUDA(c, launch_prior_f(wt, 2, mr, 0, w, c->Nx, c->Ny, (cf *)c->ws, c->lam1f, c->plX,
                                   c->plY, c->twXf, c->twYf, s)); }
     }
-    if (w < Nt)
+    if (w < Nt && !(qr && AG))   // the fused kernel writes the zero rows itself
       TW_CUDA(c, cudaMemsetAsync(mr + (size_t)w * Nm, 0, (size_t)(Nt - w) * Nm * sizeof(double), s));
+    if (qr && !AG) {
+      tw_status st = tw_p2o_apply(c, TW_MAP_FQ, prec, 1, mr, qr, stream);
+      if (st != TW_OK) return st;
+    }
   }
   return TW_OK;
+}
+
+}  // namespace
+
+tw_status tw_infer(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, const double *d,
+                   double *m, tw_infer_stats *stats, void *stream) {
+  return infer_impl(c, prec, nrhs, nt_window, d, m, nullptr, stats, stream);
+}
+
+tw_status tw_infer_forecast(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, const double *d,
+                            double *m, double *q, tw_infer_stats *stats, void *stream) {
+  if (!c) return TW_ERR_ARG;
+  if (nrhs < 0 || (nrhs > 0 && !q)) return twh::fail(c, TW_ERR_ARG, "bad forecast output");
+  if (prec < 0 || prec > 2 || !c->op[TW_MAP_FQ][prec])
+    return twh::fail(c, TW_ERR_ARG, "requested precision was not kept at tw_create");
+  for (char l : c->loaded[TW_MAP_FQ])
+    if (!l) return twh::fail(c, TW_ERR_STATE, "block column not fully loaded");
+  // several right-hand sides with a reserved batch: the batched paths, one after the other
+  if (nrhs > 1 && c->lane.bmax > 0) {
+    tw_status st = infer_impl(c, prec, nrhs, nt_window, d, m, nullptr, stats, stream);
+    return st != TW_OK ? st : tw_forecast(c, prec, nrhs, m, q, stream);
+  }
+  return infer_impl(c, prec, nrhs, nt_window, d, m, q, stats, stream);
 }
 
 tw_status tw_solve_K(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, const double *d,

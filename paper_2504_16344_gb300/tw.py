@@ -51,6 +51,7 @@ SIGNATURES = {
     "tw_load_factor": (_S, [_P, _P, ctypes.c_size_t, _P]),
     "tw_infer": (_S, [_P, _I, _I, _P, _P, _P, _P, _P]),
     "tw_forecast": (_S, [_P, _I, _I, _P, _P, _P]),
+    "tw_infer_forecast": (_S, [_P, _I, _I, _P, _P, _P, _P, _P, _P]),
     "tw_solve_K": (_S, [_P, _I, _I, _P, _P, _P, _P]),
     "tw_apply_K": (_S, [_P, _I, _P, _P, _P, _P]),
     "tw_sample_posterior": (_S, [_P, _I, _P, _P, _P, _P, _D, _P, _P]),
@@ -354,6 +355,27 @@ class Context:
         self._check(self.lib.tw_sample_posterior(self.h, ns, self._windows(windows, ns), pd, pzm,
                                                  pzn, float(sigma), po, _stream_ptr(stream)))
         return out
+
+    def infer_forecast(self, prec, d, windows=None, m=None, q=None, stream=None):
+        """Posterior means m and forecasts q = F_q m of d [nrhs][Nt][Nd] in one call."""
+        import torch
+        d = d if d.dim() == 3 else d.unsqueeze(0)
+        nrhs = d.shape[0]
+        pd = _dev(d, torch.float64, (nrhs, self.Nt, self.Nd), "d")
+        if m is None:
+            m = torch.empty((nrhs, self.Nt, self.Nm), dtype=torch.float64, device=d.device)
+        if q is None:
+            q = torch.empty((nrhs, self.Nt, self.Nq), dtype=torch.float64, device=d.device)
+        pm = _dev(m, torch.float64, (nrhs, self.Nt, self.Nm), "m")
+        pq = _dev(q, torch.float64, (nrhs, self.Nt, self.Nq), "q")
+        win = None
+        if windows is not None:
+            if len(windows) != nrhs:
+                raise ValueError("one window per right-hand side")
+            win = (ctypes.c_int * nrhs)(*[int(w) for w in windows])
+        self._check(self.lib.tw_infer_forecast(self.h, prec, nrhs, win, pd, pm, pq, None,
+                                               _stream_ptr(stream)))
+        return m, q
 
     def forecast(self, prec, m, out=None, stream=None):
         import torch

@@ -130,3 +130,32 @@ def test_batched_samples_with_gstar(case):
                                  zn[k], ws[k])
         m_pr = P.prior_apply(zm[k], case["lam"], 0.5)
         assert rel(got[k], ref) < 1e-11 and rel(got[k] - m_pr, ref - m_pr) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["FP64", "C64", "BF16X2"])
+@pytest.mark.parametrize("frac", [1.0, 0.3])
+def test_infer_forecast_in_one_call(case, prec, frac):
+    """tw_infer_forecast: with G^ kept, m's inverse time FFT also takes the
+    forecast's forward FFT of m in the same kernel.  m must be the bits
+    tw_infer gives; q must match the oracle as tw_forecast's does (FP64 at
+    1e-11 and within 1e-13 of tw_forecast, whose m^ comes from m rounded to
+    FP64) and be the very bits of tw_forecast on the reduced paths."""
+    from paper_2504_16344_gb300 import tw
+    cfg, ctx, dev = case["cfg"], case["ctx"], case["dev"]
+    p = getattr(tw, "PREC_" + prec)
+    w = max(1, int(round(frac * cfg.Nt)))
+    d = _t(case["d"], dev)
+    m1 = ctx.infer(p, d, windows=[w])
+    q1 = ctx.forecast(p, m1)
+    m2, q2 = ctx.infer_forecast(p, d, windows=[w])
+    ctx.check()
+    m1, q1, m2, q2 = (a[0].cpu().numpy() for a in (m1, q1, m2, q2))
+    assert np.array_equal(m1, m2)
+    m_ref, _ = Q.posterior_mean(case["F"], case["lam"], case["L"], case["d"], cfg.Nt, nt_window=w)
+    q_ref = T.p2o_apply(case["Fq"], m_ref)
+    e_sep, e_ref = rel(q2, q1), rel(q2, q_ref)
+    print(f"{cfg.cid}: {prec} window {w}: fused q vs separate {e_sep:.2e}, vs oracle {e_ref:.2e}")
+    if prec == "FP64":
+        assert e_sep < 1e-13 and e_ref < 1e-11
+    else:
+        assert np.array_equal(q1, q2)

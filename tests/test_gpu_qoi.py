@@ -4,8 +4,8 @@ The oracle forms Q and the QoI posterior covariance column by column from
 QoI unit vectors with its own applies and LAPACK solves (pinned against the
 dense parameter-space definitions).  Bars: Q and q = Q d 1e-11 relative L2;
 the covariance C - W^T K^-1 W cancels (the posterior variance is far below
-the prior's), so it is compared relative to C's norm at 1e-11 and the
-variances themselves at 1e-8.
+the prior's), so it is compared relative to C's norm at 1e-11 and each
+variance relative to its prior variance C_jj at 1e-11.
 """
 import json
 import os
@@ -90,9 +90,12 @@ def test_qoi_variance_matches_oracle(case):
     var = ctx.qoi_variance().cpu().numpy().ravel()
     ref = np.diag(case["C"] - case["W"] @ case["Y"].T)
     e = np.max(np.abs(var - ref) / ref)
-    print(f"{cfg.cid}: QoI variance max rel err {e:.2e}; posterior/prior variance "
-          f"{np.median(ref / np.diag(case['C'])):.2e} (median)")
-    assert np.all(var > 0) and e < 1e-8
+    # the variance is C_jj - w_j . y_j, two terms of the prior variance's size
+    # that cancel: its error is bounded at the FP64 tolerance of that scale
+    ec = np.max(np.abs(var - ref) / np.diag(case["C"]))
+    print(f"{cfg.cid}: QoI variance max rel err {e:.2e} (of the prior variance {ec:.2e}); "
+          f"posterior/prior variance {np.median(ref / np.diag(case['C'])):.2e} (median)")
+    assert np.all(var > 0) and ec < 1e-11
 
 
 def test_qoi_covariance_matches_oracle(case):
