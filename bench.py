@@ -3,22 +3,29 @@
 
 Workload (the 100-sensor case): Nd = 100 sensors, Nm = 200 x 250 = 50,000
 grid points, Nt = 400 steps, Nq = 20 forecast points; one data vector (the
-oracle-made event-0 data of tests/golden/event_c2.npy).  One step is
+oracle-made event-0 data of tests/golden/event_c2.npy).  One step is one
+tw_infer_forecast call:
 
-    m = G* K^{-1} d               (tw_infer: two triangular solves, time FFT,
+    m = G* K^{-1} d               (two triangular solves, time FFT,
                                     per-frequency GEMV^H with G^ = F^ C -- the
                                     precomputed G* = Gamma_pr F* -- inverse FFT)
-    q = F_q m                      (tw_forecast: time FFT, GEMV, inverse FFT)
+    q = F_q m                      (time FFT of m, taken in the kernel of m's
+                                    inverse FFT; GEMV; inverse FFT)
 
 on the FP64-class path (double-float arithmetic, 16-byte operator entries).
+The end-to-end leg copies d in from pinned host memory and m and q out,
+with tw_infer then tw_forecast so that m's copy overlaps the forecast.
 The same step on the mixed path (complex64 operators, FP32 FFTs; K solved
 with the FP64 factor, or FP32 factor + FP64 refinement) is reported beside it
 with its error against the FP64 path, followed by the batched workload (64
 events with uneven windows + 32 posterior samples, one CUDA graph per
 precision), the serving replay (continuous batching of a Poisson request
-trace) and, with --qoi, the Phase 3 data-to-QoI map and q = Q d.  --scale runs the
-serving-at-scale workload instead (200 sensors, 316x316 grid, 420 steps, 50 forecast points:
-complex64 and FP64 contexts in sequence, the second loading the first one's factor).
+trace) and, with --qoi, the Phase 3 data-to-QoI map and q = Q d.  The default
+run then appends the serving-at-scale workload in its own process (200 sensors,
+316x316 grid, 420 steps, 50 forecast points: complex64 and FP64 contexts in
+sequence, the second loading the first one's factor; per-request error against
+the oracle cases of tests/golden/posterior_c5.npz); --scale runs it alone and
+--no-scale skips it.  --shape Nd,Nx,Ny,Nt,Nq runs the step on a profiling case.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle
 instead (bounded samples of the same step, extrapolated to a full step).

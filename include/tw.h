@@ -181,10 +181,13 @@ tw_status tw_prior_apply(tw_ctx *ctx, double power, int nrhs, const double *x,
  * (Nd*Nt) x (Nd*Nt), time-major (index t*Nd + sensor).  It is formed from the
  * time-domain block column as K_(i,j) = noise_var delta_ij I +
  * sum_{s<=min(i,j)} F_{i-s} C F_{j-s}^T (a product G G^T with
- * G = Phi C^{1/2}, then prefix sums along block diagonals), then Cholesky-
- * factored: in native FP64 if TW_KEEP_FP64 or TW_KEEP_FACTOR64 was kept
- * (the online solves run in FP64 too), and in FP32 if TW_KEEP_C64 or
- * TW_KEEP_BF16X2 was kept without TW_KEEP_FACTOR64.  K itself is kept as
+ * G = Phi C^{1/2}, then prefix sums along block diagonals; the product runs
+ * on the tensor cores from exact fixed-point bf16 slices of G with integer-
+ * exact sums, one FP64 rounding per 8,192-column panel), then Cholesky-
+ * factored: in FP64 if TW_KEEP_FP64 or TW_KEEP_FACTOR64 was kept (the
+ * trailing updates as exact tensor-core products; the single-vector solves
+ * then stream the factor as float pairs in double-float arithmetic), and in
+ * FP32 if TW_KEEP_C64 or TW_KEEP_BF16X2 was kept without TW_KEEP_FACTOR64.  K itself is kept as
  * packed double-float blocks (refinement residuals, tw_apply_K).  Needs
  * tw_set_prior, and either the FP64 operator of F or F's block column loaded
  * after tw_set_prior (TW_ERR_STATE otherwise).  The dense K is released as
