@@ -132,11 +132,29 @@ __device__ __forceinline__ cdd cdd_conj(cdd a) { a.im = dd_neg(a.im); return a; 
 // multiply by -i: (x + iy)(-i) = y - ix
 __device__ __forceinline__ cdd cdd_mul_mi(cdd a) { cdd r; r.re = a.im; r.im = dd_neg(a.re); return r; }
 __device__ __forceinline__ cdd cdd_mul_i(cdd a) { cdd r; r.re = dd_neg(a.im); r.im = a.re; return r; }
+// a b + c d with relative error O(2^-47) of |a b| + |c d|: the two leading
+// products and their errors are exact (TwoProd), the leading parts are added
+// by TwoSum, and everything below them is gathered in one float before the
+// single renormalisation
+__device__ __forceinline__ dd dd_dot2(dd a, dd b, dd c, dd d) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float q = __fmul_rn(c.hi, d.hi);
+  float f = fmaf(c.hi, d.hi, -q);
+  f = fmaf(c.hi, d.lo, f);
+  f = fmaf(c.lo, d.hi, f);
+  float s, r;
+  two_sum(p, q, s, r);
+  r = __fadd_rn(r, __fadd_rn(e, f));
+  dd o; fast_two_sum(s, r, o.hi, o.lo); return o;
+}
 __device__ __forceinline__ cdd cdd_mul(cdd a, cdd b) {
-  dacc re = dacc_zero(), im = dacc_zero();
-  dacc_mac(re, a.re, b.re); dacc_mac(re, dd_neg(a.im), b.im);
-  dacc_mac(im, a.re, b.im); dacc_mac(im, a.im, b.re);
-  cdd r; r.re = dacc_get(re); r.im = dacc_get(im); return r;
+  cdd r;
+  r.re = dd_dot2(a.re, b.re, dd_neg(a.im), b.im);
+  r.im = dd_dot2(a.re, b.im, a.im, b.re);
+  return r;
 }
 __device__ __forceinline__ cdd cdd_scale(cdd a, dd s) { cdd r; r.re = dd_mul(a.re, s); r.im = dd_mul(a.im, s); return r; }
 __device__ __forceinline__ cdd cdd_scale2(cdd a, float p2) { a.re = dd_scale2(a.re, p2); a.im = dd_scale2(a.im, p2); return a; }

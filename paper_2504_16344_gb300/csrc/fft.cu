@@ -95,6 +95,29 @@ __device__ __forceinline__ void add_out<PolD>(void *base, int kind, long off, do
 }
 
 // --------------------------------------------------------- time axis
+// buf[k B + b] = in[k ld + n0 + b] for k < nk, b < B (zero where n0 + b >= N),
+// every element copied asynchronously (cp.async, zero-filled past N) so that
+// a thread's loads are all in flight at once; the caller's __syncthreads()
+// after this makes the tile visible to the CTA
+template <class P>
+__device__ __forceinline__ void stage_cols(typename P::cx *buf, const typename P::cx *in, long ld,
+                                           long n0, long N, int nk, int B) {
+  constexpr int SZ = (int)sizeof(typename P::cx);
+  static_assert(SZ == 8 || SZ == 16, "cp.async copies 8 or 16 bytes");
+  for (int idx = threadIdx.x; idx < nk * B; idx += blockDim.x) {
+    const int b = idx % B, k = idx / B;
+    const long n = n0 + b;
+    const bool ok = n < N;
+    const typename P::cx *src = ok ? in + (long)k * ld + n : in;
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf + idx);
+    if (SZ == 16)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
 template <class P>
 __global__ void __launch_bounds__(256, P::occ)
 k_rfft_time(const void *__restrict__ in, int in_kind, long in_ld, int n_in,
@@ -157,11 +180,7 @@ k_irfft_time(const typename P::cx *__restrict__ in, long in_ld, void *__restrict
   in += bz * ba.in_stride;
   const long ooff = bz * ba.out_stride;
   const int nkeep = ba.window(bz, n_keep);
-  for (int idx = threadIdx.x; idx < (M + 1) * B; idx += blockDim.x) {
-    const int b = idx % B, k = idx / B;
-    const long n = n0 + b;
-    buf0[k * B + b] = (n < N) ? in[(long)k * in_ld + n] : P::zero();
-  }
+  stage_cols<P>(buf0, in, in_ld, n0, N, M + 1, B);
   __syncthreads();
   // Z_k = E_k + i O_k, E_k = (X_k + conj X_{M-k})/2, O_k = (X_k - conj X_{M-k}) W_L^{-k} / 2
   for (int idx = threadIdx.x; idx < M * B; idx += blockDim.x) {
@@ -205,11 +224,7 @@ k_irfft_rfft_time(const typename P::cx *in, long in_ld, void *__restrict__ out, 
   cx *buf0 = reinterpret_cast<cx *>(smem_raw);
   cx *buf1 = buf0 + (M + 1) * B;
   const long n0 = (long)blockIdx.x * B;
-  for (int idx = threadIdx.x; idx < (M + 1) * B; idx += blockDim.x) {
-    const int b = idx % B, k = idx / B;
-    const long n = n0 + b;
-    buf0[k * B + b] = (n < N) ? in[(long)k * in_ld + n] : P::zero();
-  }
+  stage_cols<P>(buf0, in, in_ld, n0, N, M + 1, B);
   __syncthreads();
   // inverse: Z_k = E_k + i O_k (as in k_irfft_time)
   for (int idx = threadIdx.x; idx < M * B; idx += blockDim.x) {
