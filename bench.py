@@ -1022,7 +1022,8 @@ def run_ours(args):
         "dtype": "df64 (FP32 pairs, 48-bit significand; FP64-class)", "data": "synthetic",
         "config": {"workload": WORKLOAD if not args.small else (
                        f"profiling case Nd={cfg.Nd}, {cfg.Nx}x{cfg.Ny} grid, Nt={cfg.Nt}, Nq={cfg.Nq}"),
-                   "l2": "inputs larger than L2: the 32 GB operator F^ is streamed every step",
+                   "l2": (f"inputs larger than L2: the {16 * (cfg.Nt + 1) * cfg.Nd * cfg.Nx * cfg.Ny / 1e9:.1f} GB "
+                          "operator F^ is streamed every step"),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "setup_s": round(t_setup, 1), "factor_K_s": round(t_factor, 1),
                    "factor_K_phases_s": factor_phases},

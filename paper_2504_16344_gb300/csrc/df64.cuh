@@ -198,6 +198,7 @@ struct PolDD {
   static __device__ __forceinline__ cx scale2(cx a, float p2) { return cdd_scale2(a, p2); }
   static __device__ __forceinline__ re re_add(re a, re b) { return dd_add(a, b); }
   static __device__ __forceinline__ re re_sub(re a, re b) { return dd_sub(a, b); }
+  static __device__ __forceinline__ re re_neg(re a) { return dd_neg(a); }
   static __device__ __forceinline__ re re_mul(re a, re b) { return dd_mul(a, b); }
   static __device__ __forceinline__ re re_zero() { return dd_zero(); }
   static __device__ __forceinline__ cx make(re r, re i) { cx z; z.re = r; z.im = i; return z; }
@@ -220,6 +221,7 @@ struct PolF {
   static __device__ __forceinline__ cx scale2(cx a, float p2) { return cf_make(a.re * p2, a.im * p2); }
   static __device__ __forceinline__ re re_add(re a, re b) { return a + b; }
   static __device__ __forceinline__ re re_sub(re a, re b) { return a - b; }
+  static __device__ __forceinline__ re re_neg(re a) { return -a; }
   static __device__ __forceinline__ re re_mul(re a, re b) { return a * b; }
   static __device__ __forceinline__ re re_zero() { return 0.f; }
   static __device__ __forceinline__ cx make(re r, re i) { return cf_make(r, i); }
@@ -247,6 +249,7 @@ struct PolD {
   static __device__ __forceinline__ cx scale2(cx a, float p2) { return make(a.re * p2, a.im * p2); }
   static __device__ __forceinline__ re re_add(re a, re b) { return a + b; }
   static __device__ __forceinline__ re re_sub(re a, re b) { return a - b; }
+  static __device__ __forceinline__ re re_neg(re a) { return -a; }
   static __device__ __forceinline__ re re_mul(re a, re b) { return a * b; }
   static __device__ __forceinline__ re re_zero() { return 0.0; }
   static __device__ __forceinline__ re real(cx a) { return a.re; }

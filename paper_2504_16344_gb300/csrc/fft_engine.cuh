@@ -64,6 +64,22 @@ __device__ __forceinline__ typename P::cx twid(const typename P::cx *tab, int t)
   return INV ? P::conj(w) : w;
 }
 
+// Constants of the R-point DFT for odd R: W_R^t = exp(-2 pi i t / R) for
+// t = 1..(R-1)/2, read once per pass (the table entry t M / R); W_R^(R-t) is
+// their conjugate.  Radix 2 and 4 need none.
+template <class P, int R>
+struct BflyK {
+  typename P::cx w[(R - 1) / 2];
+  __device__ __forceinline__ void load(const typename P::cx *tab, int M) {
+#pragma unroll
+    for (int t = 1; t <= (R - 1) / 2; ++t) w[t - 1] = ld_cx<P>(tab + t * (M / R));
+  }
+};
+template <class P>
+struct BflyK<P, 2> { __device__ __forceinline__ void load(const typename P::cx *, int) {} };
+template <class P>
+struct BflyK<P, 4> { __device__ __forceinline__ void load(const typename P::cx *, int) {} };
+
 // R-point DFT of v (in registers), forward or inverse.
 template <class P, bool INV, int R>
 struct Bfly;
@@ -71,7 +87,7 @@ struct Bfly;
 template <class P, bool INV>
 struct Bfly<P, INV, 2> {
   typedef typename P::cx cx;
-  static __device__ __forceinline__ void run(cx *v, const cx *, int) {
+  static __device__ __forceinline__ void run(cx *v, const BflyK<P, 2> &) {
     cx a = P::add(v[0], v[1]);
     cx b = P::sub(v[0], v[1]);
     v[0] = a; v[1] = b;
@@ -81,7 +97,7 @@ struct Bfly<P, INV, 2> {
 template <class P, bool INV>
 struct Bfly<P, INV, 4> {
   typedef typename P::cx cx;
-  static __device__ __forceinline__ void run(cx *v, const cx *, int) {
+  static __device__ __forceinline__ void run(cx *v, const BflyK<P, 4> &) {
     cx s02 = P::add(v[0], v[2]), d02 = P::sub(v[0], v[2]);
     cx s13 = P::add(v[1], v[3]), d13 = P::sub(v[1], v[3]);
     // forward: W_4 = -i; inverse: +i
@@ -100,7 +116,7 @@ template <class P, bool INV, int R>
 struct Bfly {
   typedef typename P::cx cx;
   typedef typename P::re re;
-  static __device__ __forceinline__ void run(cx *v, const cx *tab, int M) {
+  static __device__ __forceinline__ void run(cx *v, const BflyK<P, R> &K) {
     constexpr int h = (R - 1) / 2;
     cx a[h], b[h];
 #pragma unroll
@@ -111,16 +127,16 @@ struct Bfly {
     cx u0 = v[0];
 #pragma unroll
     for (int j = 0; j < h; ++j) u0 = P::add(u0, a[j]);
-    const int step = M / R;
 #pragma unroll
     for (int q = 1; q <= h; ++q) {
       cx c = v[0];       // v0 + sum a_j cos
       cx s = P::zero();  // sum b_j sin
 #pragma unroll
       for (int j = 1; j <= h; ++j) {
-        cx w = ld_cx<P>(tab + (j * q % R) * step);   // forward table: cos - i sin
-        re cs = P::real(w);
-        re sn = P::imag(w);                           // = -sin
+        const int t = j * q % R;                      // W_R^t = cos - i sin
+        const re cs = P::real(K.w[(t <= h ? t : R - t) - 1]);
+        const re si = P::imag(K.w[(t <= h ? t : R - t) - 1]);
+        const re sn = t <= h ? si : P::re_neg(si);   // = -sin
         c = P::add(c, P::scale_re(a[j - 1], cs));
         s = P::add(s, P::scale_re(b[j - 1], sn));     // accumulates -sum b sin
       }
@@ -144,6 +160,8 @@ __device__ __forceinline__ void fft_pass(const typename P::cx *src, typename P::
   const int tstride = M / (p * R);
   const int total = S * B;
   const int lgB = __ffs(B) - 1;   // B is a power of two
+  BflyK<P, R> K;
+  K.load(tab, M);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     int b, i;
     if (series_fast) {
@@ -167,7 +185,7 @@ __device__ __forceinline__ void fft_pass(const typename P::cx *src, typename P::
 #pragma unroll
       for (int j = 1; j < R; ++j) v[j] = P::mul(v[j], twid<P, INV>(tab, j * k * tstride));
     }
-    Bfly<P, INV, R>::run(v, tab, M);
+    Bfly<P, INV, R>::run(v, K);
     const int base = (i - k) * R + k;
     cx *db = dst + b * ss;
 #pragma unroll

@@ -221,19 +221,21 @@ k_gemv_fwd_dd(const float4 *__restrict__ A, const cdd *__restrict__ xh, cdd *__r
     dacc re = dacc_zero(), im = dacc_zero();
     dd r = dd_zero(), i = dd_zero();
     for (int j0 = 0; j0 < FWD_JPL; j0 += 8) {
+      // the group's eight loads are issued together, without a branch: past
+      // the last grid point the index is clamped and x^ is zero there, so
+      // those terms add exact zeros
+      float4 a[8];
 #pragma unroll
-      for (int j = j0; j < j0 + 8; ++j) {
-        const int kk = lane + 32 * j;
-        if (kk < nvalid) {
-          const float4 a = ld_stream4(row + kk);
-          const cdd x = sx[kk];
-          dd ar, ai;
-          ar.hi = a.x; ar.lo = a.y; ai.hi = a.z; ai.lo = a.w;
-          dacc_mac(re, ar, x.re);
-          dacc_mac(re, dd_neg(ai), x.im);
-          dacc_mac(im, ar, x.im);
-          dacc_mac(im, ai, x.re);
-        }
+      for (int j = 0; j < 8; ++j) a[j] = ld_stream4(row + min(lane + 32 * (j0 + j), nvalid - 1));
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const cdd x = sx[lane + 32 * (j0 + j)];
+        dd ar, ai;
+        ar.hi = a[j].x; ar.lo = a[j].y; ai.hi = a[j].z; ai.lo = a[j].w;
+        dacc_mac(re, ar, x.re);
+        dacc_mac(re, dd_neg(ai), x.im);
+        dacc_mac(im, ar, x.im);
+        dacc_mac(im, ai, x.re);
       }
       dacc_fold(r, re);
       dacc_fold(i, im);
