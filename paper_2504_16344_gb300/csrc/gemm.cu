@@ -42,10 +42,6 @@ __device__ __forceinline__ float bf16lo(unsigned w) { return __uint_as_float(w <
 __device__ __forceinline__ float bf16hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
 
 template <int FMT> __device__ __forceinline__ cf ld_opf(const void *A, size_t i);
-template <> __device__ __forceinline__ cf ld_opf<FMT_C64>(const void *A, size_t i) {
-  float2 v = __ldg(reinterpret_cast<const float2 *>(A) + i);
-  return cf_make(v.x, v.y);
-}
 template <> __device__ __forceinline__ cf ld_opf<FMT_BF16X2>(const void *A, size_t i) {
   uint2 v = __ldg(reinterpret_cast<const uint2 *>(A) + i);
   return cf_make(bf16lo(v.x) + bf16hi(v.x), bf16lo(v.y) + bf16hi(v.y));
@@ -169,12 +165,20 @@ template <> struct FwdT<cf> {
   }
 };
 
-// operator entry (complex) from the stored formats
-__device__ __forceinline__ cdd ld_op(const cdd *, const void *A, size_t i) {
-  return ld_cdd(reinterpret_cast<const cdd *>(A) + i);
-}
+// operator entry (complex) of the bf16 hi+lo format
 template <int FMT>
 __device__ __forceinline__ cf ld_op_fmt(const void *A, size_t i) { return ld_opf<FMT>(A, i); }
+
+// one element copied to shared memory asynchronously (zero-filled if !ok; the
+// source is then only a valid address, nothing is read from it)
+template <class CX>
+__device__ __forceinline__ void cp_async_el(CX *dst, const CX *src, bool ok) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(CX) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
 
 // LPB lanes per right-hand side: 1 (32 right-hand sides per CTA) or 2 (16;
 // the two lanes of a right-hand side take alternate k and add their sums
@@ -208,20 +212,32 @@ k_gemm_fwd(const void *__restrict__ A, const CX *__restrict__ X, long x_bstride,
     for (int kt = kbeg; kt < kend; kt += GK) {
       const int nk = min(GK, kend - kt);
       __syncthreads();   // previous tile consumed
-      for (int idx = threadIdx.x; idx < CB * GK; idx += blockDim.x) {
-        const int bl = idx / GK, kk = idx % GK;
-        sx[bl * (GK + 1) + kk] = (bl < nb && kk < nk)
-            ? X[(size_t)(b0 + bl) * x_bstride + (size_t)w * Nm + kt + kk] : T::zx();
-      }
-      for (int idx = threadIdx.x; idx < nrp * GK; idx += blockDim.x) {
-        const int rl = idx / GK, kk = idx % GK;
-        CX v = T::zx();
-        if (kk < nk) {
-          const size_t gi = base + (size_t)(r0 + rl) * Nm + kt + kk;
-          if constexpr (FMT == FMT_DD) v = ld_op((const cdd *)nullptr, A, gi);
-          else v = ld_op_fmt<FMT>(A, gi);
+      if constexpr (FMT == FMT_DD || FMT == FMT_C64) {
+        // the stored entries are the shared tile's type: every load of the
+        // tile in flight at once (cp.async, zeros past the edges)
+        const CX *Ac = reinterpret_cast<const CX *>(A);
+        for (int idx = threadIdx.x; idx < CB * GK; idx += blockDim.x) {
+          const int bl = idx / GK, kk = idx % GK;
+          const bool ok = bl < nb && kk < nk;
+          cp_async_el(sx + bl * (GK + 1) + kk,
+                      ok ? X + (size_t)(b0 + bl) * x_bstride + (size_t)w * Nm + kt + kk : X, ok);
         }
-        sa[rl * GK + kk] = v;
+        for (int idx = threadIdx.x; idx < nrp * GK; idx += blockDim.x) {
+          const int rl = idx / GK, kk = idx % GK;
+          const bool ok = kk < nk;
+          cp_async_el(sa + rl * GK + kk, ok ? Ac + base + (size_t)(r0 + rl) * Nm + kt + kk : Ac, ok);
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+      } else {
+        for (int idx = threadIdx.x; idx < CB * GK; idx += blockDim.x) {
+          const int bl = idx / GK, kk = idx % GK;
+          sx[bl * (GK + 1) + kk] = (bl < nb && kk < nk)
+              ? X[(size_t)(b0 + bl) * x_bstride + (size_t)w * Nm + kt + kk] : T::zx();
+        }
+        for (int idx = threadIdx.x; idx < nrp * GK; idx += blockDim.x) {
+          const int rl = idx / GK, kk = idx % GK;
+          sa[rl * GK + kk] = kk < nk ? ld_op_fmt<FMT>(A, base + (size_t)(r0 + rl) * Nm + kt + kk) : T::zx();
+        }
       }
       __syncthreads();
       const CX *xs = sx + bl_l * (GK + 1);
