@@ -41,12 +41,6 @@ constexpr int GF_TILES = 32;   // tiles per CTA: a CTA sums 4096 grid points
 __device__ __forceinline__ float bf16lo(unsigned w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
 
-template <int FMT> __device__ __forceinline__ cf ld_opf(const void *A, size_t i);
-template <> __device__ __forceinline__ cf ld_opf<FMT_BF16X2>(const void *A, size_t i) {
-  uint2 v = __ldg(reinterpret_cast<const uint2 *>(A) + i);
-  return cf_make(bf16lo(v.x) + bf16hi(v.x), bf16lo(v.y) + bf16hi(v.y));
-}
-
 // ------------------------------------------------------------ adjoint, df64
 // grid (ceil(Nm/128), Nf, ceil(B/(8 RW))); 8 warps x RW right-hand sides each
 // (RW = 4, 2 or 1 after the batch size, so small batches leave no warp idle)
@@ -165,9 +159,6 @@ template <> struct FwdT<cf> {
   }
 };
 
-// operator entry (complex) of the bf16 hi+lo format
-template <int FMT>
-__device__ __forceinline__ cf ld_op_fmt(const void *A, size_t i) { return ld_opf<FMT>(A, i); }
 
 // one element copied to shared memory asynchronously (zero-filled if !ok; the
 // source is then only a valid address, nothing is read from it)
@@ -212,9 +203,11 @@ k_gemm_fwd(const void *__restrict__ A, const CX *__restrict__ X, long x_bstride,
     for (int kt = kbeg; kt < kend; kt += GK) {
       const int nk = min(GK, kend - kt);
       __syncthreads();   // previous tile consumed
-      if constexpr (FMT == FMT_DD || FMT == FMT_C64) {
-        // the stored entries are the shared tile's type: every load of the
-        // tile in flight at once (cp.async, zeros past the edges)
+      {
+        // every load of the tile in flight at once (cp.async, zeros past the
+        // edges); bf16 hi+lo words are copied as they are stored (8 bytes,
+        // the size of the complex64 slot) and converted in place below
+        static_assert(sizeof(CX) == 16 || FMT != FMT_DD, "float-pair tile");
         const CX *Ac = reinterpret_cast<const CX *>(A);
         for (int idx = threadIdx.x; idx < CB * GK; idx += blockDim.x) {
           const int bl = idx / GK, kk = idx % GK;
@@ -228,15 +221,13 @@ k_gemm_fwd(const void *__restrict__ A, const CX *__restrict__ X, long x_bstride,
           cp_async_el(sa + rl * GK + kk, ok ? Ac + base + (size_t)(r0 + rl) * Nm + kt + kk : Ac, ok);
         }
         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-      } else {
-        for (int idx = threadIdx.x; idx < CB * GK; idx += blockDim.x) {
-          const int bl = idx / GK, kk = idx % GK;
-          sx[bl * (GK + 1) + kk] = (bl < nb && kk < nk)
-              ? X[(size_t)(b0 + bl) * x_bstride + (size_t)w * Nm + kt + kk] : T::zx();
-        }
-        for (int idx = threadIdx.x; idx < nrp * GK; idx += blockDim.x) {
-          const int rl = idx / GK, kk = idx % GK;
-          sa[rl * GK + kk] = kk < nk ? ld_op_fmt<FMT>(A, base + (size_t)(r0 + rl) * Nm + kt + kk) : T::zx();
+        if constexpr (FMT == FMT_BF16X2) {
+          // a thread converts the words it copied itself (visible to it after the wait)
+          for (int idx = threadIdx.x; idx < nrp * GK; idx += blockDim.x) {
+            CX *e = sa + (idx / GK) * GK + idx % GK;
+            const uint2 v = *reinterpret_cast<const uint2 *>(e);
+            *e = cf_make(bf16lo(v.x) + bf16hi(v.x), bf16lo(v.y) + bf16hi(v.y));
+          }
         }
       }
       __syncthreads();

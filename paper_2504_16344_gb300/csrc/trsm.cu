@@ -79,6 +79,21 @@ __device__ __forceinline__ void stage_block(T *dst, const T *__restrict__ src) {
   }
 }
 
+// the slice's CS columns of dependency block J (written by other CTAs) into a
+// shared 64 x CS tile: one 16-byte piece per thread, L2 only, zeros for
+// columns past the batch
+template <class T>
+__device__ __forceinline__ void stage_z(T *Zd, const T *__restrict__ out, long out_bstride, int b0,
+                                        int B, int J) {
+  static_assert(sizeof(T) == 8, "8-byte elements");
+  static_assert(CS * NB_ / 2 == 256, "one piece per thread");
+  const int c = threadIdx.x >> 5, piece = threadIdx.x & 31;
+  const bool ok = b0 + c < B;
+  const T *src = ok ? out + (long)(b0 + c) * out_bstride + (long)J * NB_ + 2 * piece : out;
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(Zd + c * LDZ + 2 * piece);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+
 template <class T> struct TS;
 template <> struct TS<double> {
   typedef double acc;
@@ -134,8 +149,8 @@ k_trsm(const T *__restrict__ Lp, const T *__restrict__ Linv, const T *__restrict
   typedef TS<T> S;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *As = reinterpret_cast<T *>(smem_raw);   // [2][64][LDA]
-  T *Zs = As + 2 * NB_ * LDA;                 // [CS][LDZ]
-  T *Vs = Zs + CS * LDZ;                      // [CS][LDZ]
+  T *Zs = As + 2 * NB_ * LDA;                 // [2][CS][LDZ]
+  T *Vs = Zs + 2 * CS * LDZ;                  // [CS][LDZ]
   __shared__ int sT, sP, sbail;
   const int tid = threadIdx.x;
   const int r = tid >> 2, c0 = 2 * (tid & 3);
@@ -184,6 +199,7 @@ k_trsm(const T *__restrict__ Lp, const T *__restrict__ Linv, const T *__restrict
     };
     if (nbulk > 0) { stage_block(As, dep_block(0)); cp_commit(); }
     int d = 0;
+    bool zpre = false;   // Z of dependency d already requested
     while (d < nbulk) {
       if (tid == 0) {
         int p = ld_acq(progress);
@@ -206,24 +222,31 @@ k_trsm(const T *__restrict__ Lp, const T *__restrict__ Linv, const T *__restrict
       __syncthreads();
       if (sbail) { cp_wait<0>(); return; }
       const int dend = min(sP, nbulk);
+      // dependency values Z_J (written by other CTAs) are copied like the
+      // factor blocks: a dependency known to be ready has its Z requested in
+      // the same group as its block, one step ahead of its product
+      if (!zpre && d < dend) {
+        stage_z(Zs + (d & 1) * CS * LDZ, out, out_bstride, b0, B, FWD ? d : NBs - 1 - d);
+        cp_commit();
+        zpre = true;
+      }
       for (; d < dend; ++d) {
-        const int J = FWD ? d : NBs - 1 - d;
-        // dependency values Z_J for the slice (written by other CTAs: L2 loads)
-        for (int i = tid; i < CS * NB_; i += 256) {
-          const int c = i >> 6, k = i & 63;
-          Zs[c * LDZ + k] = (b0 + c < B) ? S::ld_cg(out + (long)(b0 + c) * out_bstride + (long)J * NB_ + k)
-                                         : S::zv();
-        }
+        bool znext = false;
         if (d + 1 < nbulk) {
           stage_block(As + ((d + 1) & 1) * NB_ * LDA, dep_block(d + 1));
+          if (d + 1 < dend) {
+            stage_z(Zs + ((d + 1) & 1) * CS * LDZ, out, out_bstride, b0, B, FWD ? d + 1 : NBs - 2 - d);
+            znext = true;
+          }
           cp_commit();
-          cp_wait<1>();
+          cp_wait<1>();   // all but the newest group: block d and Z_d are in
         } else {
           cp_wait<0>();
         }
         __syncthreads();
-        tile_mac<T, FWD>(acc, As + (d & 1) * NB_ * LDA, Zs, r, c0);
+        tile_mac<T, FWD>(acc, As + (d & 1) * NB_ * LDA, Zs + (d & 1) * CS * LDZ, r, c0);
         __syncthreads();
+        zpre = znext;
       }
     }
     // ---- v = b - bulk;  w = Linv v (FWD) or Linv^T v (BWD)
@@ -283,7 +306,7 @@ cudaError_t trsm(const T *Lp, const T *Linv, const T *Lchain, const void *rhs, i
   const int nslices = (B + CS - 1) / CS;
   cudaError_t e = cudaMemsetAsync(prog, 0, sizeof(int) * (1 + nslices), s);
   if (e != cudaSuccess) return e;
-  const size_t sm = sizeof(T) * (2 * NB_ * LDA + 2 * CS * LDZ);
+  const size_t sm = sizeof(T) * (2 * NB_ * LDA + 3 * CS * LDZ);
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
