@@ -109,7 +109,7 @@ struct tw_ctx {
   // tiles chosen for its products
   tw_lane lane;
   tw_tiles tiles{};
-  tw::dd *Lp_dd = nullptr, *inv_dd = nullptr, *chF_dd = nullptr, *chB_dd = nullptr;
+  tw::dd *inv_dd = nullptr;   // float-pair diagonal-block inverses of the FP64 factor (batched solves)
   // Phase 3 QoI precomputations (tw_qoi_build): rows indexed by QoI entry t*Nq + i
   double *Qmap = nullptr, *Wmap = nullptr;   // [Nq Nt][Nd Nt]: Q = F_q Gamma_pr F^T K^-1, W = (F Gamma_pr F_q^T)^T
   double *Cqq = nullptr;                     // [Nq Nt][Nq Nt]: F_q Gamma_pr F_q^T

@@ -79,10 +79,12 @@ cudaError_t launch_trsm_d(const double *Lp, const double *Linv, const double *Lc
                           const void *rhs, int rhs_kind, long rhs_bstride, double *out,
                           long out_bstride, const int *win, int Nd, int Nt, int B, int NB,
                           int *prog, bool fwd, int *err, int *abort_flag, cudaStream_t s);
-cudaError_t launch_trsm_dd(const dd *Lp, const dd *Linv, const dd *Lchain, const void *rhs,
-                           int rhs_kind, long rhs_bstride, dd *out, long out_bstride,
-                           const int *win, int Nd, int Nt, int B, int NB, int *prog, bool fwd,
-                           int *err, int *abort_flag, cudaStream_t s);
+// the same sweeps with the single-vector solve's pre-multiplied blocks: Lx =
+// Lf (Linv_I L_IJ, forward) or Lb (L_IJ Linv_J, backward), packed like L
+cudaError_t launch_trsm_dd_scaled(const dd *Lx, const dd *Linv, const void *rhs, int rhs_kind,
+                                  long rhs_bstride, dd *out, long out_bstride, const int *win, int Nd,
+                                  int Nt, int B, int NB, int *prog, bool fwd, int *err, int *abort_flag,
+                                  cudaStream_t s);
 cudaError_t launch_chain_blocks_d(const double *Lp, const double *Linv, double *Mf, double *Cb,
                                   int NB, cudaStream_t s);
 cudaError_t launch_chain_blocks_f(const float *Lp, const float *Linv, float *Mf, float *Cb, int NB,

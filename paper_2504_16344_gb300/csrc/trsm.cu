@@ -24,8 +24,10 @@
 // (2 s), after which the kernel records TW_ERR_TIMEOUT, raises the abort
 // flag that all CTAs poll, and returns.
 //
-// Element types: double (native FP64, the FP64 path) and dd (float pairs,
-// the mixed path, where the solve needs far less than FP64 accuracy).
+// Element types: double (native FP64, with L itself: the QoI set-up) and dd
+// (float pairs, with the single-vector solve's blocks pre-multiplied by the
+// diagonal-block inverses: the online batched solves of every precision path,
+// in double-float arithmetic on the FP32 pipes, like the single-vector solve).
 #include <algorithm>
 
 #include "../../include/tw.h"
@@ -140,7 +142,12 @@ __device__ __forceinline__ void tile_mac(typename TS<T>::acc *acc, const T *A, c
   }
 }
 
-template <class T, bool FWD>
+// SCALED: Lp holds the factor's blocks pre-multiplied by the diagonal-block
+// inverses, Lf_IJ = Linv_I L_IJ (FWD) or Lb_IJ = L_IJ Linv_J (BWD), so that
+//   z_I = Linv_I d_I - sum_J<I Lf_IJ z_J,   y_J = Linv_J^T z_J - sum_I>J Lb_IJ^T y_I;
+// the diagonal inverse then multiplies the right-hand side alone and the last
+// dependency's block is its own chain block (Lchain is not used).
+template <class T, bool FWD, bool SCALED>
 __global__ void __launch_bounds__(256, 2)
 k_trsm(const T *__restrict__ Lp, const T *__restrict__ Linv, const T *__restrict__ Lchain,
        const void *__restrict__ rhs, int rhs_kind, long rhs_bstride, T *__restrict__ out,
@@ -250,17 +257,30 @@ k_trsm(const T *__restrict__ Lp, const T *__restrict__ Linv, const T *__restrict
       }
     }
     // ---- v = b - bulk;  w = Linv v (FWD) or Linv^T v (BWD)
+    //      (SCALED: v = b, and the bulk is subtracted from w)
     stage_block(As, Linv + (size_t)I * NB_ * NB_);
     cp_commit();
     const bool chain = u > 0;
-    if (chain) { stage_block(As + NB_ * LDA, Lchain + (size_t)I * NB_ * NB_); cp_commit(); }
-    Vs[c0 * LDZ + r] = (gi < nrows[0]) ? S::sub(bv[0], S::get(acc[0])) : S::zv();
-    Vs[(c0 + 1) * LDZ + r] = (gi < nrows[1]) ? S::sub(bv[1], S::get(acc[1])) : S::zv();
+    if (chain) {
+      stage_block(As + NB_ * LDA, SCALED ? dep_block(u - 1) : Lchain + (size_t)I * NB_ * NB_);
+      cp_commit();
+    }
+    if constexpr (SCALED) {
+      Vs[c0 * LDZ + r] = (gi < nrows[0]) ? bv[0] : S::zv();
+      Vs[(c0 + 1) * LDZ + r] = (gi < nrows[1]) ? bv[1] : S::zv();
+    } else {
+      Vs[c0 * LDZ + r] = (gi < nrows[0]) ? S::sub(bv[0], S::get(acc[0])) : S::zv();
+      Vs[(c0 + 1) * LDZ + r] = (gi < nrows[1]) ? S::sub(bv[1], S::get(acc[1])) : S::zv();
+    }
     if (chain) cp_wait<1>(); else cp_wait<0>();
     __syncthreads();
     typename S::acc wacc[2] = {S::zero(), S::zero()};
     tile_mac<T, FWD>(wacc, As, Vs, r, c0);
     T res[2] = {S::get(wacc[0]), S::get(wacc[1])};
+    if constexpr (SCALED) {
+      res[0] = S::sub(res[0], S::get(acc[0]));
+      res[1] = S::sub(res[1], S::get(acc[1]));
+    }
     // ---- the last dependency: one product with the chain block
     if (chain) {
       if (tid == 0) {
@@ -298,7 +318,7 @@ k_trsm(const T *__restrict__ Lp, const T *__restrict__ Linv, const T *__restrict
   }
 }
 
-template <class T>
+template <class T, bool SCALED>
 cudaError_t trsm(const T *Lp, const T *Linv, const T *Lchain, const void *rhs, int rhs_kind,
                  long rhs_bstride, T *out, long out_bstride, const int *win, int Nd, int Nt, int B,
                  int NB, int *prog, bool fwd, int *err, int *abort_flag, cudaStream_t s) {
@@ -313,13 +333,13 @@ cudaError_t trsm(const T *Lp, const T *Linv, const T *Lchain, const void *rhs, i
   const long tickets = (long)NB * nslices;
   const int grid = (int)std::min<long>(tickets, 2L * nsm);
   if (fwd) {
-    cudaFuncSetAttribute(k_trsm<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_trsm<T, true><<<grid, 256, sm, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, rhs_bstride, out,
+    cudaFuncSetAttribute(k_trsm<T, true, SCALED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_trsm<T, true, SCALED><<<grid, 256, sm, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, rhs_bstride, out,
                                           out_bstride, win, Nd, Nt, B, NB, nslices, prog, err,
                                           abort_flag);
   } else {
-    cudaFuncSetAttribute(k_trsm<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_trsm<T, false><<<grid, 256, sm, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, rhs_bstride, out,
+    cudaFuncSetAttribute(k_trsm<T, false, SCALED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_trsm<T, false, SCALED><<<grid, 256, sm, s>>>(Lp, Linv, Lchain, rhs, rhs_kind, rhs_bstride, out,
                                            out_bstride, win, Nd, Nt, B, NB, nslices, prog, err,
                                            abort_flag);
   }
@@ -335,15 +355,15 @@ cudaError_t launch_trsm_d(const double *Lp, const double *Linv, const double *Lc
                           const void *rhs, int rhs_kind, long rhs_bstride, double *out,
                           long out_bstride, const int *win, int Nd, int Nt, int B, int NB,
                           int *prog, bool fwd, int *err, int *abort_flag, cudaStream_t s) {
-  return trsm<double>(Lp, Linv, Lchain, rhs, rhs_kind, rhs_bstride, out, out_bstride, win, Nd, Nt,
-                      B, NB, prog, fwd, err, abort_flag, s);
+  return trsm<double, false>(Lp, Linv, Lchain, rhs, rhs_kind, rhs_bstride, out, out_bstride, win, Nd, Nt,
+                             B, NB, prog, fwd, err, abort_flag, s);
 }
-cudaError_t launch_trsm_dd(const dd *Lp, const dd *Linv, const dd *Lchain, const void *rhs,
-                           int rhs_kind, long rhs_bstride, dd *out, long out_bstride,
-                           const int *win, int Nd, int Nt, int B, int NB, int *prog, bool fwd,
-                           int *err, int *abort_flag, cudaStream_t s) {
-  return trsm<dd>(Lp, Linv, Lchain, rhs, rhs_kind, rhs_bstride, out, out_bstride, win, Nd, Nt, B,
-                  NB, prog, fwd, err, abort_flag, s);
+cudaError_t launch_trsm_dd_scaled(const dd *Lx, const dd *Linv, const void *rhs, int rhs_kind,
+                                  long rhs_bstride, dd *out, long out_bstride, const int *win, int Nd,
+                                  int Nt, int B, int NB, int *prog, bool fwd, int *err, int *abort_flag,
+                                  cudaStream_t s) {
+  return trsm<dd, true>(Lx, Linv, nullptr, rhs, rhs_kind, rhs_bstride, out, out_bstride, win, Nd, Nt, B,
+                        NB, prog, fwd, err, abort_flag, s);
 }
 
 }  // namespace tw

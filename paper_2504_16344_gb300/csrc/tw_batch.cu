@@ -48,7 +48,7 @@ tw_status check_batch(tw_ctx *c, tw_prec prec, int nrhs, const int *win) {
   if (c->lane.bmax <= 0) return twh::fail(c, TW_ERR_STATE, "tw_reserve_batch must come first");
   if (nrhs > c->lane.bmax) return twh::fail(c, TW_ERR_ARG, "more right-hand sides than reserved");
   if (nrhs > 0 && !win) return twh::fail(c, TW_ERR_ARG, "windows (device array) required");
-  if (prec == TW_PREC_FP64 ? !c->have64 : !c->Lp_dd)
+  if (!c->inv_dd || !c->have64)
     return twh::fail(c, TW_ERR_STATE, "batched solves need the FP64 factor (tw_factor_K)");
   return TW_OK;
 }
@@ -98,14 +98,18 @@ tw_status infer_core(tw_ctx *c, tw_lane &L, tw_prec prec, int B, const int *win,
   const BatchArg ba_x{B, (long)Nf * Nm, (long)Nt * Nm, 0, win};
   const BatchArg ba_p{B, (long)Nt * Nm, (long)Nt * Nm, (long)((Nt + 1) / 2) * Nm, win};
   if (prec == TW_PREC_FP64) {
+    // double-float sweeps with the single-vector solve's pre-multiplied
+    // blocks (FP64 products rounded to float pairs); y as float pairs in the
+    // lane's 8-byte solve buffers
+    dd *bz = reinterpret_cast<dd *>(L.bz), *by = reinterpret_cast<dd *>(L.by);
     { twh::Phase p(c, TW_PH_TRSV_FWD, s);
-      TW_CUDA(c, launch_trsm_d(c->Lp64, c->inv64, c->chF64, rhs, 0, rhs_bstride, L.bz, np, win, Nd,
-                               Nt, B, c->NB, prog_f, true, c->d_err, c->abort_flag, s)); }
+      TW_CUDA(c, launch_trsm_dd_scaled(c->Lfs, c->inv_dd, rhs, 0, rhs_bstride, bz, np, win, Nd, Nt, B,
+                                       c->NB, prog_f, true, c->d_err, c->abort_flag, s)); }
     { twh::Phase p(c, TW_PH_TRSV_BWD, s);
-      TW_CUDA(c, launch_trsm_d(c->Lp64, c->inv64, c->chB64, L.bz, 0, np, L.by, np, win, Nd, Nt, B,
-                               c->NB, prog_b, false, c->d_err, c->abort_flag, s)); }
+      TW_CUDA(c, launch_trsm_dd_scaled(c->Lbs, c->inv_dd, bz, 1, np, by, np, win, Nd, Nt, B, c->NB,
+                                       prog_b, false, c->d_err, c->abort_flag, s)); }
     { twh::Phase p(c, TW_PH_RFFT_DATA, s);
-      TW_CUDA(c, launch_rfft_time_dd(L.by, 0, Nd, Nt, (cdd *)L.byh, Nd, Nd, c->plT, c->twT, c->twL, s, ba_y)); }
+      TW_CUDA(c, launch_rfft_time_dd(by, 1, Nd, Nt, (cdd *)L.byh, Nd, Nd, c->plT, c->twT, c->twL, s, ba_y)); }
     { twh::Phase p(c, TW_PH_GEMV_ADJ, s);
       TW_CUDA(c, launch_gemm_adj_dd(A, (const cdd *)L.byh, (long)Nf * Nd, (cdd *)L.bxh, (long)Nf * Nm,
                                     Nf, Nd, Nm, B, s, L.adj_rw)); }
@@ -117,12 +121,13 @@ tw_status infer_core(tw_ctx *c, tw_lane &L, tw_prec prec, int B, const int *win,
                                  c->twX, c->twY, s, ba_p, 0));
     }
   } else {
+    // the same double-float sweeps as the FP64 path
     { twh::Phase p(c, TW_PH_TRSV_FWD, s);
-      TW_CUDA(c, launch_trsm_dd(c->Lp_dd, c->inv_dd, c->chF_dd, rhs, 0, rhs_bstride, L.bzd, np, win,
-                                Nd, Nt, B, c->NB, prog_f, true, c->d_err, c->abort_flag, s)); }
+      TW_CUDA(c, launch_trsm_dd_scaled(c->Lfs, c->inv_dd, rhs, 0, rhs_bstride, L.bzd, np, win, Nd, Nt, B,
+                                       c->NB, prog_f, true, c->d_err, c->abort_flag, s)); }
     { twh::Phase p(c, TW_PH_TRSV_BWD, s);
-      TW_CUDA(c, launch_trsm_dd(c->Lp_dd, c->inv_dd, c->chB_dd, L.bzd, 1, np, L.byd, np, win, Nd, Nt,
-                                B, c->NB, prog_b, false, c->d_err, c->abort_flag, s)); }
+      TW_CUDA(c, launch_trsm_dd_scaled(c->Lbs, c->inv_dd, L.bzd, 1, np, L.byd, np, win, Nd, Nt, B, c->NB,
+                                       prog_b, false, c->d_err, c->abort_flag, s)); }
     // double-float data spectra; the product on the tensor cores with both
     // sides cut into exact fixed-point slices: F^T y cancels (y is large
     // against m), so its sum has to be formed far below FP32 rounding
@@ -264,20 +269,15 @@ namespace {
 
 void free_batch(tw_ctx *c) {
   twb::free_lane(c, c->lane);
-  void **bufs[] = {(void **)&c->Lp_dd, (void **)&c->inv_dd, (void **)&c->chF_dd, (void **)&c->chB_dd};
-  for (void **b : bufs) { twh::dfree(c, *b); *b = nullptr; }
+  twh::dfree(c, c->inv_dd);
+  c->inv_dd = nullptr;
 }
 
 }  // namespace
 
 tw_status twh::refresh_dd_factor(tw_ctx *c, cudaStream_t s) {
-  if (!c->Lp_dd || !c->have64) return TW_OK;
-  const size_t blk = (size_t)NB_ * NB_;
-  const size_t nblk = (size_t)c->NB * (c->NB + 1) / 2;
-  TW_CUDA(c, launch_double_to_dd(c->Lp64, c->Lp_dd, nblk * blk, s));
-  TW_CUDA(c, launch_double_to_dd(c->inv64, c->inv_dd, (size_t)c->NB * blk, s));
-  TW_CUDA(c, launch_double_to_dd(c->chF64, c->chF_dd, (size_t)c->NB * blk, s));
-  TW_CUDA(c, launch_double_to_dd(c->chB64, c->chB_dd, (size_t)c->NB * blk, s));
+  if (!c->have64) return TW_OK;
+  if (c->inv_dd) TW_CUDA(c, launch_double_to_dd(c->inv64, c->inv_dd, (size_t)c->NB * NB_ * NB_, s));
   TW_CUDA(c, cudaStreamSynchronize(s));
   return TW_OK;
 }
@@ -292,17 +292,12 @@ tw_status tw_reserve_batch(tw_ctx *c, int bmax) {
   TW_CUDA(c, cudaDeviceSynchronize());
   free_batch(c);
   if (bmax == 0) return TW_OK;
-  const bool mixed = c->op[TW_MAP_F][TW_PREC_C64] || c->op[TW_MAP_F][TW_PREC_BF16X2];
-  if (mixed) {   // float-pair copy of the FP64 factor for the mixed batched solves
-    const size_t blk = (size_t)NB_ * NB_, nblk = (size_t)c->NB * (c->NB + 1) / 2;
-    c->Lp_dd = (dd *)twh::dalloc(c, nblk * blk * sizeof(dd));
-    c->inv_dd = (dd *)twh::dalloc(c, c->NB * blk * sizeof(dd));
-    c->chF_dd = (dd *)twh::dalloc(c, c->NB * blk * sizeof(dd));
-    c->chB_dd = (dd *)twh::dalloc(c, c->NB * blk * sizeof(dd));
-    if (!c->Lp_dd || !c->inv_dd || !c->chF_dd || !c->chB_dd) {
-      free_batch(c);
-      return twh::fail(c, TW_ERR_OOM, "batch workspaces");
-    }
+  // float-pair diagonal-block inverses for the batched solves (their blocks
+  // are the single-vector solve's pre-multiplied float-pair factor)
+  c->inv_dd = (dd *)twh::dalloc(c, (size_t)c->NB * NB_ * NB_ * sizeof(dd));
+  if (!c->inv_dd) {
+    free_batch(c);
+    return twh::fail(c, TW_ERR_OOM, "batch workspaces");
   }
   tw_status st = twb::alloc_lane(c, c->lane, bmax);
   if (st != TW_OK) {

@@ -383,7 +383,7 @@ tw_status infer_impl(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, co
   const void *A = c->op[TW_MAP_F][prec];
   if (stats) { stats->ir_iters = 0; stats->resid_rel = 0.0; }
   // several right-hand sides with a reserved batch: batched solves and products
-  if (nrhs > 1 && c->lane.bmax > 0 && (mixed ? (!use32 && c->Lp_dd) : c->have64)) {
+  if (nrhs > 1 && c->lane.bmax > 0 && c->inv_dd && c->have64 && !use32) {
     tw_status st = twb::infer_host_windows(c, prec, nrhs, nt_window, d, m, s);
     if (st != TW_OK || !stats) return st;
     // residual of the last right-hand side (its solution is the batch's last column)
@@ -392,11 +392,9 @@ tw_status infer_impl(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_window, co
     const int nrows = Nd * w;
     const int NBw = (nrows + NB_ - 1) / NB_;
     const double *dr = d + (size_t)(nrhs - 1) * Nt * Nd;
-    if (mixed)
-      TW_CUDA(c, cudaMemcpyAsync(c->vy, c->lane.byd + (size_t)last * c->n_pad, (size_t)nrows * sizeof(dd),
-                                 cudaMemcpyDeviceToDevice, s));
-    else
-      TW_CUDA(c, launch_double_to_dd_vec(c->lane.by + (size_t)last * c->n_pad, c->vy, nrows, s));
+    // the batched solves leave y as float pairs (FP64 path: in the lane's 8-byte solve buffer)
+    const dd *ylast = (mixed ? c->lane.byd : reinterpret_cast<const dd *>(c->lane.by)) + (size_t)last * c->n_pad;
+    TW_CUDA(c, cudaMemcpyAsync(c->vy, ylast, (size_t)nrows * sizeof(dd), cudaMemcpyDeviceToDevice, s));
     if (!c->Kp64) {   // factor loaded from a checkpoint: K itself is not held
       stats->resid_rel = -1.0;
       return TW_OK;
