@@ -185,8 +185,8 @@ __device__ __forceinline__ cf cf_mul(cf a, cf b) {
 struct PolDD {
   typedef cdd cx;
   typedef dd re;
-  static constexpr int occ = 2;   // CTAs of 256 threads per SM the FFT kernels aim for
-  static constexpr int smem = 104 * 1024;   // shared-memory budget of one FFT CTA
+  static constexpr int occ = 3;   // CTAs of 256 threads per SM the FFT kernels aim for
+  static constexpr int smem = 72 * 1024;   // shared-memory budget of one FFT CTA
   static __device__ __forceinline__ cx zero() { return cdd_zero(); }
   static __device__ __forceinline__ cx add(cx a, cx b) { return cdd_add(a, b); }
   static __device__ __forceinline__ cx sub(cx a, cx b) { return cdd_sub(a, b); }
