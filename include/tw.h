@@ -185,8 +185,9 @@ tw_status tw_prior_apply(tw_ctx *ctx, double power, int nrhs, const double *x,
  * on the tensor cores from exact fixed-point bf16 slices of G with integer-
  * exact sums, one FP64 rounding per 8,192-column panel), then Cholesky-
  * factored: in FP64 if TW_KEEP_FP64 or TW_KEEP_FACTOR64 was kept (the
- * trailing updates as exact tensor-core products; the single-vector solves
- * then stream the factor as float pairs in double-float arithmetic), and in
+ * trailing updates as exact tensor-core products; the single-vector and
+ * batched solves then stream its blocks, pre-multiplied by the diagonal-block
+ * inverses, as float pairs in double-float arithmetic), and in
  * FP32 if TW_KEEP_C64 or TW_KEEP_BF16X2 was kept without TW_KEEP_FACTOR64.  K itself is kept as
  * packed double-float blocks (refinement residuals, tw_apply_K).  Needs
  * tw_set_prior, and either the FP64 operator of F or F's block column loaded
@@ -391,10 +392,10 @@ tw_status tw_p2o_apply_noalloc(tw_ctx *ctx, tw_map which, tw_prec prec, int nrhs
  * are streamed once per column slice instead of once per right-hand side.
  *
  * tw_reserve_batch -- allocate the workspaces of batches of up to bmax
- * right-hand sides (about bmax * (Nt+1) * Nm * 16 bytes, plus a float-pair
- * copy of the factor when an FP32 operator is kept); bmax = 0 frees them.
- * Needs tw_factor_K (the FP64 factor); a later tw_factor_K refreshes the
- * copy.  Set-up call: synchronises the device.  Once a batch is reserved,
+ * right-hand sides (about bmax * (Nt+1) * Nm * 16 bytes, plus float-pair
+ * copies of the factor's diagonal-block inverses); bmax = 0 frees them.
+ * Needs tw_factor_K (the FP64 factor); a later tw_factor_K or tw_load_factor
+ * refreshes the copies.  Set-up call: synchronises the device.  Once a batch is reserved,
  * tw_infer (FP64 path, or mixed path with TW_SOLVE_FACTOR64), tw_forecast and
  * tw_sample_posterior with several right-hand sides run as batches of up to
  * bmax columns.
