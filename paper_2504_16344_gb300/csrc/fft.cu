@@ -214,12 +214,19 @@ k_irfft_time(const typename P::cx *__restrict__ in, long in_ld, void *__restrict
 template <class P>
 __global__ void __launch_bounds__(256, P::occ)
 k_irfft_rfft_time(const typename P::cx *in, long in_ld, void *__restrict__ out, int out_kind,
-                  long out_ld, typename P::cx *spec, long spec_ld, int N, int n_keep, FftPlan pl,
+                  long out_ld, typename P::cx *spec, long spec_ld, int N, int n_keep_all, FftPlan pl,
                   const typename P::cx *__restrict__ twM, const typename P::cx *__restrict__ twL,
-                  typename P::re invM, int B) {
+                  typename P::re invM, int B, BatchArg ba) {
   typedef typename P::cx cx;
   typedef typename P::re re;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // right-hand side bz: spectrum at in / spec + bz * (in_stride / work_stride),
+  // m at out + bz * out_stride, its own window
+  const int bz = blockIdx.y;
+  in += bz * ba.in_stride;
+  spec += bz * ba.work_stride;
+  const long ooff = bz * ba.out_stride;
+  const int n_keep = ba.window(bz, n_keep_all);
   const int M = pl.M;
   cx *buf0 = reinterpret_cast<cx *>(smem_raw);
   cx *buf1 = buf0 + (M + 1) * B;
@@ -250,8 +257,8 @@ k_irfft_rfft_time(const typename P::cx *in, long in_ld, void *__restrict__ out, 
     if (t1 < n_keep) r1 = P::re_mul(P::imag(zz), invM);
     // the padded transform of length 2M holds m_t for t < M only
     if (n < N) {
-      if (t0 < M) st_out<P>(out, out_kind, (long)t0 * out_ld + n, r0);
-      if (t1 < M) st_out<P>(out, out_kind, (long)t1 * out_ld + n, r1);
+      if (t0 < M) st_out<P>(out, out_kind, ooff + (long)t0 * out_ld + n, r0);
+      if (t1 < M) st_out<P>(out, out_kind, ooff + (long)t1 * out_ld + n, r1);
     }
     w[j * B + b] = P::make(t0 < M ? r0 : P::re_zero(), t1 < M ? r1 : P::re_zero());
   }
@@ -511,32 +518,33 @@ template <class P>
 cudaError_t irfft_rfft_time(const typename P::cx *in, long in_ld, void *out, int out_kind, long out_ld,
                             typename P::cx *spec, long spec_ld, int N, int n_keep, const FftPlan &pl,
                             const typename P::cx *twM, const typename P::cx *twL, typename P::re invM,
-                            cudaStream_t s) {
-  if (N <= 0) return cudaSuccess;
+                            cudaStream_t s, const BatchArg &ba) {
+  if (N <= 0 || ba.count <= 0) return cudaSuccess;
   const int B = pick_batch(pl.M + 1, sizeof(typename P::cx), 32, P::smem);
   const size_t sm = (size_t)2 * (pl.M + 1) * B * sizeof(typename P::cx);
   ensure_smem(k_irfft_rfft_time<P>, sm);
-  k_irfft_rfft_time<P><<<(unsigned)((N + B - 1) / B), 256, sm, s>>>(in, in_ld, out, out_kind, out_ld, spec,
-                                                                    spec_ld, N, n_keep, pl, twM, twL, invM, B);
+  const dim3 grid((unsigned)((N + B - 1) / B), (unsigned)ba.count);
+  k_irfft_rfft_time<P><<<grid, 256, sm, s>>>(in, in_ld, out, out_kind, out_ld, spec, spec_ld, N, n_keep, pl,
+                                             twM, twL, invM, B, ba);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_irfft_rfft_time_dd(const cdd *in, long in_ld, void *out, int out_kind, long out_ld,
                                       cdd *spec, long spec_ld, int N, int n_keep, const FftPlan &pl,
-                                      const cdd *twM, const cdd *twL, cudaStream_t s) {
+                                      const cdd *twM, const cdd *twL, cudaStream_t s, const BatchArg &ba) {
   const double inv = 1.0 / pl.M;
   dd invM;
   invM.hi = (float)inv;
   invM.lo = (float)(inv - (double)invM.hi);
   return irfft_rfft_time<PolDD>(in, in_ld, out, out_kind, out_ld, spec, spec_ld, N, n_keep, pl, twM, twL,
-                                invM, s);
+                                invM, s, ba);
 }
 cudaError_t launch_irfft_rfft_time_f(const cf *in, long in_ld, void *out, int out_kind, long out_ld,
                                      cf *spec, long spec_ld, int N, int n_keep, const FftPlan &pl,
-                                     const cf *twM, const cf *twL, cudaStream_t s) {
+                                     const cf *twM, const cf *twL, cudaStream_t s, const BatchArg &ba) {
   return irfft_rfft_time<PolF>(in, in_ld, out, out_kind, out_ld, spec, spec_ld, N, n_keep, pl, twM, twL,
-                               (float)(1.0 / pl.M), s);
+                               (float)(1.0 / pl.M), s, ba);
 }
 cudaError_t launch_irfft_time_dd(const cdd *in, long in_ld, void *out, int out_kind, long out_ld,
                                  int N, int n_keep, const FftPlan &pl, const cdd *twM,

@@ -49,13 +49,18 @@ cudaError_t launch_irfft_time_f(const cf *in, long in_ld, void *out, int out_kin
                                 int N, int n_keep, const FftPlan &pl, const cf *twM,
                                 const cf *twL, cudaStream_t s, const BatchArg &ba = BatchArg{});
 // inverse as above (out: m, rows t >= n_keep zero), then the forward transform
-// of that m (zero-padded, as launch_rfft_time_*) into spec [M+1][N]; spec may be in
+// of that m (zero-padded, as launch_rfft_time_*) into spec [M+1][N]; spec may be
+// in.  Batches: right-hand side b reads in + b * ba.in_stride, writes m at
+// out + b * ba.out_stride and its spectrum at spec + b * ba.work_stride, with
+// window ba.window(b, n_keep)
 cudaError_t launch_irfft_rfft_time_dd(const cdd *in, long in_ld, void *out, int out_kind, long out_ld,
                                       cdd *spec, long spec_ld, int N, int n_keep, const FftPlan &pl,
-                                      const cdd *twM, const cdd *twL, cudaStream_t s);
+                                      const cdd *twM, const cdd *twL, cudaStream_t s,
+                                      const BatchArg &ba = BatchArg{});
 cudaError_t launch_irfft_rfft_time_f(const cf *in, long in_ld, void *out, int out_kind, long out_ld,
                                      cf *spec, long spec_ld, int N, int n_keep, const FftPlan &pl,
-                                     const cf *twM, const cf *twL, cudaStream_t s);
+                                     const cf *twM, const cf *twL, cudaStream_t s,
+                                     const BatchArg &ba = BatchArg{});
 
 // ---- Matern filter on the periodic grid: y_t = C^power x_t, t < nt -------
 // x, y: [nt][Nx][Ny] real (kind 0 double, 1 dd, 2 float); work: [ceil(nt/2)][Nx][Ny] complex

@@ -58,23 +58,28 @@ tw_status check_batch(tw_ctx *c, tw_prec prec, int nrhs, const int *win) {
 namespace twb {
 
 // q = F_q m for B right-hand sides; rows t >= win[b] of m are taken as zero
+// spec_ready: m's spectrum is already in L.bxh (the fused transform of infer_core)
 tw_status forecast_core(tw_ctx *c, tw_lane &L, tw_prec prec, int B, const int *win, const double *m,
-                        double *q, cudaStream_t s) {
+                        double *q, cudaStream_t s, bool spec_ready) {
   const int Nt = c->Nt, Nm = c->Nm, Nf = c->Nf, Nq = c->Nq;
   const void *Aq = c->op[TW_MAP_FQ][prec];
   const BatchArg ba_m{B, (long)Nt * Nm, (long)Nf * Nm, 0, win};
   const BatchArg ba_q{B, (long)Nf * Nq, (long)Nt * Nq, 0, nullptr};
   if (prec == TW_PREC_FP64) {
-    { twh::Phase p(c, TW_PH_RFFT_PARAM, s);
-      TW_CUDA(c, launch_rfft_time_dd(m, 0, Nm, Nt, (cdd *)L.bxh, Nm, Nm, c->plT, c->twT, c->twL, s, ba_m)); }
+    if (!spec_ready) {
+      twh::Phase p(c, TW_PH_RFFT_PARAM, s);
+      TW_CUDA(c, launch_rfft_time_dd(m, 0, Nm, Nt, (cdd *)L.bxh, Nm, Nm, c->plT, c->twT, c->twL, s, ba_m));
+    }
     { twh::Phase p(c, TW_PH_GEMV_FWD, s);
       TW_CUDA(c, launch_gemm_fwd_dd(Aq, (const cdd *)L.bxh, (long)Nf * Nm, (cdd *)L.bpart,
                                     (cdd *)L.byh, (long)Nf * Nq, Nf, Nq, Nm, B, s, fwd_lpb(L))); }
     { twh::Phase p(c, TW_PH_IRFFT_DATA, s);
       TW_CUDA(c, launch_irfft_time_dd((const cdd *)L.byh, Nq, q, 0, Nq, Nq, Nt, c->plT, c->twT, c->twL, s, ba_q)); }
   } else {
-    { twh::Phase p(c, TW_PH_RFFT_PARAM, s);
-      TW_CUDA(c, launch_rfft_time_f(m, 0, Nm, Nt, (cf *)L.bxh, Nm, Nm, c->plT, c->twTf, c->twLf, s, ba_m)); }
+    if (!spec_ready) {
+      twh::Phase p(c, TW_PH_RFFT_PARAM, s);
+      TW_CUDA(c, launch_rfft_time_f(m, 0, Nm, Nt, (cf *)L.bxh, Nm, Nm, c->plT, c->twTf, c->twLf, s, ba_m));
+    }
     { twh::Phase p(c, TW_PH_GEMV_FWD, s);
       TW_CUDA(c, launch_gemm_fwd_f(Aq, (int)prec, (const cf *)L.bxh, (long)Nf * Nm, (cf *)L.bpart,
                                    (cf *)L.byh, (long)Nf * Nq, Nf, Nq, Nm, B, s, fwd_lpb(L))); }
@@ -96,6 +101,11 @@ tw_status infer_core(tw_ctx *c, tw_lane &L, tw_prec prec, int B, const int *win,
   int *prog_f = L.trsm_prog, *prog_b = L.trsm_prog + trsm_prog_ints(L.bmax);
   const BatchArg ba_y{B, np, (long)Nf * Nd, 0, win};
   const BatchArg ba_x{B, (long)Nf * Nm, (long)Nt * Nm, 0, win};
+  // with G^ (no prior after the inverse transform) and a forecast requested,
+  // the inverse transform of x^ and the forecast's forward transform of m
+  // run as one kernel (as tw_infer_forecast does for one right-hand side)
+  const bool fuse = q != nullptr && useG;
+  const BatchArg ba_xf{B, (long)Nf * Nm, (long)Nt * Nm, (long)Nf * Nm, win};
   const BatchArg ba_p{B, (long)Nt * Nm, (long)Nt * Nm, (long)((Nt + 1) / 2) * Nm, win};
   if (prec == TW_PREC_FP64) {
     // double-float sweeps with the single-vector solve's pre-multiplied
@@ -114,7 +124,11 @@ tw_status infer_core(tw_ctx *c, tw_lane &L, tw_prec prec, int B, const int *win,
       TW_CUDA(c, launch_gemm_adj_dd(A, (const cdd *)L.byh, (long)Nf * Nd, (cdd *)L.bxh, (long)Nf * Nm,
                                     Nf, Nd, Nm, B, s, L.adj_rw)); }
     { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
-      TW_CUDA(c, launch_irfft_time_dd((const cdd *)L.bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s, ba_x)); }
+      if (fuse)   // m, then m's spectrum in place of x^ (each CTA owns its columns)
+        TW_CUDA(c, launch_irfft_rfft_time_dd((const cdd *)L.bxh, Nm, m, 0, Nm, (cdd *)L.bxh, Nm, Nm, Nt,
+                                             c->plT, c->twT, c->twL, s, ba_xf));
+      else
+        TW_CUDA(c, launch_irfft_time_dd((const cdd *)L.bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twT, c->twL, s, ba_x)); }
     if (!useG) {
       twh::Phase p(c, TW_PH_PRIOR, s);
       TW_CUDA(c, launch_prior_dd(m, 0, m, 0, Nt, c->Nx, c->Ny, (cdd *)L.bxh, c->lam1, c->plX, c->plY,
@@ -139,14 +153,18 @@ tw_status infer_core(tw_ctx *c, tw_lane &L, tw_prec prec, int B, const int *win,
                                     (long)Nf * Nm, Nf, Nd, Nm, B, L.sl_tile, L.bsl_ws, L.bsl_ws_n,
                                     L.bsl_eb, L.bsl_eb_n, c->d_err, s)); }
     { twh::Phase p(c, TW_PH_IRFFT_PARAM, s);
-      TW_CUDA(c, launch_irfft_time_f((const cf *)L.bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s, ba_x)); }
+      if (fuse)
+        TW_CUDA(c, launch_irfft_rfft_time_f((const cf *)L.bxh, Nm, m, 0, Nm, (cf *)L.bxh, Nm, Nm, Nt, c->plT,
+                                            c->twTf, c->twLf, s, ba_xf));
+      else
+        TW_CUDA(c, launch_irfft_time_f((const cf *)L.bxh, Nm, m, 0, Nm, Nm, Nt, c->plT, c->twTf, c->twLf, s, ba_x)); }
     if (!useG) {
       twh::Phase p(c, TW_PH_PRIOR, s);
       TW_CUDA(c, launch_prior_f(m, 0, m, 0, Nt, c->Nx, c->Ny, (cf *)L.bxh, c->lam1f, c->plX, c->plY,
                                 c->twXf, c->twYf, s, ba_p, 0));
     }
   }
-  if (q) return forecast_core(c, L, prec, B, win, m, q, s);
+  if (q) return forecast_core(c, L, prec, B, win, m, q, s, fuse);
   return TW_OK;
 }
 
@@ -344,7 +362,7 @@ tw_status tw_forecast_batch(tw_ctx *c, tw_prec prec, int nrhs, const int *nt_win
   if (nrhs > c->lane.bmax) return twh::fail(c, TW_ERR_ARG, "more right-hand sides than reserved");
   if (nrhs == 0) return TW_OK;
   TW_CUDA(c, cudaSetDevice(c->dev));
-  return twb::forecast_core(c, c->lane, prec, nrhs, nt_window_dev, m, q, (cudaStream_t)stream);
+  return twb::forecast_core(c, c->lane, prec, nrhs, nt_window_dev, m, q, (cudaStream_t)stream, false);
 }
 
 // ---- CUDA graphs of batched calls
@@ -442,7 +460,7 @@ tw_status forecast_full(tw_ctx *c, tw_prec prec, int nrhs, const double *m, doub
   const size_t pm = (size_t)c->Nt * c->Nm, pq = (size_t)c->Nt * c->Nq;
   for (int r0 = 0; r0 < nrhs; r0 += c->lane.bmax) {
     const int nb = std::min(c->lane.bmax, nrhs - r0);
-    tw_status st = forecast_core(c, c->lane, prec, nb, nullptr, m + r0 * pm, q + r0 * pq, s);
+    tw_status st = forecast_core(c, c->lane, prec, nb, nullptr, m + r0 * pm, q + r0 * pq, s, false);
     if (st != TW_OK) return st;
   }
   return TW_OK;
