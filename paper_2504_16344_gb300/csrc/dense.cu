@@ -60,7 +60,6 @@ template <> __device__ __forceinline__ dd ld_cg<dd>(const dd *p) {
   dd r; r.hi = v.x; r.lo = v.y; return r;
 }
 template <> __device__ __forceinline__ float ld_cg<float>(const float *p) { return __ldcg(p); }
-template <> __device__ __forceinline__ double ld_cg<double>(const double *p) { return __ldcg(p); }
 
 // -------------------------------------------------------------- GEMM NT
 // C[tile (I,J)] = (subtract ? C - S : S),  S = sum_k A[i][k] B[j][k]
@@ -331,16 +330,6 @@ __global__ void k_lower_to_float(const double *__restrict__ K, float *__restrict
 // FWD: L z = b (b from `rhs`, rows >= nrows zero);  BWD: L^T x = z.
 // Lp: packed blocks; Linv: [NB][64][64] inverses of the diagonal blocks.
 template <class T> __device__ __forceinline__ T ld_rhs(const void *rhs, int kind, long i);
-template <> __device__ __forceinline__ dd ld_rhs<dd>(const void *rhs, int kind, long i) {
-  if (kind == 0) return dd_from_double(reinterpret_cast<const double *>(rhs)[i]);
-  if (kind == 1) return ld_cg(reinterpret_cast<const dd *>(rhs) + i);
-  dd r; r.hi = __ldcg(reinterpret_cast<const float *>(rhs) + i); r.lo = 0.f; return r;
-}
-template <> __device__ __forceinline__ double ld_rhs<double>(const void *rhs, int kind, long i) {
-  if (kind == 0) return __ldcg(reinterpret_cast<const double *>(rhs) + i);
-  if (kind == 1) return dd_to_double(ld_cg(reinterpret_cast<const dd *>(rhs) + i));
-  return (double)__ldcg(reinterpret_cast<const float *>(rhs) + i);
-}
 template <> __device__ __forceinline__ float ld_rhs<float>(const void *rhs, int kind, long i) {
   if (kind == 0) return __double2float_rn(reinterpret_cast<const double *>(rhs)[i]);
   if (kind == 1) { dd v = ld_cg(reinterpret_cast<const dd *>(rhs) + i); return __fadd_rn(v.hi, v.lo); }
@@ -350,35 +339,17 @@ template <> __device__ __forceinline__ float ld_rhs<float>(const void *rhs, int 
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s
 
 template <class T> __device__ __forceinline__ T ldg_t(const T *p);
-template <> __device__ __forceinline__ dd ldg_t<dd>(const dd *p) {
-  float2 v = __ldg(reinterpret_cast<const float2 *>(p));
-  dd r; r.hi = v.x; r.lo = v.y; return r;
-}
 template <> __device__ __forceinline__ float ldg_t<float>(const float *p) { return __ldg(p); }
-template <> __device__ __forceinline__ double ldg_t<double>(const double *p) { return __ldg(p); }
 
 // 16 consecutive elements of T from 16-byte-aligned storage, as vector loads
 // (elements assigned one by one so the array stays in registers)
 template <class T> __device__ __forceinline__ void ld16(const T *__restrict__ p, T *v);
-template <> __device__ __forceinline__ void ld16<double>(const double *__restrict__ p, double *v) {
-  const double2 *q = reinterpret_cast<const double2 *>(p);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) { const double2 t = __ldg(q + i); v[2 * i] = t.x; v[2 * i + 1] = t.y; }
-}
 template <> __device__ __forceinline__ void ld16<float>(const float *__restrict__ p, float *v) {
   const float4 *q = reinterpret_cast<const float4 *>(p);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const float4 t = __ldg(q + i);
     v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
-  }
-}
-template <> __device__ __forceinline__ void ld16<dd>(const dd *__restrict__ p, dd *v) {
-  const float4 *q = reinterpret_cast<const float4 *>(p);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float4 t = __ldg(q + i);
-    v[2 * i].hi = t.x; v[2 * i].lo = t.y; v[2 * i + 1].hi = t.z; v[2 * i + 1].lo = t.w;
   }
 }
 

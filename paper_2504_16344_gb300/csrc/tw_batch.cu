@@ -19,8 +19,8 @@ using namespace tw;
 namespace {
 
 // r[i] = d[i] - a[i] - sigma z[i] over B * n entries
-__global__ void k_sample_rhs_b(const double *__restrict__ d, const double *__restrict__ a,
-                               const double *__restrict__ z, double sigma, double *__restrict__ r,
+// r may be a (in place): each thread reads and writes only its own entry
+__global__ void k_sample_rhs_b(const double *d, const double *a, const double *z, double sigma, double *r,
                                long n) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) r[i] = d[i] - a[i] - sigma * z[i];
